@@ -1,0 +1,115 @@
+"""Semi-implicit predictor-corrector time step (oracle; test infrastructure).
+
+Paper Sec. 3.1:
+* Crank-Nicolson on the linear operators, second-order Adams-Bashforth
+  f^{n+1/2} = 3/2 f^n - 1/2 f^{n-1} on the nonlinear terms (f^{1/2} = f^0);
+* hat fields u^ = u - (dt/2) G P^n, B^ = B - (dt/2) G P_b^n (eqn:ubhat),
+  u^0 = u^0, B^0 = B^0 on the first step;
+* Step 1: VTBE (eqn:tsvelocity, eqn:tstemperature, eqn:tsmag) for
+  (u~, Theta^{n+1}, B~); right-hand side x^ + (dt/2) M x^ + dt f^{n+1/2},
+  which equals 2 x^ - A_V x^ + dt f^{n+1/2} since A_V = I - (dt/2) M;
+* Step 2: PPBE (eqn:tsp, eqn:tspb): (dt/2) D G (P, P_b) = (D u~, D B~);
+* Step 3: u = u~ - (dt/2) G P, B = B~ - (dt/2) G P_b (eqn:ubtilde).
+Nonlinear terms (eqn:nonlinearoperator) in conservative form (Cartesian
+components, reading R1): f1 = -div(u u_k) + div(B B_k)/(E Pm),
+f2 = -div(u Theta), f3 = div(B u_k) - div(u B_k).
+Reading: the Neumann pressure is fixed to zero volume-weighted mean (its
+right-hand side is projected onto zero mean); initial guesses are the
+previous step's solutions (Sec. 3.3), the current state on the first step.
+"""
+from dataclasses import dataclass
+
+import numpy as np
+
+from .discrete import Discretization, ppbe_matrix, vtbe_matrix
+from .grid import Grid
+from .krylov import fgmres
+from .schwarz import OneLevelRAS, TwoLevelRAS
+
+
+@dataclass
+class Physics:
+    E: float = 1e-3
+    Ra: float = 100.0
+    Pr: float = 1.0
+    Pm: float = 5.0
+    dt: float = 1e-4
+
+
+@dataclass
+class SolverOptions:
+    parts: tuple = (1, 1, 1)
+    delta: int = 1
+    ppbe_levels: int = 1
+    delta_c: int = 1
+    rtol_c: float = 0.1
+    restart: int = 30
+    rtol: float = 1e-8
+    atol: float = 0.0
+    maxit: int = 3000
+
+
+class Stepper:
+    def __init__(self, grid: Grid, phys: Physics, opt: SolverOptions):
+        self.g, self.ph, self.opt = grid, phys, opt
+        self.d = Discretization(grid)
+        self.AV = vtbe_matrix(self.d, phys.E, phys.Ra, phys.Pr, phys.Pm, phys.dt)
+        self.AP = ppbe_matrix(self.d, phys.E, phys.dt)
+        self.MV = OneLevelRAS(grid, self.AV, 7, opt.parts, opt.delta)
+        if opt.ppbe_levels == 2:
+            gc = Grid(grid.Ns // 2, grid.Nr // 2, grid.ri, grid.ro)
+            Ac = ppbe_matrix(Discretization(gc), phys.E, phys.dt)
+            self.MP = TwoLevelRAS(grid, self.AP, gc, Ac, 2, opt.parts, opt.delta, opt.delta_c, opt.rtol_c)
+        else:
+            self.MP = OneLevelRAS(grid, self.AP, 2, opt.parts, opt.delta)
+        self.Eu = self.d.extension('odd')
+        self.EB = self.d.extension_B()
+
+    def nonlinear(self, u, T, B):
+        """(f1, f2, f3) stacked as 7 x N (eqn:nonlinearoperator, eqn:nonlinearint)."""
+        d, npd = self.d, self.d.n_pad
+        up = [self.Eu @ u[c] for c in range(3)]
+        Tp = self.Eu @ T
+        Bpa = self.EB @ np.concatenate(B)
+        Bp = [Bpa[c * npd:(c + 1) * npd] for c in range(3)]
+        c = 1.0 / (self.ph.E * self.ph.Pm)
+        f1 = [-d.advective_div(up, up[k]) + c * d.advective_div(Bp, Bp[k]) for k in range(3)]
+        f2 = [-d.advective_div(up, Tp)]
+        f3 = [d.advective_div(Bp, up[k]) - d.advective_div(up, Bp[k]) for k in range(3)]
+        return np.stack(f1 + f2 + f3)
+
+    def vtbe_rhs(self, state):
+        """x^ and the VTBE right-hand side of Step 1."""
+        ph, N = self.ph, self.g.N
+        f = self.nonlinear(state['u'], state['T'], state['B'])
+        fh = f if state.get('f_prev') is None else 1.5 * f - 0.5 * state['f_prev']
+        if state.get('first', True):
+            uh, Bh = state['u'], state['B']
+        else:
+            uh = state['u'] - 0.5 * ph.dt * self.d.gradient(state['P'], 'even', ph.E)
+            Bh = state['B'] - 0.5 * ph.dt * self.d.gradient(state['Pb'], 'odd', ph.E)
+        xh = np.concatenate([uh.ravel(), state['T'], Bh.ravel()])
+        return f, xh, 2.0 * xh - self.AV @ xh + ph.dt * fh.ravel()
+
+    def ppbe_rhs(self, xt):
+        N = self.g.N
+        ut, Bt = xt[:3 * N].reshape(3, N), xt[4 * N:].reshape(3, N)
+        bp = self.d.divergence(ut, 'u')
+        bp = bp - (self.d.V @ bp) / self.d.V.sum()
+        return np.concatenate([bp, self.d.divergence(Bt, 'B')])
+
+    def step(self, state):
+        ph, opt, N = self.ph, self.opt, self.g.N
+        f, xh, bV = self.vtbe_rhs(state)
+        x0 = state['xV'] if state.get('xV') is not None else np.concatenate([state['u'].ravel(), state['T'], state['B'].ravel()])
+        rv = fgmres(lambda v: self.AV @ v, self.MV.apply, bV, x0, opt.restart, opt.rtol, opt.atol, opt.maxit)
+        xt = rv.x
+        bP = self.ppbe_rhs(xt)
+        rp = fgmres(lambda v: self.AP @ v, self.MP.apply, bP, np.concatenate([state['P'], state['Pb']]),
+                    opt.restart, opt.rtol, opt.atol, opt.maxit)
+        P, Pb = rp.x[:N].copy(), rp.x[N:].copy()
+        P -= (self.d.V @ P) / self.d.V.sum()
+        u = xt[:3 * N].reshape(3, N) - 0.5 * ph.dt * self.d.gradient(P, 'even', ph.E)
+        B = xt[4 * N:].reshape(3, N) - 0.5 * ph.dt * self.d.gradient(Pb, 'odd', ph.E)
+        new = dict(u=u, T=xt[3 * N:4 * N].copy(), B=B, P=P, Pb=Pb, f_prev=f, xV=xt, first=False)
+        return new, dict(vtbe=rv, ppbe=rp)

@@ -1,0 +1,67 @@
+"""Pins of the oracle's predictor-corrector time step (paper Sec. 3.1)."""
+import numpy as np
+from scipy.sparse.linalg import expm_multiply
+
+from oracle.diagnostics import energies
+from oracle.grid import Grid
+from oracle.timestep import Physics, SolverOptions, Stepper
+from paper_2009_02171_gb300.inputs import benchmark_state, initial_state
+
+
+def test_crank_nicolson_diffusion_is_second_order_against_exponential():
+    """Ra = 0, u = B = 0: Step 1 is Crank-Nicolson for dTheta/dt = lap Theta / Pr;
+    compare with exp(t L) Theta0 of the semi-discrete system (paper Sec. 3.1 parameters of Sec. 4.1)."""
+    g = Grid(6, 6)
+    Tend, errs = 0.02, []
+    for dt in (4e-3, 2e-3, 1e-3):
+        st = Stepper(g, Physics(E=0.1, Ra=0.0, Pr=1.0, Pm=1000.0, dt=dt), SolverOptions(rtol=1e-13))
+        s = benchmark_state(6, 6)
+        s['B'][:] = 0
+        T0 = s['T'].copy()
+        for _ in range(int(round(Tend / dt))):
+            s, _ = st.step(s)
+        assert abs(s['u']).max() == 0
+        errs.append(np.linalg.norm(s['T'] - expm_multiply(st.d.laplacian('odd') * Tend, T0)))
+    assert np.log2(errs[0] / errs[1]) > 1.95 and np.log2(errs[1] / errs[2]) > 1.95
+
+
+def test_boussinesq_step_converges_in_dt():
+    """B = 0, Sec. 4.1 parameters: the step converges as dt -> 0 at fixed h (order >= 1 on 6^3)."""
+    g = Grid(6, 6)
+    sols = {}
+    for dt in (2e-3, 1e-3, 5e-4, 2.5e-4):
+        st = Stepper(g, Physics(E=0.1, Ra=100.0, Pr=1.0, Pm=1000.0, dt=dt), SolverOptions(rtol=1e-13))
+        s = benchmark_state(6, 6)
+        s['B'][:] = 0
+        for _ in range(int(round(0.02 / dt))):
+            s, _ = st.step(s)
+        sols[dt] = s
+    ref = sols[2.5e-4]
+    for k in ('u', 'T'):
+        e = [np.linalg.norm(sols[d][k] - ref[k]) for d in (2e-3, 1e-3, 5e-4)]
+        assert np.log2(e[0] / e[1]) > 0.9 and np.log2(e[1] / e[2]) > 0.9
+
+
+def test_nonlinear_terms_vanish_for_rest_state_and_first_step_uses_f0():
+    g = Grid(6, 4)
+    st = Stepper(g, Physics(), SolverOptions())
+    z = np.zeros((3, g.N))
+    f = st.nonlinear(z, np.ones(g.N), z)
+    assert abs(f).max() == 0
+    s = initial_state(6, 4, 0)
+    f0, xh, b = st.vtbe_rhs(dict(s, first=True))
+    assert np.allclose(b, 2 * xh - st.AV @ xh + st.ph.dt * f0.ravel())
+
+
+def test_mhd_step_solves_both_systems():
+    """One step of the tiny-shell workload (6 x 8^2 x 8, E = 1e-3, Pm = 5, dt = 1e-4)."""
+    g = Grid(8, 8)
+    st = Stepper(g, Physics(E=1e-3, Ra=100.0, Pr=1.0, Pm=5.0, dt=1e-4), SolverOptions(rtol=1e-8))
+    s = initial_state(8, 8, 0)
+    s1, info = st.step(s)
+    assert info['vtbe'].converged and info['ppbe'].converged
+    assert info['vtbe'].iters <= 6
+    ek, em = energies(st.d.V, s1['u'], s1['B'], 1e-3, 5.0)
+    assert np.isfinite(ek) and np.isfinite(em) and em > 0
+    s2, info2 = st.step(s1)
+    assert info2['vtbe'].converged and info2['ppbe'].converged
