@@ -1,0 +1,280 @@
+#!/usr/bin/env python
+"""Time per time step of the shell dynamo solve path on GB300 (prints one JSON line).
+
+Workload (the mid-size mixed-vs-plain shell of the project's configuration
+list): 6 x 64^2 x 64 cells (1,572,864), E = 1e-3, Pm = 5, Ra = 100, Pr = 1,
+dt = 1e-4, seeded synthetic fields (seed 1 + rank).  One step = the paper's
+predictor-corrector time step (Sec. 3.1): nonlinear terms, VTBE solve
+(FGMRES(30), one-level RAS, 96 subdomains = 6 x (2 x 2 x 4), overlap 2),
+PPBE solve (FGMRES(30), hybrid two-level RAS, coarse 32^3 x 6 with overlap 1
+and inner GMRES to 0.1), projection; both systems to a 1e-8 relative
+residual, FP64 throughout.
+
+value       -- ms per time step (max over ranks; one independent shell per GPU)
+e2e         -- the same through the C ABI with the state copied host->device
+               before and device->host after every step (pinned host buffers)
+roofline    -- live CUDA-event duration of the dominant kernel category over
+               the timed region against its algorithmic bytes
+cpu_baseline-- the CPU oracle (rank 0, N = 1) on a bounded sample
+--impl reference runs only the oracle arm.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CFG = dict(Ns=64, Nr=64, p=(2, 2, 4), overlap=2, overlap_coarse=1, levels=2, E=1e-3, Ra=100.0, Pr=1.0, Pm=5.0,
+           dt=1e-4, rtol=1e-8, restart=30, seed=1)
+WORKLOAD = ('shell 6x64^2x64 (1.57M cells), FP64 time step: VTBE one-level RAS + PPBE two-level RAS, '
+            '96 subdomains overlap 2, FGMRES(30) to 1e-8 relative residual')
+METRIC = 'wall time per time step at 1e-8 residual'
+# oracle sample: the same step on 6 x 32^2 x 32 (1/8 of the cells), scaled by the cell ratio
+ORACLE_NS = 32
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument('--gpus', type=int, default=1)
+    ap.add_argument('--steps', type=int, default=5)
+    ap.add_argument('--warmup', type=int, default=3)
+    ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
+    ap.add_argument('--no-cpu-baseline', action='store_true')
+    return ap.parse_args()
+
+
+def dist_setup(backend):
+    import torch.distributed as dist
+    ws = int(os.environ.get('WORLD_SIZE', '1'))
+    if ws > 1 and not dist.is_initialized():
+        os.environ.setdefault('MASTER_ADDR', '127.0.0.1')
+        dist.init_process_group(backend)
+    return int(os.environ.get('RANK', '0')), ws, int(os.environ.get('LOCAL_RANK', '0'))
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+    FIELDS = ('index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,'
+              'clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,'
+              'clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap')
+
+    def __init__(self, gpu):
+        self.gpu, self.proc, self.path = gpu, None, '/tmp/fv_clocks_%d_%d.csv' % (os.getpid(), gpu)
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, 'w')
+            self.proc = subprocess.Popen(['nvidia-smi', '-i', str(self.gpu), '--query-gpu=' + self.FIELDS,
+                                          '--format=csv,noheader,nounits', '-lms', '200'], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {'sm_mhz': None, 'sm_max_mhz': None, 'reasons': ['nvidia-smi unavailable']}
+        rows = [l.split(',') for l in open(self.path).read().strip().splitlines() if l.count(',') >= 8]
+        if not rows:
+            return {'sm_mhz': None, 'sm_max_mhz': None, 'reasons': ['no samples']}
+        sm = sorted(float(r[1]) for r in rows)
+        names = ['hw_slowdown', 'hw_thermal_slowdown', 'sw_thermal_slowdown', 'sw_power_cap']
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.strip() == 'Active'})
+        return {'sm_mhz': sm[len(sm) // 2], 'sm_max_mhz': float(rows[0][2]), 'samples': len(rows),
+                'power_w_max': max(float(r[3]) for r in rows if r[3].strip() not in ('', '[N/A]')),
+                'reasons': reasons}
+
+
+def oracle_step_time(steps, warmup):
+    """CPU oracle (FP64, numpy/scipy + plain-C ILU(0), one thread) on the 6 x 32^2 x 32 sample."""
+    os.environ.setdefault('OMP_NUM_THREADS', '1')
+    os.environ.setdefault('OPENBLAS_NUM_THREADS', '1')
+    from oracle.grid import Grid
+    from oracle.timestep import Physics, SolverOptions, Stepper
+    from paper_2009_02171_gb300.inputs import initial_state
+    n = ORACLE_NS
+    st = Stepper(Grid(n, n), Physics(CFG['E'], CFG['Ra'], CFG['Pr'], CFG['Pm'], CFG['dt']),
+                 SolverOptions(parts=CFG['p'], delta=CFG['overlap'], ppbe_levels=CFG['levels'],
+                               delta_c=CFG['overlap_coarse'], rtol=CFG['rtol'], restart=CFG['restart']))
+    s = dict(initial_state(n, n, CFG['seed']), first=True)
+    for _ in range(warmup):
+        s, _ = st.step(s)
+    t = time.perf_counter()
+    for _ in range(steps):
+        s, _ = st.step(s)
+    per = (time.perf_counter() - t) / steps * 1e3
+    scale = (CFG['Ns'] ** 2 * CFG['Nr']) / (n * n * n)
+    return per * scale, dict(kind='oracle', cores=1, unit='ms/step',
+                             sample='oracle time step on 6x%d^2x%d (%d cells, same solver options), %d steps '
+                                    'after %d warm-up; ms/step scaled by the cell ratio %.0f'
+                                    % (n, n, 6 * n ** 3, steps, warmup, scale))
+
+
+def reference_arm(args, rank, ws):
+    if rank != 0:
+        return
+    ms, cb = oracle_step_time(args.steps, args.warmup)
+    cb['value'] = ms
+    print(json.dumps({'impl': 'reference', 'metric': METRIC, 'value': ms, 'unit': 'ms/step', 'n_gpus': args.gpus,
+                      'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': ms, 'higher_is_better': False,
+                      'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic',
+                      'config': {'workload': WORKLOAD}, 'cpu_baseline': cb,
+                      'e2e': {'value': ms, 'unit': 'ms/step', 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0}}))
+
+
+def main():
+    args = parse()
+    if args.impl == 'reference':
+        import torch.distributed as dist
+        rank, ws, _ = dist_setup('gloo')
+        reference_arm(args, rank, ws)
+        if ws > 1:
+            dist.destroy_process_group()
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    rank, ws, local = dist_setup('nccl')
+    torch.cuda.set_device(local)
+    from paper_2009_02171_gb300 import fv
+    from paper_2009_02171_gb300.inputs import initial_state
+
+    c = CFG
+    ph = dict(E=c['E'], Ra=c['Ra'], Pr=c['Pr'], Pm=c['Pm'], dt=c['dt'])
+    t_setup = time.perf_counter()
+    g = fv.fv_build_grid(c['Ns'], c['Nr'])
+    V = fv.fv_assemble_system(g, fv.FV_VTBE, **ph, p=c['p'], overlap=c['overlap'], levels=1)
+    P = fv.fv_assemble_system(g, fv.FV_PPBE, **ph, p=c['p'], overlap=c['overlap'], levels=c['levels'],
+                              overlap_coarse=c['overlap_coarse'])
+    s0 = initial_state(c['Ns'], c['Nr'], c['seed'] + rank)
+    host = np.concatenate([s0['u'].ravel(), s0['T'], s0['B'].ravel(), s0['P'], s0['Pb']])
+    N = host.size // 9
+    st = fv.fv_state_create(g, torch.tensor(host, device='cuda'), **ph)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t_setup
+    opts = dict(restart=c['restart'], rtol=c['rtol'])
+
+    for _ in range(args.warmup):
+        fv.fv_time_step(st, V, P, 1, **opts)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    iters = []
+    with ClockSampler(local) as clk:
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        fv.fv_profile_enable(True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            s = fv.fv_time_step(st, V, P, 1, **opts)
+            iters.append((s[0].iters, s[1].iters, s[1].inner_iters))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    kern = {}
+    names = ['ghost', 'apply_vtbe', 'apply_ppbe', 'ras_fwd', 'ras_bwd', 'cgs', 'vec', 'glue', 'transfer',
+             'phase_pc_c', 'phase_pc_f', 'phase_pc_i']
+    for k, nm in enumerate(names):
+        for lvl, suffix in ((0, ''), (fv.K_COARSE, '_coarse')):
+            if lvl and k > 8:
+                continue
+            n, t = fv.fv_profile_read(k + lvl)
+            if n:
+                kern[nm + suffix] = {'launches': n, 'ms_total': round(t, 3), 'ms_per_step': round(t / args.steps, 3)}
+    fv.fv_profile_enable(False)
+    if ws > 1:
+        t = torch.tensor([ms], device='cuda')
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # end to end through the C ABI: state host -> device, step, device -> host
+    hbuf = torch.empty(9 * N, dtype=torch.float64).pin_memory()
+    dbuf = torch.empty(9 * N, dtype=torch.float64, device='cuda')
+    fv.fv_state_get(st, dbuf)
+    hbuf.copy_(dbuf)
+    torch.cuda.synchronize()
+    ke = max(1, args.steps // 2)
+    if ws > 1:
+        dist.barrier()
+    e0.record(stream)
+    for _ in range(ke):
+        dbuf.copy_(hbuf, non_blocking=True)
+        fv.fv_state_set(st, dbuf)
+        fv.fv_time_step(st, V, P, 1, **opts)
+        fv.fv_state_get(st, dbuf)
+        hbuf.copy_(dbuf, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e0.elapsed_time(e1) / ke
+    if ws > 1:
+        t = torch.tensor([ms_e2e], device='cuda')
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+
+    # roofline of the dominant kernel category (measured live over the timed region)
+    peaks = json.load(open(os.path.join(ROOT, 'MEASURED_PEAKS.json'))) if os.path.exists(
+        os.path.join(ROOT, 'MEASURED_PEAKS.json')) else {}
+    hbm = peaks.get('hbm_gbs', 6800.0)
+    ranked = sorted((v['ms_total'], k) for k, v in kern.items() if not k.startswith('phase'))
+    top = ranked[-1][1] if ranked else None
+    roof = None
+    if top:
+        bytes_per = algorithmic_bytes(top, c, N)
+        if bytes_per:
+            per_launch_ms = kern[top]['ms_total'] / kern[top]['launches']
+            ach = bytes_per / (per_launch_ms * 1e-3) / 1e9
+            roof = {'kernel': top, 'bound': 'hbm', 'achieved': round(ach, 1), 'peak': hbm, 'unit': 'GB/s',
+                    'frac': round(ach / hbm, 4), 'traffic': None, 'bytes_per_launch': bytes_per,
+                    'ms_per_launch': round(per_launch_ms, 4), 'peak_source': 'MEASURED_PEAKS.json hbm_gbs'}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, cpu = oracle_step_time(2, 1)
+        cpu['value'] = round(v, 1)
+
+    if rank == 0:
+        print(json.dumps({
+            'metric': METRIC, 'value': round(ms, 3), 'unit': 'ms/step', 'n_gpus': ws, 'steps': args.steps,
+            'warmup': args.warmup, 'ms_per_step': round(ms, 3), 'higher_is_better': False, 'scaling': 'weak',
+            'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic',
+            'config': {'workload': WORKLOAD, 'cells': 6 * c['Ns'] ** 2 * c['Nr'], 'subdomains': 6 * 16,
+                       'overlap': c['overlap'], 'ppbe_levels': c['levels'], 'rtol': c['rtol'],
+                       'restart': c['restart'], 'l2': 'working set > L2 (no flush needed)',
+                       'parallelism': 'replicas' if ws > 1 else 'single GPU'},
+            'iterations': {'vtbe': [i[0] for i in iters], 'ppbe': [i[1] for i in iters],
+                           'ppbe_inner': [i[2] for i in iters]},
+            'setup_s': round(t_setup, 2), 'clocks': clk.summary(),
+            'e2e': {'value': round(ms_e2e, 3), 'unit': 'ms/step', 'h2d_bytes_per_step': 9 * N * 8,
+                    'd2h_bytes_per_step': 9 * N * 8},
+            'gpu_launches': int(sum(v['launches'] for k, v in kern.items() if not k.startswith('phase'))),
+            'kernels': kern, 'roofline': roof, 'cpu_baseline': cpu}))
+    for h, f in ((st, fv.fv_free_state), (V, fv.fv_free_system), (P, fv.fv_free_system), (g, fv.fv_free_grid)):
+        f(h)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def algorithmic_bytes(cat, c, N):
+    """Algorithmic HBM bytes of one launch (FP64): what the kernel must read and write."""
+    d = {'apply_vtbe': 7, 'apply_ppbe': 2}.get(cat)
+    if d:
+        return 2 * d * N * 8                        # read x, write y
+    if cat.startswith('ras_'):
+        return None
+    return None
+
+
+if __name__ == '__main__':
+    main()

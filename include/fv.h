@@ -1,0 +1,176 @@
+/* fv.h -- C ABI of the GB300 shell dynamo solve path (libfv.so).
+ *
+ * Method: Yin, Yang, Ma, Cai, Zhang, "Parallel finite volume simulation of the
+ * spherical shell dynamo with pseudo-vacuum magnetic boundary conditions"
+ * (arXiv 2009.02171).  The library solves the two linear systems of the
+ * paper's approximate-factorization time step (Sec. 3.1): VTBE
+ * (eqn:tsvelocity, eqn:tstemperature, eqn:tsmag; unknowns u, Theta, B) and
+ * PPBE (eqn:tsp, eqn:tspb; unknowns P, P_b), discretized by the collocated
+ * finite-volume scheme on the equiangular cubed-sphere shell (Sec. 3.2), with
+ * restarted right-preconditioned (flexible) GMRES and one- or two-level
+ * restricted additive Schwarz preconditioning (Sec. 3.3).
+ *
+ * Conventions for every call:
+ * - Every function returns fv_status: FV_OK (0) or a negative error code.  No
+ *   function aborts or throws; fv_last_error() returns a thread-local message
+ *   describing the last failure of the calling thread.
+ * - Handles (fv_grid, fv_system, fv_state) are opaque and owned by the
+ *   library; release each with its fv_free_* call.  A system or state keeps a
+ *   reference to its grid: free it before the grid.
+ * - Vectors are CALLER-OWNED DEVICE pointers (e.g. torch.Tensor.data_ptr() of
+ *   a CUDA float64 tensor on the current device) holding FP64 values, laid out
+ *   component-major [comp][panel][k][j][i] with i fastest (N = 6 Ns^2 Nr cells
+ *   per component).  VTBE comps: u_x, u_y, u_z, Theta, B_x, B_y, B_z (Cartesian
+ *   components, 7N values); PPBE comps: P, P_b (2N values).  The library never
+ *   frees, reallocates or retains them beyond the call.
+ * - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls enqueue
+ *   their kernels on it; calls that return statistics synchronize it.
+ * - Internal scratch (ghost layers, Krylov bases, factors) is device memory
+ *   allocated by the library at fv_assemble_system / fv_state_create.
+ */
+#ifndef FV_H
+#define FV_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int fv_status;
+#define FV_OK 0
+#define FV_EINVAL (-1)      /* bad argument (null handle, bad size, odd grid for two levels) */
+#define FV_ENOMEM (-2)      /* device allocation failed */
+#define FV_ECUDA (-3)       /* a CUDA call failed; the message names it */
+#define FV_ENOCONV (-4)     /* GMRES hit max_it before the tolerance; x holds the last iterate */
+#define FV_EBREAKDOWN (-5)  /* zero pivot in ILU(0) */
+#define FV_ENAN (-6)        /* NaN/Inf residual; x holds the last finite iterate */
+
+typedef struct fv_grid fv_grid;
+typedef struct fv_system fv_system;
+typedef struct fv_state fv_state;
+
+/* Grid of 6 panels x Ns x Ns x Nr cells (paper Sec. 3.2, cell centres
+ * xi_i = -pi/4 + (i+1/2) h_s, r_k = r_i + (k+1/2) h_r).  Ns >= 4, Nr >= 2.
+ * ri < ro are the shell radii (the paper uses 7/13 and 20/13). */
+typedef struct {
+  int Ns, Nr;
+  double ri, ro;
+} fv_grid_desc;
+
+fv_status fv_build_grid(const fv_grid_desc* desc, fv_grid** out);
+fv_status fv_free_grid(fv_grid* g);
+/* number of cells N = 6 Ns^2 Nr */
+fv_status fv_grid_cells(const fv_grid* g, long long* n_cells);
+
+/* Non-dimensional parameters (paper Sec. 2, eqn:velocity ..) and time step. */
+typedef struct {
+  double E, Ra, Pr, Pm, dt;
+} fv_phys;
+
+#define FV_VTBE 0
+#define FV_PPBE 1
+
+/* Preconditioner (paper Sec. 3.3).  Each panel is split into p1 x p2 x p3
+ * boxes (xi, eta, r), overlap `overlap` cells (extended across panel edges);
+ * ILU(0) subdomain solves.  levels = 1: one-level RAS (eqn:onelevel);
+ * levels = 2: hybrid two-level RAS (eqn:twolevel) with a coarse mesh of
+ * (Ns/2, Nr/2), coarse overlap `overlap_coarse`, coarse system solved by inner
+ * FGMRES(coarse_restart) to relative tolerance coarse_rtol (at most
+ * coarse_maxit iterations) preconditioned by one-level RAS on the coarse mesh
+ * (eqn:coarsepreconditioner).  levels = 2 needs even Ns and Nr. */
+typedef struct {
+  int p1, p2, p3;
+  int overlap;
+  int levels;
+  int overlap_coarse;
+  double coarse_rtol;
+  int coarse_restart;
+  int coarse_maxit;
+} fv_pc_desc;
+
+/* Builds the system `kind` (FV_VTBE: A = I - dt/2 [L1 R1; R2 L2; L3];
+ * FV_PPBE: A = dt/2 D G for (P Neumann, P_b Dirichlet)), its subdomain
+ * matrices and their ILU(0) factors on the GPU (setup, once per grid and dt). */
+fv_status fv_assemble_system(const fv_grid* g, int kind, const fv_phys* phys, const fv_pc_desc* pc,
+                             fv_system** out);
+fv_status fv_free_system(fv_system* s);
+/* number of unknowns n = d N (d = 7 for VTBE, 2 for PPBE) */
+fv_status fv_system_size(const fv_system* s, long long* n);
+
+/* y = A x  (matrix-free, paper eqn:divdiscretization for every operator).
+ * x, y: device FP64, n values each, must not overlap. */
+fv_status fv_apply_op(const fv_system* s, const double* x, double* y, void* stream);
+
+/* z = M^{-1} r (eqn:onelevel or eqn:twolevel per the system's pc).
+ * r, z: device FP64, n values each, must not overlap. */
+fv_status fv_precond_apply(const fv_system* s, const double* r, double* z, void* stream);
+
+/* Restarted right-preconditioned flexible GMRES(restart) (paper Sec. 3.3):
+ * stops when ||b - A x|| <= max(atol, rtol ||b - A x0||) or after max_it
+ * iterations.  x: in = x0, out = solution.  stats may be NULL. */
+typedef struct {
+  int restart, max_it;
+  double atol, rtol;
+} fv_gmres_opts;
+
+typedef struct {
+  int iters;             /* outer (F)GMRES iterations */
+  int inner_iters;       /* coarse-level inner iterations (two-level only) */
+  int converged;
+  double r0, rfinal;     /* ||b - A x0||, ||b - A x|| (true residuals) */
+  double time_ms;        /* wall time of the call */
+} fv_solve_stats;
+
+fv_status fv_gmres_solve(const fv_system* s, const double* b, double* x, const fv_gmres_opts* opts,
+                         fv_solve_stats* stats, void* stream);
+
+/* Time-stepping state (paper Sec. 3.1): u, Theta, B, P, P_b at step n, the
+ * nonlinear terms at n-1 (Adams-Bashforth) and the previous VTBE solution.
+ * init: device FP64, 9N values (u_x, u_y, u_z, Theta, B_x, B_y, B_z, P, P_b),
+ * copied into the state. */
+fv_status fv_state_create(const fv_grid* g, const fv_phys* phys, const double* init, fv_state** out);
+fv_status fv_free_state(fv_state* st);
+/* copy the current 9N fields of the state into `out` (device FP64) */
+fv_status fv_state_get(const fv_state* st, double* out, void* stream);
+/* overwrite the 9N fields of the state from `in` (device FP64); the
+ * Adams-Bashforth history and previous solutions are kept */
+fv_status fv_state_set(fv_state* st, const double* in, void* stream);
+
+/* Advance nsteps steps of the predictor-corrector scheme (Steps 1-3 of
+ * Sec. 3.1): VTBE solve, PPBE solve, projection.  stats: NULL or 2*nsteps
+ * entries (VTBE, PPBE per step). */
+fv_status fv_time_step(fv_state* st, const fv_system* vtbe, const fv_system* ppbe, const fv_gmres_opts* opts,
+                       int nsteps, fv_solve_stats* stats, void* stream);
+
+/* Kernel timing (optional).  While enabled, the library brackets each launch of
+ * the categories below with CUDA events on the launching stream (a few
+ * microseconds of host time per launch, no device work); fv_profile_read
+ * synchronizes the device and returns the launch count and summed device
+ * time of one category since the last enable.  Categories + FV_K_COARSE count
+ * the same kernels on the coarse level of a two-level preconditioner.  The
+ * phases PC-C (coarse solve), PC-F (fine one-level RAS) and PC-I (restriction,
+ * prolongation and residual) follow the paper's breakdown of the two-level
+ * preconditioner (Sec. 4.3). */
+#define FV_K_GHOST 0
+#define FV_K_APPLY_VTBE 1
+#define FV_K_APPLY_PPBE 2
+#define FV_K_RAS_FWD 3
+#define FV_K_RAS_BWD 4
+#define FV_K_CGS 5
+#define FV_K_VEC 6
+#define FV_K_GLUE 7
+#define FV_K_TRANSFER 8
+#define FV_K_PHASE_PC_C 9
+#define FV_K_PHASE_PC_F 10
+#define FV_K_PHASE_PC_I 11
+#define FV_K_COARSE 16
+#define FV_K_COUNT 32
+fv_status fv_profile_enable(int on);
+fv_status fv_profile_read(int category, long long* launches, double* total_ms);
+
+/* Message of the calling thread's last failure ("" if none). */
+const char* fv_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FV_H */

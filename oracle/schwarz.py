@@ -173,8 +173,12 @@ def prolong(grid, xc, d):
 class TwoLevelRAS:
     """Hybrid two-level RAS, y = w + M_one^{-1}(x - A_f w), w = I_c^f A_c^{-1} I_f^c x."""
 
-    def __init__(self, grid, A, grid_c, A_c, d, parts, delta, delta_c, rtol_c=0.1, restart_c=30, maxit_c=30):
+    def __init__(self, grid, A, grid_c, A_c, d, parts, delta, delta_c, rtol_c=0.1, restart_c=30, maxit_c=30,
+                 neumann_first=False):
         self.g, self.A, self.Ac, self.d = grid, A, A_c, d
+        # the Neumann pressure (first PPBE component) has a singular coarse matrix whose left null
+        # vector is the coarse cell volumes; its restricted right-hand side is projected onto the range
+        self.Vc = grid_c.volumes().ravel() if neumann_first else None
         self.fine = OneLevelRAS(grid, A, d, parts, delta)
         self.coarse = OneLevelRAS(grid_c, A_c, d, parts, delta_c)
         self.rtol_c, self.restart_c, self.maxit_c = rtol_c, restart_c, maxit_c
@@ -182,6 +186,9 @@ class TwoLevelRAS:
 
     def apply(self, x):
         xc = restrict(self.g, x, self.d)
+        if self.Vc is not None:
+            n = self.Vc.size
+            xc[:n] -= (self.Vc @ xc[:n]) / self.Vc.sum()
         res = fgmres(lambda v: self.Ac @ v, self.coarse.apply, xc, np.zeros_like(xc),
                      restart=self.restart_c, rtol=self.rtol_c, atol=0.0, maxit=self.maxit_c)
         self.inner_iters += res.iters

@@ -59,7 +59,8 @@ class Stepper:
         if opt.ppbe_levels == 2:
             gc = Grid(grid.Ns // 2, grid.Nr // 2, grid.ri, grid.ro)
             Ac = ppbe_matrix(Discretization(gc), phys.E, phys.dt)
-            self.MP = TwoLevelRAS(grid, self.AP, gc, Ac, 2, opt.parts, opt.delta, opt.delta_c, opt.rtol_c)
+            self.MP = TwoLevelRAS(grid, self.AP, gc, Ac, 2, opt.parts, opt.delta, opt.delta_c, opt.rtol_c,
+                                  neumann_first=True)
         else:
             self.MP = OneLevelRAS(grid, self.AP, 2, opt.parts, opt.delta)
         self.Eu = self.d.extension('odd')

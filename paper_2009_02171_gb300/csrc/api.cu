@@ -1,0 +1,135 @@
+// C ABI entry points of libfv (declared in include/fv.h).
+#include <cstring>
+#include <string>
+
+#include "fv_internal.h"
+
+namespace fv {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+fv_status cuda_fail(cudaError_t e, const char* what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? FV_ENOMEM : FV_ECUDA;
+}
+
+static void free_system(fv_system* s) {
+  if (!s) return;
+  if (s->coarse) free_system(s->coarse);
+  free_krylov(s->kry);
+  for (void* p : s->allocs) cudaFree(p);
+  delete s;
+}
+
+static fv_status make_system(const fv_grid* g, int kind, const fv_phys* ph, const fv_pc_desc* pc, fv_system** out) {
+  fv_system* s = new fv_system();
+  s->grid = g, s->kind = kind, s->d = kind == FV_VTBE ? 7 : 2;
+  s->n = s->d * g->h.N;
+  s->phys = *ph, s->pc = *pc;
+  fv_status rc = FV_OK;
+  const size_t ng = (size_t)s->d * 6 * 4 * g->h.Nr * (g->h.Ns + 2);
+  if (cudaMalloc(&s->ghost, ng * sizeof(double)) != cudaSuccess) {
+    delete s;
+    return set_error("fv_assemble_system: ghost layer allocation failed"), FV_ENOMEM;
+  }
+  s->allocs.push_back(s->ghost);
+  if ((rc = build_subdomains(s, g)) || (rc = assemble_subdomains(s)) || (rc = ilu_factor(s))) {
+    free_system(s);
+    return rc;
+  }
+  if (pc->levels >= 2) {
+    if (g->h.Ns % 2 || g->h.Nr % 2 || g->h.Ns < 8 || g->h.Nr < 4) {
+      free_system(s);
+      return set_error("fv_assemble_system: two levels need even Ns >= 8 and even Nr >= 4"), FV_EINVAL;
+    }
+    fv_grid* gm = const_cast<fv_grid*>(g);
+    if (!gm->coarse) {
+      fv_grid_desc cd{g->h.Ns / 2, g->h.Nr / 2, g->h.ri, g->h.ro};
+      if ((rc = build_grid(&cd, &gm->coarse))) {
+        free_system(s);
+        return rc;
+      }
+    }
+    fv_pc_desc cpc = *pc;
+    cpc.levels = 1;
+    cpc.overlap = pc->overlap_coarse;
+    cpc.p1 = std::min(pc->p1, g->h.Ns / 2), cpc.p2 = std::min(pc->p2, g->h.Ns / 2), cpc.p3 = std::min(pc->p3, g->h.Nr / 2);
+    if ((rc = make_system(gm->coarse, kind, ph, &cpc, &s->coarse))) {
+      free_system(s);
+      return rc;
+    }
+    s->coarse->level = 1;
+    const size_t n = (size_t)s->n, nc = (size_t)s->coarse->n;
+    if (cudaMalloc(&s->xc, nc * sizeof(double)) != cudaSuccess || cudaMalloc(&s->ec, nc * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&s->w, n * sizeof(double)) != cudaSuccess || cudaMalloc(&s->t, n * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&s->red, (32 * 304 + 32) * sizeof(double)) != cudaSuccess) {
+      free_system(s);
+      return set_error("fv_assemble_system: two-level work allocation failed"), FV_ENOMEM;
+    }
+    s->allocs.insert(s->allocs.end(), {s->xc, s->ec, s->w, s->t, s->red});
+  }
+  FV_CUDA(cudaDeviceSynchronize());
+  *out = s;
+  return FV_OK;
+}
+
+}  // namespace fv
+
+using namespace fv;
+
+extern "C" {
+
+const char* fv_last_error(void) { return g_err.c_str(); }
+
+fv_status fv_build_grid(const fv_grid_desc* desc, fv_grid** out) { return build_grid(desc, out); }
+
+fv_status fv_free_grid(fv_grid* g) {
+  free_grid(g);
+  return FV_OK;
+}
+
+fv_status fv_grid_cells(const fv_grid* g, long long* n) {
+  if (!g || !n) return set_error("fv_grid_cells: null argument"), FV_EINVAL;
+  *n = g->h.N;
+  return FV_OK;
+}
+
+fv_status fv_assemble_system(const fv_grid* g, int kind, const fv_phys* phys, const fv_pc_desc* pc, fv_system** out) {
+  if (!g || !phys || !pc || !out || (kind != FV_VTBE && kind != FV_PPBE))
+    return set_error("fv_assemble_system: bad argument"), FV_EINVAL;
+  if (!(phys->dt > 0) || !(phys->E > 0) || !(phys->Pr > 0) || !(phys->Pm > 0))
+    return set_error("fv_assemble_system: E, Pr, Pm, dt must be positive"), FV_EINVAL;
+  return make_system(g, kind, phys, pc, out);
+}
+
+fv_status fv_free_system(fv_system* s) {
+  free_system(s);
+  return FV_OK;
+}
+
+fv_status fv_system_size(const fv_system* s, long long* n) {
+  if (!s || !n) return set_error("fv_system_size: null argument"), FV_EINVAL;
+  *n = s->n;
+  return FV_OK;
+}
+
+fv_status fv_apply_op(const fv_system* s, const double* x, double* y, void* stream) {
+  if (!s || !x || !y || x == y) return set_error("fv_apply_op: bad argument"), FV_EINVAL;
+  return apply_op(s, x, y, (cudaStream_t)stream);
+}
+
+fv_status fv_precond_apply(const fv_system* s, const double* r, double* z, void* stream) {
+  if (!s || !r || !z || r == z) return set_error("fv_precond_apply: bad argument"), FV_EINVAL;
+  s->last_inner = 0;
+  return precond_apply(s, r, z, (cudaStream_t)stream);
+}
+
+fv_status fv_gmres_solve(const fv_system* s, const double* b, double* x, const fv_gmres_opts* opts,
+                         fv_solve_stats* stats, void* stream) {
+  if (!s || !b || !x || !opts || b == x) return set_error("fv_gmres_solve: bad argument"), FV_EINVAL;
+  return gmres(s, b, x, opts, stats, (cudaStream_t)stream, false);
+}
+
+}  // extern "C"

@@ -1,0 +1,166 @@
+// Internal types of libfv: device geometry tables, systems, error plumbing.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fv.h"
+
+namespace fv {
+
+// panel sides: 0 = xi-min, 1 = xi-max, 2 = eta-min, 3 = eta-max
+enum { XI_MIN = 0, XI_MAX = 1, ETA_MIN = 2, ETA_MAX = 3 };
+// wall rules of the ghost at the mirror radius (radial direction)
+enum { WALL_ODD = 0, WALL_EVEN = 1, WALL_B = 2 };
+
+// Device-side geometry of one grid level, passed by value to kernels.
+// Angular tables are shared by the 6 panels (identical local coordinates);
+// Cartesian vectors are stored in the panel-local frame (1, X, Y) and rotated
+// by the panel's signed-permutation matrix in the kernels.
+struct Geo {
+  int Ns, Nr;
+  long long N;                 // 6 Ns^2 Nr
+  double hs, hr, ri, ro;
+  double wall_in, wall_out;    // 1 + (r_c/r_g)^2 at the inner / outer wall
+  const double* ax11;          // [j][if]  a11 * h_r            (xi faces, Ns x (Ns+1))
+  const double* ax12;          // [j][if]  a12 * h_r / 4
+  const double* ay22;          // [jf][i]  a22 * h_r            (eta faces, (Ns+1) x Ns)
+  const double* ay12;          // [jf][i]  a12 * h_r / 4
+  const double* crf;           // [j][i]   sigma h_s^2 / h_r    (radial faces, times r_f^2)
+  const double* rf2;           // [kf]     r_f^2
+  const double* invsig;        // [j][i]   1 / sigma
+  const double* invr2;         // [k]      1 / (r_k^2 h_s^2 h_r)
+  const double* rc;            // [k]      r_k
+  const double* xhat;          // [j][i][3] unit position vector, local frame
+  const double* sx;            // [j][if][3] (a11 e1 + a12 e2) h_s h_r, local frame (times r_k)
+  const double* sy;            // [jf][i][3] (a12 e1 + a22 e2) h_s h_r
+  const double* sr;            // [j][i][3]  sigma h_s^2 xhat     (times r_f^2)
+  const int* gq;               // [p][side][t]      panel holding the ghost's source line
+  const int* gsrc;             // [p][side][t][3]   source cells (j*Ns + i) on that panel
+  const double* gw;            // [p][side][t][3]   quadratic Lagrange weights
+  const int* pq;               // [p][side]  neighbour panel across the side
+  const int* psq;              // [p][side]  its side
+  const int* psgn;             // [p][side]  F_p = psgn F_q for the shared face
+  const int* ptmap;            // [p][side][t] tangential index on the neighbour side
+};
+
+struct GridHost {
+  int Ns, Nr;
+  double ri, ro, hs, hr;
+  long long N;
+  // host copies of the tables needed by host setup code
+  std::vector<int> gq, gsrc, pq, psq, psgn, ptmap;
+  std::vector<double> gw;
+};
+
+struct Krylov;
+
+}  // namespace fv
+
+struct fv_grid {
+  fv::GridHost h;
+  fv::Geo geo;                 // device pointers
+  std::vector<void*> allocs;   // device allocations owned by the grid
+  fv_grid* coarse = nullptr;   // (Ns/2, Nr/2) grid, built on demand
+};
+
+namespace fv {
+
+// structured ILU(0) subdomain set of one system on one grid level
+struct Subdomains {
+  int count = 0;
+  int d = 0;
+  long long total_cells = 0;      // sum of box cells
+  int max_levels = 0;
+  // device arrays
+  long long* cell_off = nullptr;  // [count+1] offsets into the packed per-cell arrays
+  int* dims = nullptr;            // [count][3] nx, ny, nz
+  long long* gmap = nullptr;      // [total_cells] global cell or -1 (hole)
+  unsigned char* owned = nullptr; // [total_cells]
+  int* level_off = nullptr;       // [count][max_levels+1] offsets into `order` (relative to cell_off)
+  int* order = nullptr;           // [total_cells] local cells sorted by level (i + 2 j + k)
+  double* off = nullptr;          // [total_cells][11][d] structured coefficients (slot 5 unused)
+  double* diag = nullptr;         // [total_cells][d][d] diagonal blocks (LU in place)
+  double* work = nullptr;         // [total_cells][d] sweep vector
+  int* status = nullptr;          // [1] 0 ok, else 1 + first zero-pivot cell
+  int* lpt = nullptr;             // [count] subdomains in decreasing size (processing order)
+};
+
+}  // namespace fv
+
+struct fv_system {
+  const fv_grid* grid = nullptr;
+  int kind = 0, d = 0;
+  long long n = 0;
+  fv_phys phys{};
+  fv_pc_desc pc{};
+  double* ghost = nullptr;     // [d][6][4][Nr][Ns+2] ghost layer scratch
+  fv::Subdomains subs;
+  // two-level data
+  fv_system* coarse = nullptr;
+  double* xc = nullptr;        // coarse rhs
+  double* ec = nullptr;        // coarse correction
+  double* w = nullptr;         // fine prolongated correction / temps
+  double* t = nullptr;
+  double* red = nullptr;       // [32 * 304 + 32] reduction scratch (coarse mean projection)
+  // FGMRES workspace for this system (outer) sized lazily
+  fv::Krylov* kry = nullptr;
+  mutable int last_inner = 0;
+  int level = 0;               // 0 fine, 1 coarse (kernel timing category offset)
+  std::vector<void*> allocs;
+};
+
+namespace fv {
+
+void set_error(const std::string& msg);
+fv_status cuda_fail(cudaError_t e, const char* what);
+
+// profile.cu: event brackets around one launch (slot -1 when timing is off)
+int prof_begin(int category, cudaStream_t st);
+void prof_end(int slot, cudaStream_t st);
+struct ProfScope {
+  int slot;
+  cudaStream_t st;
+  ProfScope(int category, cudaStream_t s) : slot(prof_begin(category, s)), st(s) {}
+  ~ProfScope() { prof_end(slot, st); }
+};
+
+#define FV_CUDA(call)                                        \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return fv::cuda_fail(e_, #call);  \
+  } while (0)
+
+// grid.cpp
+fv_status build_grid(const fv_grid_desc* desc, fv_grid** out);
+void free_grid(fv_grid* g);
+
+// ops.cu
+fv_status apply_op(const fv_system* s, const double* x, double* y, cudaStream_t st);
+fv_status fill_ghosts(const fv_system* s, const double* x, cudaStream_t st);
+fv_status ghost_fill(const Geo& G, const double* x, double* gh, int d, cudaStream_t st);
+fv_status assemble_subdomains(fv_system* s);
+// glue kernels of the time step
+fv_status nonlinear_terms(const fv_grid* g, const fv_phys& ph, const double* fields, double* f, double* gh7,
+                          cudaStream_t st);
+fv_status face_divergence_uB(const fv_grid* g, const double* x7, double* bP, double* gh7, cudaStream_t st);
+fv_status cell_gradient(const fv_grid* g, const double* x, int wall, double scale, double* out3, double* gh,
+                        cudaStream_t st);
+
+// precond.cu
+fv_status build_subdomains(fv_system* s, const fv_grid* g);
+fv_status ilu_factor(fv_system* s);
+fv_status precond_apply(const fv_system* s, const double* r, double* z, cudaStream_t st);
+fv_status ras_apply(const fv_system* s, const double* r, double* z, cudaStream_t st);
+fv_status restrict_mean(const fv_grid* g, int d, const double* x, double* xc, cudaStream_t st);
+fv_status prolong_inject(const fv_grid* g, int d, const double* xc, double* x, cudaStream_t st);
+
+// krylov.cu
+fv_status gmres(const fv_system* s, const double* b, double* x, const fv_gmres_opts* o, fv_solve_stats* stats,
+                cudaStream_t st, bool inner);
+void free_krylov(Krylov* k);
+fv_status axpby(long long n, double a, const double* x, double b, const double* y, double* out, cudaStream_t st);
+fv_status weighted_mean_remove(const fv_grid* g, double* x, cudaStream_t st, double* part, double* sums);
+
+}  // namespace fv

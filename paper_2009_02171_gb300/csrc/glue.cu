@@ -1,0 +1,182 @@
+// Face-flux kernels of the time step (paper Sec. 3.1 and 3.2):
+//   NL   -- nonlinear terms in conservative form (eqn:nonlinearoperator,
+//           eqn:nonlinearint) with Cartesian components:
+//           f1_k = -div(u u_k) + div(B B_k)/(E Pm), f2 = -div(u Theta),
+//           f3_k = div(B u_k) - div(u B_k); face flux (a_f . S_f) b_f.
+//   DIV  -- face divergence D(v) = (1/V) sum_faces v_f . S_f of u~ and B~
+//           (right-hand side of eqn:tsp, eqn:tspb).
+//   GRAD -- cell Gauss gradient G(phi) = (1/E)(1/V) sum_faces phi_f S_f of P
+//           and P_b (eqn:ubhat, eqn:ubtilde).
+// Face values are means of the two adjacent values (ghosts across panel edges
+// and walls); S_f is the contravariant face area vector (sqrt(g) g^i) h h in
+// Cartesian components.  A panel-edge face carries the mean of the two
+// panels' one-sided fluxes.
+#include "stencil.cuh"
+
+namespace fv {
+
+enum { MODE_NL = 0, MODE_DIV = 1, MODE_GRAD = 2 };
+
+struct Field {
+  const double* x;
+  const double* gh;
+  int wall[7];
+  int bbase;
+};
+
+// one-sided face mean of component c on panel p.  type 0: xi face f = i
+// (cells i-1, i of row j); type 1: eta face f = j (rows j-1, j of column i);
+// type 2: radial face kf = k (levels k-1, k).
+__device__ __noinline__ double face_val(const Geo& G, const Field& F, int c, int p, int type, int k, int j, int i) {
+  ApplyAcc<double> acc{&G, F.x, F.gh, 0.0};
+  if (type == 0) {
+    emit_h(G, acc, 0.5, p, k, j, i - 1, c);
+    emit_h(G, acc, 0.5, p, k, j, i, c);
+  } else if (type == 1) {
+    emit_h(G, acc, 0.5, p, k, j - 1, i, c);
+    emit_h(G, acc, 0.5, p, k, j, i, c);
+  } else if (k > 0 && k < G.Nr) {
+    acc.cell(0.5, p, k - 1, j, i, c);
+    acc.cell(0.5, p, k, j, i, c);
+  } else {
+    const int kc = k == 0 ? 0 : G.Nr - 1;
+    acc.cell(0.5, p, kc, j, i, c);
+    wall_ghost(G, acc, 0.5, p, kc, j, i, c, F.wall[c], F.bbase, k == 0 ? G.wall_in : G.wall_out);
+  }
+  return acc.sum;
+}
+
+__device__ __forceinline__ void face_area(const Geo& G, int p, int type, int k, int j, int i, double S[3]) {
+  const double* l;
+  double sc;
+  if (type == 0) l = G.sx + 3 * (j * (G.Ns + 1) + i), sc = G.rc[k];
+  else if (type == 1) l = G.sy + 3 * (j * G.Ns + i), sc = G.rc[k];
+  else l = G.sr + 3 * (j * G.Ns + i), sc = G.rf2[k];
+  double v[3] = {l[0], l[1], l[2]};
+  rotate(p, v, S);
+  S[0] *= sc, S[1] *= sc, S[2] *= sc;
+}
+
+template <int MODE>
+__device__ __noinline__ void face_flux(const Geo& G, const Field& F, double cL, int p, int type, int k, int j, int i,
+                                       double* out) {
+  double S[3];
+  face_area(G, p, type, k, j, i, S);
+  if (MODE == MODE_NL) {
+    double v[7];
+    for (int c = 0; c < 7; ++c) v[c] = face_val(G, F, c, p, type, k, j, i);
+    const double un = v[0] * S[0] + v[1] * S[1] + v[2] * S[2];
+    const double bn = v[4] * S[0] + v[5] * S[1] + v[6] * S[2];
+    for (int c = 0; c < 3; ++c) {
+      out[c] = -un * v[c] + cL * bn * v[4 + c];
+      out[4 + c] = bn * v[c] - un * v[4 + c];
+    }
+    out[3] = -un * v[3];
+  } else if (MODE == MODE_DIV) {
+    double u[3], b[3];
+    for (int c = 0; c < 3; ++c) u[c] = face_val(G, F, c, p, type, k, j, i), b[c] = face_val(G, F, 4 + c, p, type, k, j, i);
+    out[0] = u[0] * S[0] + u[1] * S[1] + u[2] * S[2];
+    out[1] = b[0] * S[0] + b[1] * S[1] + b[2] * S[2];
+  } else {
+    const double P = face_val(G, F, 0, p, type, k, j, i), Pb = face_val(G, F, 1, p, type, k, j, i);
+    for (int c = 0; c < 3; ++c) out[c] = P * S[c], out[3 + c] = Pb * S[c];
+  }
+}
+
+template <int MODE>
+__device__ __forceinline__ void side_face_flux(const Geo& G, const Field& F, double cL, int p, int side, int k, int t,
+                                               double* out) {
+  const int Ns = G.Ns;
+  switch (side) {
+    case XI_MIN: face_flux<MODE>(G, F, cL, p, 0, k, t, 0, out); break;
+    case XI_MAX: face_flux<MODE>(G, F, cL, p, 0, k, t, Ns, out); break;
+    case ETA_MIN: face_flux<MODE>(G, F, cL, p, 1, k, 0, t, out); break;
+    default: face_flux<MODE>(G, F, cL, p, 1, k, Ns, t, out); break;
+  }
+}
+
+template <int MODE, int NO>
+__device__ __noinline__ void edge_face_flux(const Geo& G, const Field& F, double cL, int p, int side, int k, int t,
+                                            double* out) {
+  const int ps = p * 4 + side;
+  double a[7], b[7];
+  side_face_flux<MODE>(G, F, cL, p, side, k, t, a);
+  side_face_flux<MODE>(G, F, cL, G.pq[ps], G.psq[ps], k, G.ptmap[ps * G.Ns + t], b);
+  const double sg = G.psgn[ps];
+  for (int m = 0; m < NO; ++m) out[m] = 0.5 * (a[m] + sg * b[m]);
+}
+
+template <int MODE, int NO>
+__global__ void face_kernel(Geo G, Field F, double cL, double scale, double* __restrict__ out) {
+  const int Ns = G.Ns;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < G.N; e += (long long)gridDim.x * blockDim.x) {
+    long long c = e;
+    const int i = (int)(c % Ns);
+    c /= Ns;
+    const int j = (int)(c % Ns);
+    c /= Ns;
+    const int k = (int)(c % G.Nr);
+    const int p = (int)(c / G.Nr);
+    double acc[NO], fl[7];
+    for (int m = 0; m < NO; ++m) acc[m] = 0.0;
+    // xi faces
+    if (i + 1 == Ns) edge_face_flux<MODE, NO>(G, F, cL, p, XI_MAX, k, j, fl);
+    else face_flux<MODE>(G, F, cL, p, 0, k, j, i + 1, fl);
+    for (int m = 0; m < NO; ++m) acc[m] += fl[m];
+    if (i == 0) edge_face_flux<MODE, NO>(G, F, cL, p, XI_MIN, k, j, fl);
+    else face_flux<MODE>(G, F, cL, p, 0, k, j, i, fl);
+    for (int m = 0; m < NO; ++m) acc[m] -= fl[m];
+    // eta faces
+    if (j + 1 == Ns) edge_face_flux<MODE, NO>(G, F, cL, p, ETA_MAX, k, i, fl);
+    else face_flux<MODE>(G, F, cL, p, 1, k, j + 1, i, fl);
+    for (int m = 0; m < NO; ++m) acc[m] += fl[m];
+    if (j == 0) edge_face_flux<MODE, NO>(G, F, cL, p, ETA_MIN, k, i, fl);
+    else face_flux<MODE>(G, F, cL, p, 1, k, j, i, fl);
+    for (int m = 0; m < NO; ++m) acc[m] -= fl[m];
+    // radial faces
+    face_flux<MODE>(G, F, cL, p, 2, k + 1, j, i, fl);
+    for (int m = 0; m < NO; ++m) acc[m] += fl[m];
+    face_flux<MODE>(G, F, cL, p, 2, k, j, i, fl);
+    for (int m = 0; m < NO; ++m) acc[m] -= fl[m];
+    const double iv = scale * G.invsig[j * Ns + i] * G.invr2[k];
+    for (int m = 0; m < NO; ++m) out[m * G.N + e] = acc[m] * iv;
+  }
+}
+
+static int fblocks(long long n) {
+  long long b = (n + 127) / 128;
+  return (int)(b < 152LL * 32 ? (b < 1 ? 1 : b) : 152LL * 32);
+}
+
+// 7-component field (u, Theta, B): odd walls for u and Theta, pseudo-vacuum for B
+static Field field7(const double* x, const double* gh) {
+  Field F{x, gh, {WALL_ODD, WALL_ODD, WALL_ODD, WALL_ODD, WALL_B, WALL_B, WALL_B}, 4};
+  return F;
+}
+
+fv_status nonlinear_terms(const fv_grid* g, const fv_phys& ph, const double* x7, double* f, double* gh7,
+                          cudaStream_t st) {
+  ProfScope ps(FV_K_GLUE, st);
+  face_kernel<MODE_NL, 7><<<fblocks(g->geo.N), 128, 0, st>>>(g->geo, field7(x7, gh7), 1.0 / (ph.E * ph.Pm), 1.0, f);
+  FV_CUDA(cudaGetLastError());
+  return FV_OK;
+}
+
+fv_status face_divergence_uB(const fv_grid* g, const double* x7, double* bP, double* gh7, cudaStream_t st) {
+  ProfScope ps(FV_K_GLUE, st);
+  face_kernel<MODE_DIV, 2><<<fblocks(g->geo.N), 128, 0, st>>>(g->geo, field7(x7, gh7), 0.0, 1.0, bP);
+  FV_CUDA(cudaGetLastError());
+  return FV_OK;
+}
+
+// gradient of (P, P_b) (2N values, P even walls, P_b odd walls) -> out6 = (G P, G P_b), times `scale`
+fv_status cell_gradient(const fv_grid* g, const double* x2, int /*wall*/, double scale, double* out6, double* gh2,
+                        cudaStream_t st) {
+  Field F{x2, gh2, {WALL_EVEN, WALL_ODD, 0, 0, 0, 0, 0}, 0};
+  ProfScope ps(FV_K_GLUE, st);
+  face_kernel<MODE_GRAD, 6><<<fblocks(g->geo.N), 128, 0, st>>>(g->geo, F, 0.0, scale, out6);
+  FV_CUDA(cudaGetLastError());
+  return FV_OK;
+}
+
+}  // namespace fv

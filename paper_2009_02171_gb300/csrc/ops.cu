@@ -1,0 +1,219 @@
+// Operator kernels: panel-edge ghost layer, matrix-free VTBE / PPBE apply,
+// and extraction of the structured subdomain matrices for ILU(0).
+#include <cstdio>
+
+#include "stencil.cuh"
+
+namespace fv {
+
+// ---------------------------------------------------------------- ghost layer
+// Ghost centre beyond `side` of panel p at tangential index t: quadratic
+// Lagrange interpolation along the neighbour's first grid line (paper
+// Sec. 3.3 overlap across block interfaces; one ghost layer).  Corner ghosts
+// (t = -1 or Ns on the xi sides): phi(-1,-1) = phi(-1,0) + phi(0,-1) - phi(0,0).
+template <class T>
+__device__ __forceinline__ double interp_ghost(const Geo& G, const T* x, int comp, int p, int side, int k, int t) {
+  const int id = (p * 4 + side) * G.Ns + t;
+  const int q = G.gq[id];
+  const T* base = x + comp * G.N + ((long long)(q * G.Nr + k) * G.Ns) * G.Ns;
+  return G.gw[3 * id] * (double)base[G.gsrc[3 * id]] + G.gw[3 * id + 1] * (double)base[G.gsrc[3 * id + 1]] +
+         G.gw[3 * id + 2] * (double)base[G.gsrc[3 * id + 2]];
+}
+
+template <class T>
+__global__ void ghost_kernel(Geo G, const T* __restrict__ x, T* __restrict__ gh, int d) {
+  const int Ns = G.Ns, Nr = G.Nr;
+  const long long total = (long long)d * 6 * 4 * Nr * (Ns + 2);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    long long r = e;
+    const int tp = (int)(r % (Ns + 2));
+    r /= (Ns + 2);
+    const int k = (int)(r % Nr);
+    r /= Nr;
+    const int side = (int)(r % 4);
+    r /= 4;
+    const int p = (int)(r % 6);
+    const int comp = (int)(r / 6);
+    const int t = tp - 1;
+    double v = 0.0;
+    if (t >= 0 && t < Ns) {
+      v = interp_ghost(G, x, comp, p, side, k, t);
+    } else if (side == XI_MIN || side == XI_MAX) {
+      const int jin = t < 0 ? 0 : Ns - 1;
+      const int iin = side == XI_MIN ? 0 : Ns - 1;
+      v = interp_ghost(G, x, comp, p, side, k, jin) + interp_ghost(G, x, comp, p, t < 0 ? ETA_MIN : ETA_MAX, k, iin) -
+          (double)x[comp * G.N + cidx(G, p, k, jin, iin)];
+    }
+    gh[e] = (T)v;
+  }
+}
+
+static int grid_blocks(long long n, int threads) {
+  long long b = (n + threads - 1) / threads;
+  return (int)(b < 152LL * 32 ? (b < 1 ? 1 : b) : 152LL * 32);
+}
+
+fv_status ghost_fill(const Geo& G, const double* x, double* gh, int d, cudaStream_t st) {
+  const long long total = (long long)d * 6 * 4 * G.Nr * (G.Ns + 2);
+  ghost_kernel<double><<<grid_blocks(total, 256), 256, 0, st>>>(G, x, gh, d);
+  FV_CUDA(cudaGetLastError());
+  return FV_OK;
+}
+
+fv_status fill_ghosts(const fv_system* s, const double* x, cudaStream_t st) {
+  const Geo& G = s->grid->geo;
+  const long long total = (long long)s->d * 6 * 4 * G.Nr * (G.Ns + 2);
+  ProfScope ps(FV_K_GHOST + FV_K_COARSE * s->level, st);
+  ghost_kernel<double><<<grid_blocks(total, 256), 256, 0, st>>>(G, x, s->ghost, s->d);
+  FV_CUDA(cudaGetLastError());
+  return FV_OK;
+}
+
+// ---------------------------------------------------------------- apply
+template <int KIND>
+__global__ void apply_kernel(Geo G, Phys ph, const double* __restrict__ x, const double* __restrict__ gh,
+                             double* __restrict__ y, int d) {
+  const long long n = (long long)d * G.N;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int a = (int)(e / G.N);
+    long long c = e - (long long)a * G.N;
+    const int i = (int)(c % G.Ns);
+    c /= G.Ns;
+    const int j = (int)(c % G.Ns);
+    c /= G.Ns;
+    const int k = (int)(c % G.Nr);
+    const int p = (int)(c / G.Nr);
+    ApplyAcc<double> acc{&G, x, gh, 0.0};
+    if (KIND == FV_VTBE) vtbe_row(G, ph, acc, p, k, j, i, a);
+    else ppbe_row(G, ph, acc, p, k, j, i, a);
+    y[e] = acc.sum;
+  }
+}
+
+fv_status apply_op(const fv_system* s, const double* x, double* y, cudaStream_t st) {
+  const Geo& G = s->grid->geo;
+  fv_status rc = fill_ghosts(s, x, st);
+  if (rc) return rc;
+  Phys ph{s->phys.E, s->phys.Ra, s->phys.Pr, s->phys.Pm, s->phys.dt};
+  const long long n = s->n;
+  ProfScope ps((s->kind == FV_VTBE ? FV_K_APPLY_VTBE : FV_K_APPLY_PPBE) + FV_K_COARSE * s->level, st);
+  if (s->kind == FV_VTBE)
+    apply_kernel<FV_VTBE><<<grid_blocks(n, 256), 256, 0, st>>>(G, ph, x, s->ghost, y, s->d);
+  else
+    apply_kernel<FV_PPBE><<<grid_blocks(n, 256), 256, 0, st>>>(G, ph, x, s->ghost, y, s->d);
+  FV_CUDA(cudaGetLastError());
+  return FV_OK;
+}
+
+// ---------------------------------------------------------------- assembly
+// Structured slots (di, dj, dk) in ascending natural order of the neighbour;
+// slot 5 is the cell itself (dense d x d block), others are component-diagonal.
+__device__ __constant__ static const signed char kOff[11][3] = {
+    {0, 0, -1}, {-1, -1, 0}, {0, -1, 0}, {1, -1, 0}, {-1, 0, 0}, {0, 0, 0},
+    {1, 0, 0},  {-1, 1, 0},  {0, 1, 0},  {1, 1, 0},  {0, 0, 1}};
+
+struct AssembleAcc {
+  const Geo* G;
+  int row_comp;
+  long long col[11];  // global cell of each slot, -1 if absent
+  double off[11];
+  double diag[8];
+  __device__ __noinline__ void cell(double c, int p, int k, int j, int i, int comp) {
+    const long long g = cidx(*G, p, k, j, i);
+    if (g == col[5]) {
+      diag[comp] += c;
+      return;
+    }
+    if (comp != row_comp) return;
+    for (int s = 0; s < 11; ++s)
+      if (s != 5 && col[s] == g) {
+        off[s] += c;
+        return;
+      }
+  }
+  __device__ __noinline__ void interp(double c, int p, int side, int k, int t, int comp) {
+    const int Ns = G->Ns;
+    const int id = (p * 4 + side) * Ns + t;
+    const int q = G->gq[id];
+    for (int m = 0; m < 3; ++m) {
+      const int src = G->gsrc[3 * id + m];
+      cell(c * G->gw[3 * id + m], q, k, src / Ns, src % Ns, comp);
+    }
+  }
+  __device__ __noinline__ void ghost(double c, int p, int side, int k, int t, int comp) {
+    const int Ns = G->Ns;
+    if (t >= 0 && t < Ns) {
+      interp(c, p, side, k, t, comp);
+    } else {
+      const int jin = t < 0 ? 0 : Ns - 1;
+      const int iin = side == XI_MIN ? 0 : Ns - 1;
+      interp(c, p, side, k, jin, comp);
+      interp(c, p, t < 0 ? ETA_MIN : ETA_MAX, k, iin, comp);
+      cell(-c, p, k, jin, iin, comp);
+    }
+  }
+};
+
+__global__ void assemble_kernel(Geo G, Phys ph, int kind, int d, int count, const long long* __restrict__ cell_off,
+                                const int* __restrict__ dims, const long long* __restrict__ gmap,
+                                double* __restrict__ off, double* __restrict__ diag) {
+  const long long total = cell_off[count];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total * d;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long cell = e / d;
+    const int a = (int)(e - cell * d);
+    // find the subdomain (binary search over offsets)
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) / 2;
+      if (cell_off[mid] <= cell) lo = mid;
+      else hi = mid - 1;
+    }
+    const int nx = dims[3 * lo], ny = dims[3 * lo + 1], nz = dims[3 * lo + 2];
+    const long long base = cell_off[lo];
+    const int loc = (int)(cell - base);
+    const int li = loc % nx, lj = (loc / nx) % ny, lk = loc / (nx * ny);
+    AssembleAcc acc;
+    acc.G = &G;
+    acc.row_comp = a;
+    for (int s = 0; s < 11; ++s) {
+      const int ni = li + kOff[s][0], nj = lj + kOff[s][1], nk = lk + kOff[s][2];
+      acc.col[s] = (ni >= 0 && ni < nx && nj >= 0 && nj < ny && nk >= 0 && nk < nz)
+                       ? gmap[base + (nk * ny + nj) * nx + ni]
+                       : -1;
+      acc.off[s] = 0.0;
+    }
+    for (int b = 0; b < 8; ++b) acc.diag[b] = 0.0;
+    const long long g = acc.col[5];
+    if (g >= 0) {
+      long long c = g;
+      const int i = (int)(c % G.Ns);
+      c /= G.Ns;
+      const int j = (int)(c % G.Ns);
+      c /= G.Ns;
+      const int k = (int)(c % G.Nr);
+      const int p = (int)(c / G.Nr);
+      if (kind == FV_VTBE) vtbe_row(G, ph, acc, p, k, j, i, a);
+      else ppbe_row(G, ph, acc, p, k, j, i, a);
+      for (int s = 0; s < 11; ++s)
+        if (acc.col[s] < 0) acc.off[s] = 0.0;
+    } else {
+      acc.diag[a] = 1.0;  // position past a cube corner: identity row
+    }
+    for (int s = 0; s < 11; ++s) off[(cell * 11 + s) * d + a] = acc.off[s];
+    for (int b = 0; b < d; ++b) diag[(cell * d + a) * d + b] = acc.diag[b];
+  }
+}
+
+fv_status assemble_subdomains(fv_system* s) {
+  const Geo& G = s->grid->geo;
+  Phys ph{s->phys.E, s->phys.Ra, s->phys.Pr, s->phys.Pm, s->phys.dt};
+  const long long work = s->subs.total_cells * s->d;
+  assemble_kernel<<<grid_blocks(work, 128), 128>>>(G, ph, s->kind, s->d, s->subs.count, s->subs.cell_off,
+                                                   s->subs.dims, s->subs.gmap, s->subs.off, s->subs.diag);
+  FV_CUDA(cudaGetLastError());
+  return FV_OK;
+}
+
+}  // namespace fv

@@ -1,0 +1,249 @@
+// Discrete operators of the shell dynamo as term visitors (device code).
+//
+// Each operator row is written once, as a sequence of (coefficient, value)
+// terms; an accumulator decides what a term does:
+//   ApplyAcc    -- y_row += coef * x[value]   (matrix-free apply; ghosts read
+//                  from the ghost layer filled beforehand)
+//   AssembleAcc -- adds coef into the structured subdomain-matrix slot of the
+//                  referenced cell (ILU(0) setup), expanding ghosts into their
+//                  interpolation sources.
+//
+// Finite-volume divergence by the Gauss theorem (paper eqn:divdiscretization):
+//   lap(phi)_c = (1/V_c) sum_faces +-F,  V = sqrt(g) h_s^2 h_r,
+//   F_xi  = h_r [a11 (phi_R - phi_L) + a12/4 (phi_{L,j+1} - phi_{L,j-1} + phi_{R,j+1} - phi_{R,j-1})]
+//   F_eta likewise with a22 and the xi-differences,
+//   F_r   = sigma h_s^2 r_f^2 (phi_{k} - phi_{k-1}) / h_r.
+// A face on a panel edge carries the mean of the two panels' one-sided fluxes
+// (each computed with that panel's own ghosts), so fluxes telescope.
+// Walls: ghost at the mirror radius; odd = -cell (u, Theta, P_b), even = +cell
+// (P), B: -B + (1 + (r_c/r_g)^2)(B.rhat) rhat (pseudo-vacuum, eqn:pvc).
+#pragma once
+#include "fv_internal.h"
+
+namespace fv {
+
+// panel rotation: Cartesian = M_p * local(1, X, Y), entries in {-1, 0, 1}
+__device__ __constant__ static const signed char kPM[6][9] = {
+    {1, 0, 0, 0, 1, 0, 0, 0, 1},  {0, -1, 0, 1, 0, 0, 0, 0, 1}, {-1, 0, 0, 0, -1, 0, 0, 0, 1},
+    {0, 1, 0, -1, 0, 0, 0, 0, 1}, {0, 0, -1, 0, 1, 0, 1, 0, 0}, {0, 0, 1, 0, 1, 0, -1, 0, 0},
+};
+
+__device__ __forceinline__ void rotate(int p, const double* l, double* v) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) v[a] = kPM[p][3 * a] * l[0] + kPM[p][3 * a + 1] * l[1] + kPM[p][3 * a + 2] * l[2];
+}
+
+__device__ __forceinline__ long long cidx(const Geo& G, int p, int k, int j, int i) {
+  return ((long long)(p * G.Nr + k) * G.Ns + j) * G.Ns + i;
+}
+
+// ghost layer: [comp][p][side][k][t+1], t in [-1, Ns] (corners stored on xi sides)
+__device__ __forceinline__ long long gidx(const Geo& G, int comp, int p, int side, int k, int t) {
+  return ((((long long)comp * 6 + p) * 4 + side) * G.Nr + k) * (G.Ns + 2) + (t + 1);
+}
+
+// value at extended horizontal position (j, i in [-1, Ns]) of panel p, level k
+template <class Acc>
+__device__ inline void emit_h(const Geo& G, Acc& acc, double c, int p, int k, int j, int i, int comp) {
+  const int Ns = G.Ns;
+  if (i >= 0 && i < Ns) {
+    if (j >= 0 && j < Ns)
+      acc.cell(c, p, k, j, i, comp);
+    else
+      acc.ghost(c, p, j < 0 ? ETA_MIN : ETA_MAX, k, i, comp);
+  } else {
+    acc.ghost(c, p, i < 0 ? XI_MIN : XI_MAX, k, j, comp);
+  }
+}
+
+// one-sided flux through the xi face f (between cells f-1 and f) of row j
+template <class Acc>
+__device__ inline void xi_flux(const Geo& G, Acc& acc, double s, int p, int k, int j, int f, int comp) {
+  const int id = j * (G.Ns + 1) + f;
+  const double a = G.ax11[id] * s, b = G.ax12[id] * s;
+  emit_h(G, acc, a, p, k, j, f, comp);
+  emit_h(G, acc, -a, p, k, j, f - 1, comp);
+  emit_h(G, acc, b, p, k, j + 1, f - 1, comp);
+  emit_h(G, acc, -b, p, k, j - 1, f - 1, comp);
+  emit_h(G, acc, b, p, k, j + 1, f, comp);
+  emit_h(G, acc, -b, p, k, j - 1, f, comp);
+}
+
+// one-sided flux through the eta face f (between rows f-1 and f) of column i
+template <class Acc>
+__device__ inline void eta_flux(const Geo& G, Acc& acc, double s, int p, int k, int f, int i, int comp) {
+  const int id = f * G.Ns + i;
+  const double a = G.ay22[id] * s, b = G.ay12[id] * s;
+  emit_h(G, acc, a, p, k, f, i, comp);
+  emit_h(G, acc, -a, p, k, f - 1, i, comp);
+  emit_h(G, acc, b, p, k, f - 1, i + 1, comp);
+  emit_h(G, acc, -b, p, k, f - 1, i - 1, comp);
+  emit_h(G, acc, b, p, k, f, i + 1, comp);
+  emit_h(G, acc, -b, p, k, f, i - 1, comp);
+}
+
+template <class Acc>
+__device__ __noinline__ void own_side_flux(const Geo& G, Acc& acc, double s, int p, int side, int k, int t,
+                                              int comp) {
+  const int Ns = G.Ns;
+  switch (side) {
+    case XI_MIN: xi_flux(G, acc, s, p, k, t, 0, comp); break;
+    case XI_MAX: xi_flux(G, acc, s, p, k, t, Ns, comp); break;
+    case ETA_MIN: eta_flux(G, acc, s, p, k, 0, t, comp); break;
+    default: eta_flux(G, acc, s, p, k, Ns, t, comp); break;
+  }
+}
+
+// panel-edge face: mean of the two panels' one-sided fluxes (measured along p's coordinate)
+template <class Acc>
+__device__ __noinline__ void edge_flux(const Geo& G, Acc& acc, double s, int p, int side, int k, int t, int comp) {
+  const int ps = p * 4 + side;
+  own_side_flux(G, acc, 0.5 * s, p, side, k, t, comp);
+  own_side_flux(G, acc, 0.5 * s * G.psgn[ps], G.pq[ps], G.psq[ps], k, G.ptmap[ps * G.Ns + t], comp);
+}
+
+// wall ghost of component `comp` at the cell (kc, j, i) next to a wall
+template <class Acc>
+__device__ __forceinline__ void wall_ghost(const Geo& G, Acc& acc, double c, int p, int kc, int j, int i, int comp,
+                                           int wall, int bbase, double fac) {
+  if (wall == WALL_ODD) {
+    acc.cell(-c, p, kc, j, i, comp);
+  } else if (wall == WALL_EVEN) {
+    acc.cell(c, p, kc, j, i, comp);
+  } else {
+    double rh[3];
+    rotate(p, G.xhat + 3 * (j * G.Ns + i), rh);
+    const int a = comp - bbase;
+    acc.cell(-c, p, kc, j, i, comp);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) acc.cell(c * fac * rh[a] * rh[b], p, kc, j, i, bbase + b);
+  }
+}
+
+// radial flux through face kf (between k = kf-1 and kf) of column (j, i)
+template <class Acc>
+__device__ __forceinline__ void r_flux(const Geo& G, Acc& acc, double s, int p, int kf, int j, int i, int comp,
+                                       int wall, int bbase) {
+  const double c = G.crf[j * G.Ns + i] * G.rf2[kf] * s;
+  if (kf > 0 && kf < G.Nr) {
+    acc.cell(c, p, kf, j, i, comp);
+    acc.cell(-c, p, kf - 1, j, i, comp);
+  } else if (kf == 0) {
+    acc.cell(c, p, 0, j, i, comp);
+    wall_ghost(G, acc, -c, p, 0, j, i, comp, wall, bbase, G.wall_in);
+  } else {
+    wall_ghost(G, acc, c, p, G.Nr - 1, j, i, comp, wall, bbase, G.wall_out);
+    acc.cell(-c, p, G.Nr - 1, j, i, comp);
+  }
+}
+
+// interior xi / eta fluxes: every value is a cell of panel p (1 <= i, j <= Ns-2)
+template <class Acc>
+__device__ __forceinline__ void xi_flux_in(const Geo& G, Acc& acc, double s, int p, int k, int j, int f, int comp) {
+  const int id = j * (G.Ns + 1) + f;
+  const double a = G.ax11[id] * s, b = G.ax12[id] * s;
+  acc.cell(a, p, k, j, f, comp);
+  acc.cell(-a, p, k, j, f - 1, comp);
+  acc.cell(b, p, k, j + 1, f - 1, comp);
+  acc.cell(-b, p, k, j - 1, f - 1, comp);
+  acc.cell(b, p, k, j + 1, f, comp);
+  acc.cell(-b, p, k, j - 1, f, comp);
+}
+
+template <class Acc>
+__device__ __forceinline__ void eta_flux_in(const Geo& G, Acc& acc, double s, int p, int k, int f, int i, int comp) {
+  const int id = f * G.Ns + i;
+  const double a = G.ay22[id] * s, b = G.ay12[id] * s;
+  acc.cell(a, p, k, f, i, comp);
+  acc.cell(-a, p, k, f - 1, i, comp);
+  acc.cell(b, p, k, f - 1, i + 1, comp);
+  acc.cell(-b, p, k, f - 1, i - 1, comp);
+  acc.cell(b, p, k, f, i + 1, comp);
+  acc.cell(-b, p, k, f, i - 1, comp);
+}
+
+// horizontal part of s * lap at a cell on a panel edge (i or j in {0, Ns-1})
+template <class Acc>
+__device__ __noinline__ void lap_h_edge(const Geo& G, Acc& acc, double sv, int p, int k, int j, int i, int comp) {
+  const int Ns = G.Ns;
+  if (i + 1 == Ns) edge_flux(G, acc, sv, p, XI_MAX, k, j, comp);
+  else xi_flux(G, acc, sv, p, k, j, i + 1, comp);
+  if (i == 0) edge_flux(G, acc, -sv, p, XI_MIN, k, j, comp);
+  else xi_flux(G, acc, -sv, p, k, j, i, comp);
+  if (j + 1 == Ns) edge_flux(G, acc, sv, p, ETA_MAX, k, i, comp);
+  else eta_flux(G, acc, sv, p, k, j + 1, i, comp);
+  if (j == 0) edge_flux(G, acc, -sv, p, ETA_MIN, k, i, comp);
+  else eta_flux(G, acc, -sv, p, k, j, i, comp);
+}
+
+// s * lap(phi_comp) at cell (p, k, j, i)
+template <class Acc>
+__device__ __forceinline__ void lap_row(const Geo& G, Acc& acc, double s, int p, int k, int j, int i, int comp,
+                                        int wall, int bbase) {
+  const int Ns = G.Ns;
+  const double sv = s * G.invsig[j * Ns + i] * G.invr2[k];
+  if (i > 0 && j > 0 && i + 1 < Ns && j + 1 < Ns) {
+    xi_flux_in(G, acc, sv, p, k, j, i + 1, comp);
+    xi_flux_in(G, acc, -sv, p, k, j, i, comp);
+    eta_flux_in(G, acc, sv, p, k, j + 1, i, comp);
+    eta_flux_in(G, acc, -sv, p, k, j, i, comp);
+  } else {
+    lap_h_edge(G, acc, sv, p, k, j, i, comp);
+  }
+  r_flux(G, acc, sv, p, k + 1, j, i, comp, wall, bbase);
+  r_flux(G, acc, -sv, p, k, j, i, comp, wall, bbase);
+}
+
+struct Phys {
+  double E, Ra, Pr, Pm, dt;
+};
+
+// Row `a` of the VTBE matrix A = I - dt/2 M (eqn:tsvelocity, eqn:tstemperature, eqn:tsmag):
+//   u_a:   u - dt/2 [lap u - (2/E) z x u + Ra/(E r_o) Theta r]_a
+//   Theta: Theta - dt/2 [lap Theta / Pr + r_i r_o / r^3 (u . r)]
+//   B_a:   B - dt/2 [lap B / Pm]_a
+template <class Acc>
+__device__ __forceinline__ void vtbe_row(const Geo& G, const Phys& ph, Acc& acc, int p, int k, int j, int i, int a) {
+  const double h = -0.5 * ph.dt;
+  acc.cell(1.0, p, k, j, i, a);
+  if (a < 3) {
+    lap_row(G, acc, h, p, k, j, i, a, WALL_ODD, 0);
+    if (a == 0) acc.cell(h * (2.0 / ph.E), p, k, j, i, 1);
+    if (a == 1) acc.cell(-h * (2.0 / ph.E), p, k, j, i, 0);
+    double xl[3], x[3];
+    for (int c = 0; c < 3; ++c) xl[c] = G.xhat[3 * (j * G.Ns + i) + c];
+    rotate(p, xl, x);
+    acc.cell(h * ph.Ra / (ph.E * G.ro) * G.rc[k] * x[a], p, k, j, i, 3);
+  } else if (a == 3) {
+    lap_row(G, acc, h / ph.Pr, p, k, j, i, 3, WALL_ODD, 0);
+    double xl[3], x[3];
+    for (int c = 0; c < 3; ++c) xl[c] = G.xhat[3 * (j * G.Ns + i) + c];
+    rotate(p, xl, x);
+    const double r = G.rc[k];
+    for (int c = 0; c < 3; ++c) acc.cell(h * G.ri * G.ro / (r * r) * x[c], p, k, j, i, c);
+  } else {
+    lap_row(G, acc, h / ph.Pm, p, k, j, i, a, WALL_B, 4);
+  }
+}
+
+// Row `a` of the PPBE matrix dt/2 D G = dt/(2E) lap (eqn:tsp, eqn:tspb): P even walls, P_b odd walls
+template <class Acc>
+__device__ __forceinline__ void ppbe_row(const Geo& G, const Phys& ph, Acc& acc, int p, int k, int j, int i, int a) {
+  lap_row(G, acc, 0.5 * ph.dt / ph.E, p, k, j, i, a, a == 0 ? WALL_EVEN : WALL_ODD, 0);
+}
+
+template <class T>
+struct ApplyAcc {
+  const Geo* G;
+  const T* x;
+  const T* gh;
+  double sum;
+  __device__ __forceinline__ void cell(double c, int p, int k, int j, int i, int comp) {
+    sum += c * (double)x[comp * G->N + cidx(*G, p, k, j, i)];
+  }
+  __device__ __forceinline__ void ghost(double c, int p, int side, int k, int t, int comp) {
+    sum += c * (double)gh[gidx(*G, comp, p, side, k, t)];
+  }
+};
+
+}  // namespace fv

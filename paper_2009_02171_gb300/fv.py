@@ -1,0 +1,201 @@
+"""Thin ctypes binding of libfv.so (the C ABI of include/fv.h).
+
+Argument marshalling only: every step of the solve runs in the CUDA library.
+Vectors are torch CUDA float64 tensors (contiguous, component-major
+[comp][panel][k][j][i]); their device pointers are passed to the library
+together with torch's current CUDA stream.  There is no CPU fallback: if
+libfv.so is missing the import of this module raises.
+"""
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, 'libfv.so')
+
+FV_VTBE, FV_PPBE = 0, 1
+ERRORS = {-1: 'FV_EINVAL', -2: 'FV_ENOMEM', -3: 'FV_ECUDA', -4: 'FV_ENOCONV', -5: 'FV_EBREAKDOWN', -6: 'FV_ENAN'}
+
+
+class FvError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__('%s: %s' % (ERRORS.get(code, code), msg))
+        self.code = code
+
+
+class fv_grid_desc(ctypes.Structure):
+    _fields_ = [('Ns', ctypes.c_int), ('Nr', ctypes.c_int), ('ri', ctypes.c_double), ('ro', ctypes.c_double)]
+
+
+class fv_phys(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ('E', 'Ra', 'Pr', 'Pm', 'dt')]
+
+
+class fv_pc_desc(ctypes.Structure):
+    _fields_ = [('p1', ctypes.c_int), ('p2', ctypes.c_int), ('p3', ctypes.c_int), ('overlap', ctypes.c_int),
+                ('levels', ctypes.c_int), ('overlap_coarse', ctypes.c_int), ('coarse_rtol', ctypes.c_double),
+                ('coarse_restart', ctypes.c_int), ('coarse_maxit', ctypes.c_int)]
+
+
+class fv_gmres_opts(ctypes.Structure):
+    _fields_ = [('restart', ctypes.c_int), ('max_it', ctypes.c_int), ('atol', ctypes.c_double),
+                ('rtol', ctypes.c_double)]
+
+
+class fv_solve_stats(ctypes.Structure):
+    _fields_ = [('iters', ctypes.c_int), ('inner_iters', ctypes.c_int), ('converged', ctypes.c_int),
+                ('r0', ctypes.c_double), ('rfinal', ctypes.c_double), ('time_ms', ctypes.c_double)]
+
+
+# (name, argtypes) of every symbol include/fv.h declares
+_P, _VP, _DP = ctypes.POINTER, ctypes.c_void_p, ctypes.c_void_p
+SIGNATURES = {
+    'fv_build_grid': [_P(fv_grid_desc), _P(_VP)],
+    'fv_free_grid': [_VP],
+    'fv_grid_cells': [_VP, _P(ctypes.c_longlong)],
+    'fv_assemble_system': [_VP, ctypes.c_int, _P(fv_phys), _P(fv_pc_desc), _P(_VP)],
+    'fv_free_system': [_VP],
+    'fv_system_size': [_VP, _P(ctypes.c_longlong)],
+    'fv_apply_op': [_VP, _DP, _DP, _VP],
+    'fv_precond_apply': [_VP, _DP, _DP, _VP],
+    'fv_gmres_solve': [_VP, _DP, _DP, _P(fv_gmres_opts), _P(fv_solve_stats), _VP],
+    'fv_state_create': [_VP, _P(fv_phys), _DP, _P(_VP)],
+    'fv_free_state': [_VP],
+    'fv_state_get': [_VP, _DP, _VP],
+    'fv_state_set': [_VP, _DP, _VP],
+    'fv_time_step': [_VP, _VP, _VP, _P(fv_gmres_opts), ctypes.c_int, _P(fv_solve_stats), _VP],
+    'fv_profile_enable': [ctypes.c_int],
+    'fv_profile_read': [ctypes.c_int, _P(ctypes.c_longlong), _P(ctypes.c_double)],
+    'fv_last_error': [],
+}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError('libfv.so is not built (run __graft_entry__.build()); there is no CPU fallback')
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, args in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_char_p if name == 'fv_last_error' else ctypes.c_int
+    return lib
+
+
+lib = _load()
+
+
+def _check(rc):
+    if rc != 0:
+        raise FvError(rc, lib.fv_last_error().decode())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t, n=None):
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError('expected a contiguous CUDA float64 tensor')
+    if n is not None and t.numel() != n:
+        raise ValueError('expected %d values, got %d' % (n, t.numel()))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------- C ABI, same names
+def fv_build_grid(Ns, Nr, ri=7.0 / 13.0, ro=20.0 / 13.0):
+    h = ctypes.c_void_p()
+    _check(lib.fv_build_grid(ctypes.byref(fv_grid_desc(Ns, Nr, ri, ro)), ctypes.byref(h)))
+    return h
+
+
+def fv_assemble_system(grid, kind, E, Ra, Pr, Pm, dt, p=(1, 1, 1), overlap=1, levels=1, overlap_coarse=1,
+                       coarse_rtol=0.1, coarse_restart=30, coarse_maxit=30):
+    h = ctypes.c_void_p()
+    pc = fv_pc_desc(p[0], p[1], p[2], overlap, levels, overlap_coarse, coarse_rtol, coarse_restart, coarse_maxit)
+    _check(lib.fv_assemble_system(grid, kind, ctypes.byref(fv_phys(E, Ra, Pr, Pm, dt)), ctypes.byref(pc),
+                                  ctypes.byref(h)))
+    return h
+
+
+def fv_system_size(system):
+    n = ctypes.c_longlong()
+    _check(lib.fv_system_size(system, ctypes.byref(n)))
+    return n.value
+
+
+def fv_apply_op(system, x, y):
+    n = fv_system_size(system)
+    _check(lib.fv_apply_op(system, _ptr(x, n), _ptr(y, n), _stream()))
+    return y
+
+
+def fv_precond_apply(system, r, z):
+    n = fv_system_size(system)
+    _check(lib.fv_precond_apply(system, _ptr(r, n), _ptr(z, n), _stream()))
+    return z
+
+
+def fv_gmres_solve(system, b, x, restart=30, max_it=3000, atol=0.0, rtol=1e-8, raise_on_noconv=True):
+    n = fv_system_size(system)
+    st = fv_solve_stats()
+    rc = lib.fv_gmres_solve(system, _ptr(b, n), _ptr(x, n), ctypes.byref(fv_gmres_opts(restart, max_it, atol, rtol)),
+                            ctypes.byref(st), _stream())
+    if rc != 0 and (raise_on_noconv or rc != -4):
+        _check(rc)
+    return st
+
+
+def fv_state_create(grid, init, E, Ra, Pr, Pm, dt):
+    h = ctypes.c_void_p()
+    ncell = ctypes.c_longlong()
+    _check(lib.fv_grid_cells(grid, ctypes.byref(ncell)))
+    _check(lib.fv_state_create(grid, ctypes.byref(fv_phys(E, Ra, Pr, Pm, dt)), _ptr(init, 9 * ncell.value),
+                               ctypes.byref(h)))
+    return h
+
+
+def fv_state_get(state, out):
+    _check(lib.fv_state_get(state, _ptr(out), _stream()))
+    return out
+
+
+def fv_state_set(state, src):
+    _check(lib.fv_state_set(state, _ptr(src), _stream()))
+
+
+def fv_time_step(state, vtbe, ppbe, nsteps=1, restart=30, max_it=3000, atol=0.0, rtol=1e-8):
+    stats = (fv_solve_stats * (2 * nsteps))()
+    _check(lib.fv_time_step(state, vtbe, ppbe, ctypes.byref(fv_gmres_opts(restart, max_it, atol, rtol)), nsteps,
+                            stats, _stream()))
+    return list(stats)
+
+
+def fv_free_grid(h):
+    _check(lib.fv_free_grid(h))
+
+
+def fv_free_system(h):
+    _check(lib.fv_free_system(h))
+
+
+def fv_free_state(h):
+    _check(lib.fv_free_state(h))
+
+
+K_GHOST, K_APPLY_VTBE, K_APPLY_PPBE, K_RAS_FWD, K_RAS_BWD, K_CGS, K_VEC, K_GLUE, K_TRANSFER = range(9)
+K_PHASE_PC_C, K_PHASE_PC_F, K_PHASE_PC_I, K_COARSE, K_COUNT = 9, 10, 11, 16, 32
+
+
+def fv_profile_enable(on=True):
+    _check(lib.fv_profile_enable(1 if on else 0))
+
+
+def fv_profile_read(category):
+    n, t = ctypes.c_longlong(), ctypes.c_double()
+    _check(lib.fv_profile_read(category, ctypes.byref(n), ctypes.byref(t)))
+    return n.value, t.value
+
+
+def fv_last_error():
+    return lib.fv_last_error().decode()

@@ -1,0 +1,156 @@
+"""GPU path (through the C ABI) against the CPU oracle, element by element."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip('torch')
+pytestmark = pytest.mark.gpu
+
+from oracle.discrete import Discretization, ppbe_matrix, vtbe_matrix  # noqa: E402
+from oracle.grid import Grid  # noqa: E402
+from oracle.krylov import fgmres  # noqa: E402
+from oracle.schwarz import OneLevelRAS, TwoLevelRAS  # noqa: E402
+from oracle.timestep import Physics, SolverOptions, Stepper  # noqa: E402
+from paper_2009_02171_gb300.inputs import initial_state, random_vector  # noqa: E402
+
+PH = dict(E=1e-3, Ra=100.0, Pr=1.0, Pm=5.0, dt=1e-4)
+
+
+@pytest.fixture(scope='module')
+def fv():
+    if not torch.cuda.is_available():
+        pytest.skip('no GPU')
+    from paper_2009_02171_gb300 import fv as f
+    return f
+
+
+def _dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device='cuda')
+
+
+def _oracle_matrix(kind, Ns, Nr):
+    d = Discretization(Grid(Ns, Nr))
+    if kind == 0:
+        return vtbe_matrix(d, PH['E'], PH['Ra'], PH['Pr'], PH['Pm'], PH['dt']), 7, d
+    return ppbe_matrix(d, PH['E'], PH['dt']), 2, d
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+@pytest.mark.parametrize('kind', [0, 1])
+@pytest.mark.parametrize('Ns,Nr', [(8, 6), (13, 5)])
+def test_apply_matches_oracle(fv, kind, Ns, Nr):
+    """y = A x (matrix-free CUDA) vs the oracle's assembled A @ x: 1e-12 relative."""
+    A, d, _ = _oracle_matrix(kind, Ns, Nr)
+    g = fv.fv_build_grid(Ns, Nr)
+    s = fv.fv_assemble_system(g, kind, **PH)
+    x = random_vector(A.shape[0], 1 + kind)
+    y = fv.fv_apply_op(s, _dev(x), torch.empty(A.shape[0], dtype=torch.float64, device='cuda')).cpu().numpy()
+    assert _rel(y, A @ x) < 1e-12
+    fv.fv_free_system(s)
+    fv.fv_free_grid(g)
+
+
+@pytest.mark.parametrize('kind,Ns,Nr,parts,delta', [(0, 8, 6, (2, 2, 2), 1), (1, 10, 8, (3, 2, 2), 2),
+                                                     (1, 8, 8, (1, 1, 1), 1), (0, 9, 5, (2, 3, 1), 2)])
+def test_one_level_ras_matches_oracle(fv, kind, Ns, Nr, parts, delta):
+    """z = M_one^{-1} r (level-scheduled ILU(0) sweeps) vs the oracle's sequential ILU(0)."""
+    A, d, _ = _oracle_matrix(kind, Ns, Nr)
+    M = OneLevelRAS(Grid(Ns, Nr), A, d, parts, delta)
+    g = fv.fv_build_grid(Ns, Nr)
+    s = fv.fv_assemble_system(g, kind, **PH, p=parts, overlap=delta)
+    r = random_vector(A.shape[0], 7)
+    z = fv.fv_precond_apply(s, _dev(r), torch.empty(A.shape[0], dtype=torch.float64, device='cuda')).cpu().numpy()
+    assert _rel(z, M.apply(r)) < 1e-11
+    fv.fv_free_system(s)
+    fv.fv_free_grid(g)
+
+
+def test_two_level_ras_matches_oracle(fv):
+    """Hybrid two-level preconditioner (eqn:twolevel) with inner coarse FGMRES to 0.1."""
+    Ns, Nr, parts = 12, 8, (2, 2, 1)
+    A, d, _ = _oracle_matrix(1, Ns, Nr)
+    Ac, _, _ = _oracle_matrix(1, Ns // 2, Nr // 2)
+    M = TwoLevelRAS(Grid(Ns, Nr), A, Grid(Ns // 2, Nr // 2), Ac, 2, parts, 1, 1, 0.1, 30, 30, neumann_first=True)
+    g = fv.fv_build_grid(Ns, Nr)
+    s = fv.fv_assemble_system(g, 1, **PH, p=parts, overlap=1, levels=2, overlap_coarse=1)
+    r = random_vector(A.shape[0], 9)
+    z = fv.fv_precond_apply(s, _dev(r), torch.empty(A.shape[0], dtype=torch.float64, device='cuda')).cpu().numpy()
+    assert _rel(z, M.apply(r)) < 1e-9
+    fv.fv_free_system(s)
+    fv.fv_free_grid(g)
+
+
+@pytest.mark.parametrize('kind,levels', [(0, 1), (1, 1), (1, 2)])
+def test_gmres_solution_matches_oracle(fv, kind, levels):
+    """Solutions at a 1e-8 relative residual agree to 1e-7 (same algorithm, same ordering)."""
+    Ns = Nr = 12
+    parts = (2, 2, 2)
+    A, d, disc = _oracle_matrix(kind, Ns, Nr)
+    G = Grid(Ns, Nr)
+    if levels == 2:
+        Ac, _, _ = _oracle_matrix(1, Ns // 2, Nr // 2)
+        M = TwoLevelRAS(G, A, Grid(Ns // 2, Nr // 2), Ac, d, parts, 1, 1, neumann_first=True)
+    else:
+        M = OneLevelRAS(G, A, d, parts, 1)
+    b = random_vector(A.shape[0], 13)
+    if kind == 1:
+        b[:G.N] -= (disc.V @ b[:G.N]) / disc.V.sum()
+    ref = fgmres(lambda v: A @ v, M.apply, b, np.zeros_like(b), restart=30, rtol=1e-8)
+    g = fv.fv_build_grid(Ns, Nr)
+    s = fv.fv_assemble_system(g, kind, **PH, p=parts, overlap=1, levels=levels)
+    x = torch.zeros(A.shape[0], dtype=torch.float64, device='cuda')
+    st = fv.fv_gmres_solve(s, _dev(b), x, rtol=1e-8)
+    xs = x.cpu().numpy()
+    assert st.converged and abs(st.iters - ref.iters) <= 1
+    assert np.linalg.norm(b - A @ xs) <= 1.0001e-8 * np.linalg.norm(b)
+    if kind == 1:
+        xs[:G.N] -= (disc.V @ xs[:G.N]) / disc.V.sum()
+        rx = ref.x.copy()
+        rx[:G.N] -= (disc.V @ rx[:G.N]) / disc.V.sum()
+    else:
+        rx = ref.x
+    assert _rel(xs, rx) < 1e-7
+    fv.fv_free_system(s)
+    fv.fv_free_grid(g)
+
+
+@pytest.mark.parametrize('levels', [1, 2])
+def test_time_step_matches_oracle(fv, levels):
+    """Two predictor-corrector steps (Sec. 3.1) from seeded synthetic fields."""
+    Ns, Nr, parts = 8, 8, (2, 2, 1)
+    s0 = initial_state(Ns, Nr, 0)
+    N = 6 * Ns * Ns * Nr
+    init = np.concatenate([s0['u'].ravel(), s0['T'], s0['B'].ravel(), s0['P'], s0['Pb']])
+    st_o = Stepper(Grid(Ns, Nr), Physics(**PH), SolverOptions(parts=parts, delta=1, ppbe_levels=levels, rtol=1e-10))
+    ref = dict(s0, first=True)
+    for _ in range(2):
+        ref, info = st_o.step(ref)
+        assert info['vtbe'].converged and info['ppbe'].converged
+    g = fv.fv_build_grid(Ns, Nr)
+    V = fv.fv_assemble_system(g, 0, **PH, p=parts, overlap=1)
+    P = fv.fv_assemble_system(g, 1, **PH, p=parts, overlap=1, levels=levels)
+    st = fv.fv_state_create(g, _dev(init), **PH)
+    stats = fv.fv_time_step(st, V, P, nsteps=2, rtol=1e-10)
+    assert all(s.converged for s in stats)
+    out = fv.fv_state_get(st, torch.empty(9 * N, dtype=torch.float64, device='cuda')).cpu().numpy()
+    assert _rel(out[:3 * N], ref['u'].ravel()) < 1e-7
+    assert _rel(out[3 * N:4 * N], ref['T']) < 1e-7
+    assert _rel(out[4 * N:7 * N], ref['B'].ravel()) < 1e-7
+    assert _rel(out[7 * N:8 * N], ref['P']) < 1e-6
+    fv.fv_free_state(st)
+    fv.fv_free_system(V)
+    fv.fv_free_system(P)
+    fv.fv_free_grid(g)
+
+
+def test_bad_arguments_raise(fv):
+    with pytest.raises(fv.FvError):
+        fv.fv_build_grid(2, 1)
+    g = fv.fv_build_grid(9, 6)
+    with pytest.raises(fv.FvError):
+        fv.fv_assemble_system(g, 1, **PH, p=(1, 1, 1), levels=2, overlap=1)  # odd Ns has no 1:2 coarse mesh
+    with pytest.raises(fv.FvError):
+        fv.fv_assemble_system(g, 1, **PH, p=(10, 1, 1), overlap=1)           # more boxes than cells
+    fv.fv_free_grid(g)

@@ -169,8 +169,23 @@ def test_two_level_beats_one_level_on_ppbe():
     V = Discretization(g).V
     b[:g.N] -= (V @ b[:g.N]) / V.sum()
     r1 = fgmres(lambda v: A @ v, OneLevelRAS(g, A, 2, (1, 1, 1), 1).apply, b, np.zeros_like(b), rtol=1e-8)
-    M2 = TwoLevelRAS(g, A, gc, Ac, 2, (1, 1, 1), 1, 1)
+    M2 = TwoLevelRAS(g, A, gc, Ac, 2, (1, 1, 1), 1, 1, neumann_first=True)
     r2 = fgmres(lambda v: A @ v, M2.apply, b, np.zeros_like(b), rtol=1e-8)
     assert r1.converged and r2.converged
     assert r2.iters * 2 < r1.iters
     assert np.linalg.norm(b - A @ r2.x) <= 1e-8 * np.linalg.norm(b) * 1.0001
+
+
+def test_two_level_neumann_coarse_projection_prevents_stagnation():
+    """Consecutive time steps with the two-level PPBE keep a steady iteration count (the coarse
+    Neumann-pressure right-hand side is projected onto the range of the singular coarse matrix)."""
+    from oracle.timestep import Physics, SolverOptions, Stepper
+    from paper_2009_02171_gb300.inputs import initial_state
+    st = Stepper(Grid(8, 8), Physics(), SolverOptions(parts=(2, 2, 1), delta=1, ppbe_levels=2, rtol=1e-10))
+    s = dict(initial_state(8, 8, 0), first=True)
+    its = []
+    for _ in range(3):
+        s, info = st.step(s)
+        assert info['ppbe'].converged
+        its.append(info['ppbe'].iters)
+    assert max(its) <= 2 * min(its) + 2
