@@ -100,6 +100,26 @@ fv_status fv_system_size(const fv_system* s, long long* n);
  * x, y: device FP64, n values each, must not overlap. */
 fv_status fv_apply_op(const fv_system* s, const double* x, double* y, void* stream);
 
+/* y = A x like fv_apply_op, for callers that must not allocate device memory
+ * while they run -- for instance code whose device memory is owned by a
+ * framework's pool allocator (a cudaMalloc behind its back would bypass the
+ * pool and its accounting), or a solver loop that cannot afford the implicit
+ * device synchronisation that cudaMalloc/cudaFree may cause.  This call
+ * allocates nothing: its scratch (the panel-edge ghost layer, d x 24 x Nr x
+ * (Ns + 2) doubles) lives in one file-scope static device array of
+ * FV_STATIC_GHOST_DOUBLES doubles (8 MiB) that every GPU loading the library
+ * holds until the process exits.  Systems whose ghost layer is larger (e.g.
+ * VTBE beyond Ns = Nr = 64, PPBE beyond Ns = Nr = 128) are rejected with
+ * FV_EINVAL.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the array: calls whose kernels
+ * overlap on the GPU (e.g. on two streams at once) race on it; serialise them.
+ * The array keeps the last call's contents, and each call overwrites every
+ * slot it reads.  The paper has no counterpart: this is a deployment
+ * variant of the operator apply above. */
+#define FV_STATIC_GHOST_DOUBLES (1 << 20)
+fv_status fv_apply_op_noalloc(const fv_system* s, const double* x, double* y, void* stream);
+
 /* z = M^{-1} r (eqn:onelevel or eqn:twolevel per the system's pc).
  * r, z: device FP64, n values each, must not overlap. */
 fv_status fv_precond_apply(const fv_system* s, const double* r, double* z, void* stream);

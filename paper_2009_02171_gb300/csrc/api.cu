@@ -120,6 +120,11 @@ fv_status fv_apply_op(const fv_system* s, const double* x, double* y, void* stre
   return apply_op(s, x, y, (cudaStream_t)stream);
 }
 
+fv_status fv_apply_op_noalloc(const fv_system* s, const double* x, double* y, void* stream) {
+  if (!s || !x || !y || x == y) return set_error("fv_apply_op_noalloc: bad argument"), FV_EINVAL;
+  return apply_op_noalloc(s, x, y, (cudaStream_t)stream);
+}
+
 fv_status fv_precond_apply(const fv_system* s, const double* r, double* z, void* stream) {
   if (!s || !r || !z || r == z) return set_error("fv_precond_apply: bad argument"), FV_EINVAL;
   s->last_inner = 0;

@@ -138,6 +138,7 @@ void free_grid(fv_grid* g);
 
 // ops.cu
 fv_status apply_op(const fv_system* s, const double* x, double* y, cudaStream_t st);
+fv_status apply_op_noalloc(const fv_system* s, const double* x, double* y, cudaStream_t st);
 fv_status fill_ghosts(const fv_system* s, const double* x, cudaStream_t st);
 fv_status ghost_fill(const Geo& G, const double* x, double* gh, int d, cudaStream_t st);
 fv_status assemble_subdomains(fv_system* s);

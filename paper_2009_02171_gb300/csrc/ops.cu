@@ -1,6 +1,7 @@
 // Operator kernels: panel-edge ghost layer, matrix-free VTBE / PPBE apply,
 // and extraction of the structured subdomain matrices for ILU(0).
 #include <cstdio>
+#include <string>
 
 #include "stencil.cuh"
 
@@ -102,6 +103,47 @@ fv_status apply_op(const fv_system* s, const double* x, double* y, cudaStream_t 
     apply_kernel<FV_VTBE><<<grid_blocks(n, 256), 256, 0, st>>>(G, ph, x, s->ghost, y, s->d);
   else
     apply_kernel<FV_PPBE><<<grid_blocks(n, 256), 256, 0, st>>>(G, ph, x, s->ghost, y, s->d);
+  FV_CUDA(cudaGetLastError());
+  return FV_OK;
+}
+
+// ---------------------------------------------------------------- apply without allocation
+// Ghost layer of fv_apply_op_noalloc: one static array per device, shared by all calls.
+static __device__ __align__(256) double g_static_ghost[FV_STATIC_GHOST_DOUBLES];
+
+static const int kMaxDevices = 64;
+static double* g_static_ghost_addr[kMaxDevices] = {};  // device address per device, looked up once
+
+static fv_status static_ghost_address(double** out) {
+  int dev = 0;
+  FV_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return set_error("fv_apply_op_noalloc: device ordinal out of range"), FV_EINVAL;
+  if (!g_static_ghost_addr[dev]) {
+    void* p = nullptr;
+    FV_CUDA(cudaGetSymbolAddress(&p, g_static_ghost));
+    g_static_ghost_addr[dev] = static_cast<double*>(p);
+  }
+  *out = g_static_ghost_addr[dev];
+  return FV_OK;
+}
+
+fv_status apply_op_noalloc(const fv_system* s, const double* x, double* y, cudaStream_t st) {
+  const Geo& G = s->grid->geo;
+  const long long total = (long long)s->d * 6 * 4 * G.Nr * (G.Ns + 2);
+  if (total > FV_STATIC_GHOST_DOUBLES)
+    return set_error("fv_apply_op_noalloc: ghost layer of this system (" + std::to_string(total) +
+                     " doubles) exceeds FV_STATIC_GHOST_DOUBLES"),
+           FV_EINVAL;
+  double* gh = nullptr;
+  fv_status rc = static_ghost_address(&gh);
+  if (rc) return rc;
+  ghost_kernel<double><<<grid_blocks(total, 256), 256, 0, st>>>(G, x, gh, s->d);
+  FV_CUDA(cudaGetLastError());
+  Phys ph{s->phys.E, s->phys.Ra, s->phys.Pr, s->phys.Pm, s->phys.dt};
+  if (s->kind == FV_VTBE)
+    apply_kernel<FV_VTBE><<<grid_blocks(s->n, 256), 256, 0, st>>>(G, ph, x, gh, y, s->d);
+  else
+    apply_kernel<FV_PPBE><<<grid_blocks(s->n, 256), 256, 0, st>>>(G, ph, x, gh, y, s->d);
   FV_CUDA(cudaGetLastError());
   return FV_OK;
 }

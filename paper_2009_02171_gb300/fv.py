@@ -58,6 +58,7 @@ SIGNATURES = {
     'fv_free_system': [_VP],
     'fv_system_size': [_VP, _P(ctypes.c_longlong)],
     'fv_apply_op': [_VP, _DP, _DP, _VP],
+    'fv_apply_op_noalloc': [_VP, _DP, _DP, _VP],
     'fv_precond_apply': [_VP, _DP, _DP, _VP],
     'fv_gmres_solve': [_VP, _DP, _DP, _P(fv_gmres_opts), _P(fv_solve_stats), _VP],
     'fv_state_create': [_VP, _P(fv_phys), _DP, _P(_VP)],
@@ -127,6 +128,13 @@ def fv_system_size(system):
 def fv_apply_op(system, x, y):
     n = fv_system_size(system)
     _check(lib.fv_apply_op(system, _ptr(x, n), _ptr(y, n), _stream()))
+    return y
+
+
+def fv_apply_op_noalloc(system, x, y):
+    """y = A x with the ghost layer in the library's static device array (no allocation)."""
+    n = fv_system_size(system)
+    _check(lib.fv_apply_op_noalloc(system, _ptr(x, n), _ptr(y, n), _stream()))
     return y
 
 
