@@ -29,9 +29,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 CFG = dict(Ns=64, Nr=64, p=(2, 2, 4), overlap=2, overlap_coarse=1, levels=2, E=1e-3, Ra=100.0, Pr=1.0, Pm=5.0,
-           dt=1e-4, rtol=1e-8, restart=30, seed=1)
-WORKLOAD = ('shell 6x64^2x64 (1.57M cells), FP64 time step: VTBE one-level RAS + PPBE two-level RAS, '
-            '96 subdomains overlap 2, FGMRES(30) to 1e-8 relative residual')
+           dt=1e-4, rtol=1e-8, restart=30, seed=1, inner_rtol=1e-3, inner_restart=30, inner_maxit=30)
+WORKLOAD = ('shell 6x64^2x64 (1.57M cells), time step: VTBE one-level RAS + PPBE two-level RAS, '
+            '96 subdomains overlap 2, FGMRES(30) to 1e-8 relative FP64 residual; mixed precision = FP32 inner '
+            'FGMRES (operator, ILU(0) sweeps, coarse level) inside FP64 outer FGMRES')
 METRIC = 'wall time per time step at 1e-8 residual'
 # oracle sample: the same step on 6 x 32^2 x 32 (1/8 of the cells), scaled by the cell ratio
 ORACLE_NS = 32
@@ -44,6 +45,9 @@ def parse():
     ap.add_argument('--warmup', type=int, default=3)
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
     ap.add_argument('--no-cpu-baseline', action='store_true')
+    ap.add_argument('--precision', default='mixed', choices=['mixed', 'fp64'],
+                    help='headline arm; the other one is timed beside it with the same steps')
+    ap.add_argument('--single', action='store_true', help='time the headline arm only (profiling runs)')
     return ap.parse_args()
 
 
@@ -151,38 +155,67 @@ def main():
 
     c = CFG
     ph = dict(E=c['E'], Ra=c['Ra'], Pr=c['Pr'], Pm=c['Pm'], dt=c['dt'])
-    t_setup = time.perf_counter()
-    g = fv.fv_build_grid(c['Ns'], c['Nr'])
-    V = fv.fv_assemble_system(g, fv.FV_VTBE, **ph, p=c['p'], overlap=c['overlap'], levels=1)
-    P = fv.fv_assemble_system(g, fv.FV_PPBE, **ph, p=c['p'], overlap=c['overlap'], levels=c['levels'],
-                              overlap_coarse=c['overlap_coarse'])
     s0 = initial_state(c['Ns'], c['Nr'], c['seed'] + rank)
     host = np.concatenate([s0['u'].ravel(), s0['T'], s0['B'].ravel(), s0['P'], s0['Pb']])
     N = host.size // 9
-    st = fv.fv_state_create(g, torch.tensor(host, device='cuda'), **ph)
-    torch.cuda.synchronize()
-    t_setup = time.perf_counter() - t_setup
     opts = dict(restart=c['restart'], rtol=c['rtol'])
-
-    for _ in range(args.warmup):
-        fv.fv_time_step(st, V, P, 1, **opts)
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    iters = []
-    with ClockSampler(local) as clk:
-        if ws > 1:
-            dist.barrier()
+
+    def build(mixed):
+        t = time.perf_counter()
+        mp = dict(precision=fv.FV_PREC_FP32, inner_rtol=c['inner_rtol'], inner_restart=c['inner_restart'],
+                  inner_maxit=c['inner_maxit']) if mixed else {}
+        g = fv.fv_build_grid(c['Ns'], c['Nr'])
+        V = fv.fv_assemble_system(g, fv.FV_VTBE, **ph, p=c['p'], overlap=c['overlap'], levels=1, **mp)
+        P = fv.fv_assemble_system(g, fv.FV_PPBE, **ph, p=c['p'], overlap=c['overlap'], levels=c['levels'],
+                                  overlap_coarse=c['overlap_coarse'], **mp)
+        st = fv.fv_state_create(g, torch.tensor(host, device='cuda'), **ph)
         torch.cuda.synchronize()
-        fv.fv_profile_enable(True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            s = fv.fv_time_step(st, V, P, 1, **opts)
-            iters.append((s[0].iters, s[1].iters, s[1].inner_iters))
-        e1.record(stream)
-        torch.cuda.synchronize()
+        return (g, V, P, st), time.perf_counter() - t
+
+    def free(h):
+        g, V, P, st = h
+        for x, f in ((st, fv.fv_free_state), (V, fv.fv_free_system), (P, fv.fv_free_system), (g, fv.fv_free_grid)):
+            f(x)
+
+    def timed(h, steps, warmup, profile):
+        g, V, P, st = h
+        for _ in range(warmup):
+            fv.fv_time_step(st, V, P, 1, **opts)
+        iters = []
+        with ClockSampler(local) as clk:
+            if ws > 1:
+                dist.barrier()
+            torch.cuda.synchronize()
+            if profile:
+                fv.fv_profile_enable(True)
+            e0.record(stream)
+            for _ in range(steps):
+                s = fv.fv_time_step(st, V, P, 1, **opts)
+                iters.append((s[0].iters, s[1].iters, s[0].inner_iters, s[1].inner_iters))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if ws > 1:
+                dist.barrier()
+        ms = e0.elapsed_time(e1) / steps
         if ws > 1:
-            dist.barrier()
-    ms = e0.elapsed_time(e1) / args.steps
+            t = torch.tensor([ms], device='cuda')
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, iters, clk.summary()
+
+    mixed = args.precision == 'mixed'
+    # the other arm first (same steps), then the headline arm with kernel timing
+    if args.single:
+        ms_other, it_other, t_other = float('nan'), [], 0.0
+    else:
+        other, t_other = build(not mixed)
+        ms_other, it_other, _ = timed(other, args.steps, args.warmup, False)
+        free(other)
+    h, t_setup = build(mixed)
+    g, V, P, st = h
+    ms, iters, clocks = timed(h, args.steps, args.warmup, True)
     kern = {}
     names = ['ghost', 'apply_vtbe', 'apply_ppbe', 'ras_fwd', 'ras_bwd', 'cgs', 'vec', 'glue', 'transfer',
              'phase_pc_c', 'phase_pc_f', 'phase_pc_i']
@@ -194,10 +227,6 @@ def main():
             if n:
                 kern[nm + suffix] = {'launches': n, 'ms_total': round(t, 3), 'ms_per_step': round(t / args.steps, 3)}
     fv.fv_profile_enable(False)
-    if ws > 1:
-        t = torch.tensor([ms], device='cuda')
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
 
     # end to end through the C ABI: state host -> device, step, device -> host
     hbuf = torch.empty(9 * N, dtype=torch.float64).pin_memory()
@@ -228,16 +257,19 @@ def main():
         os.path.join(ROOT, 'MEASURED_PEAKS.json')) else {}
     hbm = peaks.get('hbm_gbs', 6800.0)
     ranked = sorted((v['ms_total'], k) for k, v in kern.items() if not k.startswith('phase'))
-    top = ranked[-1][1] if ranked else None
     roof = None
-    if top:
-        bytes_per = algorithmic_bytes(top, c, N)
+    for _, top in reversed(ranked):
+        bytes_per = algorithmic_bytes(top, c, N, 4 if mixed else 8)
         if bytes_per:
             per_launch_ms = kern[top]['ms_total'] / kern[top]['launches']
             ach = bytes_per / (per_launch_ms * 1e-3) / 1e9
             roof = {'kernel': top, 'bound': 'hbm', 'achieved': round(ach, 1), 'peak': hbm, 'unit': 'GB/s',
                     'frac': round(ach / hbm, 4), 'traffic': None, 'bytes_per_launch': bytes_per,
-                    'ms_per_launch': round(per_launch_ms, 4), 'peak_source': 'MEASURED_PEAKS.json hbm_gbs'}
+                    'ms_per_launch': round(per_launch_ms, 4), 'share_of_step': round(kern[top]['ms_total'] /
+                                                                                      (ms * args.steps), 3),
+                    'peak_source': 'MEASURED_PEAKS.json hbm_gbs (of measured)',
+                    'top_kernel': ranked[-1][1]}
+            break
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -248,31 +280,63 @@ def main():
         print(json.dumps({
             'metric': METRIC, 'value': round(ms, 3), 'unit': 'ms/step', 'n_gpus': ws, 'steps': args.steps,
             'warmup': args.warmup, 'ms_per_step': round(ms, 3), 'higher_is_better': False, 'scaling': 'weak',
-            'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic',
+            'vs_baseline': None, 'dtype': 'f32 inner / f64 outer' if mixed else 'f64', 'data': 'synthetic',
+            'precision': args.precision,
+            ('fp64' if mixed else 'mixed'): {'ms_per_step': round(ms_other, 3),
+                                             'iterations_vtbe_ppbe': [(i[0], i[1]) for i in it_other],
+                                             'setup_s': round(t_other, 2)},
             'config': {'workload': WORKLOAD, 'cells': 6 * c['Ns'] ** 2 * c['Nr'], 'subdomains': 6 * 16,
                        'overlap': c['overlap'], 'ppbe_levels': c['levels'], 'rtol': c['rtol'],
                        'restart': c['restart'], 'l2': 'working set > L2 (no flush needed)',
                        'parallelism': 'replicas' if ws > 1 else 'single GPU'},
             'iterations': {'vtbe': [i[0] for i in iters], 'ppbe': [i[1] for i in iters],
-                           'ppbe_inner': [i[2] for i in iters]},
-            'setup_s': round(t_setup, 2), 'clocks': clk.summary(),
+                           'vtbe_inner': [i[2] for i in iters], 'ppbe_inner': [i[3] for i in iters]},
+            'setup_s': round(t_setup, 2), 'clocks': clocks,
             'e2e': {'value': round(ms_e2e, 3), 'unit': 'ms/step', 'h2d_bytes_per_step': 9 * N * 8,
                     'd2h_bytes_per_step': 9 * N * 8},
             'gpu_launches': int(sum(v['launches'] for k, v in kern.items() if not k.startswith('phase'))),
             'kernels': kern, 'roofline': roof, 'cpu_baseline': cpu}))
-    for h, f in ((st, fv.fv_free_state), (V, fv.fv_free_system), (P, fv.fv_free_system), (g, fv.fv_free_grid)):
-        f(h)
+    free(h)
     if ws > 1:
         dist.destroy_process_group()
 
 
-def algorithmic_bytes(cat, c, N):
-    """Algorithmic HBM bytes of one launch (FP64): what the kernel must read and write."""
+def _split(n, parts):
+    return [n // parts + (1 if q < n % parts else 0) for q in range(parts)]
+
+
+def box_cells(Ns, Nr, p, delta):
+    """Cells of all overlapping subdomain boxes (panel boxes extended by delta, radially clipped)."""
+    tot = 0
+    ks = _split(Nr, p[2])
+    k0 = 0
+    for kz in ks:
+        nz = min(Nr, k0 + kz + delta) - max(0, k0 - delta)
+        for sx in _split(Ns, p[0]):
+            for sy in _split(Ns, p[1]):
+                tot += (sx + 2 * delta) * (sy + 2 * delta) * nz
+        k0 += kz
+    return 6 * tot
+
+
+def algorithmic_bytes(cat, c, N, es):
+    """Algorithmic HBM bytes of one launch: what the kernel must read and write (es = element bytes)."""
     d = {'apply_vtbe': 7, 'apply_ppbe': 2}.get(cat)
     if d:
-        return 2 * d * N * 8                        # read x, write y
+        return 2 * d * N * es                       # read x, write y
+    if cat == 'apply_ppbe_coarse':
+        return 2 * 2 * (N // 8) * es
     if cat.startswith('ras_'):
-        return None
+        coarse = cat.endswith('_coarse')
+        # per-launch category: the most frequent system in the category is PPBE (d = 2) for the
+        # coarse level; the fine category mixes VTBE and PPBE launches, so it is not reported
+        if not coarse:
+            return None
+        d = 2
+        cells = box_cells(c['Ns'] // 2, c['Nr'] // 2, c['p'], c['overlap_coarse'])
+        if cat.startswith('ras_fwd'):   # gather (read r, write loc) + L sweep (read loc + factors, write loc)
+            return cells * es * (4 * d + 5 * d + d * (d - 1) // 2)
+        return cells * es * (4 * d + 5 * d + d * (d + 1) // 2)  # U sweep + scatter
     return None
 
 

@@ -85,7 +85,20 @@ typedef struct {
   double coarse_rtol;
   int coarse_restart;
   int coarse_maxit;
+  /* Mixed precision (not in the paper).  precision = FV_PREC_FP64: everything
+   * above runs in FP64.  precision = FV_PREC_FP32: the preconditioner M^{-1}
+   * of the FP64 outer FGMRES is an inner FGMRES(inner_restart) in FP32 (FP32
+   * operator applies, FP32 ILU(0) factors and sweeps, FP32 coarse level) to
+   * relative tolerance inner_rtol, at most inner_maxit iterations; the outer
+   * residual, its Arnoldi dot products and norms and the Hessenberg least
+   * squares stay FP64, so the final residual is a true FP64 residual. */
+  int precision;
+  double inner_rtol;
+  int inner_restart;
+  int inner_maxit;
 } fv_pc_desc;
+#define FV_PREC_FP64 0
+#define FV_PREC_FP32 1
 
 /* Builds the system `kind` (FV_VTBE: A = I - dt/2 [L1 R1; R2 L2; L3];
  * FV_PPBE: A = dt/2 D G for (P Neumann, P_b Dirichlet)), its subdomain

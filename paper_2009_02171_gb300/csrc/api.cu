@@ -28,6 +28,7 @@ static fv_status make_system(const fv_grid* g, int kind, const fv_phys* ph, cons
   s->grid = g, s->kind = kind, s->d = kind == FV_VTBE ? 7 : 2;
   s->n = s->d * g->h.N;
   s->phys = *ph, s->pc = *pc;
+  s->prec32 = pc->precision == FV_PREC_FP32;
   fv_status rc = FV_OK;
   const size_t ng = (size_t)s->d * 6 * 4 * g->h.Nr * (g->h.Ns + 2);
   if (cudaMalloc(&s->ghost, ng * sizeof(double)) != cudaSuccess) {
@@ -35,7 +36,23 @@ static fv_status make_system(const fv_grid* g, int kind, const fv_phys* ph, cons
     return set_error("fv_assemble_system: ghost layer allocation failed"), FV_ENOMEM;
   }
   s->allocs.push_back(s->ghost);
-  if ((rc = build_subdomains(s, g)) || (rc = assemble_subdomains(s)) || (rc = ilu_factor(s))) {
+  if (s->prec32) {
+    if (pc->inner_restart < 1 || pc->inner_restart > 31 || pc->inner_maxit < 1 || !(pc->inner_rtol > 0)) {
+      free_system(s);
+      return set_error("fv_assemble_system: mixed precision needs inner_restart in [1, 31], inner_maxit >= 1, "
+                       "inner_rtol > 0"),
+             FV_EINVAL;
+    }
+    if (cudaMalloc(&s->ghost32, ng * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&s->r32, s->n * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&s->x32, s->n * sizeof(float)) != cudaSuccess) {
+      free_system(s);
+      return set_error("fv_assemble_system: FP32 work allocation failed"), FV_ENOMEM;
+    }
+    s->allocs.insert(s->allocs.end(), {s->ghost32, s->r32, s->x32});
+  }
+  if ((rc = build_subdomains(s, g)) || (rc = assemble_subdomains(s)) || (rc = ilu_factor(s)) ||
+      (rc = prepare_sweeps(s, s->prec32)) || (rc = sweeps_smem_attr(s))) {
     free_system(s);
     return rc;
   }
@@ -69,6 +86,15 @@ static fv_status make_system(const fv_grid* g, int kind, const fv_phys* ph, cons
       return set_error("fv_assemble_system: two-level work allocation failed"), FV_ENOMEM;
     }
     s->allocs.insert(s->allocs.end(), {s->xc, s->ec, s->w, s->t, s->red});
+    if (s->prec32) {
+      if (cudaMalloc(&s->xc32, nc * sizeof(float)) != cudaSuccess ||
+          cudaMalloc(&s->ec32, nc * sizeof(float)) != cudaSuccess ||
+          cudaMalloc(&s->w32, n * sizeof(float)) != cudaSuccess || cudaMalloc(&s->t32, n * sizeof(float)) != cudaSuccess) {
+        free_system(s);
+        return set_error("fv_assemble_system: FP32 two-level work allocation failed"), FV_ENOMEM;
+      }
+      s->allocs.insert(s->allocs.end(), {s->xc32, s->ec32, s->w32, s->t32});
+    }
   }
   FV_CUDA(cudaDeviceSynchronize());
   *out = s;

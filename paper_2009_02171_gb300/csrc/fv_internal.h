@@ -17,33 +17,41 @@ enum { WALL_ODD = 0, WALL_EVEN = 1, WALL_B = 2 };
 // Device-side geometry of one grid level, passed by value to kernels.
 // Angular tables are shared by the 6 panels (identical local coordinates);
 // Cartesian vectors are stored in the panel-local frame (1, X, Y) and rotated
-// by the panel's signed-permutation matrix in the kernels.
-struct Geo {
+// by the panel's signed-permutation matrix in the kernels.  R is the type of
+// the coefficient tables and of the coefficient arithmetic: double for the
+// FP64 path, float for the FP32 inner solves of mixed precision.
+template <class R>
+struct GeoT {
+  using real = R;
   int Ns, Nr;
   long long N;                 // 6 Ns^2 Nr
-  double hs, hr, ri, ro;
-  double wall_in, wall_out;    // 1 + (r_c/r_g)^2 at the inner / outer wall
-  const double* ax11;          // [j][if]  a11 * h_r            (xi faces, Ns x (Ns+1))
-  const double* ax12;          // [j][if]  a12 * h_r / 4
-  const double* ay22;          // [jf][i]  a22 * h_r            (eta faces, (Ns+1) x Ns)
-  const double* ay12;          // [jf][i]  a12 * h_r / 4
-  const double* crf;           // [j][i]   sigma h_s^2 / h_r    (radial faces, times r_f^2)
-  const double* rf2;           // [kf]     r_f^2
-  const double* invsig;        // [j][i]   1 / sigma
-  const double* invr2;         // [k]      1 / (r_k^2 h_s^2 h_r)
-  const double* rc;            // [k]      r_k
-  const double* xhat;          // [j][i][3] unit position vector, local frame
-  const double* sx;            // [j][if][3] (a11 e1 + a12 e2) h_s h_r, local frame (times r_k)
-  const double* sy;            // [jf][i][3] (a12 e1 + a22 e2) h_s h_r
-  const double* sr;            // [j][i][3]  sigma h_s^2 xhat     (times r_f^2)
+  R hs, hr, ri, ro;
+  R wall_in, wall_out;         // 1 + (r_c/r_g)^2 at the inner / outer wall
+  const R* ax11;               // [j][if]  a11 * h_r            (xi faces, Ns x (Ns+1))
+  const R* ax12;               // [j][if]  a12 * h_r / 4
+  const R* ay22;               // [jf][i]  a22 * h_r            (eta faces, (Ns+1) x Ns)
+  const R* ay12;               // [jf][i]  a12 * h_r / 4
+  const R* crf;                // [j][i]   sigma h_s^2 / h_r    (radial faces, times r_f^2)
+  const R* rf2;                // [kf]     r_f^2
+  const R* invsig;             // [j][i]   1 / sigma
+  const R* invr2;              // [k]      1 / (r_k^2 h_s^2 h_r)
+  const R* rc;                 // [k]      r_k
+  const R* xhat;               // [j][i][3] unit position vector, local frame
+  const R* sx;                 // [j][if][3] (a11 e1 + a12 e2) h_s h_r, local frame (times r_k)
+  const R* sy;                 // [jf][i][3] (a12 e1 + a22 e2) h_s h_r
+  const R* sr;                 // [j][i][3]  sigma h_s^2 xhat     (times r_f^2)
   const int* gq;               // [p][side][t]      panel holding the ghost's source line
   const int* gsrc;             // [p][side][t][3]   source cells (j*Ns + i) on that panel
-  const double* gw;            // [p][side][t][3]   quadratic Lagrange weights
+  const R* gw;                 // [p][side][t][3]   quadratic Lagrange weights
   const int* pq;               // [p][side]  neighbour panel across the side
   const int* psq;              // [p][side]  its side
   const int* psgn;             // [p][side]  F_p = psgn F_q for the shared face
   const int* ptmap;            // [p][side][t] tangential index on the neighbour side
+  const GeoT* self;            // device copy of this struct (out-of-line device code reads it
+                               // through this pointer so kernels never take a parameter's address)
 };
+using Geo = GeoT<double>;
+using GeoF = GeoT<float>;
 
 struct GridHost {
   int Ns, Nr;
@@ -60,7 +68,8 @@ struct Krylov;
 
 struct fv_grid {
   fv::GridHost h;
-  fv::Geo geo;                 // device pointers
+  fv::Geo geo;                 // device pointers (FP64 tables)
+  fv::GeoF geof;               // the same tables in FP32 (mixed-precision inner solves)
   std::vector<void*> allocs;   // device allocations owned by the grid
   fv_grid* coarse = nullptr;   // (Ns/2, Nr/2) grid, built on demand
 };
@@ -82,9 +91,21 @@ struct Subdomains {
   int* order = nullptr;           // [total_cells] local cells sorted by level (i + 2 j + k)
   double* off = nullptr;          // [total_cells][11][d] structured coefficients (slot 5 unused)
   double* diag = nullptr;         // [total_cells][d][d] diagonal blocks (LU in place)
-  double* work = nullptr;         // [total_cells][d] sweep vector
   int* status = nullptr;          // [1] 0 ok, else 1 + first zero-pivot cell
   int* lpt = nullptr;             // [count] subdomains in decreasing size (processing order)
+  // sweep layout (built after factorization): per subdomain, cells in wavefront
+  // order (level i + 2j + k, then j, then i), structure of arrays
+  int* perm = nullptr;            // [total_cells] natural local index -> packed position (setup only)
+  long long* gmap_p = nullptr;    // [total_cells] packed: global cell or -1
+  unsigned char* owned_p = nullptr;
+  void* F = nullptr;              // [cell_off * Q + q * ncell + pos], Q = 10 d + d^2, element type per `fp32`
+  void* loc = nullptr;            // [cell_off * d + a * ncell + pos] sweep vector
+  void* ring = nullptr;           // global 4-plane ring per CTA when it does not fit in shared memory
+  int fp32 = 0;                   // 1: factors and sweeps in FP32
+  int max_cols = 0;               // max nx * ny
+  int threads = 0;                // CTA size of the sweeps
+  size_t smem = 0;                // dynamic shared memory of the sweeps
+  int ring_in_smem = 0;
 };
 
 }  // namespace fv
@@ -104,6 +125,11 @@ struct fv_system {
   double* w = nullptr;         // fine prolongated correction / temps
   double* t = nullptr;
   double* red = nullptr;       // [32 * 304 + 32] reduction scratch (coarse mean projection)
+  // mixed precision (pc.precision == FV_PREC_FP32)
+  int prec32 = 0;
+  float* ghost32 = nullptr;    // FP32 ghost layer
+  float *r32 = nullptr, *x32 = nullptr;                  // inner solve right-hand side / solution
+  float *xc32 = nullptr, *ec32 = nullptr, *w32 = nullptr, *t32 = nullptr;  // FP32 two-level work
   // FGMRES workspace for this system (outer) sized lazily
   fv::Krylov* kry = nullptr;
   mutable int last_inner = 0;
@@ -138,6 +164,7 @@ void free_grid(fv_grid* g);
 
 // ops.cu
 fv_status apply_op(const fv_system* s, const double* x, double* y, cudaStream_t st);
+fv_status apply_op32(const fv_system* s, const float* x, float* y, cudaStream_t st);
 fv_status apply_op_noalloc(const fv_system* s, const double* x, double* y, cudaStream_t st);
 fv_status fill_ghosts(const fv_system* s, const double* x, cudaStream_t st);
 fv_status ghost_fill(const Geo& G, const double* x, double* gh, int d, cudaStream_t st);
@@ -152,7 +179,10 @@ fv_status cell_gradient(const fv_grid* g, const double* x, int wall, double scal
 // precond.cu
 fv_status build_subdomains(fv_system* s, const fv_grid* g);
 fv_status ilu_factor(fv_system* s);
+fv_status prepare_sweeps(fv_system* s, int fp32);
+fv_status sweeps_smem_attr(const fv_system* s);
 fv_status precond_apply(const fv_system* s, const double* r, double* z, cudaStream_t st);
+fv_status precond_apply32(const fv_system* s, const float* r, float* z, cudaStream_t st);
 fv_status ras_apply(const fv_system* s, const double* r, double* z, cudaStream_t st);
 fv_status restrict_mean(const fv_grid* g, int d, const double* x, double* xc, cudaStream_t st);
 fv_status prolong_inject(const fv_grid* g, int d, const double* xc, double* x, cudaStream_t st);
@@ -162,6 +192,12 @@ fv_status gmres(const fv_system* s, const double* b, double* x, const fv_gmres_o
                 cudaStream_t st, bool inner);
 void free_krylov(Krylov* k);
 fv_status axpby(long long n, double a, const double* x, double b, const double* y, double* out, cudaStream_t st);
+fv_status axpby32(long long n, double a, const float* x, double b, const float* y, float* out, cudaStream_t st);
+fv_status to_fp32(long long n, const double* x, float* out, cudaStream_t st);
+fv_status to_fp64(long long n, const float* x, double* out, cudaStream_t st);
+fv_status gmres32(const fv_system* s, const float* b, float* x, const fv_gmres_opts* o, fv_solve_stats* stats,
+                  cudaStream_t st);
+fv_status weighted_mean_remove32(const fv_grid* g, float* x, cudaStream_t st, double* part, double* sums);
 fv_status weighted_mean_remove(const fv_grid* g, double* x, cudaStream_t st, double* part, double* sums);
 
 }  // namespace fv

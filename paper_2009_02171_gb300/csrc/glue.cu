@@ -28,7 +28,7 @@ struct Field {
 // (cells i-1, i of row j); type 1: eta face f = j (rows j-1, j of column i);
 // type 2: radial face kf = k (levels k-1, k).
 __device__ __noinline__ double face_val(const Geo& G, const Field& F, int c, int p, int type, int k, int j, int i) {
-  ApplyAcc<double> acc{&G, F.x, F.gh, 0.0};
+  ApplyAcc<double> acc(G, F.x, F.gh);
   if (type == 0) {
     emit_h(G, acc, 0.5, p, k, j, i - 1, c);
     emit_h(G, acc, 0.5, p, k, j, i, c);
@@ -106,17 +106,14 @@ __device__ __noinline__ void edge_face_flux(const Geo& G, const Field& F, double
   for (int m = 0; m < NO; ++m) out[m] = 0.5 * (a[m] + sg * b[m]);
 }
 
+// grid: x = tiles of the (j, i) plane, y = k, z = panel
 template <int MODE, int NO>
 __global__ void face_kernel(Geo G, Field F, double cL, double scale, double* __restrict__ out) {
   const int Ns = G.Ns;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < G.N; e += (long long)gridDim.x * blockDim.x) {
-    long long c = e;
-    const int i = (int)(c % Ns);
-    c /= Ns;
-    const int j = (int)(c % Ns);
-    c /= Ns;
-    const int k = (int)(c % G.Nr);
-    const int p = (int)(c / G.Nr);
+  const int ij = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ij < Ns * Ns) {
+    const int i = ij % Ns, j = ij / Ns, k = blockIdx.y, p = blockIdx.z;
+    const long long e = ((long long)(p * G.Nr + k) * Ns + j) * Ns + i;
     double acc[NO], fl[7];
     for (int m = 0; m < NO; ++m) acc[m] = 0.0;
     // xi faces
@@ -143,10 +140,7 @@ __global__ void face_kernel(Geo G, Field F, double cL, double scale, double* __r
   }
 }
 
-static int fblocks(long long n) {
-  long long b = (n + 127) / 128;
-  return (int)(b < 152LL * 32 ? (b < 1 ? 1 : b) : 152LL * 32);
-}
+static dim3 face_grid(const Geo& G) { return dim3((G.Ns * G.Ns + 127) / 128, G.Nr, 6); }
 
 // 7-component field (u, Theta, B): odd walls for u and Theta, pseudo-vacuum for B
 static Field field7(const double* x, const double* gh) {
@@ -157,14 +151,14 @@ static Field field7(const double* x, const double* gh) {
 fv_status nonlinear_terms(const fv_grid* g, const fv_phys& ph, const double* x7, double* f, double* gh7,
                           cudaStream_t st) {
   ProfScope ps(FV_K_GLUE, st);
-  face_kernel<MODE_NL, 7><<<fblocks(g->geo.N), 128, 0, st>>>(g->geo, field7(x7, gh7), 1.0 / (ph.E * ph.Pm), 1.0, f);
+  face_kernel<MODE_NL, 7><<<face_grid(g->geo), 128, 0, st>>>(g->geo, field7(x7, gh7), 1.0 / (ph.E * ph.Pm), 1.0, f);
   FV_CUDA(cudaGetLastError());
   return FV_OK;
 }
 
 fv_status face_divergence_uB(const fv_grid* g, const double* x7, double* bP, double* gh7, cudaStream_t st) {
   ProfScope ps(FV_K_GLUE, st);
-  face_kernel<MODE_DIV, 2><<<fblocks(g->geo.N), 128, 0, st>>>(g->geo, field7(x7, gh7), 0.0, 1.0, bP);
+  face_kernel<MODE_DIV, 2><<<face_grid(g->geo), 128, 0, st>>>(g->geo, field7(x7, gh7), 0.0, 1.0, bP);
   FV_CUDA(cudaGetLastError());
   return FV_OK;
 }
@@ -174,7 +168,7 @@ fv_status cell_gradient(const fv_grid* g, const double* x2, int /*wall*/, double
                         cudaStream_t st) {
   Field F{x2, gh2, {WALL_EVEN, WALL_ODD, 0, 0, 0, 0, 0}, 0};
   ProfScope ps(FV_K_GLUE, st);
-  face_kernel<MODE_GRAD, 6><<<fblocks(g->geo.N), 128, 0, st>>>(g->geo, F, 0.0, scale, out6);
+  face_kernel<MODE_GRAD, 6><<<face_grid(g->geo), 128, 0, st>>>(g->geo, F, 0.0, scale, out6);
   FV_CUDA(cudaGetLastError());
   return FV_OK;
 }

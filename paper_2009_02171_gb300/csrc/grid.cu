@@ -221,6 +221,35 @@ fv_status build_grid(const fv_grid_desc* desc, fv_grid** out) {
             (G.sr = upload(g, sr)) && (G.gq = upload(g, h.gq)) && (G.gsrc = upload(g, h.gsrc)) &&
             (G.gw = upload(g, h.gw)) && (G.pq = upload(g, h.pq)) && (G.psq = upload(g, h.psq)) &&
             (G.psgn = upload(g, h.psgn)) && (G.ptmap = upload(g, h.ptmap));
+  if (ok) {
+    Geo* dself = nullptr;
+    if (cudaMalloc(&dself, sizeof(Geo)) != cudaSuccess) ok = false;
+    else {
+      g->allocs.push_back(dself);
+      G.self = dself;
+      ok = cudaMemcpy(dself, &G, sizeof(Geo), cudaMemcpyHostToDevice) == cudaSuccess;
+    }
+  }
+  // FP32 copy of the tables for the mixed-precision inner solves
+  auto f32 = [](const std::vector<double>& v) { return std::vector<float>(v.begin(), v.end()); };
+  GeoF& F = g->geof;
+  F.Ns = Ns, F.Nr = Nr, F.N = h.N, F.hs = (float)hs, F.hr = (float)hr, F.ri = (float)h.ri, F.ro = (float)h.ro;
+  F.wall_in = (float)G.wall_in, F.wall_out = (float)G.wall_out;
+  F.gq = G.gq, F.gsrc = G.gsrc, F.pq = G.pq, F.psq = G.psq, F.psgn = G.psgn, F.ptmap = G.ptmap;
+  ok = ok && (F.ax11 = upload(g, f32(ax11))) && (F.ax12 = upload(g, f32(ax12))) && (F.ay22 = upload(g, f32(ay22))) &&
+       (F.ay12 = upload(g, f32(ay12))) && (F.crf = upload(g, f32(crf))) && (F.rf2 = upload(g, f32(rf2))) &&
+       (F.invsig = upload(g, f32(invsig))) && (F.invr2 = upload(g, f32(invr2))) && (F.rc = upload(g, f32(rc))) &&
+       (F.xhat = upload(g, f32(xhat))) && (F.sx = upload(g, f32(sx))) && (F.sy = upload(g, f32(sy))) &&
+       (F.sr = upload(g, f32(sr))) && (F.gw = upload(g, f32(h.gw)));
+  if (ok) {
+    GeoF* dself = nullptr;
+    if (cudaMalloc(&dself, sizeof(GeoF)) != cudaSuccess) ok = false;
+    else {
+      g->allocs.push_back(dself);
+      F.self = dself;
+      ok = cudaMemcpy(dself, &F, sizeof(GeoF), cudaMemcpyHostToDevice) == cudaSuccess;
+    }
+  }
   if (!ok) {
     free_grid(g);
     return set_error("fv_build_grid: device allocation of geometry tables failed"), FV_ENOMEM;

@@ -4,15 +4,22 @@
 // the preconditioned system is the true residual b - A x; stop when
 // ||b - A x|| <= max(eps_a, eps_r ||b - A x_0||).  The flexible form stores
 // Z_j = M^{-1} v_j and updates x = x_0 + Z y, which allows the variable
-// two-level preconditioner (inner GMRES on the coarse mesh).  Arnoldi uses
-// classical Gram-Schmidt applied twice (CGS2): each pass is one fused sweep
-// over the basis (multi-dot, then update-and-dot, then update-and-norm), with
-// deterministic two-stage reductions (per-block partials summed in a fixed
-// order).  Hessenberg, Givens rotations and the small least-squares solve
-// run on the host in FP64; vectors never leave the device.
+// two-level preconditioner (inner GMRES on the coarse mesh) and, in mixed
+// precision, an FP32 inner solve as preconditioner of the FP64 outer solve.
+// Arnoldi uses classical Gram-Schmidt applied twice (CGS2): each pass is one
+// fused sweep over the basis (multi-dot, then update-and-dot, then
+// update-and-norm), with deterministic two-stage reductions (per-block
+// partials in FP64 summed in a fixed order).  Hessenberg, Givens rotations and
+// the small least-squares solve run on the host in FP64.
+//
+// The vector type T is double (FP64 path, outer solve of mixed precision) or
+// float (inner solves of mixed precision).  For float vectors each thread sums
+// at most 32 products in FP32 before adding them into its FP64 accumulators;
+// block and grid reductions are FP64.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <utility>
 #include <vector>
 
 #include "fv_internal.h"
@@ -23,38 +30,57 @@ constexpr int KMAX = 32;     // max basis vectors in one fused pass
 constexpr int RBLOCKS = 304; // reduction blocks (2 per SM)
 constexpr int RTHREADS = 256;
 
-struct Krylov {
+template <class T>
+struct KrylovT {
   int m = 0;
   long long n = 0;
-  double *V = nullptr, *Z = nullptr, *w = nullptr, *r = nullptr;
-  double* part = nullptr;  // [KMAX][RBLOCKS]
-  double* h = nullptr;     // [3][KMAX]: h1, h2, nrm2
-  double* hhost = nullptr; // pinned [3][KMAX]
+  T *V = nullptr, *Z = nullptr, *w = nullptr, *r = nullptr;
+  double* part = nullptr;   // [KMAX][RBLOCKS]
+  double* h = nullptr;      // [3][KMAX]: h1, h2, nrm2
+  double* hhost = nullptr;  // pinned [3][KMAX]
 };
+
+struct Krylov {
+  KrylovT<double> d;
+  KrylovT<float> f;
+};
+
+template <class T>
+static void free_kt(KrylovT<T>& k) {
+  cudaFree(k.V), cudaFree(k.Z), cudaFree(k.w), cudaFree(k.r), cudaFree(k.part), cudaFree(k.h);
+  cudaFreeHost(k.hhost);
+  k = KrylovT<T>();
+}
 
 void free_krylov(Krylov* k) {
   if (!k) return;
-  cudaFree(k->V), cudaFree(k->Z), cudaFree(k->w), cudaFree(k->r), cudaFree(k->part), cudaFree(k->h);
-  cudaFreeHost(k->hhost);
+  free_kt(k->d);
+  free_kt(k->f);
   delete k;
 }
 
+template <class T>
+static KrylovT<T>& kt(Krylov* k);
+template <>
+KrylovT<double>& kt<double>(Krylov* k) { return k->d; }
+template <>
+KrylovT<float>& kt<float>(Krylov* k) { return k->f; }
+
+template <class T>
 static fv_status ensure_krylov(const fv_system* s, int m) {
-  Krylov* k = s->kry;
-  if (k && k->m >= m && k->n == s->n) return FV_OK;
-  free_krylov(k);
-  k = new Krylov();
-  const_cast<fv_system*>(s)->kry = k;
-  k->m = m, k->n = s->n;
+  fv_system* sm = const_cast<fv_system*>(s);
+  if (!sm->kry) sm->kry = new Krylov();
+  KrylovT<T>& k = kt<T>(sm->kry);
+  if (k.m >= m && k.n == s->n) return FV_OK;
+  free_kt(k);
+  k.m = m, k.n = s->n;
   const size_t n = (size_t)s->n;
-  if (cudaMalloc(&k->V, (m + 1) * n * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&k->Z, m * n * sizeof(double)) != cudaSuccess || cudaMalloc(&k->w, n * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&k->r, n * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&k->part, KMAX * RBLOCKS * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&k->h, 3 * KMAX * sizeof(double)) != cudaSuccess ||
-      cudaMallocHost(&k->hhost, 3 * KMAX * sizeof(double)) != cudaSuccess) {
-    free_krylov(k);
-    const_cast<fv_system*>(s)->kry = nullptr;
+  if (cudaMalloc(&k.V, (m + 1) * n * sizeof(T)) != cudaSuccess || cudaMalloc(&k.Z, m * n * sizeof(T)) != cudaSuccess ||
+      cudaMalloc(&k.w, n * sizeof(T)) != cudaSuccess || cudaMalloc(&k.r, n * sizeof(T)) != cudaSuccess ||
+      cudaMalloc(&k.part, KMAX * RBLOCKS * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&k.h, 3 * KMAX * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost(&k.hhost, 3 * KMAX * sizeof(double)) != cudaSuccess) {
+    free_kt(k);
     return set_error("fv_gmres_solve: device allocation of the Krylov basis failed"), FV_ENOMEM;
   }
   return FV_OK;
@@ -89,38 +115,70 @@ __device__ __forceinline__ void block_store(double (&acc)[KMAX], int nv, double*
 // mode 0: part = V^T w
 // mode 1: w -= V h; part = V^T w
 // mode 2: w -= V h; part[0] = w^T w
-__global__ void __launch_bounds__(RTHREADS) cgs_kernel(long long n, const double* __restrict__ V, int nv,
-                                                       const double* __restrict__ h, double* __restrict__ w,
+// NV (the number of basis vectors) is a template parameter so the loops over
+// the basis unroll exactly.  Products are summed in T for up to 32 elements
+// of a thread, then in FP64.
+template <int NV, class T>
+__global__ void __launch_bounds__(RTHREADS) cgs_kernel(long long n, const T* __restrict__ V,
+                                                       const double* __restrict__ h, T* __restrict__ w,
                                                        double* __restrict__ part, int mode) {
   double acc[KMAX];
-  double hv[KMAX];
+  T hv[NV > 0 ? NV : 1];
+  T cur[NV > 0 ? NV : 1];
+  T curn = T(0);
 #pragma unroll
-  for (int v = 0; v < KMAX; ++v) {
-    acc[v] = 0.0;
-    hv[v] = (mode > 0 && v < nv) ? h[v] : 0.0;
-  }
+  for (int v = 0; v < KMAX; ++v) acc[v] = 0.0;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) hv[v] = mode > 0 ? (T)h[v] : T(0), cur[v] = T(0);
+  int cnt = 0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    double we = w[e];
+    T we = w[e];
     if (mode > 0) {
 #pragma unroll
-      for (int v = 0; v < KMAX; ++v)
-        if (v < nv) we -= hv[v] * V[v * n + e];
+      for (int v = 0; v < NV; ++v) we -= hv[v] * V[v * n + e];
       w[e] = we;
     }
     if (mode < 2) {
 #pragma unroll
-      for (int v = 0; v < KMAX; ++v)
-        if (v < nv) acc[v] += V[v * n + e] * we;
+      for (int v = 0; v < NV; ++v) cur[v] += V[v * n + e] * we;
     } else {
-      acc[0] += we * we;
+      curn += we * we;
+    }
+    if (++cnt == 32) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) acc[v] += (double)cur[v], cur[v] = T(0);
+      acc[0] += mode == 2 ? (double)curn : 0.0;
+      curn = T(0);
+      cnt = 0;
     }
   }
-  block_store(acc, mode < 2 ? nv : 1, part);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] += (double)cur[v];
+  if (mode == 2) acc[0] += (double)curn;
+  block_store(acc, mode < 2 ? NV : 1, part);
 }
 
-// out[v] = sum_b part[v * nb + b] (fixed order); if add: out[v] += previous value in `prev`
-__global__ void reduce_kernel(const double* __restrict__ part, int nb, int nv, double* __restrict__ out,
-                              const double* __restrict__ prev) {
+template <int NV, class T>
+static void cgs_launch_t(long long n, const T* V, const double* h, T* w, double* part, int mode, cudaStream_t st) {
+  cgs_kernel<NV, T><<<RBLOCKS, RTHREADS, 0, st>>>(n, V, h, w, part, mode);
+}
+
+template <class T, int... I>
+static void cgs_dispatch(int nv, long long n, const T* V, const double* h, T* w, double* part, int mode,
+                         cudaStream_t st, std::integer_sequence<int, I...>) {
+  using F = void (*)(long long, const T*, const double*, T*, double*, int, cudaStream_t);
+  static const F table[] = {&cgs_launch_t<I, T>...};
+  table[nv](n, V, h, w, part, mode, st);
+}
+
+template <class T>
+static void cgs_launch(int nv, long long n, const T* V, const double* h, T* w, double* part, int mode,
+                       cudaStream_t st) {
+  cgs_dispatch<T>(nv, n, V, h, w, part, mode, st, std::make_integer_sequence<int, KMAX>{});
+}
+
+// out[v] = sum_b part[v * nb + b] (fixed order)
+__global__ void reduce_kernel(const double* __restrict__ part, int nb, int nv, double* __restrict__ out) {
   __shared__ double sm[RTHREADS];
   for (int v = 0; v < nv; ++v) {
     double t = 0.0;
@@ -131,99 +189,167 @@ __global__ void reduce_kernel(const double* __restrict__ part, int nb, int nv, d
       if (threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
       __syncthreads();
     }
-    if (threadIdx.x == 0) out[v] = sm[0] + (prev ? prev[v] : 0.0);
+    if (threadIdx.x == 0) out[v] = sm[0];
     __syncthreads();
   }
 }
 
-__global__ void axpby_kernel(long long n, double a, const double* __restrict__ x, double b, const double* y,
-                             double* out) {
+template <class T, class U>
+__global__ void axpby_kernel(long long n, double a, const U* __restrict__ x, double b, const T* y, T* out) {
+  const T at = (T)a, bt = (T)b;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
-    out[e] = a * x[e] + (b == 0.0 ? 0.0 : b * y[e]);
+    out[e] = at * (T)x[e] + (b == 0.0 ? T(0) : bt * y[e]);
 }
 
+template <class T>
 struct Coef {
-  double c[KMAX];
+  T c[KMAX];
 };
 
 // x += sum_v y_v Z_v
-__global__ void update_kernel(long long n, const double* __restrict__ Z, int nv, Coef y, double* __restrict__ x) {
+template <int NV, class T>
+__global__ void update_kernel(long long n, const T* __restrict__ Z, Coef<T> y, T* __restrict__ x) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    double s = x[e];
+    T s = x[e];
 #pragma unroll
-    for (int v = 0; v < KMAX; ++v)
-      if (v < nv) s += y.c[v] * Z[v * n + e];
+    for (int v = 0; v < NV; ++v) s += y.c[v] * Z[v * n + e];
     x[e] = s;
   }
+}
+
+template <int NV, class T>
+static void update_launch_t(int blocks, long long n, const T* Z, const Coef<T>& y, T* x, cudaStream_t st) {
+  update_kernel<NV, T><<<blocks, 256, 0, st>>>(n, Z, y, x);
+}
+
+template <class T, int... I>
+static void update_dispatch(int nv, int blocks, long long n, const T* Z, const Coef<T>& y, T* x, cudaStream_t st,
+                            std::integer_sequence<int, I...>) {
+  using F = void (*)(int, long long, const T*, const Coef<T>&, T*, cudaStream_t);
+  static const F table[] = {&update_launch_t<I, T>...};
+  table[nv](blocks, n, Z, y, x, st);
 }
 
 static int vblocks(long long n) { return (int)std::min<long long>(std::max<long long>((n + 255) / 256, 1), 152LL * 16); }
 
 fv_status axpby(long long n, double a, const double* x, double b, const double* y, double* out, cudaStream_t st) {
   ProfScope ps(FV_K_VEC, st);
-  axpby_kernel<<<vblocks(n), 256, 0, st>>>(n, a, x, b, y, out);
+  axpby_kernel<double, double><<<vblocks(n), 256, 0, st>>>(n, a, x, b, y, out);
   FV_CUDA(cudaGetLastError());
   return FV_OK;
 }
 
-static fv_status norm2(Krylov* k, long long n, const double* x, cudaStream_t st, double* out) {
-  cgs_kernel<<<RBLOCKS, RTHREADS, 0, st>>>(n, x, 0, nullptr, const_cast<double*>(x), k->part, 2);
-  reduce_kernel<<<1, RTHREADS, 0, st>>>(k->part, RBLOCKS, 1, k->h + 2 * KMAX, nullptr);
+fv_status axpby32(long long n, double a, const float* x, double b, const float* y, float* out, cudaStream_t st) {
+  ProfScope ps(FV_K_VEC, st);
+  axpby_kernel<float, float><<<vblocks(n), 256, 0, st>>>(n, a, x, b, y, out);
   FV_CUDA(cudaGetLastError());
-  FV_CUDA(cudaMemcpyAsync(k->hhost, k->h + 2 * KMAX, sizeof(double), cudaMemcpyDeviceToHost, st));
-  FV_CUDA(cudaStreamSynchronize(st));
-  *out = std::sqrt(k->hhost[0]);
   return FV_OK;
+}
+
+fv_status to_fp32(long long n, const double* x, float* out, cudaStream_t st) {
+  ProfScope ps(FV_K_VEC, st);
+  axpby_kernel<float, double><<<vblocks(n), 256, 0, st>>>(n, 1.0, x, 0.0, nullptr, out);
+  FV_CUDA(cudaGetLastError());
+  return FV_OK;
+}
+
+fv_status to_fp64(long long n, const float* x, double* out, cudaStream_t st) {
+  ProfScope ps(FV_K_VEC, st);
+  axpby_kernel<double, float><<<vblocks(n), 256, 0, st>>>(n, 1.0, x, 0.0, nullptr, out);
+  FV_CUDA(cudaGetLastError());
+  return FV_OK;
+}
+
+template <class T>
+static fv_status axpby_t(long long n, double a, const T* x, double b, const T* y, T* out, cudaStream_t st) {
+  ProfScope ps(FV_K_VEC, st);
+  axpby_kernel<T, T><<<vblocks(n), 256, 0, st>>>(n, a, x, b, y, out);
+  FV_CUDA(cudaGetLastError());
+  return FV_OK;
+}
+
+template <class T>
+static fv_status norm2(KrylovT<T>& k, long long n, const T* x, cudaStream_t st, double* out) {
+  cgs_launch<T>(0, n, x, nullptr, const_cast<T*>(x), k.part, 2, st);
+  reduce_kernel<<<1, RTHREADS, 0, st>>>(k.part, RBLOCKS, 1, k.h + 2 * KMAX);
+  FV_CUDA(cudaGetLastError());
+  FV_CUDA(cudaMemcpyAsync(k.hhost, k.h + 2 * KMAX, sizeof(double), cudaMemcpyDeviceToHost, st));
+  FV_CUDA(cudaStreamSynchronize(st));
+  *out = std::sqrt(k.hhost[0]);
+  return FV_OK;
+}
+
+template <class T>
+static fv_status apply_t(const fv_system* s, const T* x, T* y, cudaStream_t st);
+template <>
+fv_status apply_t<double>(const fv_system* s, const double* x, double* y, cudaStream_t st) {
+  return apply_op(s, x, y, st);
+}
+template <>
+fv_status apply_t<float>(const fv_system* s, const float* x, float* y, cudaStream_t st) {
+  return apply_op32(s, x, y, st);
+}
+
+template <class T>
+static fv_status precond_t(const fv_system* s, const T* r, T* z, cudaStream_t st);
+template <>
+fv_status precond_t<double>(const fv_system* s, const double* r, double* z, cudaStream_t st) {
+  return precond_apply(s, r, z, st);
+}
+template <>
+fv_status precond_t<float>(const fv_system* s, const float* r, float* z, cudaStream_t st) {
+  return precond_apply32(s, r, z, st);
 }
 
 // ------------------------------------------------------------------ FGMRES
-fv_status gmres(const fv_system* s, const double* b, double* x, const fv_gmres_opts* o, fv_solve_stats* stats,
-                cudaStream_t st, bool inner) {
+template <class T>
+static fv_status gmres_t(const fv_system* s, const T* b, T* x, const fv_gmres_opts* o, fv_solve_stats* stats,
+                         cudaStream_t st, bool inner) {
   auto t0 = std::chrono::steady_clock::now();
   const int m = o->restart;
   if (m < 1 || m > KMAX - 1 || o->max_it < 0) return set_error("fv_gmres_solve: restart must be in [1, 31]"), FV_EINVAL;
-  fv_status rc = ensure_krylov(s, m);
+  fv_status rc = ensure_krylov<T>(s, m);
   if (rc) return rc;
-  Krylov* k = s->kry;
+  KrylovT<T>& k = kt<T>(s->kry);
   const long long n = s->n;
+  const int lvl = FV_K_COARSE * s->level;
   if (!inner) s->last_inner = 0;
   // r = b - A x
-  if ((rc = apply_op(s, x, k->r, st))) return rc;
-  if ((rc = axpby(n, 1.0, b, -1.0, k->r, k->r, st))) return rc;
+  if ((rc = apply_t<T>(s, x, k.r, st))) return rc;
+  if ((rc = axpby_t<T>(n, 1.0, b, -1.0, k.r, k.r, st))) return rc;
   double beta;
-  if ((rc = norm2(k, n, k->r, st, &beta))) return rc;
+  if ((rc = norm2<T>(k, n, k.r, st, &beta))) return rc;
   const double r0 = beta, target = std::max(o->atol, o->rtol * r0);
   int its = 0;
   bool nan = !std::isfinite(beta);
   std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
   while (!nan && beta > target && its < o->max_it) {
-    if ((rc = axpby(n, 1.0 / beta, k->r, 0.0, nullptr, k->V, st))) return rc;
+    if ((rc = axpby_t<T>(n, 1.0 / beta, k.r, 0.0, nullptr, k.V, st))) return rc;
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
     int j = 0;
     bool breakdown = false;
     for (; j < m; ++j) {
-      double* vj = k->V + (size_t)j * n;
-      double* zj = k->Z + (size_t)j * n;
-      if ((rc = precond_apply(s, vj, zj, st))) return rc;
-      if ((rc = apply_op(s, zj, k->w, st))) return rc;
+      T* vj = k.V + (size_t)j * n;
+      T* zj = k.Z + (size_t)j * n;
+      if ((rc = precond_t<T>(s, vj, zj, st))) return rc;
+      if ((rc = apply_t<T>(s, zj, k.w, st))) return rc;
       const int nv = j + 1;
       {
-      ProfScope ps(FV_K_CGS + FV_K_COARSE * s->level, st);
-      cgs_kernel<<<RBLOCKS, RTHREADS, 0, st>>>(n, k->V, nv, nullptr, k->w, k->part, 0);
-      reduce_kernel<<<1, RTHREADS, 0, st>>>(k->part, RBLOCKS, nv, k->h, nullptr);
-      cgs_kernel<<<RBLOCKS, RTHREADS, 0, st>>>(n, k->V, nv, k->h, k->w, k->part, 1);
-      reduce_kernel<<<1, RTHREADS, 0, st>>>(k->part, RBLOCKS, nv, k->h + KMAX, nullptr);
-      cgs_kernel<<<RBLOCKS, RTHREADS, 0, st>>>(n, k->V, nv, k->h + KMAX, k->w, k->part, 2);
-      reduce_kernel<<<1, RTHREADS, 0, st>>>(k->part, RBLOCKS, 1, k->h + 2 * KMAX, nullptr);
+        ProfScope ps(FV_K_CGS + lvl, st);
+        cgs_launch<T>(nv, n, k.V, nullptr, k.w, k.part, 0, st);
+        reduce_kernel<<<1, RTHREADS, 0, st>>>(k.part, RBLOCKS, nv, k.h);
+        cgs_launch<T>(nv, n, k.V, k.h, k.w, k.part, 1, st);
+        reduce_kernel<<<1, RTHREADS, 0, st>>>(k.part, RBLOCKS, nv, k.h + KMAX);
+        cgs_launch<T>(nv, n, k.V, k.h + KMAX, k.w, k.part, 2, st);
+        reduce_kernel<<<1, RTHREADS, 0, st>>>(k.part, RBLOCKS, 1, k.h + 2 * KMAX);
       }
       FV_CUDA(cudaGetLastError());
-      FV_CUDA(cudaMemcpyAsync(k->hhost, k->h, 3 * KMAX * sizeof(double), cudaMemcpyDeviceToHost, st));
+      FV_CUDA(cudaMemcpyAsync(k.hhost, k.h, 3 * KMAX * sizeof(double), cudaMemcpyDeviceToHost, st));
       FV_CUDA(cudaStreamSynchronize(st));
-      double* hc = &H[0];
       std::vector<double> col(j + 2);
-      for (int i = 0; i <= j; ++i) col[i] = k->hhost[i] + k->hhost[KMAX + i];  // CGS2: h = h1 + h2
-      const double hn = std::sqrt(k->hhost[2 * KMAX]);
+      for (int i = 0; i <= j; ++i) col[i] = k.hhost[i] + k.hhost[KMAX + i];  // CGS2: h = h1 + h2
+      const double hn = std::sqrt(k.hhost[2 * KMAX]);
       col[j + 1] = hn;
       for (int i = 0; i < j; ++i) {
         const double t = cs[i] * col[i] + sn[i] * col[i + 1];
@@ -235,7 +361,7 @@ fv_status gmres(const fv_system* s, const double* b, double* x, const fv_gmres_o
       col[j] = den, col[j + 1] = 0.0;
       g[j + 1] = -sn[j] * g[j];
       g[j] = cs[j] * g[j];
-      for (int i = 0; i <= j; ++i) hc[i * m + j] = col[i];
+      for (int i = 0; i <= j; ++i) H[i * m + j] = col[i];
       ++its;
       if (!std::isfinite(hn) || !std::isfinite(g[j + 1])) {
         nan = true;
@@ -247,7 +373,7 @@ fv_status gmres(const fv_system* s, const double* b, double* x, const fv_gmres_o
         ++j;
         break;
       }
-      if ((rc = axpby(n, 1.0 / hn, k->w, 0.0, nullptr, k->V + (size_t)(j + 1) * n, st))) return rc;
+      if ((rc = axpby_t<T>(n, 1.0 / hn, k.w, 0.0, nullptr, k.V + (size_t)(j + 1) * n, st))) return rc;
     }
     const int kk = std::min(j, m);
     if (!nan) {
@@ -256,15 +382,15 @@ fv_status gmres(const fv_system* s, const double* b, double* x, const fv_gmres_o
         for (int q = i + 1; q < kk; ++q) sacc -= H[i * m + q] * y[q];
         y[i] = sacc / H[i * m + i];
       }
-      Coef c{};
-      for (int i = 0; i < kk; ++i) c.c[i] = y[i];
+      Coef<T> c{};
+      for (int i = 0; i < kk; ++i) c.c[i] = (T)y[i];
       ProfScope ps(FV_K_VEC, st);
-      update_kernel<<<vblocks(n), 256, 0, st>>>(n, k->Z, kk, c, x);
+      update_dispatch<T>(kk, vblocks(n), n, k.Z, c, x, st, std::make_integer_sequence<int, KMAX>{});
       FV_CUDA(cudaGetLastError());
     }
-    if ((rc = apply_op(s, x, k->r, st))) return rc;
-    if ((rc = axpby(n, 1.0, b, -1.0, k->r, k->r, st))) return rc;
-    if ((rc = norm2(k, n, k->r, st, &beta))) return rc;
+    if ((rc = apply_t<T>(s, x, k.r, st))) return rc;
+    if ((rc = axpby_t<T>(n, 1.0, b, -1.0, k.r, k.r, st))) return rc;
+    if ((rc = norm2<T>(k, n, k.r, st, &beta))) return rc;
     if (!std::isfinite(beta)) nan = true;
     if (breakdown) break;
   }
@@ -282,34 +408,56 @@ fv_status gmres(const fv_system* s, const double* b, double* x, const fv_gmres_o
   return FV_OK;
 }
 
+fv_status gmres(const fv_system* s, const double* b, double* x, const fv_gmres_opts* o, fv_solve_stats* stats,
+                cudaStream_t st, bool inner) {
+  return gmres_t<double>(s, b, x, o, stats, st, inner);
+}
+
+fv_status gmres32(const fv_system* s, const float* b, float* x, const fv_gmres_opts* o, fv_solve_stats* stats,
+                  cudaStream_t st) {
+  return gmres_t<float>(s, b, x, o, stats, st, true);
+}
+
 // volume-weighted mean removal of the first component (Neumann pressure gauge)
-__global__ void wsum_kernel(long long N, int Ns, int Nr, const double* __restrict__ invsig, const double* __restrict__ invr2,
-                            const double* __restrict__ x, double* __restrict__ part) {
+template <class T>
+__global__ void wsum_kernel(long long N, int Ns, int Nr, const double* __restrict__ invsig,
+                            const double* __restrict__ invr2, const T* __restrict__ x, double* __restrict__ part) {
   double acc[KMAX];
   acc[0] = 0.0, acc[1] = 0.0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
     const int ij = (int)(e % ((long long)Ns * Ns));
     const int k = (int)((e / ((long long)Ns * Ns)) % Nr);
     const double V = 1.0 / (invsig[ij] * invr2[k]);
-    acc[0] += V * x[e];
+    acc[0] += V * (double)x[e];
     acc[1] += V;
   }
   block_store(acc, 2, part);
 }
 
-__global__ void shift_kernel(long long N, const double* __restrict__ sums, double* __restrict__ x) {
-  const double mean = sums[0] / sums[1];
+template <class T>
+__global__ void shift_kernel(long long N, const double* __restrict__ sums, T* __restrict__ x) {
+  const T mean = (T)(sums[0] / sums[1]);
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x)
     x[e] -= mean;
 }
 
-fv_status weighted_mean_remove(const fv_grid* g, double* x, cudaStream_t st, double* part, double* sums) {
+template <class T>
+static fv_status wmr(const fv_grid* g, T* x, cudaStream_t st, double* part, double* sums) {
   const Geo& G = g->geo;
-  wsum_kernel<<<RBLOCKS, RTHREADS, 0, st>>>(G.N, G.Ns, G.Nr, G.invsig, G.invr2, x, part);
-  reduce_kernel<<<1, RTHREADS, 0, st>>>(part, RBLOCKS, 2, sums, nullptr);
-  shift_kernel<<<vblocks(G.N), 256, 0, st>>>(G.N, sums, x);
+  ProfScope ps(FV_K_VEC, st);
+  wsum_kernel<T><<<RBLOCKS, RTHREADS, 0, st>>>(G.N, G.Ns, G.Nr, G.invsig, G.invr2, x, part);
+  reduce_kernel<<<1, RTHREADS, 0, st>>>(part, RBLOCKS, 2, sums);
+  shift_kernel<T><<<vblocks(G.N), 256, 0, st>>>(G.N, sums, x);
   FV_CUDA(cudaGetLastError());
   return FV_OK;
+}
+
+fv_status weighted_mean_remove(const fv_grid* g, double* x, cudaStream_t st, double* part, double* sums) {
+  return wmr<double>(g, x, st, part, sums);
+}
+
+fv_status weighted_mean_remove32(const fv_grid* g, float* x, cudaStream_t st, double* part, double* sums) {
+  return wmr<float>(g, x, st, part, sums);
 }
 
 }  // namespace fv

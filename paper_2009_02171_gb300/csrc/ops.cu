@@ -12,17 +12,20 @@ namespace fv {
 // Lagrange interpolation along the neighbour's first grid line (paper
 // Sec. 3.3 overlap across block interfaces; one ghost layer).  Corner ghosts
 // (t = -1 or Ns on the xi sides): phi(-1,-1) = phi(-1,0) + phi(0,-1) - phi(0,0).
-template <class T>
-__device__ __forceinline__ double interp_ghost(const Geo& G, const T* x, int comp, int p, int side, int k, int t) {
+template <class T, class GT>
+__device__ __forceinline__ typename GT::real interp_ghost(const GT& G, const T* x, int comp, int p, int side, int k,
+                                                          int t) {
+  using R = typename GT::real;
   const int id = (p * 4 + side) * G.Ns + t;
   const int q = G.gq[id];
   const T* base = x + comp * G.N + ((long long)(q * G.Nr + k) * G.Ns) * G.Ns;
-  return G.gw[3 * id] * (double)base[G.gsrc[3 * id]] + G.gw[3 * id + 1] * (double)base[G.gsrc[3 * id + 1]] +
-         G.gw[3 * id + 2] * (double)base[G.gsrc[3 * id + 2]];
+  return G.gw[3 * id] * (R)base[G.gsrc[3 * id]] + G.gw[3 * id + 1] * (R)base[G.gsrc[3 * id + 1]] +
+         G.gw[3 * id + 2] * (R)base[G.gsrc[3 * id + 2]];
 }
 
-template <class T>
-__global__ void ghost_kernel(Geo G, const T* __restrict__ x, T* __restrict__ gh, int d) {
+template <class T, class GT>
+__global__ void ghost_kernel(GT G, const T* __restrict__ x, T* __restrict__ gh, int d) {
+  using R = typename GT::real;
   const int Ns = G.Ns, Nr = G.Nr;
   const long long total = (long long)d * 6 * 4 * Nr * (Ns + 2);
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
@@ -37,14 +40,14 @@ __global__ void ghost_kernel(Geo G, const T* __restrict__ x, T* __restrict__ gh,
     const int p = (int)(r % 6);
     const int comp = (int)(r / 6);
     const int t = tp - 1;
-    double v = 0.0;
+    R v = R(0);
     if (t >= 0 && t < Ns) {
       v = interp_ghost(G, x, comp, p, side, k, t);
     } else if (side == XI_MIN || side == XI_MAX) {
       const int jin = t < 0 ? 0 : Ns - 1;
       const int iin = side == XI_MIN ? 0 : Ns - 1;
       v = interp_ghost(G, x, comp, p, side, k, jin) + interp_ghost(G, x, comp, p, t < 0 ? ETA_MIN : ETA_MAX, k, iin) -
-          (double)x[comp * G.N + cidx(G, p, k, jin, iin)];
+          (R)x[comp * G.N + cidx(G, p, k, jin, iin)];
     }
     gh[e] = (T)v;
   }
@@ -57,7 +60,7 @@ static int grid_blocks(long long n, int threads) {
 
 fv_status ghost_fill(const Geo& G, const double* x, double* gh, int d, cudaStream_t st) {
   const long long total = (long long)d * 6 * 4 * G.Nr * (G.Ns + 2);
-  ghost_kernel<double><<<grid_blocks(total, 256), 256, 0, st>>>(G, x, gh, d);
+  ghost_kernel<double, Geo><<<grid_blocks(total, 256), 256, 0, st>>>(G, x, gh, d);
   FV_CUDA(cudaGetLastError());
   return FV_OK;
 }
@@ -66,31 +69,28 @@ fv_status fill_ghosts(const fv_system* s, const double* x, cudaStream_t st) {
   const Geo& G = s->grid->geo;
   const long long total = (long long)s->d * 6 * 4 * G.Nr * (G.Ns + 2);
   ProfScope ps(FV_K_GHOST + FV_K_COARSE * s->level, st);
-  ghost_kernel<double><<<grid_blocks(total, 256), 256, 0, st>>>(G, x, s->ghost, s->d);
+  ghost_kernel<double, Geo><<<grid_blocks(total, 256), 256, 0, st>>>(G, x, s->ghost, s->d);
   FV_CUDA(cudaGetLastError());
   return FV_OK;
 }
 
 // ---------------------------------------------------------------- apply
-template <int KIND>
-__global__ void apply_kernel(Geo G, Phys ph, const double* __restrict__ x, const double* __restrict__ gh,
-                             double* __restrict__ y, int d) {
-  const long long n = (long long)d * G.N;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    const int a = (int)(e / G.N);
-    long long c = e - (long long)a * G.N;
-    const int i = (int)(c % G.Ns);
-    c /= G.Ns;
-    const int j = (int)(c % G.Ns);
-    c /= G.Ns;
-    const int k = (int)(c % G.Nr);
-    const int p = (int)(c / G.Nr);
-    ApplyAcc<double> acc{&G, x, gh, 0.0};
-    if (KIND == FV_VTBE) vtbe_row(G, ph, acc, p, k, j, i, a);
-    else ppbe_row(G, ph, acc, p, k, j, i, a);
-    y[e] = acc.sum;
-  }
+// grid: x = tiles of the (j, i) plane, y = k, z = comp * 6 + panel (32-bit index math)
+template <int KIND, class T, class GT>
+__global__ void __launch_bounds__(256) apply_kernel(GT G, Phys ph, const T* __restrict__ x, const T* __restrict__ gh,
+                                                    T* __restrict__ y) {
+  const int ij = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ij >= G.Ns * G.Ns) return;
+  const int i = ij % G.Ns, j = ij / G.Ns, k = blockIdx.y;
+  const int a = blockIdx.z / 6, p = blockIdx.z - 6 * a;
+  ApplyAcc<T, typename GT::real> acc(G, x, gh);
+  if (KIND == FV_VTBE) vtbe_row(G, ph, acc, p, k, j, i, a);
+  else ppbe_row(G, ph, acc, p, k, j, i, a);
+  y[(long long)a * G.N + ((long long)(p * G.Nr + k) * G.Ns + j) * G.Ns + i] = (T)acc.sum;
 }
+
+template <class GT>
+static dim3 apply_grid(const GT& G, int d) { return dim3((G.Ns * G.Ns + 255) / 256, G.Nr, 6 * d); }
 
 fv_status apply_op(const fv_system* s, const double* x, double* y, cudaStream_t st) {
   const Geo& G = s->grid->geo;
@@ -99,10 +99,30 @@ fv_status apply_op(const fv_system* s, const double* x, double* y, cudaStream_t 
   Phys ph{s->phys.E, s->phys.Ra, s->phys.Pr, s->phys.Pm, s->phys.dt};
   const long long n = s->n;
   ProfScope ps((s->kind == FV_VTBE ? FV_K_APPLY_VTBE : FV_K_APPLY_PPBE) + FV_K_COARSE * s->level, st);
+  (void)n;
   if (s->kind == FV_VTBE)
-    apply_kernel<FV_VTBE><<<grid_blocks(n, 256), 256, 0, st>>>(G, ph, x, s->ghost, y, s->d);
+    apply_kernel<FV_VTBE, double, Geo><<<apply_grid(G, s->d), 256, 0, st>>>(G, ph, x, s->ghost, y);
   else
-    apply_kernel<FV_PPBE><<<grid_blocks(n, 256), 256, 0, st>>>(G, ph, x, s->ghost, y, s->d);
+    apply_kernel<FV_PPBE, double, Geo><<<apply_grid(G, s->d), 256, 0, st>>>(G, ph, x, s->ghost, y);
+  FV_CUDA(cudaGetLastError());
+  return FV_OK;
+}
+
+// FP32 operator (mixed-precision inner solves): FP32 tables, FP32 arithmetic
+fv_status apply_op32(const fv_system* s, const float* x, float* y, cudaStream_t st) {
+  const GeoF& G = s->grid->geof;
+  const long long total = (long long)s->d * 6 * 4 * G.Nr * (G.Ns + 2);
+  {
+    ProfScope ps(FV_K_GHOST + FV_K_COARSE * s->level, st);
+    ghost_kernel<float, GeoF><<<grid_blocks(total, 256), 256, 0, st>>>(G, x, s->ghost32, s->d);
+  }
+  FV_CUDA(cudaGetLastError());
+  Phys ph{s->phys.E, s->phys.Ra, s->phys.Pr, s->phys.Pm, s->phys.dt};
+  ProfScope ps((s->kind == FV_VTBE ? FV_K_APPLY_VTBE : FV_K_APPLY_PPBE) + FV_K_COARSE * s->level, st);
+  if (s->kind == FV_VTBE)
+    apply_kernel<FV_VTBE, float, GeoF><<<apply_grid(G, s->d), 256, 0, st>>>(G, ph, x, s->ghost32, y);
+  else
+    apply_kernel<FV_PPBE, float, GeoF><<<apply_grid(G, s->d), 256, 0, st>>>(G, ph, x, s->ghost32, y);
   FV_CUDA(cudaGetLastError());
   return FV_OK;
 }
@@ -137,13 +157,13 @@ fv_status apply_op_noalloc(const fv_system* s, const double* x, double* y, cudaS
   double* gh = nullptr;
   fv_status rc = static_ghost_address(&gh);
   if (rc) return rc;
-  ghost_kernel<double><<<grid_blocks(total, 256), 256, 0, st>>>(G, x, gh, s->d);
+  ghost_kernel<double, Geo><<<grid_blocks(total, 256), 256, 0, st>>>(G, x, gh, s->d);
   FV_CUDA(cudaGetLastError());
   Phys ph{s->phys.E, s->phys.Ra, s->phys.Pr, s->phys.Pm, s->phys.dt};
   if (s->kind == FV_VTBE)
-    apply_kernel<FV_VTBE><<<grid_blocks(s->n, 256), 256, 0, st>>>(G, ph, x, gh, y, s->d);
+    apply_kernel<FV_VTBE, double, Geo><<<apply_grid(G, s->d), 256, 0, st>>>(G, ph, x, gh, y);
   else
-    apply_kernel<FV_PPBE><<<grid_blocks(s->n, 256), 256, 0, st>>>(G, ph, x, gh, y, s->d);
+    apply_kernel<FV_PPBE, double, Geo><<<apply_grid(G, s->d), 256, 0, st>>>(G, ph, x, gh, y);
   FV_CUDA(cudaGetLastError());
   return FV_OK;
 }
@@ -217,7 +237,7 @@ __global__ void assemble_kernel(Geo G, Phys ph, int kind, int d, int count, cons
     const int loc = (int)(cell - base);
     const int li = loc % nx, lj = (loc / nx) % ny, lk = loc / (nx * ny);
     AssembleAcc acc;
-    acc.G = &G;
+    acc.G = G.self;
     acc.row_comp = a;
     for (int s = 0; s < 11; ++s) {
       const int ni = li + kOff[s][0], nj = lj + kOff[s][1], nk = lk + kOff[s][2];

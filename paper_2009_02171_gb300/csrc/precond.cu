@@ -81,8 +81,8 @@ fv_status build_subdomains(fv_system* s, const fv_grid* g) {
   std::vector<long long> cell_off{0}, gmap;
   std::vector<int> dims;
   std::vector<unsigned char> owned;
-  std::vector<std::vector<int>> orders;
-  int max_levels = 0;
+  std::vector<std::vector<int>> orders, perms;
+  int max_levels = 0, max_cols = 0;
   for (int p = 0; p < 6; ++p)
     for (int c = 0; c < pc.p3; ++c)
       for (int b = 0; b < pc.p2; ++b)
@@ -91,6 +91,7 @@ fv_status build_subdomains(fv_system* s, const fv_grid* g) {
           const int lo_i = i0 - delta, lo_j = j0 - delta, lo_k = std::max(0, k0 - delta);
           const int nx = i1 - i0 + 2 * delta, ny = j1 - j0 + 2 * delta, nz = std::min(h.Nr, k1 + delta) - lo_k;
           dims.insert(dims.end(), {nx, ny, nz});
+          max_cols = std::max(max_cols, nx * ny);
           const int levels = (nx - 1) + 2 * (ny - 1) + (nz - 1) + 1;
           max_levels = std::max(max_levels, levels);
           std::vector<int> cnt(levels + 1, 0), ord(nx * ny * nz);
@@ -109,6 +110,15 @@ fv_status build_subdomains(fv_system* s, const fv_grid* g) {
               for (int li = 0; li < nx; ++li) ord[pos[li + 2 * lj + lk]++] = (lk * ny + lj) * nx + li;
           orders.push_back(ord);
           cell_off.push_back(cell_off.back() + (long long)nx * ny * nz);
+          // wavefront order for the sweeps: level, then j, then i
+          std::vector<int> pp(nx * ny * nz);
+          int pos_ = 0;
+          for (int L = 0; L < levels; ++L)
+            for (int lj = 0; lj < ny; ++lj) {
+              const int lo_ = std::max(0, L - 2 * lj - (nz - 1)), hi_ = std::min(nx - 1, L - 2 * lj);
+              for (int li = lo_; li <= hi_; ++li) pp[((L - li - 2 * lj) * ny + lj) * nx + li] = pos_++;
+            }
+          perms.push_back(pp);
         }
   const int count = (int)dims.size() / 3;
   // level offsets per subdomain, padded to max_levels + 1
@@ -125,13 +135,24 @@ fv_status build_subdomains(fv_system* s, const fv_grid* g) {
     for (int L = 0; L <= max_levels; ++L) level_off[(size_t)sd * (max_levels + 1) + L] = cnt[std::min(L, levels)];
     order.insert(order.end(), orders[sd].begin(), orders[sd].end());
   }
+  std::vector<int> perm;
+  std::vector<long long> gmap_p(gmap.size());
+  std::vector<unsigned char> owned_p(owned.size());
+  perm.reserve(gmap.size());
+  for (int sd = 0; sd < count; ++sd) {
+    perm.insert(perm.end(), perms[sd].begin(), perms[sd].end());
+    for (size_t c = 0; c < perms[sd].size(); ++c) {
+      gmap_p[cell_off[sd] + perms[sd][c]] = gmap[cell_off[sd] + c];
+      owned_p[cell_off[sd] + perms[sd][c]] = owned[cell_off[sd] + c];
+    }
+  }
   std::vector<int> lpt(count);
   std::iota(lpt.begin(), lpt.end(), 0);
   std::stable_sort(lpt.begin(), lpt.end(),
                    [&](int a, int b) { return cell_off[a + 1] - cell_off[a] > cell_off[b + 1] - cell_off[b]; });
 
   Subdomains& S = s->subs;
-  S.count = count, S.d = d, S.total_cells = cell_off.back(), S.max_levels = max_levels;
+  S.count = count, S.d = d, S.total_cells = cell_off.back(), S.max_levels = max_levels, S.max_cols = max_cols;
   const long long T = S.total_cells;
   S.cell_off = dalloc<long long>(s, count + 1);
   S.dims = dalloc<int>(s, dims.size());
@@ -141,11 +162,13 @@ fv_status build_subdomains(fv_system* s, const fv_grid* g) {
   S.order = dalloc<int>(s, T);
   S.off = dalloc<double>(s, (size_t)T * 11 * d);
   S.diag = dalloc<double>(s, (size_t)T * d * d);
-  S.work = dalloc<double>(s, (size_t)T * d);
   S.status = dalloc<int>(s, 1);
   S.lpt = dalloc<int>(s, count);
-  if (!S.cell_off || !S.dims || !S.gmap || !S.owned || !S.level_off || !S.order || !S.off || !S.diag || !S.work ||
-      !S.status || !S.lpt)
+  S.perm = dalloc<int>(s, T);
+  S.gmap_p = dalloc<long long>(s, T);
+  S.owned_p = dalloc<unsigned char>(s, T);
+  if (!S.cell_off || !S.dims || !S.gmap || !S.owned || !S.level_off || !S.order || !S.off || !S.diag ||
+      !S.status || !S.lpt || !S.perm || !S.gmap_p || !S.owned_p)
     return set_error("fv_assemble_system: device allocation of subdomain data failed"), FV_ENOMEM;
   FV_CUDA(cudaMemcpy(S.cell_off, cell_off.data(), cell_off.size() * sizeof(long long), cudaMemcpyHostToDevice));
   FV_CUDA(cudaMemcpy(S.dims, dims.data(), dims.size() * sizeof(int), cudaMemcpyHostToDevice));
@@ -154,6 +177,9 @@ fv_status build_subdomains(fv_system* s, const fv_grid* g) {
   FV_CUDA(cudaMemcpy(S.level_off, level_off.data(), level_off.size() * sizeof(int), cudaMemcpyHostToDevice));
   FV_CUDA(cudaMemcpy(S.order, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice));
   FV_CUDA(cudaMemcpy(S.lpt, lpt.data(), lpt.size() * sizeof(int), cudaMemcpyHostToDevice));
+  FV_CUDA(cudaMemcpy(S.perm, perm.data(), perm.size() * sizeof(int), cudaMemcpyHostToDevice));
+  FV_CUDA(cudaMemcpy(S.gmap_p, gmap_p.data(), gmap_p.size() * sizeof(long long), cudaMemcpyHostToDevice));
+  FV_CUDA(cudaMemcpy(S.owned_p, owned_p.data(), owned_p.size(), cudaMemcpyHostToDevice));
   FV_CUDA(cudaMemset(S.status, 0, sizeof(int)));
   return FV_OK;
 }
@@ -227,90 +253,316 @@ fv_status ilu_factor(fv_system* s) {
   return FV_OK;
 }
 
-// ------------------------------------------------------------------ RAS apply
-__global__ void ras_forward_kernel(int d, long long N, const long long* __restrict__ cell_off,
-                                   const int* __restrict__ dims, const int* __restrict__ level_off, int max_levels,
-                                   const int* __restrict__ order, const int* __restrict__ lpt,
-                                   const long long* __restrict__ gmap, const double* __restrict__ off,
-                                   const double* __restrict__ diag, const double* __restrict__ r,
-                                   double* __restrict__ work) {
-  const int sd = lpt[blockIdx.x];
-  const long long base = cell_off[sd];
-  const Box b{dims[3 * sd], dims[3 * sd + 1], dims[3 * sd + 2]};
-  const int* lo = level_off + (size_t)sd * (max_levels + 1);
-  const int levels = (b.nx - 1) + 2 * (b.ny - 1) + (b.nz - 1) + 1;
-  for (int L = 0; L < levels; ++L) {
-    for (int idx = lo[L] + threadIdx.x; idx < lo[L + 1]; idx += blockDim.x) {
-      const int c = order[base + idx];
-      const int li = c % b.nx, lj = (c / b.nx) % b.ny, lk = c / (b.nx * b.ny);
-      const long long C = base + c;
-      const long long g = gmap[C];
+// ------------------------------------------------------------------ sweep layout
+static void release(fv_system* s, void* ptr) {
+  for (auto it = s->allocs.begin(); it != s->allocs.end(); ++it)
+    if (*it == ptr) {
+      cudaFree(ptr);
+      s->allocs.erase(it);
+      return;
+    }
+}
+
+__device__ __forceinline__ int find_subdomain(const long long* cell_off, int count, long long cell) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (cell_off[mid] <= cell) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// factors: natural layout off[C][11][d], diag[C][d][d]  ->  packed SoA in wavefront order:
+// q = s d + a (lower slots 0..4), 5 d + a d + b (diagonal block), 5 d + d^2 + (s-6) d + a (upper slots)
+template <class T>
+__global__ void repack_kernel(int d, int count, const long long* __restrict__ cell_off, const int* __restrict__ perm,
+                              const double* __restrict__ off, const double* __restrict__ diag, T* __restrict__ F) {
+  const long long total = cell_off[count];
+  const int Q = 10 * d + d * d;
+  for (long long C = blockIdx.x * (long long)blockDim.x + threadIdx.x; C < total;
+       C += (long long)gridDim.x * blockDim.x) {
+    const int sd = find_subdomain(cell_off, count, C);
+    const long long base = cell_off[sd];
+    const long long nc = cell_off[sd + 1] - base;
+    T* Fs = F + base * Q + perm[C];
+    for (int s = 0; s < 11; ++s) {
+      if (s == 5) continue;
       for (int a = 0; a < d; ++a) {
-        double y = g >= 0 ? r[a * N + g] : 0.0;
-        for (int s = 0; s < 5; ++s) {
-          if (!b.in(li + kSlot[s][0], lj + kSlot[s][1], lk + kSlot[s][2])) continue;
-          y -= off[(C * 11 + s) * d + a] * work[(C + slot_delta(b, s)) * d + a];
-        }
-        for (int bb = 0; bb < a; ++bb) y -= diag[(C * d + a) * d + bb] * work[C * d + bb];
-        work[C * d + a] = y;
+        const int q = s < 5 ? s * d + a : 5 * d + d * d + (s - 6) * d + a;
+        Fs[q * nc] = (T)off[(C * 11 + s) * d + a];
       }
     }
-    __syncthreads();
+    for (int a = 0; a < d; ++a)
+      for (int b = 0; b < d; ++b) Fs[(5 * d + a * d + b) * nc] = (T)diag[(C * d + a) * d + b];
   }
 }
 
-__global__ void ras_backward_kernel(int d, long long N, const long long* __restrict__ cell_off,
-                                    const int* __restrict__ dims, const int* __restrict__ level_off, int max_levels,
-                                    const int* __restrict__ order, const int* __restrict__ lpt,
-                                    const long long* __restrict__ gmap, const unsigned char* __restrict__ owned,
-                                    const double* __restrict__ off, const double* __restrict__ diag,
-                                    double* __restrict__ work, double* __restrict__ z) {
+static size_t table_bytes(int levels, int ny) { return (size_t)(levels + 1 + levels * ny) * sizeof(int); }
+
+fv_status prepare_sweeps(fv_system* s, int fp32) {
+  Subdomains& S = s->subs;
+  const int d = S.d, Q = 10 * d + d * d;
+  const size_t es = fp32 ? sizeof(float) : sizeof(double);
+  S.fp32 = fp32;
+  S.F = fp32 ? (void*)dalloc<float>(s, (size_t)S.total_cells * Q) : (void*)dalloc<double>(s, (size_t)S.total_cells * Q);
+  S.loc = fp32 ? (void*)dalloc<float>(s, (size_t)S.total_cells * d) : (void*)dalloc<double>(s, (size_t)S.total_cells * d);
+  if (!S.F || !S.loc) return set_error("fv_assemble_system: allocation of sweep data failed"), FV_ENOMEM;
+  const int blocks = (int)std::min<long long>((S.total_cells + 255) / 256, 152LL * 32);
+  if (fp32)
+    repack_kernel<float><<<blocks, 256>>>(d, S.count, S.cell_off, S.perm, S.off, S.diag, (float*)S.F);
+  else
+    repack_kernel<double><<<blocks, 256>>>(d, S.count, S.cell_off, S.perm, S.off, S.diag, (double*)S.F);
+  FV_CUDA(cudaGetLastError());
+  FV_CUDA(cudaDeviceSynchronize());
+  release(s, S.off), release(s, S.diag), release(s, S.perm);
+  S.off = S.diag = nullptr;
+  S.perm = nullptr;
+  // CTA shape: one thread per (i, j) column, at most 1024 threads (columns loop)
+  S.threads = std::min(1024, ((S.max_cols + 31) / 32) * 32);
+  // the widest box's level table; the 4-plane ring in shared memory when it fits
+  std::vector<int> dims(3 * S.count);
+  FV_CUDA(cudaMemcpy(dims.data(), S.dims, dims.size() * sizeof(int), cudaMemcpyDeviceToHost));
+  size_t tab = 0;
+  for (int sd = 0; sd < S.count; ++sd) {
+    const int nx = dims[3 * sd], ny = dims[3 * sd + 1], nz = dims[3 * sd + 2];
+    tab = std::max(tab, table_bytes((nx - 1) + 2 * (ny - 1) + (nz - 1) + 1, ny));
+  }
+  const size_t ring = 4 * (size_t)S.max_cols * d * es;
+  const size_t ring_al = (ring + 15) / 16 * 16;
+  S.ring_in_smem = ring_al + tab <= 200 * 1024;
+  S.smem = (S.ring_in_smem ? ring_al : 0) + tab;
+  if (!S.ring_in_smem) {
+    S.ring = fp32 ? (void*)dalloc<float>(s, (size_t)S.count * 4 * S.max_cols * d)
+                  : (void*)dalloc<double>(s, (size_t)S.count * 4 * S.max_cols * d);
+    if (!S.ring) return set_error("fv_assemble_system: allocation of the sweep ring failed"), FV_ENOMEM;
+  }
+  return FV_OK;
+}
+
+// ------------------------------------------------------------------ RAS apply
+// gather R_i^delta r into the packed sweep vector (zero past cube corners)
+template <class T, class V>
+__global__ void gather_kernel(int d, long long N, const long long* __restrict__ cell_off,
+                              const long long* __restrict__ gmap_p, const V* __restrict__ r, T* __restrict__ loc) {
+  const int sd = blockIdx.x;
+  const long long base = cell_off[sd], nc = cell_off[sd + 1] - base;
+  for (long long e = blockIdx.y * (long long)blockDim.x + threadIdx.x; e < nc * d; e += (long long)gridDim.y * blockDim.x) {
+    const int a = (int)(e / nc);
+    const long long pos = e - a * nc;
+    const long long g = gmap_p[base + pos];
+    loc[base * d + e] = g >= 0 ? (T)r[a * N + g] : (T)0;
+  }
+}
+
+// scatter the owned cells, (R_i^0)^T
+template <class T, class V>
+__global__ void scatter_kernel(int d, long long N, const long long* __restrict__ cell_off,
+                               const long long* __restrict__ gmap_p, const unsigned char* __restrict__ owned_p,
+                               const T* __restrict__ loc, V* __restrict__ z) {
+  const int sd = blockIdx.x;
+  const long long base = cell_off[sd], nc = cell_off[sd + 1] - base;
+  for (long long e = blockIdx.y * (long long)blockDim.x + threadIdx.x; e < nc * d; e += (long long)gridDim.y * blockDim.x) {
+    const int a = (int)(e / nc);
+    const long long pos = e - a * nc;
+    if (owned_p[base + pos]) z[a * N + gmap_p[base + pos]] = (V)loc[base * d + e];
+  }
+}
+
+// Wavefront sweeps: thread <-> (i, j) column; at step L the column's cell is k = L - i - 2j.
+// In-plane neighbours and the own column's previous cell are read from a ring of 4 planes
+// indexed by k mod 4 (a neighbour of level L-1..L-3 is never overwritten before it is read).
+struct SweepBox {
+  int nx, ny, nz, levels, ncols;
+  long long base, nc;
+};
+
+__device__ __forceinline__ SweepBox sweep_box(const long long* cell_off, const int* dims, int sd) {
+  SweepBox b;
+  b.nx = dims[3 * sd], b.ny = dims[3 * sd + 1], b.nz = dims[3 * sd + 2];
+  b.levels = (b.nx - 1) + 2 * (b.ny - 1) + (b.nz - 1) + 1;
+  b.ncols = b.nx * b.ny;
+  b.base = cell_off[sd];
+  b.nc = cell_off[sd + 1] - b.base;
+  return b;
+}
+
+// level start offsets and per-(level, row) offsets of the wavefront order
+__device__ __forceinline__ void build_tables(const SweepBox& b, int* lvl, int* rowoff) {
+  for (int L = threadIdx.x; L < b.levels; L += blockDim.x) {
+    int cnt = 0;
+    for (int j = 0; j < b.ny; ++j) {
+      rowoff[L * b.ny + j] = cnt;
+      const int lo = max(0, L - 2 * j - (b.nz - 1)), hi = min(b.nx - 1, L - 2 * j);
+      if (hi >= lo) cnt += hi - lo + 1;
+    }
+    lvl[L + 1] = cnt;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    lvl[0] = 0;
+    for (int L = 0; L < b.levels; ++L) lvl[L + 1] += lvl[L];
+  }
+  __syncthreads();
+}
+
+template <class T, int D>
+__global__ void __launch_bounds__(1024) ras_fwd_kernel(long long N, const long long* __restrict__ cell_off,
+                                                       const int* __restrict__ dims, const int* __restrict__ lpt,
+                                                       const T* __restrict__ F, T* __restrict__ loc, T* ring_g,
+                                                       int ring_in_smem, int max_cols) {
+  extern __shared__ __align__(16) unsigned char smem[];
   const int sd = lpt[blockIdx.x];
-  const long long base = cell_off[sd];
-  const Box b{dims[3 * sd], dims[3 * sd + 1], dims[3 * sd + 2]};
-  const int* lo = level_off + (size_t)sd * (max_levels + 1);
-  const int levels = (b.nx - 1) + 2 * (b.ny - 1) + (b.nz - 1) + 1;
-  for (int L = levels - 1; L >= 0; --L) {
-    for (int idx = lo[L] + threadIdx.x; idx < lo[L + 1]; idx += blockDim.x) {
-      const int c = order[base + idx];
-      const int li = c % b.nx, lj = (c / b.nx) % b.ny, lk = c / (b.nx * b.ny);
-      const long long C = base + c;
-      const bool own = owned[C];
-      const long long g = gmap[C];
-      for (int a = d - 1; a >= 0; --a) {
-        double x = work[C * d + a];
-        for (int bb = a + 1; bb < d; ++bb) x -= diag[(C * d + a) * d + bb] * work[C * d + bb];
-        for (int s = 6; s < 11; ++s) {
-          if (!b.in(li + kSlot[s][0], lj + kSlot[s][1], lk + kSlot[s][2])) continue;
-          x -= off[(C * 11 + s) * d + a] * work[(C + slot_delta(b, s)) * d + a];
-        }
-        x /= diag[(C * d + a) * d + a];
-        work[C * d + a] = x;
-        if (own) z[a * N + g] = x;
+  const SweepBox b = sweep_box(cell_off, dims, sd);
+  const size_t ring_bytes = ring_in_smem ? ((4 * (size_t)max_cols * D * sizeof(T) + 15) / 16 * 16) : 0;
+  T* ring = ring_in_smem ? (T*)smem : ring_g + (size_t)blockIdx.x * 4 * max_cols * D;
+  int* lvl = (int*)(smem + ring_bytes);
+  int* rowoff = lvl + b.levels + 1;
+  build_tables(b, lvl, rowoff);
+  constexpr int Q = 10 * D + D * D;
+  const T* Fb = F + b.base * Q;
+  T* Lb = loc + b.base * D;
+  const long long nc = b.nc;
+  for (int L = 0; L < b.levels; ++L) {
+    for (int col = threadIdx.x; col < b.ncols; col += blockDim.x) {
+      const int j = col / b.nx, i = col - j * b.nx, k = L - i - 2 * j;
+      if (k < 0 || k >= b.nz) continue;
+      const long long pos = lvl[L] + rowoff[L * b.ny + j] + i - max(0, L - 2 * j - (b.nz - 1));
+      const int pk = k & 3;
+      T* rp = ring + (size_t)(pk * b.ncols) * D;
+      const T* r0 = ring + (size_t)(((k - 1) & 3) * b.ncols + col) * D;
+      double y[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) y[a] = (double)Lb[a * nc + pos];
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        if (k > 0) y[a] -= (double)Fb[(0 * D + a) * nc + pos] * (double)r0[a];
+        if (i > 0 && j > 0) y[a] -= (double)Fb[(1 * D + a) * nc + pos] * (double)rp[(col - b.nx - 1) * D + a];
+        if (j > 0) y[a] -= (double)Fb[(2 * D + a) * nc + pos] * (double)rp[(col - b.nx) * D + a];
+        if (j > 0 && i + 1 < b.nx) y[a] -= (double)Fb[(3 * D + a) * nc + pos] * (double)rp[(col - b.nx + 1) * D + a];
+        if (i > 0) y[a] -= (double)Fb[(4 * D + a) * nc + pos] * (double)rp[(col - 1) * D + a];
+#pragma unroll
+        for (int c = 0; c < a; ++c) y[a] -= (double)Fb[(5 * D + a * D + c) * nc + pos] * y[c];
+      }
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        rp[col * D + a] = (T)y[a];
+        Lb[a * nc + pos] = (T)y[a];
       }
     }
     __syncthreads();
   }
 }
 
-fv_status ras_apply(const fv_system* s, const double* r, double* z, cudaStream_t st) {
+template <class T, int D>
+__global__ void __launch_bounds__(1024) ras_bwd_kernel(long long N, const long long* __restrict__ cell_off,
+                                                       const int* __restrict__ dims, const int* __restrict__ lpt,
+                                                       const T* __restrict__ F, T* __restrict__ loc, T* ring_g,
+                                                       int ring_in_smem, int max_cols) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int sd = lpt[blockIdx.x];
+  const SweepBox b = sweep_box(cell_off, dims, sd);
+  const size_t ring_bytes = ring_in_smem ? ((4 * (size_t)max_cols * D * sizeof(T) + 15) / 16 * 16) : 0;
+  T* ring = ring_in_smem ? (T*)smem : ring_g + (size_t)blockIdx.x * 4 * max_cols * D;
+  int* lvl = (int*)(smem + ring_bytes);
+  int* rowoff = lvl + b.levels + 1;
+  build_tables(b, lvl, rowoff);
+  constexpr int Q = 10 * D + D * D;
+  const T* Fb = F + b.base * Q;
+  T* Lb = loc + b.base * D;
+  const long long nc = b.nc;
+  for (int L = b.levels - 1; L >= 0; --L) {
+    for (int col = threadIdx.x; col < b.ncols; col += blockDim.x) {
+      const int j = col / b.nx, i = col - j * b.nx, k = L - i - 2 * j;
+      if (k < 0 || k >= b.nz) continue;
+      const long long pos = lvl[L] + rowoff[L * b.ny + j] + i - max(0, L - 2 * j - (b.nz - 1));
+      T* rp = ring + (size_t)((k & 3) * b.ncols) * D;
+      const T* r1 = ring + (size_t)(((k + 1) & 3) * b.ncols + col) * D;
+      double x[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) x[a] = (double)Lb[a * nc + pos];
+#pragma unroll
+      for (int a = D - 1; a >= 0; --a) {
+#pragma unroll
+        for (int c = a + 1; c < D; ++c) x[a] -= (double)Fb[(5 * D + a * D + c) * nc + pos] * x[c];
+        const int U = 5 * D + D * D;
+        if (i + 1 < b.nx) x[a] -= (double)Fb[(U + 0 * D + a) * nc + pos] * (double)rp[(col + 1) * D + a];
+        if (i > 0 && j + 1 < b.ny) x[a] -= (double)Fb[(U + 1 * D + a) * nc + pos] * (double)rp[(col + b.nx - 1) * D + a];
+        if (j + 1 < b.ny) x[a] -= (double)Fb[(U + 2 * D + a) * nc + pos] * (double)rp[(col + b.nx) * D + a];
+        if (i + 1 < b.nx && j + 1 < b.ny)
+          x[a] -= (double)Fb[(U + 3 * D + a) * nc + pos] * (double)rp[(col + b.nx + 1) * D + a];
+        if (k + 1 < b.nz) x[a] -= (double)Fb[(U + 4 * D + a) * nc + pos] * (double)r1[a];
+        x[a] /= (double)Fb[(5 * D + a * D + a) * nc + pos];
+      }
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        rp[col * D + a] = (T)x[a];
+        Lb[a * nc + pos] = (T)x[a];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <class T, int D, class V>
+static fv_status ras_apply_t(const fv_system* s, const V* r, V* z, cudaStream_t st) {
   const Subdomains& S = s->subs;
   const long long N = s->grid->geo.N;
+  T* loc = (T*)S.loc;
+  const dim3 gs(S.count, 4);
   {
-  ProfScope ps(FV_K_RAS_FWD + FV_K_COARSE * s->level, st);
-  ras_forward_kernel<<<S.count, 256, 0, st>>>(S.d, N, S.cell_off, S.dims, S.level_off, S.max_levels, S.order, S.lpt,
-                                               S.gmap, S.off, S.diag, r, S.work);
+    ProfScope ps(FV_K_RAS_FWD + FV_K_COARSE * s->level, st);
+    gather_kernel<T, V><<<gs, 256, 0, st>>>(D, N, S.cell_off, S.gmap_p, r, loc);
+    ras_fwd_kernel<T, D><<<S.count, S.threads, S.smem, st>>>(N, S.cell_off, S.dims, S.lpt, (const T*)S.F, loc,
+                                                             (T*)S.ring, S.ring_in_smem, S.max_cols);
   }
   FV_CUDA(cudaGetLastError());
-  ProfScope ps(FV_K_RAS_BWD + FV_K_COARSE * s->level, st);
-  ras_backward_kernel<<<S.count, 256, 0, st>>>(S.d, N, S.cell_off, S.dims, S.level_off, S.max_levels, S.order,
-                                                S.lpt, S.gmap, S.owned, S.off, S.diag, S.work, z);
+  {
+    ProfScope ps(FV_K_RAS_BWD + FV_K_COARSE * s->level, st);
+    ras_bwd_kernel<T, D><<<S.count, S.threads, S.smem, st>>>(N, S.cell_off, S.dims, S.lpt, (const T*)S.F, loc,
+                                                             (T*)S.ring, S.ring_in_smem, S.max_cols);
+    scatter_kernel<T, V><<<gs, 256, 0, st>>>(D, N, S.cell_off, S.gmap_p, S.owned_p, loc, z);
+  }
   FV_CUDA(cudaGetLastError());
   return FV_OK;
 }
 
+// The limit is a property of the kernel function, shared by every system that launches it:
+// raise it to the device's opt-in maximum (never lower it for a smaller system).
+template <class T, int D>
+static fv_status set_smem_attr(int limit) {
+  FV_CUDA(cudaFuncSetAttribute(ras_fwd_kernel<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+  FV_CUDA(cudaFuncSetAttribute(ras_bwd_kernel<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+  return FV_OK;
+}
+
+fv_status sweeps_smem_attr(const fv_system* s) {
+  const Subdomains& S = s->subs;
+  int dev = 0, limit = 0;
+  FV_CUDA(cudaGetDevice(&dev));
+  FV_CUDA(cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (S.smem > (size_t)limit) return set_error("fv_assemble_system: sweep tables exceed shared memory"), FV_EINVAL;
+  if (S.d == 2) return S.fp32 ? set_smem_attr<float, 2>(limit) : set_smem_attr<double, 2>(limit);
+  return S.fp32 ? set_smem_attr<float, 7>(limit) : set_smem_attr<double, 7>(limit);
+}
+
+fv_status ras_apply(const fv_system* s, const double* r, double* z, cudaStream_t st) {
+  const Subdomains& S = s->subs;
+  if (S.fp32) return set_error("ras_apply: FP32 factors need FP32 vectors"), FV_EINVAL;
+  if (S.d == 2) return ras_apply_t<double, 2, double>(s, r, z, st);
+  return ras_apply_t<double, 7, double>(s, r, z, st);
+}
+
+static fv_status ras_apply32(const fv_system* s, const float* r, float* z, cudaStream_t st) {
+  const Subdomains& S = s->subs;
+  if (!S.fp32) return set_error("ras_apply32: FP64 factors need FP64 vectors"), FV_EINVAL;
+  if (S.d == 2) return ras_apply_t<float, 2, float>(s, r, z, st);
+  return ras_apply_t<float, 7, float>(s, r, z, st);
+}
+
 // ------------------------------------------------------------------ two levels
-__global__ void restrict_kernel(int d, int Ns, int Nr, const double* __restrict__ x, double* __restrict__ xc) {
+template <class T>
+__global__ void restrict_kernel(int d, int Ns, int Nr, const T* __restrict__ x, T* __restrict__ xc) {
   const int nc = Ns / 2, mc = Nr / 2;
   const long long Nc = 6LL * nc * nc * mc, N = 6LL * Ns * Ns * Nr;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < d * Nc;
@@ -324,17 +576,18 @@ __global__ void restrict_kernel(int d, int Ns, int Nr, const double* __restrict_
     r /= mc;
     const int p = (int)(r % 6);
     const int a = (int)(r / 6);
-    const double* xa = x + a * N;
-    double sum = 0.0;
+    const T* xa = x + a * N;
+    T sum = T(0);
     for (int dk = 0; dk < 2; ++dk)
       for (int dj = 0; dj < 2; ++dj)
         for (int di = 0; di < 2; ++di)
           sum += xa[((long long)(p * Nr + 2 * k + dk) * Ns + 2 * j + dj) * Ns + 2 * i + di];
-    xc[e] = sum * 0.125;
+    xc[e] = sum * T(0.125);
   }
 }
 
-__global__ void prolong_kernel(int d, int Ns, int Nr, const double* __restrict__ xc, double* __restrict__ x) {
+template <class T>
+__global__ void prolong_kernel(int d, int Ns, int Nr, const T* __restrict__ xc, T* __restrict__ x) {
   const int nc = Ns / 2, mc = Nr / 2;
   const long long N = 6LL * Ns * Ns * Nr, Nc = 6LL * nc * nc * mc;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < d * N;
@@ -357,21 +610,45 @@ static int nblocks(long long n) {
   return (int)std::min<long long>(std::max<long long>(b, 1), 152LL * 32);
 }
 
-fv_status restrict_mean(const fv_grid* g, int d, const double* x, double* xc, cudaStream_t st) {
+template <class T>
+static fv_status restrict_t(const fv_grid* g, int d, const T* x, T* xc, cudaStream_t st) {
   ProfScope ps(FV_K_TRANSFER, st);
-  restrict_kernel<<<nblocks(d * g->h.N / 8), 256, 0, st>>>(d, g->h.Ns, g->h.Nr, x, xc);
+  restrict_kernel<T><<<nblocks(d * g->h.N / 8), 256, 0, st>>>(d, g->h.Ns, g->h.Nr, x, xc);
   FV_CUDA(cudaGetLastError());
   return FV_OK;
+}
+
+template <class T>
+static fv_status prolong_t(const fv_grid* g, int d, const T* xc, T* x, cudaStream_t st) {
+  ProfScope ps(FV_K_TRANSFER, st);
+  prolong_kernel<T><<<nblocks(d * g->h.N), 256, 0, st>>>(d, g->h.Ns, g->h.Nr, xc, x);
+  FV_CUDA(cudaGetLastError());
+  return FV_OK;
+}
+
+fv_status restrict_mean(const fv_grid* g, int d, const double* x, double* xc, cudaStream_t st) {
+  return restrict_t<double>(g, d, x, xc, st);
 }
 
 fv_status prolong_inject(const fv_grid* g, int d, const double* xc, double* x, cudaStream_t st) {
-  ProfScope ps(FV_K_TRANSFER, st);
-  prolong_kernel<<<nblocks(d * g->h.N), 256, 0, st>>>(d, g->h.Ns, g->h.Nr, xc, x);
-  FV_CUDA(cudaGetLastError());
-  return FV_OK;
+  return prolong_t<double>(g, d, xc, x, st);
+}
+
+// Mixed precision: M^{-1} r of the FP64 outer solve is an FP32 inner FGMRES solve.
+static fv_status inner_solve(const fv_system* s, const double* r, double* z, cudaStream_t st) {
+  fv_status rc;
+  if ((rc = to_fp32(s->n, r, s->r32, st))) return rc;
+  FV_CUDA(cudaMemsetAsync(s->x32, 0, s->n * sizeof(float), st));
+  fv_gmres_opts o{s->pc.inner_restart, s->pc.inner_maxit, 0.0, s->pc.inner_rtol};
+  fv_solve_stats is{};
+  rc = gmres32(s, s->r32, s->x32, &o, &is, st);
+  if (rc && rc != FV_ENOCONV) return rc;
+  s->last_inner += is.iters;
+  return to_fp64(s->n, s->x32, z, st);
 }
 
 fv_status precond_apply(const fv_system* s, const double* r, double* z, cudaStream_t st) {
+  if (s->prec32) return inner_solve(s, r, z, st);
   if (s->pc.levels < 2) return ras_apply(s, r, z, st);
   // w = I_c^f A_c^{-1} I_f^c r   (eqn:coarsesolve), inner FGMRES to coarse_rtol
   const fv_system* c = s->coarse;
@@ -405,6 +682,39 @@ fv_status precond_apply(const fv_system* s, const double* r, double* z, cudaStre
   }
   ProfScope ph(FV_K_PHASE_PC_I, st);
   return axpby(s->n, 1.0, z, 1.0, s->w, z, st);
+}
+
+// The same preconditioners on FP32 vectors (inner solves of mixed precision)
+fv_status precond_apply32(const fv_system* s, const float* r, float* z, cudaStream_t st) {
+  if (s->pc.levels < 2) return ras_apply32(s, r, z, st);
+  const fv_system* c = s->coarse;
+  fv_status rc;
+  {
+    ProfScope ph(FV_K_PHASE_PC_I, st);
+    if ((rc = restrict_t<float>(s->grid, s->d, r, s->xc32, st))) return rc;
+    if (s->kind == FV_PPBE && (rc = weighted_mean_remove32(c->grid, s->xc32, st, s->red, s->red + 32 * 304)))
+      return rc;
+    FV_CUDA(cudaMemsetAsync(s->ec32, 0, c->n * sizeof(float), st));
+  }
+  {
+    ProfScope ph(FV_K_PHASE_PC_C, st);
+    fv_gmres_opts o{s->pc.coarse_restart, s->pc.coarse_maxit, 0.0, s->pc.coarse_rtol};
+    fv_solve_stats cs{};
+    rc = gmres32(c, s->xc32, s->ec32, &o, &cs, st);
+    if (rc && rc != FV_ENOCONV) return rc;
+  }
+  {
+    ProfScope ph(FV_K_PHASE_PC_I, st);
+    if ((rc = prolong_t<float>(s->grid, s->d, s->ec32, s->w32, st))) return rc;
+    if ((rc = apply_op32(s, s->w32, s->t32, st))) return rc;
+    if ((rc = axpby32(s->n, 1.0, r, -1.0, s->t32, s->t32, st))) return rc;
+  }
+  {
+    ProfScope ph(FV_K_PHASE_PC_F, st);
+    if ((rc = ras_apply32(s, s->t32, z, st))) return rc;
+  }
+  ProfScope ph(FV_K_PHASE_PC_I, st);
+  return axpby32(s->n, 1.0, z, 1.0, s->w32, z, st);
 }
 
 }  // namespace fv

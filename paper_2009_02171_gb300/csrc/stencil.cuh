@@ -28,23 +28,26 @@ __device__ __constant__ static const signed char kPM[6][9] = {
     {0, 1, 0, -1, 0, 0, 0, 0, 1}, {0, 0, -1, 0, 1, 0, 1, 0, 0}, {0, 0, 1, 0, 1, 0, -1, 0, 0},
 };
 
-__device__ __forceinline__ void rotate(int p, const double* l, double* v) {
+template <class R>
+__device__ __forceinline__ void rotate(int p, const R* l, R* v) {
 #pragma unroll
   for (int a = 0; a < 3; ++a) v[a] = kPM[p][3 * a] * l[0] + kPM[p][3 * a + 1] * l[1] + kPM[p][3 * a + 2] * l[2];
 }
 
-__device__ __forceinline__ long long cidx(const Geo& G, int p, int k, int j, int i) {
-  return ((long long)(p * G.Nr + k) * G.Ns + j) * G.Ns + i;
+template <class GT>
+__device__ __forceinline__ long long cidx(const GT& G, int p, int k, int j, int i) {
+  return (long long)(((p * G.Nr + k) * G.Ns + j) * G.Ns + i);
 }
 
 // ghost layer: [comp][p][side][k][t+1], t in [-1, Ns] (corners stored on xi sides)
-__device__ __forceinline__ long long gidx(const Geo& G, int comp, int p, int side, int k, int t) {
+template <class GT>
+__device__ __forceinline__ long long gidx(const GT& G, int comp, int p, int side, int k, int t) {
   return ((((long long)comp * 6 + p) * 4 + side) * G.Nr + k) * (G.Ns + 2) + (t + 1);
 }
 
 // value at extended horizontal position (j, i in [-1, Ns]) of panel p, level k
-template <class Acc>
-__device__ inline void emit_h(const Geo& G, Acc& acc, double c, int p, int k, int j, int i, int comp) {
+template <class GT, class Acc>
+__device__ inline void emit_h(const GT& G, Acc& acc, typename GT::real c, int p, int k, int j, int i, int comp) {
   const int Ns = G.Ns;
   if (i >= 0 && i < Ns) {
     if (j >= 0 && j < Ns)
@@ -57,10 +60,10 @@ __device__ inline void emit_h(const Geo& G, Acc& acc, double c, int p, int k, in
 }
 
 // one-sided flux through the xi face f (between cells f-1 and f) of row j
-template <class Acc>
-__device__ inline void xi_flux(const Geo& G, Acc& acc, double s, int p, int k, int j, int f, int comp) {
+template <class GT, class Acc>
+__device__ inline void xi_flux(const GT& G, Acc& acc, typename GT::real s, int p, int k, int j, int f, int comp) {
   const int id = j * (G.Ns + 1) + f;
-  const double a = G.ax11[id] * s, b = G.ax12[id] * s;
+  const typename GT::real a = G.ax11[id] * s, b = G.ax12[id] * s;
   emit_h(G, acc, a, p, k, j, f, comp);
   emit_h(G, acc, -a, p, k, j, f - 1, comp);
   emit_h(G, acc, b, p, k, j + 1, f - 1, comp);
@@ -70,10 +73,10 @@ __device__ inline void xi_flux(const Geo& G, Acc& acc, double s, int p, int k, i
 }
 
 // one-sided flux through the eta face f (between rows f-1 and f) of column i
-template <class Acc>
-__device__ inline void eta_flux(const Geo& G, Acc& acc, double s, int p, int k, int f, int i, int comp) {
+template <class GT, class Acc>
+__device__ inline void eta_flux(const GT& G, Acc& acc, typename GT::real s, int p, int k, int f, int i, int comp) {
   const int id = f * G.Ns + i;
-  const double a = G.ay22[id] * s, b = G.ay12[id] * s;
+  const typename GT::real a = G.ay22[id] * s, b = G.ay12[id] * s;
   emit_h(G, acc, a, p, k, f, i, comp);
   emit_h(G, acc, -a, p, k, f - 1, i, comp);
   emit_h(G, acc, b, p, k, f - 1, i + 1, comp);
@@ -82,8 +85,8 @@ __device__ inline void eta_flux(const Geo& G, Acc& acc, double s, int p, int k, 
   emit_h(G, acc, -b, p, k, f, i - 1, comp);
 }
 
-template <class Acc>
-__device__ __noinline__ void own_side_flux(const Geo& G, Acc& acc, double s, int p, int side, int k, int t,
+template <class GT, class Acc>
+__device__ __noinline__ void own_side_flux(const GT& G, Acc& acc, typename GT::real s, int p, int side, int k, int t,
                                               int comp) {
   const int Ns = G.Ns;
   switch (side) {
@@ -95,23 +98,24 @@ __device__ __noinline__ void own_side_flux(const Geo& G, Acc& acc, double s, int
 }
 
 // panel-edge face: mean of the two panels' one-sided fluxes (measured along p's coordinate)
-template <class Acc>
-__device__ __noinline__ void edge_flux(const Geo& G, Acc& acc, double s, int p, int side, int k, int t, int comp) {
+template <class GT, class Acc>
+__device__ __noinline__ void edge_flux(const GT& G, Acc& acc, typename GT::real s, int p, int side, int k, int t, int comp) {
   const int ps = p * 4 + side;
-  own_side_flux(G, acc, 0.5 * s, p, side, k, t, comp);
-  own_side_flux(G, acc, 0.5 * s * G.psgn[ps], G.pq[ps], G.psq[ps], k, G.ptmap[ps * G.Ns + t], comp);
+  using R = typename GT::real;
+  own_side_flux(*G.self, acc, R(0.5) * s, p, side, k, t, comp);
+  own_side_flux(*G.self, acc, R(0.5) * s * R(G.psgn[ps]), G.pq[ps], G.psq[ps], k, G.ptmap[ps * G.Ns + t], comp);
 }
 
 // wall ghost of component `comp` at the cell (kc, j, i) next to a wall
-template <class Acc>
-__device__ __forceinline__ void wall_ghost(const Geo& G, Acc& acc, double c, int p, int kc, int j, int i, int comp,
-                                           int wall, int bbase, double fac) {
+template <class GT, class Acc>
+__device__ __forceinline__ void wall_ghost(const GT& G, Acc& acc, typename GT::real c, int p, int kc, int j, int i, int comp,
+                                           int wall, int bbase, typename GT::real fac) {
   if (wall == WALL_ODD) {
     acc.cell(-c, p, kc, j, i, comp);
   } else if (wall == WALL_EVEN) {
     acc.cell(c, p, kc, j, i, comp);
   } else {
-    double rh[3];
+    typename GT::real rh[3];
     rotate(p, G.xhat + 3 * (j * G.Ns + i), rh);
     const int a = comp - bbase;
     acc.cell(-c, p, kc, j, i, comp);
@@ -121,10 +125,10 @@ __device__ __forceinline__ void wall_ghost(const Geo& G, Acc& acc, double c, int
 }
 
 // radial flux through face kf (between k = kf-1 and kf) of column (j, i)
-template <class Acc>
-__device__ __forceinline__ void r_flux(const Geo& G, Acc& acc, double s, int p, int kf, int j, int i, int comp,
+template <class GT, class Acc>
+__device__ __forceinline__ void r_flux(const GT& G, Acc& acc, typename GT::real s, int p, int kf, int j, int i, int comp,
                                        int wall, int bbase) {
-  const double c = G.crf[j * G.Ns + i] * G.rf2[kf] * s;
+  const typename GT::real c = G.crf[j * G.Ns + i] * G.rf2[kf] * s;
   if (kf > 0 && kf < G.Nr) {
     acc.cell(c, p, kf, j, i, comp);
     acc.cell(-c, p, kf - 1, j, i, comp);
@@ -138,10 +142,10 @@ __device__ __forceinline__ void r_flux(const Geo& G, Acc& acc, double s, int p, 
 }
 
 // interior xi / eta fluxes: every value is a cell of panel p (1 <= i, j <= Ns-2)
-template <class Acc>
-__device__ __forceinline__ void xi_flux_in(const Geo& G, Acc& acc, double s, int p, int k, int j, int f, int comp) {
+template <class GT, class Acc>
+__device__ __forceinline__ void xi_flux_in(const GT& G, Acc& acc, typename GT::real s, int p, int k, int j, int f, int comp) {
   const int id = j * (G.Ns + 1) + f;
-  const double a = G.ax11[id] * s, b = G.ax12[id] * s;
+  const typename GT::real a = G.ax11[id] * s, b = G.ax12[id] * s;
   acc.cell(a, p, k, j, f, comp);
   acc.cell(-a, p, k, j, f - 1, comp);
   acc.cell(b, p, k, j + 1, f - 1, comp);
@@ -150,10 +154,10 @@ __device__ __forceinline__ void xi_flux_in(const Geo& G, Acc& acc, double s, int
   acc.cell(-b, p, k, j - 1, f, comp);
 }
 
-template <class Acc>
-__device__ __forceinline__ void eta_flux_in(const Geo& G, Acc& acc, double s, int p, int k, int f, int i, int comp) {
+template <class GT, class Acc>
+__device__ __forceinline__ void eta_flux_in(const GT& G, Acc& acc, typename GT::real s, int p, int k, int f, int i, int comp) {
   const int id = f * G.Ns + i;
-  const double a = G.ay22[id] * s, b = G.ay12[id] * s;
+  const typename GT::real a = G.ay22[id] * s, b = G.ay12[id] * s;
   acc.cell(a, p, k, f, i, comp);
   acc.cell(-a, p, k, f - 1, i, comp);
   acc.cell(b, p, k, f - 1, i + 1, comp);
@@ -163,8 +167,8 @@ __device__ __forceinline__ void eta_flux_in(const Geo& G, Acc& acc, double s, in
 }
 
 // horizontal part of s * lap at a cell on a panel edge (i or j in {0, Ns-1})
-template <class Acc>
-__device__ __noinline__ void lap_h_edge(const Geo& G, Acc& acc, double sv, int p, int k, int j, int i, int comp) {
+template <class GT, class Acc>
+__device__ __noinline__ void lap_h_edge(const GT& G, Acc& acc, typename GT::real sv, int p, int k, int j, int i, int comp) {
   const int Ns = G.Ns;
   if (i + 1 == Ns) edge_flux(G, acc, sv, p, XI_MAX, k, j, comp);
   else xi_flux(G, acc, sv, p, k, j, i + 1, comp);
@@ -177,18 +181,20 @@ __device__ __noinline__ void lap_h_edge(const Geo& G, Acc& acc, double sv, int p
 }
 
 // s * lap(phi_comp) at cell (p, k, j, i)
-template <class Acc>
-__device__ __forceinline__ void lap_row(const Geo& G, Acc& acc, double s, int p, int k, int j, int i, int comp,
+template <class GT, class Acc>
+__device__ __forceinline__ void lap_row(const GT& G, Acc& acc, typename GT::real s, int p, int k, int j, int i, int comp,
                                         int wall, int bbase) {
   const int Ns = G.Ns;
-  const double sv = s * G.invsig[j * Ns + i] * G.invr2[k];
+  const typename GT::real sv = s * G.invsig[j * Ns + i] * G.invr2[k];
   if (i > 0 && j > 0 && i + 1 < Ns && j + 1 < Ns) {
     xi_flux_in(G, acc, sv, p, k, j, i + 1, comp);
     xi_flux_in(G, acc, -sv, p, k, j, i, comp);
     eta_flux_in(G, acc, sv, p, k, j + 1, i, comp);
     eta_flux_in(G, acc, -sv, p, k, j, i, comp);
   } else {
-    lap_h_edge(G, acc, sv, p, k, j, i, comp);
+    Acc tmp = acc;  // only the copy's address escapes into the out-of-line edge path
+    lap_h_edge(*G.self, tmp, sv, p, k, j, i, comp);
+    acc = tmp;
   }
   r_flux(G, acc, sv, p, k + 1, j, i, comp, wall, bbase);
   r_flux(G, acc, -sv, p, k, j, i, comp, wall, bbase);
@@ -202,47 +208,55 @@ struct Phys {
 //   u_a:   u - dt/2 [lap u - (2/E) z x u + Ra/(E r_o) Theta r]_a
 //   Theta: Theta - dt/2 [lap Theta / Pr + r_i r_o / r^3 (u . r)]
 //   B_a:   B - dt/2 [lap B / Pm]_a
-template <class Acc>
-__device__ __forceinline__ void vtbe_row(const Geo& G, const Phys& ph, Acc& acc, int p, int k, int j, int i, int a) {
-  const double h = -0.5 * ph.dt;
-  acc.cell(1.0, p, k, j, i, a);
+template <class GT, class Acc>
+__device__ __forceinline__ void vtbe_row(const GT& G, const Phys& ph, Acc& acc, int p, int k, int j, int i, int a) {
+  using R = typename GT::real;
+  const R h = R(-0.5 * ph.dt);
+  acc.cell(R(1), p, k, j, i, a);
   if (a < 3) {
     lap_row(G, acc, h, p, k, j, i, a, WALL_ODD, 0);
-    if (a == 0) acc.cell(h * (2.0 / ph.E), p, k, j, i, 1);
-    if (a == 1) acc.cell(-h * (2.0 / ph.E), p, k, j, i, 0);
-    double xl[3], x[3];
+    if (a == 0) acc.cell(R(h * (2.0 / ph.E)), p, k, j, i, 1);
+    if (a == 1) acc.cell(R(-h * (2.0 / ph.E)), p, k, j, i, 0);
+    R xl[3], x[3];
     for (int c = 0; c < 3; ++c) xl[c] = G.xhat[3 * (j * G.Ns + i) + c];
     rotate(p, xl, x);
-    acc.cell(h * ph.Ra / (ph.E * G.ro) * G.rc[k] * x[a], p, k, j, i, 3);
+    acc.cell(R(h * ph.Ra / (ph.E * (double)G.ro)) * G.rc[k] * x[a], p, k, j, i, 3);
   } else if (a == 3) {
-    lap_row(G, acc, h / ph.Pr, p, k, j, i, 3, WALL_ODD, 0);
-    double xl[3], x[3];
+    lap_row(G, acc, R(h / ph.Pr), p, k, j, i, 3, WALL_ODD, 0);
+    R xl[3], x[3];
     for (int c = 0; c < 3; ++c) xl[c] = G.xhat[3 * (j * G.Ns + i) + c];
     rotate(p, xl, x);
-    const double r = G.rc[k];
+    const R r = G.rc[k];
     for (int c = 0; c < 3; ++c) acc.cell(h * G.ri * G.ro / (r * r) * x[c], p, k, j, i, c);
   } else {
-    lap_row(G, acc, h / ph.Pm, p, k, j, i, a, WALL_B, 4);
+    lap_row(G, acc, R(h / ph.Pm), p, k, j, i, a, WALL_B, 4);
   }
 }
 
 // Row `a` of the PPBE matrix dt/2 D G = dt/(2E) lap (eqn:tsp, eqn:tspb): P even walls, P_b odd walls
-template <class Acc>
-__device__ __forceinline__ void ppbe_row(const Geo& G, const Phys& ph, Acc& acc, int p, int k, int j, int i, int a) {
-  lap_row(G, acc, 0.5 * ph.dt / ph.E, p, k, j, i, a, a == 0 ? WALL_EVEN : WALL_ODD, 0);
+template <class GT, class Acc>
+__device__ __forceinline__ void ppbe_row(const GT& G, const Phys& ph, Acc& acc, int p, int k, int j, int i, int a) {
+  using R = typename GT::real;
+  lap_row(G, acc, R(0.5 * ph.dt / ph.E), p, k, j, i, a, a == 0 ? WALL_EVEN : WALL_ODD, 0);
 }
 
-template <class T>
+// T: element type of x and the ghost layer; R: accumulation type (FP64 for the
+// FP64 path, FP32 for the inner solves of mixed precision)
+template <class T, class R = double>
 struct ApplyAcc {
-  const Geo* G;
+  long long N;
+  int Ns, Nr;
   const T* x;
   const T* gh;
-  double sum;
-  __device__ __forceinline__ void cell(double c, int p, int k, int j, int i, int comp) {
-    sum += c * (double)x[comp * G->N + cidx(*G, p, k, j, i)];
+  R sum;
+  template <class GT>
+  __device__ __forceinline__ ApplyAcc(const GT& G, const T* x_, const T* gh_)
+      : N(G.N), Ns(G.Ns), Nr(G.Nr), x(x_), gh(gh_), sum(R(0)) {}
+  __device__ __forceinline__ void cell(R c, int p, int k, int j, int i, int comp) {
+    sum += c * (R)x[(long long)comp * N + (long long)(((p * Nr + k) * Ns + j) * Ns + i)];
   }
-  __device__ __forceinline__ void ghost(double c, int p, int side, int k, int t, int comp) {
-    sum += c * (double)gh[gidx(*G, comp, p, side, k, t)];
+  __device__ __forceinline__ void ghost(R c, int p, int side, int k, int t, int comp) {
+    sum += c * (R)gh[((((long long)comp * 6 + p) * 4 + side) * Nr + k) * (Ns + 2) + (t + 1)];
   }
 };
 

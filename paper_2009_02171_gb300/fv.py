@@ -15,6 +15,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, 'libfv.so')
 
 FV_VTBE, FV_PPBE = 0, 1
+FV_PREC_FP64, FV_PREC_FP32 = 0, 1
 ERRORS = {-1: 'FV_EINVAL', -2: 'FV_ENOMEM', -3: 'FV_ECUDA', -4: 'FV_ENOCONV', -5: 'FV_EBREAKDOWN', -6: 'FV_ENAN'}
 
 
@@ -35,7 +36,8 @@ class fv_phys(ctypes.Structure):
 class fv_pc_desc(ctypes.Structure):
     _fields_ = [('p1', ctypes.c_int), ('p2', ctypes.c_int), ('p3', ctypes.c_int), ('overlap', ctypes.c_int),
                 ('levels', ctypes.c_int), ('overlap_coarse', ctypes.c_int), ('coarse_rtol', ctypes.c_double),
-                ('coarse_restart', ctypes.c_int), ('coarse_maxit', ctypes.c_int)]
+                ('coarse_restart', ctypes.c_int), ('coarse_maxit', ctypes.c_int), ('precision', ctypes.c_int),
+                ('inner_rtol', ctypes.c_double), ('inner_restart', ctypes.c_int), ('inner_maxit', ctypes.c_int)]
 
 
 class fv_gmres_opts(ctypes.Structure):
@@ -111,9 +113,11 @@ def fv_build_grid(Ns, Nr, ri=7.0 / 13.0, ro=20.0 / 13.0):
 
 
 def fv_assemble_system(grid, kind, E, Ra, Pr, Pm, dt, p=(1, 1, 1), overlap=1, levels=1, overlap_coarse=1,
-                       coarse_rtol=0.1, coarse_restart=30, coarse_maxit=30):
+                       coarse_rtol=0.1, coarse_restart=30, coarse_maxit=30, precision=FV_PREC_FP64, inner_rtol=1e-3,
+                       inner_restart=30, inner_maxit=30):
     h = ctypes.c_void_p()
-    pc = fv_pc_desc(p[0], p[1], p[2], overlap, levels, overlap_coarse, coarse_rtol, coarse_restart, coarse_maxit)
+    pc = fv_pc_desc(p[0], p[1], p[2], overlap, levels, overlap_coarse, coarse_rtol, coarse_restart, coarse_maxit,
+                    precision, inner_rtol, inner_restart, inner_maxit)
     _check(lib.fv_assemble_system(grid, kind, ctypes.byref(fv_phys(E, Ra, Pr, Pm, dt)), ctypes.byref(pc),
                                   ctypes.byref(h)))
     return h

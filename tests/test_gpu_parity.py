@@ -154,3 +154,58 @@ def test_bad_arguments_raise(fv):
     with pytest.raises(fv.FvError):
         fv.fv_assemble_system(g, 1, **PH, p=(10, 1, 1), overlap=1)           # more boxes than cells
     fv.fv_free_grid(g)
+
+
+@pytest.mark.parametrize('kind,levels', [(0, 1), (1, 2)])
+def test_mixed_precision_solve_reaches_fp64_residual(fv, kind, levels):
+    """FP32 inner FGMRES (FP32 operator, FP32 ILU(0) sweeps, FP32 coarse level) as the
+    preconditioner of the FP64 outer FGMRES: the true FP64 residual (oracle matrix) reaches
+    1e-8 and the solution matches the FP64 solution to the conditioning-limited accuracy."""
+    Ns = Nr = 12
+    parts = (2, 2, 2)
+    A, d, disc = _oracle_matrix(kind, Ns, Nr)
+    b = random_vector(A.shape[0], 17)
+    if kind == 1:
+        b[:disc.g.N] -= (disc.V @ b[:disc.g.N]) / disc.V.sum()
+    g = fv.fv_build_grid(Ns, Nr)
+    s64 = fv.fv_assemble_system(g, kind, **PH, p=parts, overlap=1, levels=levels)
+    s32 = fv.fv_assemble_system(g, kind, **PH, p=parts, overlap=1, levels=levels, precision=fv.FV_PREC_FP32,
+                                inner_rtol=1e-3, inner_restart=30, inner_maxit=30)
+    x64 = torch.zeros(A.shape[0], dtype=torch.float64, device='cuda')
+    x32 = torch.zeros_like(x64)
+    st64 = fv.fv_gmres_solve(s64, _dev(b), x64, rtol=1e-8)
+    st32 = fv.fv_gmres_solve(s32, _dev(b), x32, rtol=1e-8)
+    assert st64.converged and st32.converged
+    xs = x32.cpu().numpy()
+    assert np.linalg.norm(b - A @ xs) <= 1.0001e-8 * np.linalg.norm(b)
+    ref = x64.cpu().numpy()
+    if kind == 1:
+        for v in (xs, ref):
+            v[:disc.g.N] -= (disc.V @ v[:disc.g.N]) / disc.V.sum()
+    assert _rel(xs, ref) < 1e-6
+    assert st32.iters <= st64.iters            # each outer step carries an FP32 inner solve
+    for h in (s64, s32):
+        fv.fv_free_system(h)
+    fv.fv_free_grid(g)
+
+
+def test_mixed_precision_time_step_matches_oracle(fv):
+    Ns, Nr, parts = 8, 8, (2, 2, 1)
+    s0 = initial_state(Ns, Nr, 0)
+    N = 6 * Ns * Ns * Nr
+    init = np.concatenate([s0['u'].ravel(), s0['T'], s0['B'].ravel(), s0['P'], s0['Pb']])
+    st_o = Stepper(Grid(Ns, Nr), Physics(**PH), SolverOptions(parts=parts, delta=1, ppbe_levels=2, rtol=1e-10))
+    ref, _ = st_o.step(dict(s0, first=True))
+    g = fv.fv_build_grid(Ns, Nr)
+    mp = dict(precision=fv.FV_PREC_FP32, inner_rtol=1e-3, inner_restart=30, inner_maxit=30)
+    V = fv.fv_assemble_system(g, 0, **PH, p=parts, overlap=1, **mp)
+    P = fv.fv_assemble_system(g, 1, **PH, p=parts, overlap=1, levels=2, **mp)
+    st = fv.fv_state_create(g, _dev(init), **PH)
+    stats = fv.fv_time_step(st, V, P, nsteps=1, rtol=1e-10)
+    assert all(s.converged for s in stats)
+    out = fv.fv_state_get(st, torch.empty(9 * N, dtype=torch.float64, device='cuda')).cpu().numpy()
+    assert _rel(out[:3 * N], ref['u'].ravel()) < 1e-7
+    assert _rel(out[3 * N:4 * N], ref['T']) < 1e-7
+    assert _rel(out[4 * N:7 * N], ref['B'].ravel()) < 1e-7
+    for h, f in ((st, fv.fv_free_state), (V, fv.fv_free_system), (P, fv.fv_free_system), (g, fv.fv_free_grid)):
+        f(h)
