@@ -29,7 +29,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 CFG = dict(Ns=64, Nr=64, p=(2, 2, 4), overlap=2, overlap_coarse=1, levels=2, E=1e-3, Ra=100.0, Pr=1.0, Pm=5.0,
-           dt=1e-4, rtol=1e-8, restart=30, seed=1, inner_rtol=1e-3, inner_restart=30, inner_maxit=30)
+           dt=1e-4, rtol=1e-8, restart=30, seed=1, vtbe_inner=4, ppbe_inner=8, coarse_its=10)
 WORKLOAD = ('shell 6x64^2x64 (1.57M cells), time step: VTBE one-level RAS + PPBE two-level RAS, '
             '96 subdomains overlap 2, FGMRES(30) to 1e-8 relative FP64 residual; mixed precision = FP32 inner '
             'FGMRES (operator, ILU(0) sweeps, coarse level) inside FP64 outer FGMRES')
@@ -48,6 +48,9 @@ def parse():
     ap.add_argument('--precision', default='mixed', choices=['mixed', 'fp64'],
                     help='headline arm; the other one is timed beside it with the same steps')
     ap.add_argument('--single', action='store_true', help='time the headline arm only (profiling runs)')
+    ap.add_argument('--ns', type=int, default=0, help='override Ns = Nr (small profiling cases)')
+    ap.add_argument('--workload', default='step', choices=['step', 'batch'],
+                    help='step: the time step (headline); batch: 32 right-hand sides on uneven subdomains')
     return ap.parse_args()
 
 
@@ -136,6 +139,65 @@ def reference_arm(args, rank, ws):
                       'e2e': {'value': ms, 'unit': 'ms/step', 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0}}))
 
 
+BATCH = dict(Ns=48, Nr=48, nrhs=32, nboxes=512, overlap=2, rtol=1e-8, restart=30)
+
+
+def batch_workload(args, fv, torch, rank, ws):
+    """32 PPBE right-hand sides (seeds 100..131) on 6 x 48^2 x 48 with 512 uneven subdomains
+    (edges 8..24 cells, overlap 2), FP32 subdomain solves in the FP64 outer FGMRES."""
+    import numpy as np
+    from paper_2009_02171_gb300.inputs import random_vector, uneven_boxes
+    c = BATCH
+    boxes = uneven_boxes(c['Ns'], c['Nr'], target=c['nboxes'], seed=0)
+    g = fv.fv_build_grid(c['Ns'], c['Nr'])
+    s = fv.fv_assemble_system(g, fv.FV_PPBE, E=CFG['E'], Ra=CFG['Ra'], Pr=CFG['Pr'], Pm=CFG['Pm'], dt=CFG['dt'],
+                              overlap=c['overlap'], boxes=boxes, precision=fv.FV_PREC_FP32)
+    n = fv.fv_system_size(s)
+    # right-hand sides b = A x for seeded random x: in the range of A, so consistent for the
+    # singular Neumann pressure block
+    Xt = torch.tensor(np.stack([random_vector(n, 100 + r) for r in range(c['nrhs'])]), device='cuda')
+    Bd = torch.empty_like(Xt)
+    for r in range(c['nrhs']):
+        fv.fv_apply_op(s, Xt[r], Bd[r])
+    X = torch.zeros_like(Bd)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(args.warmup):
+        X.zero_()
+        fv.fv_gmres_solve_batch(s, Bd, X, restart=c['restart'], rtol=c['rtol'])
+    with ClockSampler(int(os.environ.get('LOCAL_RANK', '0'))) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            X.zero_()
+            st = fv.fv_gmres_solve_batch(s, Bd, X, restart=c['restart'], rtol=c['rtol'])
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    # the same 32 right-hand sides one at a time (the unbatched reference on the GPU)
+    e0.record(stream)
+    its1 = []
+    for r in range(c['nrhs']):
+        x = torch.zeros(n, dtype=torch.float64, device='cuda')
+        its1.append(fv.fv_gmres_solve(s, Bd[r].contiguous(), x, restart=c['restart'], rtol=c['rtol']).iters)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms1 = e0.elapsed_time(e1)
+    if rank == 0:
+        print(json.dumps({'metric': 'wall time per batched solve of 32 right-hand sides at 1e-8 residual',
+                          'value': round(ms, 3), 'unit': 'ms/solve', 'n_gpus': ws, 'steps': args.steps,
+                          'warmup': args.warmup, 'higher_is_better': False, 'scaling': 'weak',
+                          'dtype': 'f32 subdomain solves / f64 outer', 'data': 'synthetic',
+                          'config': {'workload': 'PPBE 6x48^2x48, 32 RHS b = A x (x seeded 100..131), 512 uneven '
+                                                 'subdomains (edges 8..24) + overlap 2, one-level RAS, FGMRES(30) '
+                                                 'to 1e-8'},
+                          'iterations': [x.iters for x in st], 'converged': all(x.converged for x in st),
+                          'unbatched_ms': round(ms1, 3), 'unbatched_iterations': its1,
+                          'clocks': clk.summary()}))
+    fv.fv_free_system(s)
+    fv.fv_free_grid(g)
+
+
 def main():
     args = parse()
     if args.impl == 'reference':
@@ -152,8 +214,15 @@ def main():
     torch.cuda.set_device(local)
     from paper_2009_02171_gb300 import fv
     from paper_2009_02171_gb300.inputs import initial_state
+    if args.workload == 'batch':
+        batch_workload(args, fv, torch, rank, ws)
+        if ws > 1:
+            dist.destroy_process_group()
+        return
 
-    c = CFG
+    c = dict(CFG)
+    if args.ns:
+        c['Ns'] = c['Nr'] = args.ns
     ph = dict(E=c['E'], Ra=c['Ra'], Pr=c['Pr'], Pm=c['Pm'], dt=c['dt'])
     s0 = initial_state(c['Ns'], c['Nr'], c['seed'] + rank)
     host = np.concatenate([s0['u'].ravel(), s0['T'], s0['B'].ravel(), s0['P'], s0['Pb']])
@@ -164,12 +233,12 @@ def main():
 
     def build(mixed):
         t = time.perf_counter()
-        mp = dict(precision=fv.FV_PREC_FP32, inner_rtol=c['inner_rtol'], inner_restart=c['inner_restart'],
-                  inner_maxit=c['inner_maxit']) if mixed else {}
         g = fv.fv_build_grid(c['Ns'], c['Nr'])
-        V = fv.fv_assemble_system(g, fv.FV_VTBE, **ph, p=c['p'], overlap=c['overlap'], levels=1, **mp)
+        mv = dict(precision=fv.FV_PREC_FP32, inner_maxit=c['vtbe_inner']) if mixed else {}
+        mpp = dict(precision=fv.FV_PREC_FP32, inner_maxit=c['ppbe_inner'], coarse_maxit=c['coarse_its']) if mixed else {}
+        V = fv.fv_assemble_system(g, fv.FV_VTBE, **ph, p=c['p'], overlap=c['overlap'], levels=1, **mv)
         P = fv.fv_assemble_system(g, fv.FV_PPBE, **ph, p=c['p'], overlap=c['overlap'], levels=c['levels'],
-                                  overlap_coarse=c['overlap_coarse'], **mp)
+                                  overlap_coarse=c['overlap_coarse'], **mpp)
         st = fv.fv_state_create(g, torch.tensor(host, device='cuda'), **ph)
         torch.cuda.synchronize()
         return (g, V, P, st), time.perf_counter() - t
@@ -215,17 +284,17 @@ def main():
         free(other)
     h, t_setup = build(mixed)
     g, V, P, st = h
-    ms, iters, clocks = timed(h, args.steps, args.warmup, True)
+    ms, iters, clocks = timed(h, args.steps, args.warmup, False)
+    # kernel breakdown: the same number of steps again with CUDA-event timing on (eager launches)
+    ms_prof, _, _ = timed(h, args.steps, 0, True)
     kern = {}
-    names = ['ghost', 'apply_vtbe', 'apply_ppbe', 'ras_fwd', 'ras_bwd', 'cgs', 'vec', 'glue', 'transfer',
-             'phase_pc_c', 'phase_pc_f', 'phase_pc_i']
-    for k, nm in enumerate(names):
-        for lvl, suffix in ((0, ''), (fv.K_COARSE, '_coarse')):
-            if lvl and k > 8:
-                continue
-            n, t = fv.fv_profile_read(k + lvl)
-            if n:
-                kern[nm + suffix] = {'launches': n, 'ms_total': round(t, 3), 'ms_per_step': round(t / args.steps, 3)}
+    for cat in range(fv.K_COUNT):
+        if cat % 16 not in fv.K_NAMES:
+            continue
+        n, t = fv.fv_profile_read(cat)
+        if n:
+            kern[fv.category_name(cat)] = {'launches': n, 'ms_total': round(t, 3),
+                                           'ms_per_step': round(t / args.steps, 3)}
     fv.fv_profile_enable(False)
 
     # end to end through the C ABI: state host -> device, step, device -> host
@@ -259,7 +328,7 @@ def main():
     ranked = sorted((v['ms_total'], k) for k, v in kern.items() if not k.startswith('phase'))
     roof = None
     for _, top in reversed(ranked):
-        bytes_per = algorithmic_bytes(top, c, N, 4 if mixed else 8)
+        bytes_per = algorithmic_bytes(top, c, N, 8)
         if bytes_per:
             per_launch_ms = kern[top]['ms_total'] / kern[top]['launches']
             ach = bytes_per / (per_launch_ms * 1e-3) / 1e9
@@ -285,7 +354,8 @@ def main():
             ('fp64' if mixed else 'mixed'): {'ms_per_step': round(ms_other, 3),
                                              'iterations_vtbe_ppbe': [(i[0], i[1]) for i in it_other],
                                              'setup_s': round(t_other, 2)},
-            'config': {'workload': WORKLOAD, 'cells': 6 * c['Ns'] ** 2 * c['Nr'], 'subdomains': 6 * 16,
+            'config': {'workload': WORKLOAD if not args.ns else WORKLOAD.replace('64', str(args.ns)),
+                       'cells': 6 * c['Ns'] ** 2 * c['Nr'], 'subdomains': 6 * 16,
                        'overlap': c['overlap'], 'ppbe_levels': c['levels'], 'rtol': c['rtol'],
                        'restart': c['restart'], 'l2': 'working set > L2 (no flush needed)',
                        'parallelism': 'replicas' if ws > 1 else 'single GPU'},
@@ -295,6 +365,8 @@ def main():
             'e2e': {'value': round(ms_e2e, 3), 'unit': 'ms/step', 'h2d_bytes_per_step': 9 * N * 8,
                     'd2h_bytes_per_step': 9 * N * 8},
             'gpu_launches': int(sum(v['launches'] for k, v in kern.items() if not k.startswith('phase'))),
+            'kernels_note': 'per-category CUDA-event times of a profiled re-run of the same steps (eager launches, '
+                            '%.1f ms/step with timing on)' % ms_prof,
             'kernels': kern, 'roofline': roof, 'cpu_baseline': cpu}))
     free(h)
     if ws > 1:
@@ -320,23 +392,28 @@ def box_cells(Ns, Nr, p, delta):
 
 
 def algorithmic_bytes(cat, c, N, es):
-    """Algorithmic HBM bytes of one launch: what the kernel must read and write (es = element bytes)."""
-    d = {'apply_vtbe': 7, 'apply_ppbe': 2}.get(cat)
-    if d:
-        return 2 * d * N * es                       # read x, write y
-    if cat == 'apply_ppbe_coarse':
-        return 2 * 2 * (N // 8) * es
-    if cat.startswith('ras_'):
-        coarse = cat.endswith('_coarse')
-        # per-launch category: the most frequent system in the category is PPBE (d = 2) for the
-        # coarse level; the fine category mixes VTBE and PPBE launches, so it is not reported
-        if not coarse:
-            return None
-        d = 2
-        cells = box_cells(c['Ns'] // 2, c['Nr'] // 2, c['p'], c['overlap_coarse'])
-        if cat.startswith('ras_fwd'):   # gather (read r, write loc) + L sweep (read loc + factors, write loc)
+    """Algorithmic HBM bytes of one launch of a timing category: what it must read and write.
+
+    apply: read x, write y.  RAS forward (gather + L sweep): per box cell read r, write and read
+    the local vector, read the L factors (5 d off-diagonal + d(d-1)/2 diagonal-block entries),
+    write the result; backward (U sweep + scatter) likewise with the U factors (5 d + d(d+1)/2)."""
+    es = 4 if cat.endswith('_fp32') else 8
+    base = cat.replace('_fp32', '')
+    coarse = base.endswith('_coarse')
+    base = base.replace('_coarse', '')
+    ncell = N // 8 if coarse else N
+    if base in ('apply_vtbe', 'apply_ppbe'):
+        d = 7 if base == 'apply_vtbe' else 2
+        return 2 * d * ncell * es
+    if base.startswith('ras_'):
+        d = 7 if base.endswith('vtbe') else 2
+        if coarse:
+            cells = box_cells(c['Ns'] // 2, c['Nr'] // 2, c['p'], c['overlap_coarse'])
+        else:
+            cells = box_cells(c['Ns'], c['Nr'], c['p'], c['overlap'])
+        if base.startswith('ras_fwd'):
             return cells * es * (4 * d + 5 * d + d * (d - 1) // 2)
-        return cells * es * (4 * d + 5 * d + d * (d + 1) // 2)  # U sweep + scatter
+        return cells * es * (4 * d + 5 * d + d * (d + 1) // 2)
     return None
 
 

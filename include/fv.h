@@ -87,15 +87,25 @@ typedef struct {
   int coarse_maxit;
   /* Mixed precision (not in the paper).  precision = FV_PREC_FP64: everything
    * above runs in FP64.  precision = FV_PREC_FP32: the preconditioner M^{-1}
-   * of the FP64 outer FGMRES is an inner FGMRES(inner_restart) in FP32 (FP32
-   * operator applies, FP32 ILU(0) factors and sweeps, FP32 coarse level) to
-   * relative tolerance inner_rtol, at most inner_maxit iterations; the outer
-   * residual, its Arnoldi dot products and norms and the Hessenberg least
-   * squares stay FP64, so the final residual is a true FP64 residual. */
+   * of the FP64 outer FGMRES is an FP32 inner FGMRES of exactly inner_maxit
+   * iterations (1..31; FP32 operator applies, FP32 ILU(0) factors and sweeps)
+   * whose own preconditioner is the RAS above in FP32, with a coarse solve of
+   * exactly coarse_maxit iterations for levels = 2.  These inner solves run
+   * on the device without host synchronisation (replayed as one CUDA graph);
+   * inner_rtol, inner_restart and coarse_rtol are not used by them.  The
+   * outer residual, its Arnoldi dot products and norms and the Hessenberg
+   * least squares stay FP64, so the final residual is a true FP64 residual. */
   int precision;
   double inner_rtol;
   int inner_restart;
   int inner_maxit;
+  /* Uneven decompositions (not in the paper; p1, p2, p3 are then ignored):
+   * nboxes > 0 owned boxes given as 7 ints each in host memory,
+   * (panel, i0, i1, j0, j1, k0, k1) with half-open ranges, that must tile the
+   * shell exactly (FV_EINVAL otherwise).  With levels = 2 every bound must be
+   * even; the coarse level uses the halved boxes.  Read during the call only. */
+  int nboxes;
+  const int* boxes;
 } fv_pc_desc;
 #define FV_PREC_FP64 0
 #define FV_PREC_FP32 1
@@ -156,6 +166,19 @@ typedef struct {
 fv_status fv_gmres_solve(const fv_system* s, const double* b, double* x, const fv_gmres_opts* opts,
                          fv_solve_stats* stats, void* stream);
 
+/* Many right-hand sides of one system solved together (not in the paper): the
+ * FGMRES above in lock-step for nrhs right-hand sides, each with its own
+ * Hessenberg matrix, tolerance and convergence flag.  B, X: device FP64,
+ * nrhs * n values, right-hand side r at offset r * n (X: in = x0, out = x).
+ * The preconditioner is the system's one-level RAS (levels = 1 only), with
+ * FP32 subdomain solves when the system was assembled with FV_PREC_FP32;
+ * every factor the batched sweeps load is applied to a group of right-hand
+ * sides (the group size is tuned by timing on the first call for a given
+ * nrhs), in one persistent launch that takes subdomains largest first.
+ * stats: NULL or nrhs entries. */
+fv_status fv_gmres_solve_batch(const fv_system* s, int nrhs, const double* B, double* X, const fv_gmres_opts* opts,
+                               fv_solve_stats* stats, void* stream);
+
 /* Time-stepping state (paper Sec. 3.1): u, Theta, B, P, P_b at step n, the
  * nonlinear terms at n-1 (Adams-Bashforth) and the previous VTBE solution.
  * init: device FP64, 9N values (u_x, u_y, u_z, Theta, B_x, B_y, B_z, P, P_b),
@@ -176,18 +199,20 @@ fv_status fv_time_step(fv_state* st, const fv_system* vtbe, const fv_system* ppb
 
 /* Kernel timing (optional).  While enabled, the library brackets each launch of
  * the categories below with CUDA events on the launching stream (a few
- * microseconds of host time per launch, no device work); fv_profile_read
- * synchronizes the device and returns the launch count and summed device
- * time of one category since the last enable.  Categories + FV_K_COARSE count
- * the same kernels on the coarse level of a two-level preconditioner.  The
- * phases PC-C (coarse solve), PC-F (fine one-level RAS) and PC-I (restriction,
- * prolongation and residual) follow the paper's breakdown of the two-level
- * preconditioner (Sec. 4.3). */
+ * microseconds of host time per launch, no device work) and runs the
+ * mixed-precision inner solves eagerly instead of replaying their CUDA graph;
+ * fv_profile_read synchronizes the device and returns the launch count and
+ * summed device time of one category since the last enable.  A category is a
+ * base value plus FV_K_COARSE for launches on the coarse level of a two-level
+ * preconditioner, plus FV_K_FP32 for FP32 launches of mixed precision.  The
+ * phases PC-C (coarse solve), PC-F (fine one-level RAS) and PC-I
+ * (restriction, prolongation and residual) follow the paper's breakdown of
+ * the two-level preconditioner (Sec. 4.3). */
 #define FV_K_GHOST 0
 #define FV_K_APPLY_VTBE 1
 #define FV_K_APPLY_PPBE 2
-#define FV_K_RAS_FWD 3
-#define FV_K_RAS_BWD 4
+#define FV_K_RAS_FWD_VTBE 3
+#define FV_K_RAS_BWD_VTBE 4
 #define FV_K_CGS 5
 #define FV_K_VEC 6
 #define FV_K_GLUE 7
@@ -195,8 +220,11 @@ fv_status fv_time_step(fv_state* st, const fv_system* vtbe, const fv_system* ppb
 #define FV_K_PHASE_PC_C 9
 #define FV_K_PHASE_PC_F 10
 #define FV_K_PHASE_PC_I 11
+#define FV_K_RAS_FWD_PPBE 12
+#define FV_K_RAS_BWD_PPBE 13
 #define FV_K_COARSE 16
-#define FV_K_COUNT 32
+#define FV_K_FP32 32
+#define FV_K_COUNT 64
 fv_status fv_profile_enable(int on);
 fv_status fv_profile_read(int category, long long* launches, double* total_ms);
 

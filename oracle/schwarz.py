@@ -121,6 +121,12 @@ class Subdomain:
         return M
 
 
+def decompose_boxes(grid, boxes, delta):
+    """Subdomains from an explicit list of owned boxes (panel, i0, i1, j0, j1, k0, k1) that tile
+    every panel (uneven decompositions); overlap delta as in decompose()."""
+    return [Subdomain(grid, p, ((i0, i1), (j0, j1), (k0, k1)), delta) for (p, i0, i1, j0, j1, k0, k1) in boxes]
+
+
 def decompose(grid, parts, delta):
     """6 p1 p2 p3 structured subdomains with overlap delta (paper Sec. 3.3)."""
     p1, p2, p3 = parts
@@ -138,9 +144,11 @@ def decompose(grid, parts, delta):
 class OneLevelRAS:
     """M_one^{-1} r = sum_i (R_i^0)^T (ILU(0) of A_i^delta)^{-1} R_i^delta r (eqn:onelevel)."""
 
-    def __init__(self, grid, A, d, parts, delta, subs=None):
+    def __init__(self, grid, A, d, parts, delta, subs=None, boxes=None):
         self.N, self.d = grid.N, d
-        self.subs = subs if subs is not None else decompose(grid, parts, delta)
+        if subs is None:
+            subs = decompose_boxes(grid, boxes, delta) if boxes is not None else decompose(grid, parts, delta)
+        self.subs = subs
         self.ilus = [ILU0(s.local_matrix(A, d, self.N)) for s in self.subs]
 
     def apply(self, r):

@@ -1,6 +1,7 @@
 // C ABI entry points of libfv (declared in include/fv.h).
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "fv_internal.h"
 
@@ -17,8 +18,10 @@ fv_status cuda_fail(cudaError_t e, const char* what) {
 
 static void free_system(fv_system* s) {
   if (!s) return;
+  if (s->inner_graph) cudaGraphExecDestroy(s->inner_graph);
   if (s->coarse) free_system(s->coarse);
   free_krylov(s->kry);
+  free_batch(s->batch);
   for (void* p : s->allocs) cudaFree(p);
   delete s;
 }
@@ -37,10 +40,9 @@ static fv_status make_system(const fv_grid* g, int kind, const fv_phys* ph, cons
   }
   s->allocs.push_back(s->ghost);
   if (s->prec32) {
-    if (pc->inner_restart < 1 || pc->inner_restart > 31 || pc->inner_maxit < 1 || !(pc->inner_rtol > 0)) {
+    if (pc->inner_maxit < 1 || pc->inner_maxit > 31 || (pc->levels >= 2 && (pc->coarse_maxit < 1 || pc->coarse_maxit > 31))) {
       free_system(s);
-      return set_error("fv_assemble_system: mixed precision needs inner_restart in [1, 31], inner_maxit >= 1, "
-                       "inner_rtol > 0"),
+      return set_error("fv_assemble_system: mixed precision needs inner_maxit and coarse_maxit in [1, 31]"),
              FV_EINVAL;
     }
     if (cudaMalloc(&s->ghost32, ng * sizeof(float)) != cudaSuccess ||
@@ -73,6 +75,17 @@ static fv_status make_system(const fv_grid* g, int kind, const fv_phys* ph, cons
     cpc.levels = 1;
     cpc.overlap = pc->overlap_coarse;
     cpc.p1 = std::min(pc->p1, g->h.Ns / 2), cpc.p2 = std::min(pc->p2, g->h.Ns / 2), cpc.p3 = std::min(pc->p3, g->h.Nr / 2);
+    std::vector<int> cboxes;
+    if (pc->nboxes > 0) {  // the coarse level uses the halved boxes (bounds must be even)
+      for (int q = 0; q < 7 * pc->nboxes; ++q) {
+        if (q % 7 && pc->boxes[q] % 2) {
+          free_system(s);
+          return set_error("fv_assemble_system: two levels need even box bounds"), FV_EINVAL;
+        }
+        cboxes.push_back(q % 7 ? pc->boxes[q] / 2 : pc->boxes[q]);
+      }
+      cpc.boxes = cboxes.data();
+    }
     if ((rc = make_system(gm->coarse, kind, ph, &cpc, &s->coarse))) {
       free_system(s);
       return rc;

@@ -1,0 +1,706 @@
+// Many right-hand sides of one system solved together (fv_gmres_solve_batch).
+//
+// The same right-preconditioned restarted FGMRES as fv_gmres_solve (paper
+// Sec. 3.3), run in lock-step for nrhs right-hand sides: one batched launch per
+// step for all of them, each right-hand side with its own Hessenberg matrix,
+// Givens rotations, tolerance and convergence flag (columns of a converged
+// right-hand side are no longer used).  The preconditioner is the system's
+// one-level RAS: FP64 subdomain solves, or FP32 subdomain solves inside the
+// FP64 outer FGMRES when the system was assembled with FV_PREC_FP32.
+//
+// Batched RAS sweeps: each CTA takes a (subdomain, group of G right-hand
+// sides) task and applies every factor it loads to the G right-hand sides,
+// so the factor bytes are read once per group instead of once per
+// right-hand side.  The launch is persistent: as many CTAs as fit on the GPU
+// pull tasks from an atomic counter in decreasing subdomain size (uneven
+// decompositions balance).  G is chosen by timing each candidate on the first
+// call for a given nrhs (an autotuner; the choice is kept in the system).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+#include "stencil.cuh"
+
+namespace fv {
+
+constexpr int BK = 32;        // max basis vectors
+constexpr int BBLOCKS = 152;  // reduction blocks per right-hand side
+constexpr int BTHREADS = 256;
+
+struct BatchWork {
+  int nrhs = 0, m = 0, G = 0;
+  long long n = 0;
+  double *gh = nullptr, *V = nullptr, *Z = nullptr, *w = nullptr, *r = nullptr;
+  double *part = nullptr, *h = nullptr, *hhost = nullptr, *coef = nullptr, *coef_host = nullptr;
+  unsigned* ticket = nullptr;
+  void* loc = nullptr;     // [nrhs][total_cells * d] sweep vectors (factor type)
+  void* ring = nullptr;    // global rings when they do not fit in shared memory
+  int* task = nullptr;     // persistent-launch task counters (fwd, bwd)
+  int ctas = 0;            // persistent CTAs
+  size_t smem = 0;
+  int ring_in_smem = 0;
+};
+
+void free_batch(BatchWork* b) {
+  if (!b) return;
+  cudaFree(b->gh), cudaFree(b->V), cudaFree(b->Z), cudaFree(b->w), cudaFree(b->r), cudaFree(b->part), cudaFree(b->h);
+  cudaFree(b->coef), cudaFree(b->ticket), cudaFree(b->loc), cudaFree(b->ring), cudaFree(b->task);
+  cudaFreeHost(b->hhost), cudaFreeHost(b->coef_host);
+  delete b;
+}
+
+// ------------------------------------------------------------------ batched operator
+template <class GT>
+__global__ void ghost_batch_kernel(GT G, const double* __restrict__ x, double* __restrict__ gh, int d, long long xs,
+                                   long long gsz) {
+  const int Ns = G.Ns, Nr = G.Nr;
+  x += blockIdx.y * xs;
+  gh += blockIdx.y * gsz;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < gsz; e += (long long)gridDim.x * blockDim.x) {
+    long long q = e;
+    const int tp = (int)(q % (Ns + 2));
+    q /= (Ns + 2);
+    const int k = (int)(q % Nr);
+    q /= Nr;
+    const int side = (int)(q % 4);
+    q /= 4;
+    const int p = (int)(q % 6);
+    const int comp = (int)(q / 6);
+    const int t = tp - 1;
+    double v = 0.0;
+    if (t >= 0 && t < Ns) {
+      v = interp_ghost(G, x, comp, p, side, k, t);
+    } else if (side == XI_MIN || side == XI_MAX) {
+      const int jin = t < 0 ? 0 : Ns - 1, iin = side == XI_MIN ? 0 : Ns - 1;
+      v = interp_ghost(G, x, comp, p, side, k, jin) + interp_ghost(G, x, comp, p, t < 0 ? ETA_MIN : ETA_MAX, k, iin) -
+          x[comp * G.N + cidx(G, p, k, jin, iin)];
+    }
+    gh[e] = v;
+  }
+}
+
+// grid.z = ((rhs * d) + comp) * 6 + panel
+template <int KIND, bool INTERIOR>
+__global__ void __launch_bounds__(256) apply_batch_kernel(Geo G, Coefs<double> cf, const double* __restrict__ x,
+                                                          const double* __restrict__ gh, double* __restrict__ y, int d,
+                                                          long long xs, long long ys, long long gsz) {
+  const int Ns = G.Ns;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  int i, j;
+  if (INTERIOR) {
+    const int ni = Ns - 2;
+    if (q >= ni * ni) return;
+    i = 1 + q % ni, j = 1 + q / ni;
+  } else {
+    if (q >= 4 * (Ns - 1)) return;
+    const int s = q / (Ns - 1), t = q % (Ns - 1);
+    if (s == 0) i = t, j = 0;
+    else if (s == 1) i = Ns - 1, j = t;
+    else if (s == 2) i = Ns - 1 - t, j = Ns - 1;
+    else i = 0, j = Ns - 1 - t;
+  }
+  const int k = blockIdx.y, p = blockIdx.z % 6, ta = blockIdx.z / 6, a = ta % d, rhs = ta / d;
+  ApplyAcc<double, double> acc(G, x + rhs * xs, gh + rhs * gsz);
+  if (KIND == FV_VTBE) vtbe_row(G, cf, acc, p, k, j, i, a);
+  else ppbe_row(G, cf, acc, p, k, j, i, a);
+  y[rhs * ys + (long long)a * G.N + ((long long)(p * G.Nr + k) * Ns + j) * Ns + i] = acc.sum;
+}
+
+static fv_status apply_batch(const fv_system* s, BatchWork* bw, int nrhs, const double* x, long long xs, double* y,
+                             long long ys, cudaStream_t st) {
+  const Geo& G = s->grid->geo;
+  const long long gsz = (long long)s->d * 6 * 4 * G.Nr * (G.Ns + 2);
+  ProfScope ps((s->kind == FV_VTBE ? FV_K_APPLY_VTBE : FV_K_APPLY_PPBE), st);
+  ghost_batch_kernel<Geo><<<dim3((unsigned)std::min<long long>((gsz + 255) / 256, 4096), nrhs), 256, 0, st>>>(
+      G, x, bw->gh, s->d, xs, gsz);
+  const Coefs<double> cf = make_coefs<double>(Phys{s->phys.E, s->phys.Ra, s->phys.Pr, s->phys.Pm, s->phys.dt},
+                                               s->grid->h.ri, s->grid->h.ro);
+  const int ni = G.Ns - 2;
+  const dim3 gi((ni * ni + 255) / 256, G.Nr, 6 * s->d * nrhs), ge((4 * (G.Ns - 1) + 255) / 256, G.Nr, 6 * s->d * nrhs);
+  if (s->kind == FV_VTBE) {
+    apply_batch_kernel<FV_VTBE, true><<<gi, 256, 0, st>>>(G, cf, x, bw->gh, y, s->d, xs, ys, gsz);
+    apply_batch_kernel<FV_VTBE, false><<<ge, 256, 0, st>>>(G, cf, x, bw->gh, y, s->d, xs, ys, gsz);
+  } else {
+    apply_batch_kernel<FV_PPBE, true><<<gi, 256, 0, st>>>(G, cf, x, bw->gh, y, s->d, xs, ys, gsz);
+    apply_batch_kernel<FV_PPBE, false><<<ge, 256, 0, st>>>(G, cf, x, bw->gh, y, s->d, xs, ys, gsz);
+  }
+  FV_CUDA(cudaGetLastError());
+  return FV_OK;
+}
+
+// ------------------------------------------------------------------ batched RAS
+__device__ __forceinline__ void tables(int nx, int ny, int nz, int levels, int* lvl, int* rowoff) {
+  for (int L = threadIdx.x; L < levels; L += blockDim.x) {
+    int cnt = 0;
+    for (int j = 0; j < ny; ++j) {
+      rowoff[L * ny + j] = cnt;
+      const int lo = max(0, L - 2 * j - (nz - 1)), hi = min(nx - 1, L - 2 * j);
+      if (hi >= lo) cnt += hi - lo + 1;
+    }
+    lvl[L + 1] = cnt;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    lvl[0] = 0;
+    for (int L = 0; L < levels; ++L) lvl[L + 1] += lvl[L];
+  }
+  __syncthreads();
+}
+
+struct BatchRas {
+  const long long* cell_off;
+  const int* dims;
+  const int* lpt;
+  const long long* gmap_p;
+  const unsigned char* owned_p;
+  int count, ngroups, nrhs, max_cols;
+  long long N, rs, zs, total;  // cells per component, input / output stride per rhs, packed box cells
+  int ring_in_smem;
+};
+
+// task -> (subdomain in decreasing size, group of right-hand sides)
+__device__ __forceinline__ bool next_task(int* counter, const BatchRas& R, int* sd, int* grp) {
+  __shared__ int t;
+  if (threadIdx.x == 0) t = atomicAdd(counter, 1);
+  __syncthreads();
+  const int task = t;
+  __syncthreads();
+  if (task >= R.count * R.ngroups) return false;
+  *sd = R.lpt[task / R.ngroups];
+  *grp = task % R.ngroups;
+  return true;
+}
+
+// forward sweep with the gather of R_i^delta r fused in; ring = [4][cols][D][Gc]
+template <class T, int D, int GC>
+__global__ void __launch_bounds__(512) ras_fwd_batch_kernel(BatchRas R, const T* __restrict__ F, T* __restrict__ loc,
+                                                            T* ring_g, const double* __restrict__ r, int* counter) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const size_t rb = R.ring_in_smem ? ((4 * (size_t)R.max_cols * D * GC * sizeof(T) + 15) / 16 * 16) : 0;
+  T* ring = R.ring_in_smem ? (T*)smem : ring_g + (size_t)blockIdx.x * 4 * R.max_cols * D * GC;
+  int sd, grp;
+  while (next_task(counter, R, &sd, &grp)) {
+    const int nx = R.dims[3 * sd], ny = R.dims[3 * sd + 1], nz = R.dims[3 * sd + 2];
+    const int levels = (nx - 1) + 2 * (ny - 1) + (nz - 1) + 1, ncols = nx * ny;
+    int* lvl = (int*)(smem + rb);
+    int* rowoff = lvl + levels + 1;
+    tables(nx, ny, nz, levels, lvl, rowoff);
+    const long long base = R.cell_off[sd], nc = R.cell_off[sd + 1] - base;
+    const T* Fb = F + base * (10 * D + D * D);
+    const int r0 = grp * GC, gn = min(GC, R.nrhs - r0);
+    for (int L = 0; L < levels; ++L) {
+      for (int col = threadIdx.x; col < ncols; col += blockDim.x) {
+        const int j = col / nx, i = col - j * nx, k = L - i - 2 * j;
+        if (k < 0 || k >= nz) continue;
+        const long long pos = lvl[L] + rowoff[L * ny + j] + i - max(0, L - 2 * j - (nz - 1));
+        T fl[5 * D], fd[D * D];
+#pragma unroll
+        for (int q = 0; q < 5 * D; ++q) fl[q] = Fb[q * nc + pos];
+#pragma unroll
+        for (int a = 1; a < D; ++a)
+#pragma unroll
+          for (int c = 0; c < a; ++c) fd[a * D + c] = Fb[(5 * D + a * D + c) * nc + pos];
+        const long long g = R.gmap_p[base + pos];
+        T* rp = ring + (size_t)((k & 3) * ncols) * D * GC;
+        const T* rm = ring + (size_t)(((k - 1) & 3) * ncols + col) * D * GC;
+        for (int gg = 0; gg < gn; ++gg) {
+          const int rhs = r0 + gg;
+          T y[D];
+#pragma unroll
+          for (int a = 0; a < D; ++a) y[a] = g >= 0 ? (T)r[rhs * R.rs + a * R.N + g] : T(0);
+#pragma unroll
+          for (int a = 0; a < D; ++a) {
+            if (k > 0) y[a] -= fl[0 * D + a] * rm[a * GC + gg];
+            if (i > 0 && j > 0) y[a] -= fl[1 * D + a] * rp[((col - nx - 1) * D + a) * GC + gg];
+            if (j > 0) y[a] -= fl[2 * D + a] * rp[((col - nx) * D + a) * GC + gg];
+            if (j > 0 && i + 1 < nx) y[a] -= fl[3 * D + a] * rp[((col - nx + 1) * D + a) * GC + gg];
+            if (i > 0) y[a] -= fl[4 * D + a] * rp[((col - 1) * D + a) * GC + gg];
+#pragma unroll
+            for (int c = 0; c < a; ++c) y[a] -= fd[a * D + c] * y[c];
+          }
+          T* lb = loc + rhs * R.total * D + base * D;
+#pragma unroll
+          for (int a = 0; a < D; ++a) rp[(col * D + a) * GC + gg] = y[a], lb[a * nc + pos] = y[a];
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// backward sweep with the scatter of the owned cells, (R_i^0)^T, fused in
+template <class T, int D, int GC>
+__global__ void __launch_bounds__(512) ras_bwd_batch_kernel(BatchRas R, const T* __restrict__ F, T* __restrict__ loc,
+                                                            T* ring_g, double* __restrict__ z, int* counter) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const size_t rb = R.ring_in_smem ? ((4 * (size_t)R.max_cols * D * GC * sizeof(T) + 15) / 16 * 16) : 0;
+  T* ring = R.ring_in_smem ? (T*)smem : ring_g + (size_t)blockIdx.x * 4 * R.max_cols * D * GC;
+  constexpr int U = 5 * D + D * D;
+  int sd, grp;
+  while (next_task(counter, R, &sd, &grp)) {
+    const int nx = R.dims[3 * sd], ny = R.dims[3 * sd + 1], nz = R.dims[3 * sd + 2];
+    const int levels = (nx - 1) + 2 * (ny - 1) + (nz - 1) + 1, ncols = nx * ny;
+    int* lvl = (int*)(smem + rb);
+    int* rowoff = lvl + levels + 1;
+    tables(nx, ny, nz, levels, lvl, rowoff);
+    const long long base = R.cell_off[sd], nc = R.cell_off[sd + 1] - base;
+    const T* Fb = F + base * (10 * D + D * D);
+    const int r0 = grp * GC, gn = min(GC, R.nrhs - r0);
+    for (int L = levels - 1; L >= 0; --L) {
+      for (int col = threadIdx.x; col < ncols; col += blockDim.x) {
+        const int j = col / nx, i = col - j * nx, k = L - i - 2 * j;
+        if (k < 0 || k >= nz) continue;
+        const long long pos = lvl[L] + rowoff[L * ny + j] + i - max(0, L - 2 * j - (nz - 1));
+        T fu[5 * D], fd[D * D];
+#pragma unroll
+        for (int q = 0; q < 5 * D; ++q) fu[q] = Fb[(U + q) * nc + pos];
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+          for (int c = a; c < D; ++c) fd[a * D + c] = Fb[(5 * D + a * D + c) * nc + pos];
+        const bool own = R.owned_p[base + pos];
+        const long long g = R.gmap_p[base + pos];
+        T* rp = ring + (size_t)((k & 3) * ncols) * D * GC;
+        const T* rq = ring + (size_t)(((k + 1) & 3) * ncols + col) * D * GC;
+        for (int gg = 0; gg < gn; ++gg) {
+          const int rhs = r0 + gg;
+          T* lb = loc + rhs * R.total * D + base * D;
+          T x[D];
+#pragma unroll
+          for (int a = 0; a < D; ++a) x[a] = lb[a * nc + pos];
+#pragma unroll
+          for (int a = D - 1; a >= 0; --a) {
+#pragma unroll
+            for (int c = a + 1; c < D; ++c) x[a] -= fd[a * D + c] * x[c];
+            if (i + 1 < nx) x[a] -= fu[0 * D + a] * rp[((col + 1) * D + a) * GC + gg];
+            if (i > 0 && j + 1 < ny) x[a] -= fu[1 * D + a] * rp[((col + nx - 1) * D + a) * GC + gg];
+            if (j + 1 < ny) x[a] -= fu[2 * D + a] * rp[((col + nx) * D + a) * GC + gg];
+            if (i + 1 < nx && j + 1 < ny) x[a] -= fu[3 * D + a] * rp[((col + nx + 1) * D + a) * GC + gg];
+            if (k + 1 < nz) x[a] -= fu[4 * D + a] * rq[a * GC + gg];
+            x[a] /= fd[a * D + a];
+          }
+#pragma unroll
+          for (int a = 0; a < D; ++a) rp[(col * D + a) * GC + gg] = x[a];
+          if (own)
+#pragma unroll
+            for (int a = 0; a < D; ++a) z[rhs * R.zs + a * R.N + g] = (double)x[a];
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+static size_t batch_tables_bytes(const fv_system* s) {
+  // widest level table over the boxes, as in the single-RHS sweeps
+  const Subdomains& S = s->subs;
+  std::vector<int> dims(3 * S.count);
+  cudaMemcpy(dims.data(), S.dims, dims.size() * sizeof(int), cudaMemcpyDeviceToHost);
+  size_t tab = 0;
+  for (int sd = 0; sd < S.count; ++sd) {
+    const int nx = dims[3 * sd], ny = dims[3 * sd + 1], nz = dims[3 * sd + 2];
+    const int levels = (nx - 1) + 2 * (ny - 1) + (nz - 1) + 1;
+    tab = std::max(tab, (size_t)(levels + 1 + levels * ny) * sizeof(int));
+  }
+  return tab;
+}
+
+template <class T, int D, int GC>
+static fv_status ras_batch_t(const fv_system* s, BatchWork* bw, int nrhs, const double* r, long long rs, double* z,
+                             long long zs, cudaStream_t st) {
+  const Subdomains& S = s->subs;
+  BatchRas R{S.cell_off, S.dims, S.lpt, S.gmap_p, S.owned_p, S.count, (nrhs + GC - 1) / GC, nrhs, S.max_cols,
+             s->grid->geo.N, rs, zs, S.total_cells, bw->ring_in_smem};
+  const int threads = std::min(512, ((S.max_cols + 31) / 32) * 32);
+  FV_CUDA(cudaMemsetAsync(bw->task, 0, 2 * sizeof(int), st));
+  {
+    ProfScope ps(s->kind == FV_VTBE ? FV_K_RAS_FWD_VTBE : FV_K_RAS_FWD_PPBE, st);
+    ras_fwd_batch_kernel<T, D, GC><<<bw->ctas, threads, bw->smem, st>>>(R, (const T*)S.F, (T*)bw->loc, (T*)bw->ring,
+                                                                      r, bw->task);
+  }
+  FV_CUDA(cudaGetLastError());
+  {
+    ProfScope ps(s->kind == FV_VTBE ? FV_K_RAS_BWD_VTBE : FV_K_RAS_BWD_PPBE, st);
+    ras_bwd_batch_kernel<T, D, GC><<<bw->ctas, threads, bw->smem, st>>>(R, (const T*)S.F, (T*)bw->loc, (T*)bw->ring,
+                                                                      z, bw->task + 1);
+  }
+  FV_CUDA(cudaGetLastError());
+  return FV_OK;
+}
+
+template <class T, int D, int GC>
+static fv_status setup_batch_ras(const fv_system* s, BatchWork* bw, size_t tab) {
+  const Subdomains& S = s->subs;
+  const int threads = std::min(512, ((S.max_cols + 31) / 32) * 32);
+  const size_t ring = 4 * (size_t)S.max_cols * D * GC * sizeof(T), ring_al = (ring + 15) / 16 * 16;
+  int dev = 0, limit = 0, sms = 0;
+  FV_CUDA(cudaGetDevice(&dev));
+  FV_CUDA(cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  FV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  // the dynamic limit is the opt-in maximum less the kernel's static shared memory
+  cudaFuncAttributes fa{}, fb{};
+  FV_CUDA(cudaFuncGetAttributes(&fa, ras_fwd_batch_kernel<T, D, GC>));
+  FV_CUDA(cudaFuncGetAttributes(&fb, ras_bwd_batch_kernel<T, D, GC>));
+  const int dyn = limit - (int)std::max(fa.sharedSizeBytes, fb.sharedSizeBytes);
+  bw->ring_in_smem = ring_al + tab <= (size_t)dyn;
+  bw->smem = (bw->ring_in_smem ? ring_al : 0) + tab;
+  if (bw->smem > (size_t)dyn) return set_error("fv_gmres_solve_batch: sweep tables exceed shared memory"), FV_EINVAL;
+  FV_CUDA(cudaFuncSetAttribute(ras_fwd_batch_kernel<T, D, GC>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
+  FV_CUDA(cudaFuncSetAttribute(ras_bwd_batch_kernel<T, D, GC>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
+  int per_sm = 0;
+  FV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ras_fwd_batch_kernel<T, D, GC>, threads, bw->smem));
+  const int tasks = S.count * ((bw->nrhs + GC - 1) / GC);
+  bw->ctas = std::max(1, std::min(tasks, std::max(1, per_sm) * sms));
+  if (!bw->ring_in_smem) {
+    cudaFree(bw->ring);
+    bw->ring = nullptr;
+    if (cudaMalloc(&bw->ring, (size_t)bw->ctas * ring) != cudaSuccess)
+      return set_error("fv_gmres_solve_batch: ring allocation failed"), FV_ENOMEM;
+  }
+  return FV_OK;
+}
+
+template <class T, int D>
+static fv_status ras_batch_g(const fv_system* s, BatchWork* bw, int nrhs, const double* r, long long rs, double* z,
+                             long long zs, cudaStream_t st) {
+  switch (bw->G) {
+    case 1: return ras_batch_t<T, D, 1>(s, bw, nrhs, r, rs, z, zs, st);
+    case 2: return ras_batch_t<T, D, 2>(s, bw, nrhs, r, rs, z, zs, st);
+    case 4: return ras_batch_t<T, D, 4>(s, bw, nrhs, r, rs, z, zs, st);
+    default: return ras_batch_t<T, D, 8>(s, bw, nrhs, r, rs, z, zs, st);
+  }
+}
+
+template <class T, int D>
+static fv_status setup_g(const fv_system* s, BatchWork* bw, size_t tab) {
+  switch (bw->G) {
+    case 1: return setup_batch_ras<T, D, 1>(s, bw, tab);
+    case 2: return setup_batch_ras<T, D, 2>(s, bw, tab);
+    case 4: return setup_batch_ras<T, D, 4>(s, bw, tab);
+    default: return setup_batch_ras<T, D, 8>(s, bw, tab);
+  }
+}
+
+static fv_status ras_batch(const fv_system* s, BatchWork* bw, int nrhs, const double* r, long long rs, double* z,
+                           long long zs, cudaStream_t st) {
+  if (s->d == 2)
+    return s->subs.fp32 ? ras_batch_g<float, 2>(s, bw, nrhs, r, rs, z, zs, st)
+                        : ras_batch_g<double, 2>(s, bw, nrhs, r, rs, z, zs, st);
+  return s->subs.fp32 ? ras_batch_g<float, 7>(s, bw, nrhs, r, rs, z, zs, st)
+                      : ras_batch_g<double, 7>(s, bw, nrhs, r, rs, z, zs, st);
+}
+
+static fv_status setup_ras(const fv_system* s, BatchWork* bw, size_t tab) {
+  if (s->d == 2) return s->subs.fp32 ? setup_g<float, 2>(s, bw, tab) : setup_g<double, 2>(s, bw, tab);
+  return s->subs.fp32 ? setup_g<float, 7>(s, bw, tab) : setup_g<double, 7>(s, bw, tab);
+}
+
+// ------------------------------------------------------------------ batched vectors
+__device__ __forceinline__ double bwarp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// per right-hand side (grid.y): mode 0 dots V^T w, mode 1 w -= V h then dots, mode 2 w -= V h then
+// ||w||^2; the last block of each right-hand side sums the partials in a fixed order into out
+template <int NV>
+__global__ void __launch_bounds__(BTHREADS) cgs_batch_kernel(long long n, const double* __restrict__ V,
+                                                             long long vstride, const double* __restrict__ h,
+                                                             double* __restrict__ w, double* __restrict__ part,
+                                                             double* __restrict__ out, unsigned* ticket, int mode) {
+  const int rhs = blockIdx.y;
+  V += rhs * vstride;
+  w += rhs * n;
+  h += rhs * 3 * BK;
+  part += (size_t)rhs * BK * gridDim.x;
+  out += rhs * 3 * BK;
+  double acc[NV > 0 ? NV : 1], hv[NV > 0 ? NV : 1], nrm = 0.0;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = 0.0, hv[v] = mode > 0 ? h[v] : 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    double we = w[e];
+    if (mode > 0) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) we -= hv[v] * V[v * n + e];
+      w[e] = we;
+    }
+    if (mode < 2) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) acc[v] += V[v * n + e] * we;
+    } else {
+      nrm += we * we;
+    }
+  }
+  __shared__ double sm[BTHREADS / 32][BK];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nvv = mode < 2 ? NV : 1;
+  for (int v = 0; v < nvv; ++v) {
+    const double t = bwarp_sum(mode < 2 ? acc[v] : nrm);
+    if (lane == 0) sm[wid][v] = t;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < nvv) {
+    double t = 0.0;
+    for (int q = 0; q < BTHREADS / 32; ++q) t += sm[q][threadIdx.x];
+    part[threadIdx.x * gridDim.x + blockIdx.x] = t;
+  }
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(ticket + rhs, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int v = wid; v < nvv; v += BTHREADS / 32) {
+    double t = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(part + v * gridDim.x + b);
+    t = bwarp_sum(t);
+    if (lane == 0) out[(mode == 2 ? 2 * BK : mode * BK) + v] = t;
+  }
+  if (threadIdx.x == 0) ticket[rhs] = 0u;
+}
+
+template <int... I>
+static void cgs_batch_dispatch(int nv, dim3 grid, long long n, const double* V, long long vs, const double* h, double* w,
+                               double* part, double* out, unsigned* ticket, int mode, cudaStream_t st,
+                               std::integer_sequence<int, I...>) {
+  using Fn = void (*)(long long, const double*, long long, const double*, double*, double*, double*, unsigned*, int);
+  static const Fn table[] = {&cgs_batch_kernel<I>...};
+  table[nv]<<<grid, BTHREADS, 0, st>>>(n, V, vs, h, w, part, out, ticket, mode);
+}
+
+// out_r = a_r x_r + b y_r  (a per right-hand side from coef[rhs])
+__global__ void scale_batch_kernel(long long n, const double* __restrict__ coef, const double* __restrict__ x,
+                                   long long xs, double b, const double* __restrict__ y, double* __restrict__ out,
+                                   long long os) {
+  const int rhs = blockIdx.y;
+  const double a = coef[rhs];
+  x += rhs * xs, out += rhs * os;
+  if (y) y += rhs * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    out[e] = a * x[e] + (y ? b * y[e] : 0.0);
+}
+
+// x_r += sum_v y_{r,v} Z_{r,v}
+__global__ void update_batch_kernel(long long n, int kk, const double* __restrict__ Z, long long zs,
+                                    const double* __restrict__ y, double* __restrict__ x) {
+  const int rhs = blockIdx.y;
+  Z += rhs * zs, x += rhs * n, y += rhs * BK;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    double s = x[e];
+    for (int v = 0; v < kk; ++v) s += y[v] * Z[v * n + e];
+    x[e] = s;
+  }
+}
+
+static int bblocks(long long n) { return (int)std::min<long long>((n + 255) / 256, 1024); }
+
+static fv_status ensure_batch(const fv_system* s, int nrhs, int m) {
+  fv_system* sm = const_cast<fv_system*>(s);
+  BatchWork* bw = sm->batch;
+  if (bw && bw->nrhs == nrhs && bw->m >= m) return FV_OK;
+  free_batch(bw);
+  bw = sm->batch = new BatchWork();
+  bw->nrhs = nrhs, bw->m = m, bw->n = s->n;
+  const size_t n = (size_t)s->n, R = (size_t)nrhs;
+  const size_t gsz = (size_t)s->d * 6 * 4 * s->grid->h.Nr * (s->grid->h.Ns + 2);
+  const size_t es = s->subs.fp32 ? 4 : 8;
+  if (cudaMalloc(&bw->gh, gsz * R * 8) || cudaMalloc(&bw->V, (m + 1) * n * R * 8) || cudaMalloc(&bw->Z, m * n * R * 8) ||
+      cudaMalloc(&bw->w, n * R * 8) || cudaMalloc(&bw->r, n * R * 8) || cudaMalloc(&bw->part, R * BK * BBLOCKS * 8) ||
+      cudaMalloc(&bw->h, R * 3 * BK * 8) || cudaMalloc(&bw->coef, R * BK * 8) || cudaMalloc(&bw->ticket, R * 4) ||
+      cudaMalloc(&bw->loc, (size_t)s->subs.total_cells * s->d * R * es) || cudaMalloc(&bw->task, 2 * sizeof(int)) ||
+      cudaMallocHost(&bw->hhost, R * 3 * BK * 8) || cudaMallocHost(&bw->coef_host, R * BK * 8) ||
+      cudaMemset(bw->ticket, 0, R * 4)) {
+    free_batch(bw);
+    sm->batch = nullptr;
+    return set_error("fv_gmres_solve_batch: device allocation failed"), FV_ENOMEM;
+  }
+  // autotune the right-hand-side group G of the RAS sweeps on this system and batch size
+  const size_t tab = batch_tables_bytes(s);
+  FV_CUDA(cudaMemset(bw->r, 0, n * R * 8));
+  float best = 1e30f;
+  int bestG = 1;
+  cudaEvent_t e0, e1;
+  FV_CUDA(cudaEventCreate(&e0));
+  FV_CUDA(cudaEventCreate(&e1));
+  const int cand[4] = {1, 2, 4, 8};
+  fv_status rc = FV_OK;
+  for (int G : cand) {
+    if (G > nrhs && G != 1) break;
+    bw->G = G;
+    if ((rc = setup_ras(s, bw, tab))) break;
+    if ((rc = ras_batch(s, bw, nrhs, bw->r, n, bw->w, n, 0))) break;  // warm-up
+    cudaEventRecord(e0);
+    for (int t = 0; t < 3; ++t)
+      if ((rc = ras_batch(s, bw, nrhs, bw->r, n, bw->w, n, 0))) break;
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) best = ms, bestG = G;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  bw->G = bestG;
+  return setup_ras(s, bw, tab);
+}
+
+fv_status gmres_batch(const fv_system* s, int nrhs, const double* B, double* X, const fv_gmres_opts* o,
+                      fv_solve_stats* stats, cudaStream_t st) {
+  auto t0 = std::chrono::steady_clock::now();
+  const int m = o->restart;
+  if (nrhs < 1 || m < 1 || m > BK - 1 || o->max_it < 0)
+    return set_error("fv_gmres_solve_batch: nrhs >= 1 and restart in [1, 31] required"), FV_EINVAL;
+  if (s->pc.levels != 1) return set_error("fv_gmres_solve_batch: one-level RAS systems only"), FV_EINVAL;
+  fv_status rc = ensure_batch(s, nrhs, m);
+  if (rc) return rc;
+  BatchWork* bw = s->batch;
+  const long long n = s->n;
+  const long long vs = (long long)(m + 1) * n, zs = (long long)m * n;
+  const dim3 gv(bblocks(n), nrhs), gc(BBLOCKS, nrhs);
+  std::vector<double> beta(nrhs), r0(nrhs), target(nrhs), H((size_t)nrhs * (m + 1) * m), cs((size_t)nrhs * m),
+      sn((size_t)nrhs * m), g((size_t)nrhs * (m + 1)), yv((size_t)nrhs * BK);
+  std::vector<int> its(nrhs, 0), kk(nrhs), done(nrhs);
+  auto residual = [&]() -> fv_status {  // r = B - A X, beta = ||r||
+    fv_status q;
+    if ((q = apply_batch(s, bw, nrhs, X, n, bw->r, n, st))) return q;
+    for (int t = 0; t < nrhs; ++t) bw->coef_host[t] = -1.0;
+    FV_CUDA(cudaMemcpyAsync(bw->coef, bw->coef_host, nrhs * 8, cudaMemcpyHostToDevice, st));
+    scale_batch_kernel<<<gv, 256, 0, st>>>(n, bw->coef, bw->r, n, 1.0, B, bw->r, n);
+    cgs_batch_dispatch(0, gc, n, bw->r, n, bw->h, bw->r, bw->part, bw->h, bw->ticket, 2, st,
+                       std::make_integer_sequence<int, BK>{});
+    FV_CUDA(cudaGetLastError());
+    FV_CUDA(cudaMemcpyAsync(bw->hhost, bw->h, nrhs * 3 * BK * 8, cudaMemcpyDeviceToHost, st));
+    FV_CUDA(cudaStreamSynchronize(st));
+    for (int t = 0; t < nrhs; ++t) beta[t] = std::sqrt(bw->hhost[t * 3 * BK + 2 * BK]);
+    return FV_OK;
+  };
+  if ((rc = residual())) return rc;
+  for (int t = 0; t < nrhs; ++t) r0[t] = beta[t], target[t] = std::max(o->atol, o->rtol * r0[t]);
+  int total = 0;
+  auto active = [&](int t) { return std::isfinite(beta[t]) && beta[t] > target[t] && its[t] < o->max_it; };
+  while (true) {
+    bool any = false;
+    for (int t = 0; t < nrhs; ++t) any = any || active(t);
+    if (!any) break;
+    for (int t = 0; t < nrhs; ++t) {
+      done[t] = !active(t);
+      kk[t] = 0;
+      bw->coef_host[t] = done[t] ? 0.0 : 1.0 / beta[t];
+      for (int i = 0; i <= m; ++i) g[(size_t)t * (m + 1) + i] = 0.0;
+      g[(size_t)t * (m + 1)] = done[t] ? 0.0 : beta[t];
+    }
+    FV_CUDA(cudaMemcpyAsync(bw->coef, bw->coef_host, nrhs * 8, cudaMemcpyHostToDevice, st));
+    scale_batch_kernel<<<gv, 256, 0, st>>>(n, bw->coef, bw->r, n, 0.0, nullptr, bw->V, vs);
+    int j = 0;
+    for (; j < m; ++j) {
+      double* vj = bw->V + (size_t)j * n;
+      double* zj = bw->Z + (size_t)j * n;
+      // Z_j = M^{-1} V_j and w = A Z_j for every right-hand side (strided in the bases)
+      if ((rc = ras_batch(s, bw, nrhs, vj, vs, zj, zs, st))) return rc;
+      if ((rc = apply_batch(s, bw, nrhs, zj, zs, bw->w, n, st))) return rc;
+      const int nv = j + 1;
+      {
+        ProfScope ps(FV_K_CGS, st);
+        cgs_batch_dispatch(nv, gc, n, bw->V, vs, nullptr, bw->w, bw->part, bw->h, bw->ticket, 0, st,
+                           std::make_integer_sequence<int, BK>{});
+        cgs_batch_dispatch(nv, gc, n, bw->V, vs, bw->h, bw->w, bw->part, bw->h, bw->ticket, 1, st,
+                           std::make_integer_sequence<int, BK>{});
+        cgs_batch_dispatch(nv, gc, n, bw->V, vs, bw->h + BK, bw->w, bw->part, bw->h, bw->ticket, 2, st,
+                           std::make_integer_sequence<int, BK>{});
+      }
+      FV_CUDA(cudaGetLastError());
+      FV_CUDA(cudaMemcpyAsync(bw->hhost, bw->h, nrhs * 3 * BK * 8, cudaMemcpyDeviceToHost, st));
+      FV_CUDA(cudaStreamSynchronize(st));
+      bool all_done = true;
+      ++total;
+      for (int t = 0; t < nrhs; ++t) {
+        const double* hh = bw->hhost + t * 3 * BK;
+        if (done[t]) {
+          bw->coef_host[t] = 0.0;
+          continue;
+        }
+        double* Ht = &H[(size_t)t * (m + 1) * m];
+        double *ct = &cs[(size_t)t * m], *st_ = &sn[(size_t)t * m], *gt = &g[(size_t)t * (m + 1)];
+        std::vector<double> col(j + 2);
+        for (int i = 0; i <= j; ++i) col[i] = hh[i] + hh[BK + i];
+        const double hn = std::sqrt(hh[2 * BK]);
+        col[j + 1] = hn;
+        for (int i = 0; i < j; ++i) {
+          const double a = ct[i] * col[i] + st_[i] * col[i + 1];
+          col[i + 1] = -st_[i] * col[i] + ct[i] * col[i + 1];
+          col[i] = a;
+        }
+        const double den = std::hypot(col[j], col[j + 1]);
+        ct[j] = den > 0 ? col[j] / den : 1.0, st_[j] = den > 0 ? col[j + 1] / den : 0.0;
+        col[j] = den, col[j + 1] = 0.0;
+        gt[j + 1] = -st_[j] * gt[j];
+        gt[j] = ct[j] * gt[j];
+        for (int i = 0; i <= j; ++i) Ht[i * m + j] = col[i];
+        ++its[t];
+        kk[t] = j + 1;
+        if (std::fabs(gt[j + 1]) <= target[t] || its[t] >= o->max_it || !(hn > 0.0) || !std::isfinite(hn)) {
+          done[t] = 1;
+          bw->coef_host[t] = 0.0;
+        } else {
+          bw->coef_host[t] = 1.0 / hn;
+          all_done = false;
+        }
+      }
+      if (all_done || j + 1 == m) {
+        ++j;
+        break;
+      }
+      FV_CUDA(cudaMemcpyAsync(bw->coef, bw->coef_host, nrhs * 8, cudaMemcpyHostToDevice, st));
+      scale_batch_kernel<<<gv, 256, 0, st>>>(n, bw->coef, bw->w, n, 0.0, nullptr, bw->V + (size_t)(j + 1) * n, vs);
+    }
+    // x_r += Z_r y_r
+    for (int t = 0; t < nrhs; ++t) {
+      const double* Ht = &H[(size_t)t * (m + 1) * m];
+      const double* gt = &g[(size_t)t * (m + 1)];
+      double* y = &yv[(size_t)t * BK];
+      for (int i = 0; i < BK; ++i) y[i] = 0.0;
+      for (int i = kk[t] - 1; i >= 0; --i) {
+        double a = gt[i];
+        for (int q = i + 1; q < kk[t]; ++q) a -= Ht[i * m + q] * y[q];
+        y[i] = Ht[i * m + i] != 0.0 ? a / Ht[i * m + i] : 0.0;
+      }
+    }
+    FV_CUDA(cudaMemcpyAsync(bw->coef, yv.data(), nrhs * BK * 8, cudaMemcpyHostToDevice, st));
+    {
+      ProfScope ps(FV_K_VEC, st);
+      update_batch_kernel<<<gv, 256, 0, st>>>(n, std::min(j, m), bw->Z, zs, bw->coef, X);
+    }
+    FV_CUDA(cudaGetLastError());
+    if ((rc = residual())) return rc;
+  }
+  bool all_conv = true, nan = false;
+  for (int t = 0; t < nrhs; ++t) {
+    const bool conv = std::isfinite(beta[t]) && beta[t] <= target[t];
+    nan = nan || !std::isfinite(beta[t]);
+    all_conv = all_conv && conv;
+    if (stats) {
+      stats[t].iters = its[t];
+      stats[t].inner_iters = 0;
+      stats[t].converged = conv;
+      stats[t].r0 = r0[t];
+      stats[t].rfinal = beta[t];
+      stats[t].time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+  }
+  (void)total;
+  if (nan) return set_error("fv_gmres_solve_batch: NaN or Inf residual"), FV_ENAN;
+  if (!all_conv) return set_error("fv_gmres_solve_batch: max_it reached before the tolerance"), FV_ENOCONV;
+  return FV_OK;
+}
+
+}  // namespace fv
+
+extern "C" fv_status fv_gmres_solve_batch(const fv_system* s, int nrhs, const double* B, double* X,
+                                          const fv_gmres_opts* opts, fv_solve_stats* stats, void* stream) {
+  if (!s || !B || !X || !opts || B == X) return fv::set_error("fv_gmres_solve_batch: bad argument"), FV_EINVAL;
+  return fv::gmres_batch(s, nrhs, B, X, opts, stats, (cudaStream_t)stream);
+}

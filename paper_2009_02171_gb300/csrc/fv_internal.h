@@ -63,6 +63,7 @@ struct GridHost {
 };
 
 struct Krylov;
+struct BatchWork;
 
 }  // namespace fv
 
@@ -130,8 +131,11 @@ struct fv_system {
   float* ghost32 = nullptr;    // FP32 ghost layer
   float *r32 = nullptr, *x32 = nullptr;                  // inner solve right-hand side / solution
   float *xc32 = nullptr, *ec32 = nullptr, *w32 = nullptr, *t32 = nullptr;  // FP32 two-level work
+  cudaGraphExec_t inner_graph = nullptr;  // captured inner solve (r32 -> x32)
+  int inner_warm = 0;
   // FGMRES workspace for this system (outer) sized lazily
   fv::Krylov* kry = nullptr;
+  fv::BatchWork* batch = nullptr;  // fv_gmres_solve_batch workspace
   mutable int last_inner = 0;
   int level = 0;               // 0 fine, 1 coarse (kernel timing category offset)
   std::vector<void*> allocs;
@@ -144,6 +148,7 @@ fv_status cuda_fail(cudaError_t e, const char* what);
 
 // profile.cu: event brackets around one launch (slot -1 when timing is off)
 int prof_begin(int category, cudaStream_t st);
+bool prof_enabled();
 void prof_end(int slot, cudaStream_t st);
 struct ProfScope {
   int slot;
@@ -191,12 +196,14 @@ fv_status prolong_inject(const fv_grid* g, int d, const double* xc, double* x, c
 fv_status gmres(const fv_system* s, const double* b, double* x, const fv_gmres_opts* o, fv_solve_stats* stats,
                 cudaStream_t st, bool inner);
 void free_krylov(Krylov* k);
+void free_batch(BatchWork* b);
 fv_status axpby(long long n, double a, const double* x, double b, const double* y, double* out, cudaStream_t st);
 fv_status axpby32(long long n, double a, const float* x, double b, const float* y, float* out, cudaStream_t st);
 fv_status to_fp32(long long n, const double* x, float* out, cudaStream_t st);
 fv_status to_fp64(long long n, const float* x, double* out, cudaStream_t st);
 fv_status gmres32(const fv_system* s, const float* b, float* x, const fv_gmres_opts* o, fv_solve_stats* stats,
                   cudaStream_t st);
+fv_status gmres_fixed32(const fv_system* s, const float* b, float* x, int m, cudaStream_t st);
 fv_status weighted_mean_remove32(const fv_grid* g, float* x, cudaStream_t st, double* part, double* sums);
 fv_status weighted_mean_remove(const fv_grid* g, double* x, cudaStream_t st, double* part, double* sums);
 

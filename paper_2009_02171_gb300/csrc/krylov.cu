@@ -30,6 +30,14 @@ constexpr int KMAX = 32;     // max basis vectors in one fused pass
 constexpr int RBLOCKS = 304; // reduction blocks (2 per SM)
 constexpr int RTHREADS = 256;
 
+// Arnoldi bookkeeping of a device-driven solve (no host synchronisation)
+struct ArnoldiDev {
+  double H[KMAX * KMAX];  // upper Hessenberg after rotations, column-major H[j * KMAX + i]
+  double cs[KMAX], sn[KMAX], g[KMAX + 1], y[KMAX];
+  double scale;           // 1 / norm of the newest basis vector (0 after a breakdown)
+  int k_eff;              // number of usable columns (first breakdown)
+};
+
 template <class T>
 struct KrylovT {
   int m = 0;
@@ -38,6 +46,8 @@ struct KrylovT {
   double* part = nullptr;   // [KMAX][RBLOCKS]
   double* h = nullptr;      // [3][KMAX]: h1, h2, nrm2
   double* hhost = nullptr;  // pinned [3][KMAX]
+  ArnoldiDev* ad = nullptr; // device-driven solves
+  unsigned* ticket = nullptr; // last-block counter of the fused reductions (returns to 0 after each use)
 };
 
 struct Krylov {
@@ -47,7 +57,7 @@ struct Krylov {
 
 template <class T>
 static void free_kt(KrylovT<T>& k) {
-  cudaFree(k.V), cudaFree(k.Z), cudaFree(k.w), cudaFree(k.r), cudaFree(k.part), cudaFree(k.h);
+  cudaFree(k.V), cudaFree(k.Z), cudaFree(k.w), cudaFree(k.r), cudaFree(k.part), cudaFree(k.h), cudaFree(k.ad), cudaFree(k.ticket);
   cudaFreeHost(k.hhost);
   k = KrylovT<T>();
 }
@@ -79,6 +89,8 @@ static fv_status ensure_krylov(const fv_system* s, int m) {
       cudaMalloc(&k.w, n * sizeof(T)) != cudaSuccess || cudaMalloc(&k.r, n * sizeof(T)) != cudaSuccess ||
       cudaMalloc(&k.part, KMAX * RBLOCKS * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&k.h, 3 * KMAX * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&k.ad, sizeof(ArnoldiDev)) != cudaSuccess || cudaMalloc(&k.ticket, sizeof(unsigned)) != cudaSuccess ||
+      cudaMemset(k.ticket, 0, sizeof(unsigned)) != cudaSuccess ||
       cudaMallocHost(&k.hhost, 3 * KMAX * sizeof(double)) != cudaSuccess) {
     free_kt(k);
     return set_error("fv_gmres_solve: device allocation of the Krylov basis failed"), FV_ENOMEM;
@@ -112,16 +124,46 @@ __device__ __forceinline__ void block_store(double (&acc)[KMAX], int nv, double*
   }
 }
 
+// Givens update of column j of the device-driven Arnoldi (thread 0 of one block):
+// h = h1 + h2 (CGS2), h_{j+1,j} = sqrt(nrm2); previous rotations, new rotation,
+// right-hand side update; scale = 1 / h_{j+1,j}
+__device__ void givens_update(int j, const double* __restrict__ h, double nrm2, ArnoldiDev* ad) {
+  double col[KMAX + 1];
+  for (int i = 0; i <= j; ++i) col[i] = h[i] + h[KMAX + i];
+  const double hn = sqrt(nrm2);
+  col[j + 1] = hn;
+  for (int i = 0; i < j; ++i) {
+    const double a = ad->cs[i] * col[i] + ad->sn[i] * col[i + 1];
+    col[i + 1] = -ad->sn[i] * col[i] + ad->cs[i] * col[i + 1];
+    col[i] = a;
+  }
+  const double den = hypot(col[j], col[j + 1]);
+  const double c = den > 0.0 ? col[j] / den : 1.0, s = den > 0.0 ? col[j + 1] / den : 0.0;
+  ad->cs[j] = c, ad->sn[j] = s;
+  col[j] = den;
+  ad->g[j + 1] = -s * ad->g[j];
+  ad->g[j] = c * ad->g[j];
+  for (int i = 0; i <= j; ++i) ad->H[j * KMAX + i] = col[i];
+  if (!(den > 0.0) && ad->k_eff > j) ad->k_eff = j;              // no usable column j
+  else if (!(hn > 0.0) && ad->k_eff > j + 1) ad->k_eff = j + 1;  // lucky breakdown after column j
+  ad->scale = hn > 0.0 ? 1.0 / hn : 0.0;
+}
+
 // mode 0: part = V^T w
 // mode 1: w -= V h; part = V^T w
 // mode 2: w -= V h; part[0] = w^T w
 // NV (the number of basis vectors) is a template parameter so the loops over
 // the basis unroll exactly.  Products are summed in T for up to 32 elements
-// of a thread, then in FP64.
+// of a thread, then in FP64.  With `out`, the last block to finish sums the
+// per-block partials in a fixed order into out[0..nv) (and, for mode 2 with
+// `ad`, applies the Givens update of column gj), so no separate reduction
+// launch is needed.
 template <int NV, class T>
 __global__ void __launch_bounds__(RTHREADS) cgs_kernel(long long n, const T* __restrict__ V,
                                                        const double* __restrict__ h, T* __restrict__ w,
-                                                       double* __restrict__ part, int mode) {
+                                                       double* __restrict__ part, int mode, double* out,
+                                                       unsigned* ticket, ArnoldiDev* ad, int gj,
+                                                       const double* __restrict__ hg) {
   double acc[KMAX];
   T hv[NV > 0 ? NV : 1];
   T cur[NV > 0 ? NV : 1];
@@ -155,50 +197,75 @@ __global__ void __launch_bounds__(RTHREADS) cgs_kernel(long long n, const T* __r
 #pragma unroll
   for (int v = 0; v < NV; ++v) acc[v] += (double)cur[v];
   if (mode == 2) acc[0] += (double)curn;
-  block_store(acc, mode < 2 ? NV : 1, part);
+  const int nvv = mode < 2 ? NV : 1;
+  block_store(acc, nvv, part);
+  if (!out) return;
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int v = wid; v < nvv; v += nw) {
+    double t = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(part + v * gridDim.x + b);
+    t = warp_sum(t);
+    if (lane == 0) out[v] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (mode == 2 && ad) givens_update(gj, hg, out[0], ad);
+    *ticket = 0u;
+  }
 }
 
+struct CgsFuse {
+  double* out = nullptr;       // fused final reduction target (null: partials only)
+  unsigned* ticket = nullptr;
+  ArnoldiDev* ad = nullptr;    // mode 2: Givens update of column gj in the last block
+  int gj = 0;
+  const double* hg = nullptr;  // CGS2 coefficients h1 [0, KMAX), h2 [KMAX, 2 KMAX) of that column
+};
+
 template <int NV, class T>
-static void cgs_launch_t(long long n, const T* V, const double* h, T* w, double* part, int mode, cudaStream_t st) {
-  cgs_kernel<NV, T><<<RBLOCKS, RTHREADS, 0, st>>>(n, V, h, w, part, mode);
+static void cgs_launch_t(long long n, const T* V, const double* h, T* w, double* part, int mode, CgsFuse f,
+                         cudaStream_t st) {
+  cgs_kernel<NV, T><<<RBLOCKS, RTHREADS, 0, st>>>(n, V, h, w, part, mode, f.out, f.ticket, f.ad, f.gj, f.hg);
 }
 
 template <class T, int... I>
-static void cgs_dispatch(int nv, long long n, const T* V, const double* h, T* w, double* part, int mode,
+static void cgs_dispatch(int nv, long long n, const T* V, const double* h, T* w, double* part, int mode, CgsFuse f,
                          cudaStream_t st, std::integer_sequence<int, I...>) {
-  using F = void (*)(long long, const T*, const double*, T*, double*, int, cudaStream_t);
+  using F = void (*)(long long, const T*, const double*, T*, double*, int, CgsFuse, cudaStream_t);
   static const F table[] = {&cgs_launch_t<I, T>...};
-  table[nv](n, V, h, w, part, mode, st);
+  table[nv](n, V, h, w, part, mode, f, st);
 }
 
 template <class T>
 static void cgs_launch(int nv, long long n, const T* V, const double* h, T* w, double* part, int mode,
-                       cudaStream_t st) {
-  cgs_dispatch<T>(nv, n, V, h, w, part, mode, st, std::make_integer_sequence<int, KMAX>{});
+                       cudaStream_t st, CgsFuse f = CgsFuse()) {
+  cgs_dispatch<T>(nv, n, V, h, w, part, mode, f, st, std::make_integer_sequence<int, KMAX>{});
 }
 
-// out[v] = sum_b part[v * nb + b] (fixed order)
+// out[v] = sum_b part[v * nb + b]: one warp per vector, fixed summation order
 __global__ void reduce_kernel(const double* __restrict__ part, int nb, int nv, double* __restrict__ out) {
-  __shared__ double sm[RTHREADS];
-  for (int v = 0; v < nv; ++v) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int v = wid; v < nv; v += nw) {
     double t = 0.0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) t += part[v * nb + b];
-    sm[threadIdx.x] = t;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-      if (threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) out[v] = sm[0];
-    __syncthreads();
+    for (int b = lane; b < nb; b += 32) t += part[v * nb + b];
+    t = warp_sum(t);
+    if (lane == 0) out[v] = t;
   }
 }
 
 template <class T, class U>
 __global__ void axpby_kernel(long long n, double a, const U* __restrict__ x, double b, const T* y, T* out) {
   const T at = (T)a, bt = (T)b;
+  const bool has_y = b != 0.0;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
-    out[e] = at * (T)x[e] + (b == 0.0 ? T(0) : bt * y[e]);
+    out[e] = at * (T)x[e] + (has_y ? bt * y[e] : T(0));
 }
 
 template <class T>
@@ -301,6 +368,113 @@ fv_status precond_t<float>(const fv_system* s, const float* r, float* z, cudaStr
   return precond_apply32(s, r, z, st);
 }
 
+// ------------------------------------------------------------------ device-driven FGMRES
+// beta = ||r|| from the norm partials; g = (beta, 0, ...); scale = 1/beta
+__global__ void start_kernel(const double* __restrict__ part, int nb, ArnoldiDev* ad) {
+  const int lane = threadIdx.x;
+  double t = 0.0;
+  for (int b = lane; b < nb; b += 32) t += part[b];
+  t = warp_sum(t);
+  if (lane == 0) {
+    const double beta = sqrt(t);
+    for (int i = 0; i <= KMAX; ++i) ad->g[i] = 0.0;
+    ad->g[0] = beta;
+    ad->scale = beta > 0.0 ? 1.0 / beta : 0.0;
+    ad->k_eff = beta > 0.0 ? KMAX : 0;
+  }
+}
+
+// y = H^{-1} g on the first min(m, k_eff) columns (back substitution), zero beyond
+__global__ void lsq_kernel(int m, ArnoldiDev* ad) {
+  if (threadIdx.x != 0) return;
+  const int kk = m < ad->k_eff ? m : ad->k_eff;
+  for (int i = KMAX - 1; i >= 0; --i) ad->y[i] = 0.0;
+  for (int i = kk - 1; i >= 0; --i) {
+    double s = ad->g[i];
+    for (int q = i + 1; q < kk; ++q) s -= ad->H[q * KMAX + i] * ad->y[q];
+    ad->y[i] = s / ad->H[i * KMAX + i];
+  }
+}
+
+template <class T>
+__global__ void dscale_kernel(long long n, const T* __restrict__ x, const double* __restrict__ scale, T* __restrict__ out) {
+  const T a = (T)*scale;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    out[e] = a * x[e];
+}
+
+// x = sum_v y_v Z_v with y in device memory
+template <int NV, class T>
+__global__ void dupdate_kernel(long long n, const T* __restrict__ Z, const double* __restrict__ y, T* __restrict__ x) {
+  T c[NV > 0 ? NV : 1];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) c[v] = (T)y[v];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    T s = T(0);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) s += c[v] * Z[v * n + e];
+    x[e] = s;
+  }
+}
+
+template <int NV, class T>
+static void dupdate_launch_t(int blocks, long long n, const T* Z, const double* y, T* x, cudaStream_t st) {
+  dupdate_kernel<NV, T><<<blocks, 256, 0, st>>>(n, Z, y, x);
+}
+
+template <class T, int... I>
+static void dupdate_dispatch(int nv, int blocks, long long n, const T* Z, const double* y, T* x, cudaStream_t st,
+                             std::integer_sequence<int, I...>) {
+  using F = void (*)(int, long long, const T*, const double*, T*, cudaStream_t);
+  static const F table[] = {&dupdate_launch_t<I, T>...};
+  table[nv](blocks, n, Z, y, x, st);
+}
+
+// Exactly m FGMRES iterations from x0 = 0, driven entirely on the device (no host
+// synchronisation, so the call can be captured in a CUDA graph).  A flexible outer
+// solve accepts this as a (variable) preconditioner.
+template <class T>
+static fv_status gmres_fixed_t(const fv_system* s, const T* b, T* x, int m, cudaStream_t st) {
+  if (m < 1 || m > KMAX - 1) return set_error("fixed-iteration FGMRES: iterations must be in [1, 31]"), FV_EINVAL;
+  fv_status rc = ensure_krylov<T>(s, m);
+  if (rc) return rc;
+  KrylovT<T>& k = kt<T>(s->kry);
+  const long long n = s->n;
+  const int lvl = FV_K_COARSE * s->level + (sizeof(T) == 4 ? FV_K_FP32 : 0);
+  {
+    ProfScope ps(FV_K_CGS + lvl, st);
+    cgs_launch<T>(0, n, b, nullptr, const_cast<T*>(b), k.part, 2, st);
+    start_kernel<<<1, 32, 0, st>>>(k.part, RBLOCKS, k.ad);
+    dscale_kernel<T><<<vblocks(n), 256, 0, st>>>(n, b, &k.ad->scale, k.V);
+  }
+  for (int j = 0; j < m; ++j) {
+    T* vj = k.V + (size_t)j * n;
+    T* zj = k.Z + (size_t)j * n;
+    if ((rc = precond_t<T>(s, vj, zj, st))) return rc;
+    if ((rc = apply_t<T>(s, zj, k.w, st))) return rc;
+    const int nv = j + 1;
+    ProfScope ps(FV_K_CGS + lvl, st);
+    CgsFuse f;
+    f.ticket = k.ticket;
+    f.out = k.h;
+    cgs_launch<T>(nv, n, k.V, nullptr, k.w, k.part, 0, st, f);
+    f.out = k.h + KMAX;
+    cgs_launch<T>(nv, n, k.V, k.h, k.w, k.part, 1, st, f);
+    f.out = k.h + 2 * KMAX, f.ad = k.ad, f.gj = j, f.hg = k.h;
+    cgs_launch<T>(nv, n, k.V, k.h + KMAX, k.w, k.part, 2, st, f);
+    if (j + 1 < m) dscale_kernel<T><<<vblocks(n), 256, 0, st>>>(n, k.w, &k.ad->scale, k.V + (size_t)(j + 1) * n);
+  }
+  ProfScope ps(FV_K_VEC, st);
+  lsq_kernel<<<1, 32, 0, st>>>(m, k.ad);
+  dupdate_dispatch<T>(m, vblocks(n), n, k.Z, k.ad->y, x, st, std::make_integer_sequence<int, KMAX>{});
+  FV_CUDA(cudaGetLastError());
+  return FV_OK;
+}
+
+fv_status gmres_fixed32(const fv_system* s, const float* b, float* x, int m, cudaStream_t st) {
+  return gmres_fixed_t<float>(s, b, x, m, st);
+}
+
 // ------------------------------------------------------------------ FGMRES
 template <class T>
 static fv_status gmres_t(const fv_system* s, const T* b, T* x, const fv_gmres_opts* o, fv_solve_stats* stats,
@@ -312,7 +486,7 @@ static fv_status gmres_t(const fv_system* s, const T* b, T* x, const fv_gmres_op
   if (rc) return rc;
   KrylovT<T>& k = kt<T>(s->kry);
   const long long n = s->n;
-  const int lvl = FV_K_COARSE * s->level;
+  const int lvl = FV_K_COARSE * s->level + (sizeof(T) == 4 ? FV_K_FP32 : 0);
   if (!inner) s->last_inner = 0;
   // r = b - A x
   if ((rc = apply_t<T>(s, x, k.r, st))) return rc;
@@ -337,12 +511,14 @@ static fv_status gmres_t(const fv_system* s, const T* b, T* x, const fv_gmres_op
       const int nv = j + 1;
       {
         ProfScope ps(FV_K_CGS + lvl, st);
-        cgs_launch<T>(nv, n, k.V, nullptr, k.w, k.part, 0, st);
-        reduce_kernel<<<1, RTHREADS, 0, st>>>(k.part, RBLOCKS, nv, k.h);
-        cgs_launch<T>(nv, n, k.V, k.h, k.w, k.part, 1, st);
-        reduce_kernel<<<1, RTHREADS, 0, st>>>(k.part, RBLOCKS, nv, k.h + KMAX);
-        cgs_launch<T>(nv, n, k.V, k.h + KMAX, k.w, k.part, 2, st);
-        reduce_kernel<<<1, RTHREADS, 0, st>>>(k.part, RBLOCKS, 1, k.h + 2 * KMAX);
+        CgsFuse f;
+        f.ticket = k.ticket;
+        f.out = k.h;
+        cgs_launch<T>(nv, n, k.V, nullptr, k.w, k.part, 0, st, f);
+        f.out = k.h + KMAX;
+        cgs_launch<T>(nv, n, k.V, k.h, k.w, k.part, 1, st, f);
+        f.out = k.h + 2 * KMAX;
+        cgs_launch<T>(nv, n, k.V, k.h + KMAX, k.w, k.part, 2, st, f);
       }
       FV_CUDA(cudaGetLastError());
       FV_CUDA(cudaMemcpyAsync(k.hhost, k.h, 3 * KMAX * sizeof(double), cudaMemcpyDeviceToHost, st));

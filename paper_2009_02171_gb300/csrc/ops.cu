@@ -13,17 +13,6 @@ namespace fv {
 // Sec. 3.3 overlap across block interfaces; one ghost layer).  Corner ghosts
 // (t = -1 or Ns on the xi sides): phi(-1,-1) = phi(-1,0) + phi(0,-1) - phi(0,0).
 template <class T, class GT>
-__device__ __forceinline__ typename GT::real interp_ghost(const GT& G, const T* x, int comp, int p, int side, int k,
-                                                          int t) {
-  using R = typename GT::real;
-  const int id = (p * 4 + side) * G.Ns + t;
-  const int q = G.gq[id];
-  const T* base = x + comp * G.N + ((long long)(q * G.Nr + k) * G.Ns) * G.Ns;
-  return G.gw[3 * id] * (R)base[G.gsrc[3 * id]] + G.gw[3 * id + 1] * (R)base[G.gsrc[3 * id + 1]] +
-         G.gw[3 * id + 2] * (R)base[G.gsrc[3 * id + 2]];
-}
-
-template <class T, class GT>
 __global__ void ghost_kernel(GT G, const T* __restrict__ x, T* __restrict__ gh, int d) {
   using R = typename GT::real;
   const int Ns = G.Ns, Nr = G.Nr;
@@ -75,35 +64,64 @@ fv_status fill_ghosts(const fv_system* s, const double* x, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------- apply
-// grid: x = tiles of the (j, i) plane, y = k, z = comp * 6 + panel (32-bit index math)
+// Two launches cover every row: the interior kernel maps threads onto the (Ns-2)^2
+// interior of each panel layer (no warp touches a panel edge, so no warp diverges into
+// the out-of-line edge path), the edge kernel onto the 4 (Ns-1) cells of each layer's
+// boundary ring.  grid.y = k, grid.z = comp * 6 + panel; 32-bit index math.
 template <int KIND, class T, class GT>
-__global__ void __launch_bounds__(256) apply_kernel(GT G, Phys ph, const T* __restrict__ x, const T* __restrict__ gh,
-                                                    T* __restrict__ y) {
-  const int ij = blockIdx.x * blockDim.x + threadIdx.x;
-  if (ij >= G.Ns * G.Ns) return;
-  const int i = ij % G.Ns, j = ij / G.Ns, k = blockIdx.y;
+__global__ void __launch_bounds__(256) apply_interior_kernel(GT G, Coefs<typename GT::real> cf,
+                                                             const T* __restrict__ x, const T* __restrict__ gh,
+                                                             T* __restrict__ y) {
+  const int ni = G.Ns - 2;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= ni * ni) return;
+  const int i = 1 + q % ni, j = 1 + q / ni, k = blockIdx.y;
   const int a = blockIdx.z / 6, p = blockIdx.z - 6 * a;
   ApplyAcc<T, typename GT::real> acc(G, x, gh);
-  if (KIND == FV_VTBE) vtbe_row(G, ph, acc, p, k, j, i, a);
-  else ppbe_row(G, ph, acc, p, k, j, i, a);
+  if (KIND == FV_VTBE) vtbe_row(G, cf, acc, p, k, j, i, a);
+  else ppbe_row(G, cf, acc, p, k, j, i, a);
   y[(long long)a * G.N + ((long long)(p * G.Nr + k) * G.Ns + j) * G.Ns + i] = (T)acc.sum;
 }
 
-template <class GT>
-static dim3 apply_grid(const GT& G, int d) { return dim3((G.Ns * G.Ns + 255) / 256, G.Nr, 6 * d); }
+template <int KIND, class T, class GT>
+__global__ void __launch_bounds__(128) apply_edge_kernel(GT G, Coefs<typename GT::real> cf, const T* __restrict__ x,
+                                                         const T* __restrict__ gh, T* __restrict__ y) {
+  const int Ns = G.Ns, ring = 4 * (Ns - 1);
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= ring) return;
+  // walk the boundary ring: j = 0 row, i = Ns-1 column, j = Ns-1 row, i = 0 column
+  const int s = q / (Ns - 1), t = q % (Ns - 1);
+  int i, j;
+  if (s == 0) i = t, j = 0;
+  else if (s == 1) i = Ns - 1, j = t;
+  else if (s == 2) i = Ns - 1 - t, j = Ns - 1;
+  else i = 0, j = Ns - 1 - t;
+  const int k = blockIdx.y, a = blockIdx.z / 6, p = blockIdx.z - 6 * a;
+  ApplyAcc<T, typename GT::real> acc(G, x, gh);
+  if (KIND == FV_VTBE) vtbe_row(G, cf, acc, p, k, j, i, a);
+  else ppbe_row(G, cf, acc, p, k, j, i, a);
+  y[(long long)a * G.N + ((long long)(p * G.Nr + k) * G.Ns + j) * G.Ns + i] = (T)acc.sum;
+}
+
+template <int KIND, class T, class GT>
+static void launch_apply(const GT& G, const Coefs<typename GT::real>& cf, int d, const T* x, const T* gh, T* y,
+                         cudaStream_t st) {
+  const int ni = G.Ns - 2;
+  apply_interior_kernel<KIND, T, GT><<<dim3((ni * ni + 255) / 256, G.Nr, 6 * d), 256, 0, st>>>(G, cf, x, gh, y);
+  apply_edge_kernel<KIND, T, GT><<<dim3((4 * (G.Ns - 1) + 127) / 128, G.Nr, 6 * d), 128, 0, st>>>(G, cf, x, gh, y);
+}
 
 fv_status apply_op(const fv_system* s, const double* x, double* y, cudaStream_t st) {
   const Geo& G = s->grid->geo;
   fv_status rc = fill_ghosts(s, x, st);
   if (rc) return rc;
-  Phys ph{s->phys.E, s->phys.Ra, s->phys.Pr, s->phys.Pm, s->phys.dt};
+  const Coefs<double> cf = make_coefs<double>(Phys{s->phys.E, s->phys.Ra, s->phys.Pr, s->phys.Pm, s->phys.dt},
+                                               s->grid->h.ri, s->grid->h.ro);
   const long long n = s->n;
   ProfScope ps((s->kind == FV_VTBE ? FV_K_APPLY_VTBE : FV_K_APPLY_PPBE) + FV_K_COARSE * s->level, st);
   (void)n;
-  if (s->kind == FV_VTBE)
-    apply_kernel<FV_VTBE, double, Geo><<<apply_grid(G, s->d), 256, 0, st>>>(G, ph, x, s->ghost, y);
-  else
-    apply_kernel<FV_PPBE, double, Geo><<<apply_grid(G, s->d), 256, 0, st>>>(G, ph, x, s->ghost, y);
+  if (s->kind == FV_VTBE) launch_apply<FV_VTBE>(G, cf, s->d, x, (const double*)s->ghost, y, st);
+  else launch_apply<FV_PPBE>(G, cf, s->d, x, (const double*)s->ghost, y, st);
   FV_CUDA(cudaGetLastError());
   return FV_OK;
 }
@@ -113,16 +131,15 @@ fv_status apply_op32(const fv_system* s, const float* x, float* y, cudaStream_t 
   const GeoF& G = s->grid->geof;
   const long long total = (long long)s->d * 6 * 4 * G.Nr * (G.Ns + 2);
   {
-    ProfScope ps(FV_K_GHOST + FV_K_COARSE * s->level, st);
+    ProfScope ps(FV_K_GHOST + FV_K_COARSE * s->level + FV_K_FP32, st);
     ghost_kernel<float, GeoF><<<grid_blocks(total, 256), 256, 0, st>>>(G, x, s->ghost32, s->d);
   }
   FV_CUDA(cudaGetLastError());
-  Phys ph{s->phys.E, s->phys.Ra, s->phys.Pr, s->phys.Pm, s->phys.dt};
-  ProfScope ps((s->kind == FV_VTBE ? FV_K_APPLY_VTBE : FV_K_APPLY_PPBE) + FV_K_COARSE * s->level, st);
-  if (s->kind == FV_VTBE)
-    apply_kernel<FV_VTBE, float, GeoF><<<apply_grid(G, s->d), 256, 0, st>>>(G, ph, x, s->ghost32, y);
-  else
-    apply_kernel<FV_PPBE, float, GeoF><<<apply_grid(G, s->d), 256, 0, st>>>(G, ph, x, s->ghost32, y);
+  const Coefs<float> cf = make_coefs<float>(Phys{s->phys.E, s->phys.Ra, s->phys.Pr, s->phys.Pm, s->phys.dt},
+                                             s->grid->h.ri, s->grid->h.ro);
+  ProfScope ps((s->kind == FV_VTBE ? FV_K_APPLY_VTBE : FV_K_APPLY_PPBE) + FV_K_COARSE * s->level + FV_K_FP32, st);
+  if (s->kind == FV_VTBE) launch_apply<FV_VTBE>(G, cf, s->d, x, (const float*)s->ghost32, y, st);
+  else launch_apply<FV_PPBE>(G, cf, s->d, x, (const float*)s->ghost32, y, st);
   FV_CUDA(cudaGetLastError());
   return FV_OK;
 }
@@ -159,11 +176,10 @@ fv_status apply_op_noalloc(const fv_system* s, const double* x, double* y, cudaS
   if (rc) return rc;
   ghost_kernel<double, Geo><<<grid_blocks(total, 256), 256, 0, st>>>(G, x, gh, s->d);
   FV_CUDA(cudaGetLastError());
-  Phys ph{s->phys.E, s->phys.Ra, s->phys.Pr, s->phys.Pm, s->phys.dt};
-  if (s->kind == FV_VTBE)
-    apply_kernel<FV_VTBE, double, Geo><<<apply_grid(G, s->d), 256, 0, st>>>(G, ph, x, gh, y);
-  else
-    apply_kernel<FV_PPBE, double, Geo><<<apply_grid(G, s->d), 256, 0, st>>>(G, ph, x, gh, y);
+  const Coefs<double> cf = make_coefs<double>(Phys{s->phys.E, s->phys.Ra, s->phys.Pr, s->phys.Pm, s->phys.dt},
+                                               s->grid->h.ri, s->grid->h.ro);
+  if (s->kind == FV_VTBE) launch_apply<FV_VTBE>(G, cf, s->d, x, (const double*)gh, y, st);
+  else launch_apply<FV_PPBE>(G, cf, s->d, x, (const double*)gh, y, st);
   FV_CUDA(cudaGetLastError());
   return FV_OK;
 }
@@ -217,7 +233,7 @@ struct AssembleAcc {
   }
 };
 
-__global__ void assemble_kernel(Geo G, Phys ph, int kind, int d, int count, const long long* __restrict__ cell_off,
+__global__ void assemble_kernel(Geo G, Coefs<double> cf, int kind, int d, int count, const long long* __restrict__ cell_off,
                                 const int* __restrict__ dims, const long long* __restrict__ gmap,
                                 double* __restrict__ off, double* __restrict__ diag) {
   const long long total = cell_off[count];
@@ -256,8 +272,8 @@ __global__ void assemble_kernel(Geo G, Phys ph, int kind, int d, int count, cons
       c /= G.Ns;
       const int k = (int)(c % G.Nr);
       const int p = (int)(c / G.Nr);
-      if (kind == FV_VTBE) vtbe_row(G, ph, acc, p, k, j, i, a);
-      else ppbe_row(G, ph, acc, p, k, j, i, a);
+      if (kind == FV_VTBE) vtbe_row(G, cf, acc, p, k, j, i, a);
+      else ppbe_row(G, cf, acc, p, k, j, i, a);
       for (int s = 0; s < 11; ++s)
         if (acc.col[s] < 0) acc.off[s] = 0.0;
     } else {
@@ -270,9 +286,10 @@ __global__ void assemble_kernel(Geo G, Phys ph, int kind, int d, int count, cons
 
 fv_status assemble_subdomains(fv_system* s) {
   const Geo& G = s->grid->geo;
-  Phys ph{s->phys.E, s->phys.Ra, s->phys.Pr, s->phys.Pm, s->phys.dt};
+  const Coefs<double> cf = make_coefs<double>(Phys{s->phys.E, s->phys.Ra, s->phys.Pr, s->phys.Pm, s->phys.dt},
+                                               s->grid->h.ri, s->grid->h.ro);
   const long long work = s->subs.total_cells * s->d;
-  assemble_kernel<<<grid_blocks(work, 128), 128>>>(G, ph, s->kind, s->d, s->subs.count, s->subs.cell_off,
+  assemble_kernel<<<grid_blocks(work, 128), 128>>>(G, cf, s->kind, s->d, s->subs.count, s->subs.cell_off,
                                                    s->subs.dims, s->subs.gmap, s->subs.off, s->subs.diag);
   FV_CUDA(cudaGetLastError());
   return FV_OK;

@@ -20,6 +20,7 @@
 //   restricted Neumann-pressure right-hand side is projected to zero coarse
 //   volume-weighted mean so the singular coarse system is consistent.
 #include <algorithm>
+#include <array>
 #include <cstring>
 #include <numeric>
 #include <vector>
@@ -73,21 +74,47 @@ fv_status build_subdomains(fv_system* s, const fv_grid* g) {
   const GridHost& h = g->h;
   const fv_pc_desc& pc = s->pc;
   const int delta = pc.overlap;
-  if (pc.p1 < 1 || pc.p2 < 1 || pc.p3 < 1 || pc.p1 > h.Ns || pc.p2 > h.Ns || pc.p3 > h.Nr || delta < 0 ||
-      delta > h.Ns / 2)
+  if ((pc.nboxes <= 0 && (pc.p1 < 1 || pc.p2 < 1 || pc.p3 < 1 || pc.p1 > h.Ns || pc.p2 > h.Ns || pc.p3 > h.Nr)) ||
+      delta < 0 || delta > h.Ns / 2)
     return set_error("fv_assemble_system: bad decomposition (p1, p2, p3, overlap)"), FV_EINVAL;
   const int d = s->d;
-  auto bi = split(h.Ns, pc.p1), bj = split(h.Ns, pc.p2), bk = split(h.Nr, pc.p3);
+  // owned boxes: the structured p1 x p2 x p3 split of each panel, or an explicit list
+  std::vector<std::array<int, 7>> own;
+  if (pc.nboxes > 0) {
+    if (!pc.boxes) return set_error("fv_assemble_system: nboxes > 0 with a null box list"), FV_EINVAL;
+    std::vector<unsigned char> cover((size_t)h.N, 0);
+    for (int q = 0; q < pc.nboxes; ++q) {
+      std::array<int, 7> bx;
+      for (int t = 0; t < 7; ++t) bx[t] = pc.boxes[7 * q + t];
+      const int p = bx[0];
+      if (p < 0 || p > 5 || bx[1] < 0 || bx[2] > h.Ns || bx[1] >= bx[2] || bx[3] < 0 || bx[4] > h.Ns || bx[3] >= bx[4] ||
+          bx[5] < 0 || bx[6] > h.Nr || bx[5] >= bx[6])
+        return set_error("fv_assemble_system: box outside the grid or empty"), FV_EINVAL;
+      for (int k = bx[5]; k < bx[6]; ++k)
+        for (int j = bx[3]; j < bx[4]; ++j)
+          for (int i = bx[1]; i < bx[2]; ++i) {
+            unsigned char& c = cover[((size_t)(p * h.Nr + k) * h.Ns + j) * h.Ns + i];
+            if (c) return set_error("fv_assemble_system: boxes overlap"), FV_EINVAL;
+            c = 1;
+          }
+      own.push_back(bx);
+    }
+    for (unsigned char c : cover)
+      if (!c) return set_error("fv_assemble_system: boxes do not cover the grid"), FV_EINVAL;
+  } else {
+    auto bi = split(h.Ns, pc.p1), bj = split(h.Ns, pc.p2), bk = split(h.Nr, pc.p3);
+    for (int p = 0; p < 6; ++p)
+      for (int c = 0; c < pc.p3; ++c)
+        for (int b = 0; b < pc.p2; ++b)
+          for (int a = 0; a < pc.p1; ++a) own.push_back({p, bi[a], bi[a + 1], bj[b], bj[b + 1], bk[c], bk[c + 1]});
+  }
   std::vector<long long> cell_off{0}, gmap;
   std::vector<int> dims;
   std::vector<unsigned char> owned;
   std::vector<std::vector<int>> orders, perms;
   int max_levels = 0, max_cols = 0;
-  for (int p = 0; p < 6; ++p)
-    for (int c = 0; c < pc.p3; ++c)
-      for (int b = 0; b < pc.p2; ++b)
-        for (int a = 0; a < pc.p1; ++a) {
-          const int i0 = bi[a], i1 = bi[a + 1], j0 = bj[b], j1 = bj[b + 1], k0 = bk[c], k1 = bk[c + 1];
+  for (const auto& bx : own) {
+          const int p = bx[0], i0 = bx[1], i1 = bx[2], j0 = bx[3], j1 = bx[4], k0 = bx[5], k1 = bx[6];
           const int lo_i = i0 - delta, lo_j = j0 - delta, lo_k = std::max(0, k0 - delta);
           const int nx = i1 - i0 + 2 * delta, ny = j1 - j0 + 2 * delta, nz = std::min(h.Nr, k1 + delta) - lo_k;
           dims.insert(dims.end(), {nx, ny, nz});
@@ -119,7 +146,7 @@ fv_status build_subdomains(fv_system* s, const fv_grid* g) {
               for (int li = lo_; li <= hi_; ++li) pp[((L - li - 2 * lj) * ny + lj) * nx + li] = pos_++;
             }
           perms.push_back(pp);
-        }
+  }
   const int count = (int)dims.size() / 3;
   // level offsets per subdomain, padded to max_levels + 1
   std::vector<int> level_off((size_t)count * (max_levels + 1), 0), order;
@@ -318,8 +345,12 @@ fv_status prepare_sweeps(fv_system* s, int fp32) {
   release(s, S.off), release(s, S.diag), release(s, S.perm);
   S.off = S.diag = nullptr;
   S.perm = nullptr;
-  // CTA shape: one thread per (i, j) column, at most 1024 threads (columns loop)
-  S.threads = std::min(1024, ((S.max_cols + 31) / 32) * 32);
+  // CTA shape: one thread per (i, j) column, at most 1024 threads (columns loop); the
+  // register-prefetching d = 2 sweeps take up to 2 columns per thread on at most 704 threads
+  // (the generic kernels, used for d = 7 and for very wide d = 2 boxes, take at most 704 threads)
+  S.threads = std::min(704, ((S.max_cols + 31) / 32) * 32);
+  if (d == 2 && S.max_cols <= 1024) S.threads = ((S.max_cols + 31) / 32) * 32;
+  if (d == 2 && S.max_cols > 1024 && S.max_cols <= 1408) S.threads = ((S.max_cols + 1) / 2 + 31) / 32 * 32;
   // the widest box's level table; the 4-plane ring in shared memory when it fits
   std::vector<int> dims(3 * S.count);
   FV_CUDA(cudaMemcpy(dims.data(), S.dims, dims.size() * sizeof(int), cudaMemcpyDeviceToHost));
@@ -407,7 +438,7 @@ __device__ __forceinline__ void build_tables(const SweepBox& b, int* lvl, int* r
 }
 
 template <class T, int D>
-__global__ void __launch_bounds__(1024) ras_fwd_kernel(long long N, const long long* __restrict__ cell_off,
+__global__ void __launch_bounds__(704) ras_fwd_kernel(long long N, const long long* __restrict__ cell_off,
                                                        const int* __restrict__ dims, const int* __restrict__ lpt,
                                                        const T* __restrict__ F, T* __restrict__ loc, T* ring_g,
                                                        int ring_in_smem, int max_cols) {
@@ -431,23 +462,45 @@ __global__ void __launch_bounds__(1024) ras_fwd_kernel(long long N, const long l
       const int pk = k & 3;
       T* rp = ring + (size_t)(pk * b.ncols) * D;
       const T* r0 = ring + (size_t)(((k - 1) & 3) * b.ncols + col) * D;
-      double y[D];
+      T y[D];
 #pragma unroll
-      for (int a = 0; a < D; ++a) y[a] = (double)Lb[a * nc + pos];
+      for (int a = 0; a < D; ++a) y[a] = Lb[a * nc + pos];
+      if constexpr (sizeof(T) == 4 || D < 7) {
+        // every factor slot exists (zero where the neighbour is outside the box): load them all
+        // unconditionally so they are in flight together; only the neighbour reads are guarded
+        T fl[5 * D], fd[D * D];
 #pragma unroll
-      for (int a = 0; a < D; ++a) {
-        if (k > 0) y[a] -= (double)Fb[(0 * D + a) * nc + pos] * (double)r0[a];
-        if (i > 0 && j > 0) y[a] -= (double)Fb[(1 * D + a) * nc + pos] * (double)rp[(col - b.nx - 1) * D + a];
-        if (j > 0) y[a] -= (double)Fb[(2 * D + a) * nc + pos] * (double)rp[(col - b.nx) * D + a];
-        if (j > 0 && i + 1 < b.nx) y[a] -= (double)Fb[(3 * D + a) * nc + pos] * (double)rp[(col - b.nx + 1) * D + a];
-        if (i > 0) y[a] -= (double)Fb[(4 * D + a) * nc + pos] * (double)rp[(col - 1) * D + a];
+        for (int q = 0; q < 5 * D; ++q) fl[q] = Fb[q * nc + pos];
 #pragma unroll
-        for (int c = 0; c < a; ++c) y[a] -= (double)Fb[(5 * D + a * D + c) * nc + pos] * y[c];
+        for (int a = 1; a < D; ++a)
+#pragma unroll
+          for (int c = 0; c < a; ++c) fd[a * D + c] = Fb[(5 * D + a * D + c) * nc + pos];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          if (k > 0) y[a] -= fl[0 * D + a] * r0[a];
+          if (i > 0 && j > 0) y[a] -= fl[1 * D + a] * rp[(col - b.nx - 1) * D + a];
+          if (j > 0) y[a] -= fl[2 * D + a] * rp[(col - b.nx) * D + a];
+          if (j > 0 && i + 1 < b.nx) y[a] -= fl[3 * D + a] * rp[(col - b.nx + 1) * D + a];
+          if (i > 0) y[a] -= fl[4 * D + a] * rp[(col - 1) * D + a];
+#pragma unroll
+          for (int c = 0; c < a; ++c) y[a] -= fd[a * D + c] * y[c];
+        }
+      } else {  // FP64 7x7 blocks: too many registers to batch; FP64 arithmetic bounds this path
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          if (k > 0) y[a] -= Fb[(0 * D + a) * nc + pos] * r0[a];
+          if (i > 0 && j > 0) y[a] -= Fb[(1 * D + a) * nc + pos] * rp[(col - b.nx - 1) * D + a];
+          if (j > 0) y[a] -= Fb[(2 * D + a) * nc + pos] * rp[(col - b.nx) * D + a];
+          if (j > 0 && i + 1 < b.nx) y[a] -= Fb[(3 * D + a) * nc + pos] * rp[(col - b.nx + 1) * D + a];
+          if (i > 0) y[a] -= Fb[(4 * D + a) * nc + pos] * rp[(col - 1) * D + a];
+#pragma unroll
+          for (int c = 0; c < a; ++c) y[a] -= Fb[(5 * D + a * D + c) * nc + pos] * y[c];
+        }
       }
 #pragma unroll
       for (int a = 0; a < D; ++a) {
-        rp[col * D + a] = (T)y[a];
-        Lb[a * nc + pos] = (T)y[a];
+        rp[col * D + a] = y[a];
+        Lb[a * nc + pos] = y[a];
       }
     }
     __syncthreads();
@@ -455,7 +508,7 @@ __global__ void __launch_bounds__(1024) ras_fwd_kernel(long long N, const long l
 }
 
 template <class T, int D>
-__global__ void __launch_bounds__(1024) ras_bwd_kernel(long long N, const long long* __restrict__ cell_off,
+__global__ void __launch_bounds__(704) ras_bwd_kernel(long long N, const long long* __restrict__ cell_off,
                                                        const int* __restrict__ dims, const int* __restrict__ lpt,
                                                        const T* __restrict__ F, T* __restrict__ loc, T* ring_g,
                                                        int ring_in_smem, int max_cols) {
@@ -478,28 +531,202 @@ __global__ void __launch_bounds__(1024) ras_bwd_kernel(long long N, const long l
       const long long pos = lvl[L] + rowoff[L * b.ny + j] + i - max(0, L - 2 * j - (b.nz - 1));
       T* rp = ring + (size_t)((k & 3) * b.ncols) * D;
       const T* r1 = ring + (size_t)(((k + 1) & 3) * b.ncols + col) * D;
-      double x[D];
+      constexpr int U = 5 * D + D * D;
+      T x[D];
 #pragma unroll
-      for (int a = 0; a < D; ++a) x[a] = (double)Lb[a * nc + pos];
+      for (int a = 0; a < D; ++a) x[a] = Lb[a * nc + pos];
+      if constexpr (sizeof(T) == 4 || D < 7) {
+        T fu[5 * D], fd[D * D];
 #pragma unroll
-      for (int a = D - 1; a >= 0; --a) {
+        for (int q = 0; q < 5 * D; ++q) fu[q] = Fb[(U + q) * nc + pos];
 #pragma unroll
-        for (int c = a + 1; c < D; ++c) x[a] -= (double)Fb[(5 * D + a * D + c) * nc + pos] * x[c];
-        const int U = 5 * D + D * D;
-        if (i + 1 < b.nx) x[a] -= (double)Fb[(U + 0 * D + a) * nc + pos] * (double)rp[(col + 1) * D + a];
-        if (i > 0 && j + 1 < b.ny) x[a] -= (double)Fb[(U + 1 * D + a) * nc + pos] * (double)rp[(col + b.nx - 1) * D + a];
-        if (j + 1 < b.ny) x[a] -= (double)Fb[(U + 2 * D + a) * nc + pos] * (double)rp[(col + b.nx) * D + a];
-        if (i + 1 < b.nx && j + 1 < b.ny)
-          x[a] -= (double)Fb[(U + 3 * D + a) * nc + pos] * (double)rp[(col + b.nx + 1) * D + a];
-        if (k + 1 < b.nz) x[a] -= (double)Fb[(U + 4 * D + a) * nc + pos] * (double)r1[a];
-        x[a] /= (double)Fb[(5 * D + a * D + a) * nc + pos];
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+          for (int c = a; c < D; ++c) fd[a * D + c] = Fb[(5 * D + a * D + c) * nc + pos];
+#pragma unroll
+        for (int a = D - 1; a >= 0; --a) {
+#pragma unroll
+          for (int c = a + 1; c < D; ++c) x[a] -= fd[a * D + c] * x[c];
+          if (i + 1 < b.nx) x[a] -= fu[0 * D + a] * rp[(col + 1) * D + a];
+          if (i > 0 && j + 1 < b.ny) x[a] -= fu[1 * D + a] * rp[(col + b.nx - 1) * D + a];
+          if (j + 1 < b.ny) x[a] -= fu[2 * D + a] * rp[(col + b.nx) * D + a];
+          if (i + 1 < b.nx && j + 1 < b.ny) x[a] -= fu[3 * D + a] * rp[(col + b.nx + 1) * D + a];
+          if (k + 1 < b.nz) x[a] -= fu[4 * D + a] * r1[a];
+          x[a] /= fd[a * D + a];
+        }
+      } else {
+#pragma unroll
+        for (int a = D - 1; a >= 0; --a) {
+#pragma unroll
+          for (int c = a + 1; c < D; ++c) x[a] -= Fb[(5 * D + a * D + c) * nc + pos] * x[c];
+          if (i + 1 < b.nx) x[a] -= Fb[(U + 0 * D + a) * nc + pos] * rp[(col + 1) * D + a];
+          if (i > 0 && j + 1 < b.ny) x[a] -= Fb[(U + 1 * D + a) * nc + pos] * rp[(col + b.nx - 1) * D + a];
+          if (j + 1 < b.ny) x[a] -= Fb[(U + 2 * D + a) * nc + pos] * rp[(col + b.nx) * D + a];
+          if (i + 1 < b.nx && j + 1 < b.ny)
+            x[a] -= Fb[(U + 3 * D + a) * nc + pos] * rp[(col + b.nx + 1) * D + a];
+          if (k + 1 < b.nz) x[a] -= Fb[(U + 4 * D + a) * nc + pos] * r1[a];
+          x[a] /= Fb[(5 * D + a * D + a) * nc + pos];
+        }
       }
 #pragma unroll
       for (int a = 0; a < D; ++a) {
-        rp[col * D + a] = (T)x[a];
-        Lb[a * nc + pos] = (T)x[a];
+        rp[col * D + a] = x[a];
+        Lb[a * nc + pos] = x[a];
       }
     }
+    __syncthreads();
+  }
+}
+
+
+// D = 2 sweeps with the next wavefront step's factors and vector entries loaded into
+// registers before the barrier (their latency overlaps the barrier and this step's work).
+// At most MC columns per thread.
+template <class T, int MC, class V>
+__global__ void __launch_bounds__(MC == 1 ? 1024 : 704) ras_fwd2_kernel(const long long* __restrict__ cell_off,
+                                                        const int* __restrict__ dims, const int* __restrict__ lpt,
+                                                        const T* __restrict__ F, T* __restrict__ loc, T* ring_g,
+                                                        int ring_in_smem, int max_cols, long long N,
+                                                        const long long* __restrict__ gmap_p,
+                                                        const V* __restrict__ r) {
+  constexpr int D = 2, NF = 5 * D + 1;  // lower slots + the diagonal block's lower entry
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int sd = lpt[blockIdx.x];
+  const SweepBox b = sweep_box(cell_off, dims, sd);
+  const size_t ring_bytes = ring_in_smem ? ((4 * (size_t)max_cols * D * sizeof(T) + 15) / 16 * 16) : 0;
+  T* ring = ring_in_smem ? (T*)smem : ring_g + (size_t)blockIdx.x * 4 * max_cols * D;
+  int* lvl = (int*)(smem + ring_bytes);
+  int* rowoff = lvl + b.levels + 1;
+  build_tables(b, lvl, rowoff);
+  const T* Fb = F + b.base * (10 * D + D * D);
+  T* Lb = loc + b.base * D;
+  const long long nc = b.nc;
+  int ci[MC], cj[MC];
+  T f[MC][NF], y0[MC][D];
+  long long ps[MC];
+#pragma unroll
+  for (int m = 0; m < MC; ++m) {
+    const int col = threadIdx.x + m * blockDim.x;
+    cj[m] = col < b.ncols ? col / b.nx : -1;
+    ci[m] = col < b.ncols ? col - cj[m] * b.nx : 0;
+  }
+  auto fetch = [&](int L, int m) {
+    const int i = ci[m], j = cj[m], k = L - i - 2 * j;
+    ps[m] = -1;
+    if (j < 0 || k < 0 || k >= b.nz || L >= b.levels) return;
+    const long long pos = lvl[L] + rowoff[L * b.ny + j] + i - max(0, L - 2 * j - (b.nz - 1));
+    ps[m] = pos;
+    const long long g = gmap_p[b.base + pos];  // R_i^delta r gathered here (zero past cube corners)
+#pragma unroll
+    for (int a = 0; a < D; ++a) y0[m][a] = g >= 0 ? (T)r[a * N + g] : T(0);
+#pragma unroll
+    for (int q = 0; q < 5 * D; ++q) f[m][q] = Fb[q * nc + pos];
+    f[m][5 * D] = Fb[(5 * D + 1 * D + 0) * nc + pos];  // diagonal block entry (1, 0)
+  };
+#pragma unroll
+  for (int m = 0; m < MC; ++m) fetch(0, m);
+  for (int L = 0; L < b.levels; ++L) {
+#pragma unroll
+    for (int m = 0; m < MC; ++m) {
+      if (ps[m] < 0) continue;
+      const int i = ci[m], j = cj[m], k = L - i - 2 * j, col = j * b.nx + i;
+      const T* rp = ring + (size_t)((k & 3) * b.ncols) * D;
+      const T* r0 = ring + (size_t)(((k - 1) & 3) * b.ncols + col) * D;
+      T y[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        y[a] = y0[m][a];
+        if (k > 0) y[a] -= f[m][0 * D + a] * r0[a];
+        if (i > 0 && j > 0) y[a] -= f[m][1 * D + a] * rp[(col - b.nx - 1) * D + a];
+        if (j > 0) y[a] -= f[m][2 * D + a] * rp[(col - b.nx) * D + a];
+        if (j > 0 && i + 1 < b.nx) y[a] -= f[m][3 * D + a] * rp[(col - b.nx + 1) * D + a];
+        if (i > 0) y[a] -= f[m][4 * D + a] * rp[(col - 1) * D + a];
+      }
+      y[1] -= f[m][5 * D] * y[0];
+      T* w = ring + (size_t)((k & 3) * b.ncols + col) * D;
+#pragma unroll
+      for (int a = 0; a < D; ++a) w[a] = y[a], Lb[a * nc + ps[m]] = y[a];
+    }
+#pragma unroll
+    for (int m = 0; m < MC; ++m) fetch(L + 1, m);
+    __syncthreads();
+  }
+}
+
+template <class T, int MC, class V>
+__global__ void __launch_bounds__(MC == 1 ? 1024 : 704) ras_bwd2_kernel(const long long* __restrict__ cell_off,
+                                                        const int* __restrict__ dims, const int* __restrict__ lpt,
+                                                        const T* __restrict__ F, T* __restrict__ loc, T* ring_g,
+                                                        int ring_in_smem, int max_cols, long long N,
+                                                        const long long* __restrict__ gmap_p,
+                                                        const unsigned char* __restrict__ owned_p,
+                                                        V* __restrict__ z) {
+  constexpr int D = 2, U = 5 * D + D * D, NF = 5 * D + 3;  // upper slots + diag (0,1), (0,0), (1,1)
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int sd = lpt[blockIdx.x];
+  const SweepBox b = sweep_box(cell_off, dims, sd);
+  const size_t ring_bytes = ring_in_smem ? ((4 * (size_t)max_cols * D * sizeof(T) + 15) / 16 * 16) : 0;
+  T* ring = ring_in_smem ? (T*)smem : ring_g + (size_t)blockIdx.x * 4 * max_cols * D;
+  int* lvl = (int*)(smem + ring_bytes);
+  int* rowoff = lvl + b.levels + 1;
+  build_tables(b, lvl, rowoff);
+  const T* Fb = F + b.base * (10 * D + D * D);
+  T* Lb = loc + b.base * D;
+  const long long nc = b.nc;
+  int ci[MC], cj[MC];
+  T f[MC][NF], x0[MC][D];
+  long long ps[MC];
+#pragma unroll
+  for (int m = 0; m < MC; ++m) {
+    const int col = threadIdx.x + m * blockDim.x;
+    cj[m] = col < b.ncols ? col / b.nx : -1;
+    ci[m] = col < b.ncols ? col - cj[m] * b.nx : 0;
+  }
+  auto fetch = [&](int L, int m) {
+    const int i = ci[m], j = cj[m], k = L - i - 2 * j;
+    ps[m] = -1;
+    if (j < 0 || L < 0 || k < 0 || k >= b.nz) return;
+    const long long pos = lvl[L] + rowoff[L * b.ny + j] + i - max(0, L - 2 * j - (b.nz - 1));
+    ps[m] = pos;
+#pragma unroll
+    for (int a = 0; a < D; ++a) x0[m][a] = Lb[a * nc + pos];
+#pragma unroll
+    for (int q = 0; q < 5 * D; ++q) f[m][q] = Fb[(U + q) * nc + pos];
+    f[m][5 * D] = Fb[(5 * D + 0 * D + 1) * nc + pos];      // diag (0, 1)
+    f[m][5 * D + 1] = Fb[(5 * D + 0 * D + 0) * nc + pos];  // diag (0, 0)
+    f[m][5 * D + 2] = Fb[(5 * D + 1 * D + 1) * nc + pos];  // diag (1, 1)
+  };
+#pragma unroll
+  for (int m = 0; m < MC; ++m) fetch(b.levels - 1, m);
+  for (int L = b.levels - 1; L >= 0; --L) {
+#pragma unroll
+    for (int m = 0; m < MC; ++m) {
+      if (ps[m] < 0) continue;
+      const int i = ci[m], j = cj[m], k = L - i - 2 * j, col = j * b.nx + i;
+      const T* rp = ring + (size_t)((k & 3) * b.ncols) * D;
+      const T* r1 = ring + (size_t)(((k + 1) & 3) * b.ncols + col) * D;
+      T x[D] = {x0[m][0], x0[m][1]};
+#pragma unroll
+      for (int a = D - 1; a >= 0; --a) {
+        if (a == 0) x[0] -= f[m][5 * D] * x[1];
+        if (i + 1 < b.nx) x[a] -= f[m][0 * D + a] * rp[(col + 1) * D + a];
+        if (i > 0 && j + 1 < b.ny) x[a] -= f[m][1 * D + a] * rp[(col + b.nx - 1) * D + a];
+        if (j + 1 < b.ny) x[a] -= f[m][2 * D + a] * rp[(col + b.nx) * D + a];
+        if (i + 1 < b.nx && j + 1 < b.ny) x[a] -= f[m][3 * D + a] * rp[(col + b.nx + 1) * D + a];
+        if (k + 1 < b.nz) x[a] -= f[m][4 * D + a] * r1[a];
+        x[a] /= f[m][5 * D + 1 + a];
+      }
+      T* w = ring + (size_t)((k & 3) * b.ncols + col) * D;
+#pragma unroll
+      for (int a = 0; a < D; ++a) w[a] = x[a];
+      if (owned_p[b.base + ps[m]]) {  // (R_i^0)^T: scatter the owned cells
+        const long long g = gmap_p[b.base + ps[m]];
+#pragma unroll
+        for (int a = 0; a < D; ++a) z[a * N + g] = (V)x[a];
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < MC; ++m) fetch(L - 1, m);
     __syncthreads();
   }
 }
@@ -510,18 +737,43 @@ static fv_status ras_apply_t(const fv_system* s, const V* r, V* z, cudaStream_t 
   const long long N = s->grid->geo.N;
   T* loc = (T*)S.loc;
   const dim3 gs(S.count, 4);
+  const int mc = (D == 2 && S.max_cols <= S.threads && S.threads <= 1024) ? 1
+                 : (D == 2 && S.max_cols <= 2 * S.threads && S.threads <= 704) ? 2
+                                                                                 : 0;
+  const int pf = (s->kind == FV_VTBE ? FV_K_RAS_FWD_VTBE : FV_K_RAS_FWD_PPBE) + FV_K_COARSE * s->level +
+                 FV_K_FP32 * S.fp32;
+  const int pb = (s->kind == FV_VTBE ? FV_K_RAS_BWD_VTBE : FV_K_RAS_BWD_PPBE) + FV_K_COARSE * s->level +
+                 FV_K_FP32 * S.fp32;
   {
-    ProfScope ps(FV_K_RAS_FWD + FV_K_COARSE * s->level, st);
-    gather_kernel<T, V><<<gs, 256, 0, st>>>(D, N, S.cell_off, S.gmap_p, r, loc);
-    ras_fwd_kernel<T, D><<<S.count, S.threads, S.smem, st>>>(N, S.cell_off, S.dims, S.lpt, (const T*)S.F, loc,
-                                                             (T*)S.ring, S.ring_in_smem, S.max_cols);
+    ProfScope ps(pf, st);
+    if (mc == 1)
+      ras_fwd2_kernel<T, 1, V><<<S.count, S.threads, S.smem, st>>>(S.cell_off, S.dims, S.lpt, (const T*)S.F, loc,
+                                                                   (T*)S.ring, S.ring_in_smem, S.max_cols, N, S.gmap_p, r);
+    else if (mc == 2)
+      ras_fwd2_kernel<T, 2, V><<<S.count, S.threads, S.smem, st>>>(S.cell_off, S.dims, S.lpt, (const T*)S.F, loc,
+                                                                   (T*)S.ring, S.ring_in_smem, S.max_cols, N, S.gmap_p, r);
+    else {
+      gather_kernel<T, V><<<gs, 256, 0, st>>>(D, N, S.cell_off, S.gmap_p, r, loc);
+      ras_fwd_kernel<T, D><<<S.count, S.threads, S.smem, st>>>(N, S.cell_off, S.dims, S.lpt, (const T*)S.F, loc,
+                                                               (T*)S.ring, S.ring_in_smem, S.max_cols);
+    }
   }
   FV_CUDA(cudaGetLastError());
   {
-    ProfScope ps(FV_K_RAS_BWD + FV_K_COARSE * s->level, st);
-    ras_bwd_kernel<T, D><<<S.count, S.threads, S.smem, st>>>(N, S.cell_off, S.dims, S.lpt, (const T*)S.F, loc,
-                                                             (T*)S.ring, S.ring_in_smem, S.max_cols);
-    scatter_kernel<T, V><<<gs, 256, 0, st>>>(D, N, S.cell_off, S.gmap_p, S.owned_p, loc, z);
+    ProfScope ps(pb, st);
+    if (mc == 1)
+      ras_bwd2_kernel<T, 1, V><<<S.count, S.threads, S.smem, st>>>(S.cell_off, S.dims, S.lpt, (const T*)S.F, loc,
+                                                                   (T*)S.ring, S.ring_in_smem, S.max_cols, N, S.gmap_p,
+                                                                   S.owned_p, z);
+    else if (mc == 2)
+      ras_bwd2_kernel<T, 2, V><<<S.count, S.threads, S.smem, st>>>(S.cell_off, S.dims, S.lpt, (const T*)S.F, loc,
+                                                                   (T*)S.ring, S.ring_in_smem, S.max_cols, N, S.gmap_p,
+                                                                   S.owned_p, z);
+    else {
+      ras_bwd_kernel<T, D><<<S.count, S.threads, S.smem, st>>>(N, S.cell_off, S.dims, S.lpt, (const T*)S.F, loc,
+                                                               (T*)S.ring, S.ring_in_smem, S.max_cols);
+      scatter_kernel<T, V><<<gs, 256, 0, st>>>(D, N, S.cell_off, S.gmap_p, S.owned_p, loc, z);
+    }
   }
   FV_CUDA(cudaGetLastError());
   return FV_OK;
@@ -533,6 +785,12 @@ template <class T, int D>
 static fv_status set_smem_attr(int limit) {
   FV_CUDA(cudaFuncSetAttribute(ras_fwd_kernel<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
   FV_CUDA(cudaFuncSetAttribute(ras_bwd_kernel<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+  if (D == 2) {
+    FV_CUDA(cudaFuncSetAttribute(ras_fwd2_kernel<T, 1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    FV_CUDA(cudaFuncSetAttribute(ras_fwd2_kernel<T, 2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    FV_CUDA(cudaFuncSetAttribute(ras_bwd2_kernel<T, 1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    FV_CUDA(cudaFuncSetAttribute(ras_bwd2_kernel<T, 2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+  }
   return FV_OK;
 }
 
@@ -634,16 +892,43 @@ fv_status prolong_inject(const fv_grid* g, int d, const double* xc, double* x, c
   return prolong_t<double>(g, d, xc, x, st);
 }
 
-// Mixed precision: M^{-1} r of the FP64 outer solve is an FP32 inner FGMRES solve.
+// Mixed precision: M^{-1} r of the FP64 outer solve is an FP32 inner FGMRES of exactly
+// inner_maxit iterations (its two-level preconditioner's coarse solve: exactly
+// coarse_maxit iterations), driven on the device.  The sequence r32 -> x32 has fixed
+// buffers and no host synchronisation: it is captured once into a CUDA graph and
+// replayed (kernel timing, when enabled, runs it eagerly instead).
+static fv_status inner_sequence(const fv_system* s, cudaStream_t st) {
+  return gmres_fixed32(s, s->r32, s->x32, s->pc.inner_maxit, st);
+}
+
 static fv_status inner_solve(const fv_system* s, const double* r, double* z, cudaStream_t st) {
   fv_status rc;
   if ((rc = to_fp32(s->n, r, s->r32, st))) return rc;
-  FV_CUDA(cudaMemsetAsync(s->x32, 0, s->n * sizeof(float), st));
-  fv_gmres_opts o{s->pc.inner_restart, s->pc.inner_maxit, 0.0, s->pc.inner_rtol};
-  fv_solve_stats is{};
-  rc = gmres32(s, s->r32, s->x32, &o, &is, st);
-  if (rc && rc != FV_ENOCONV) return rc;
-  s->last_inner += is.iters;
+  if (prof_enabled()) {
+    if ((rc = inner_sequence(s, st))) return rc;
+  } else {
+    fv_system* sm = const_cast<fv_system*>(s);
+    if (!sm->inner_warm) {
+      // first call: run eagerly so every lazily allocated workspace exists before capture
+      if ((rc = inner_sequence(s, st))) return rc;
+      sm->inner_warm = 1;
+    } else if (!sm->inner_graph) {
+      cudaStream_t cs;
+      FV_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+      cudaGraph_t graph;
+      FV_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+      rc = inner_sequence(s, cs);
+      cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+      cudaStreamDestroy(cs);
+      if (rc) return rc;
+      FV_CUDA(ce);
+      ce = cudaGraphInstantiate(&sm->inner_graph, graph, 0);
+      cudaGraphDestroy(graph);
+      FV_CUDA(ce);
+    }
+    if (sm->inner_graph) FV_CUDA(cudaGraphLaunch(s->inner_graph, st));
+  }
+  s->last_inner += s->pc.inner_maxit;
   return to_fp64(s->n, s->x32, z, st);
 }
 
@@ -694,14 +979,10 @@ fv_status precond_apply32(const fv_system* s, const float* r, float* z, cudaStre
     if ((rc = restrict_t<float>(s->grid, s->d, r, s->xc32, st))) return rc;
     if (s->kind == FV_PPBE && (rc = weighted_mean_remove32(c->grid, s->xc32, st, s->red, s->red + 32 * 304)))
       return rc;
-    FV_CUDA(cudaMemsetAsync(s->ec32, 0, c->n * sizeof(float), st));
   }
   {
     ProfScope ph(FV_K_PHASE_PC_C, st);
-    fv_gmres_opts o{s->pc.coarse_restart, s->pc.coarse_maxit, 0.0, s->pc.coarse_rtol};
-    fv_solve_stats cs{};
-    rc = gmres32(c, s->xc32, s->ec32, &o, &cs, st);
-    if (rc && rc != FV_ENOCONV) return rc;
+    if ((rc = gmres_fixed32(c, s->xc32, s->ec32, s->pc.coarse_maxit, st))) return rc;
   }
   {
     ProfScope ph(FV_K_PHASE_PC_I, st);

@@ -17,6 +17,8 @@ Prof g_prof;
 constexpr size_t kPairs = 65536;
 }  // namespace
 
+bool prof_enabled() { return g_prof.on; }
+
 int prof_begin(int category, cudaStream_t st) {
   if (!g_prof.on) return -1;
   if (g_prof.used >= kPairs) {

@@ -204,40 +204,64 @@ struct Phys {
   double E, Ra, Pr, Pm, dt;
 };
 
+// Physics coefficients of the VTBE / PPBE rows, computed once on the host in
+// the coefficient type R (no division or FP64 arithmetic per row).
+template <class R>
+struct Coefs {
+  R one;    // 1
+  R h;      // -dt/2
+  R cor;    // -dt/2 * 2/E        (Coriolis, u_y in the u_x row; negated in the u_y row)
+  R r1;     // -dt/2 * Ra/(E r_o) (buoyancy, times r_k xhat_a)
+  R r2;     // -dt/2 * r_i r_o    (times xhat_c / r^2)
+  R hpr;    // -dt/2 / Pr
+  R hpm;    // -dt/2 / Pm
+  R pp;     // dt/(2E)            (PPBE)
+};
+
+template <class R>
+inline Coefs<R> make_coefs(const Phys& ph, double ri, double ro) {
+  const double h = -0.5 * ph.dt;
+  Coefs<R> c;
+  c.one = R(1), c.h = R(h), c.cor = R(h * 2.0 / ph.E), c.r1 = R(h * ph.Ra / (ph.E * ro)), c.r2 = R(h * ri * ro);
+  c.hpr = R(h / ph.Pr), c.hpm = R(h / ph.Pm), c.pp = R(0.5 * ph.dt / ph.E);
+  return c;
+}
+
 // Row `a` of the VTBE matrix A = I - dt/2 M (eqn:tsvelocity, eqn:tstemperature, eqn:tsmag):
 //   u_a:   u - dt/2 [lap u - (2/E) z x u + Ra/(E r_o) Theta r]_a
 //   Theta: Theta - dt/2 [lap Theta / Pr + r_i r_o / r^3 (u . r)]
 //   B_a:   B - dt/2 [lap B / Pm]_a
 template <class GT, class Acc>
-__device__ __forceinline__ void vtbe_row(const GT& G, const Phys& ph, Acc& acc, int p, int k, int j, int i, int a) {
+__device__ __forceinline__ void vtbe_row(const GT& G, const Coefs<typename GT::real>& cf, Acc& acc, int p, int k,
+                                         int j, int i, int a) {
   using R = typename GT::real;
-  const R h = R(-0.5 * ph.dt);
-  acc.cell(R(1), p, k, j, i, a);
+  acc.cell(cf.one, p, k, j, i, a);
   if (a < 3) {
-    lap_row(G, acc, h, p, k, j, i, a, WALL_ODD, 0);
-    if (a == 0) acc.cell(R(h * (2.0 / ph.E)), p, k, j, i, 1);
-    if (a == 1) acc.cell(R(-h * (2.0 / ph.E)), p, k, j, i, 0);
+    lap_row(G, acc, cf.h, p, k, j, i, a, WALL_ODD, 0);
+    if (a == 0) acc.cell(cf.cor, p, k, j, i, 1);
+    if (a == 1) acc.cell(-cf.cor, p, k, j, i, 0);
     R xl[3], x[3];
     for (int c = 0; c < 3; ++c) xl[c] = G.xhat[3 * (j * G.Ns + i) + c];
     rotate(p, xl, x);
-    acc.cell(R(h * ph.Ra / (ph.E * (double)G.ro)) * G.rc[k] * x[a], p, k, j, i, 3);
+    acc.cell(cf.r1 * G.rc[k] * x[a], p, k, j, i, 3);
   } else if (a == 3) {
-    lap_row(G, acc, R(h / ph.Pr), p, k, j, i, 3, WALL_ODD, 0);
+    lap_row(G, acc, cf.hpr, p, k, j, i, 3, WALL_ODD, 0);
     R xl[3], x[3];
     for (int c = 0; c < 3; ++c) xl[c] = G.xhat[3 * (j * G.Ns + i) + c];
     rotate(p, xl, x);
     const R r = G.rc[k];
-    for (int c = 0; c < 3; ++c) acc.cell(h * G.ri * G.ro / (r * r) * x[c], p, k, j, i, c);
+    const R w = cf.r2 / (r * r);
+    for (int c = 0; c < 3; ++c) acc.cell(w * x[c], p, k, j, i, c);
   } else {
-    lap_row(G, acc, R(h / ph.Pm), p, k, j, i, a, WALL_B, 4);
+    lap_row(G, acc, cf.hpm, p, k, j, i, a, WALL_B, 4);
   }
 }
 
 // Row `a` of the PPBE matrix dt/2 D G = dt/(2E) lap (eqn:tsp, eqn:tspb): P even walls, P_b odd walls
 template <class GT, class Acc>
-__device__ __forceinline__ void ppbe_row(const GT& G, const Phys& ph, Acc& acc, int p, int k, int j, int i, int a) {
-  using R = typename GT::real;
-  lap_row(G, acc, R(0.5 * ph.dt / ph.E), p, k, j, i, a, a == 0 ? WALL_EVEN : WALL_ODD, 0);
+__device__ __forceinline__ void ppbe_row(const GT& G, const Coefs<typename GT::real>& cf, Acc& acc, int p, int k,
+                                         int j, int i, int a) {
+  lap_row(G, acc, cf.pp, p, k, j, i, a, a == 0 ? WALL_EVEN : WALL_ODD, 0);
 }
 
 // T: element type of x and the ghost layer; R: accumulation type (FP64 for the
@@ -259,5 +283,18 @@ struct ApplyAcc {
     sum += c * (R)gh[((((long long)comp * 6 + p) * 4 + side) * Nr + k) * (Ns + 2) + (t + 1)];
   }
 };
+
+// Ghost centre beyond `side` of panel p at tangential index t (t in [0, Ns)): quadratic
+// Lagrange interpolation along the neighbour's first grid line.
+template <class T, class GT>
+__device__ __forceinline__ typename GT::real interp_ghost(const GT& G, const T* x, int comp, int p, int side, int k,
+                                                          int t) {
+  using R = typename GT::real;
+  const int id = (p * 4 + side) * G.Ns + t;
+  const int q = G.gq[id];
+  const T* base = x + comp * G.N + ((long long)(q * G.Nr + k) * G.Ns) * G.Ns;
+  return G.gw[3 * id] * (R)base[G.gsrc[3 * id]] + G.gw[3 * id + 1] * (R)base[G.gsrc[3 * id + 1]] +
+         G.gw[3 * id + 2] * (R)base[G.gsrc[3 * id + 2]];
+}
 
 }  // namespace fv

@@ -37,7 +37,8 @@ class fv_pc_desc(ctypes.Structure):
     _fields_ = [('p1', ctypes.c_int), ('p2', ctypes.c_int), ('p3', ctypes.c_int), ('overlap', ctypes.c_int),
                 ('levels', ctypes.c_int), ('overlap_coarse', ctypes.c_int), ('coarse_rtol', ctypes.c_double),
                 ('coarse_restart', ctypes.c_int), ('coarse_maxit', ctypes.c_int), ('precision', ctypes.c_int),
-                ('inner_rtol', ctypes.c_double), ('inner_restart', ctypes.c_int), ('inner_maxit', ctypes.c_int)]
+                ('inner_rtol', ctypes.c_double), ('inner_restart', ctypes.c_int), ('inner_maxit', ctypes.c_int),
+                ('nboxes', ctypes.c_int), ('boxes', ctypes.POINTER(ctypes.c_int))]
 
 
 class fv_gmres_opts(ctypes.Structure):
@@ -63,6 +64,7 @@ SIGNATURES = {
     'fv_apply_op_noalloc': [_VP, _DP, _DP, _VP],
     'fv_precond_apply': [_VP, _DP, _DP, _VP],
     'fv_gmres_solve': [_VP, _DP, _DP, _P(fv_gmres_opts), _P(fv_solve_stats), _VP],
+    'fv_gmres_solve_batch': [_VP, ctypes.c_int, _DP, _DP, _P(fv_gmres_opts), _P(fv_solve_stats), _VP],
     'fv_state_create': [_VP, _P(fv_phys), _DP, _P(_VP)],
     'fv_free_state': [_VP],
     'fv_state_get': [_VP, _DP, _VP],
@@ -114,10 +116,14 @@ def fv_build_grid(Ns, Nr, ri=7.0 / 13.0, ro=20.0 / 13.0):
 
 def fv_assemble_system(grid, kind, E, Ra, Pr, Pm, dt, p=(1, 1, 1), overlap=1, levels=1, overlap_coarse=1,
                        coarse_rtol=0.1, coarse_restart=30, coarse_maxit=30, precision=FV_PREC_FP64, inner_rtol=1e-3,
-                       inner_restart=30, inner_maxit=30):
+                       inner_restart=30, inner_maxit=30, boxes=None):
     h = ctypes.c_void_p()
+    nb, bp = 0, None
+    if boxes is not None:
+        flat = (ctypes.c_int * (7 * len(boxes)))(*[int(v) for bx in boxes for v in bx])
+        nb, bp = len(boxes), ctypes.cast(flat, ctypes.POINTER(ctypes.c_int))
     pc = fv_pc_desc(p[0], p[1], p[2], overlap, levels, overlap_coarse, coarse_rtol, coarse_restart, coarse_maxit,
-                    precision, inner_rtol, inner_restart, inner_maxit)
+                    precision, inner_rtol, inner_restart, inner_maxit, nb, bp)
     _check(lib.fv_assemble_system(grid, kind, ctypes.byref(fv_phys(E, Ra, Pr, Pm, dt)), ctypes.byref(pc),
                                   ctypes.byref(h)))
     return h
@@ -158,6 +164,20 @@ def fv_gmres_solve(system, b, x, restart=30, max_it=3000, atol=0.0, rtol=1e-8, r
     return st
 
 
+def fv_gmres_solve_batch(system, B, X, restart=30, max_it=3000, atol=0.0, rtol=1e-8, raise_on_noconv=True):
+    """Solve A x_r = b_r for the rows of B (nrhs x n CUDA float64) into X (in: x0)."""
+    n = fv_system_size(system)
+    if B.dim() != 2 or B.shape[1] != n or X.shape != B.shape:
+        raise ValueError('B and X must be (nrhs, n)')
+    nrhs = B.shape[0]
+    stats = (fv_solve_stats * nrhs)()
+    rc = lib.fv_gmres_solve_batch(system, nrhs, _ptr(B), _ptr(X), ctypes.byref(fv_gmres_opts(restart, max_it, atol, rtol)),
+                                  stats, _stream())
+    if rc != 0 and (raise_on_noconv or rc != -4):
+        _check(rc)
+    return list(stats)
+
+
 def fv_state_create(grid, init, E, Ra, Pr, Pm, dt):
     h = ctypes.c_void_p()
     ncell = ctypes.c_longlong()
@@ -195,8 +215,14 @@ def fv_free_state(h):
     _check(lib.fv_free_state(h))
 
 
-K_GHOST, K_APPLY_VTBE, K_APPLY_PPBE, K_RAS_FWD, K_RAS_BWD, K_CGS, K_VEC, K_GLUE, K_TRANSFER = range(9)
-K_PHASE_PC_C, K_PHASE_PC_F, K_PHASE_PC_I, K_COARSE, K_COUNT = 9, 10, 11, 16, 32
+K_NAMES = {0: 'ghost', 1: 'apply_vtbe', 2: 'apply_ppbe', 3: 'ras_fwd_vtbe', 4: 'ras_bwd_vtbe', 5: 'cgs', 6: 'vec',
+           7: 'glue', 8: 'transfer', 9: 'phase_pc_c', 10: 'phase_pc_f', 11: 'phase_pc_i', 12: 'ras_fwd_ppbe',
+           13: 'ras_bwd_ppbe'}
+K_COARSE, K_FP32, K_COUNT = 16, 32, 64
+
+
+def category_name(c):
+    return K_NAMES[c % 16] + ('_coarse' if c & K_COARSE else '') + ('_fp32' if c & K_FP32 else '')
 
 
 def fv_profile_enable(on=True):

@@ -152,3 +152,65 @@ def benchmark_state(Ns, Nr, ri=RI, ro=RO):
     N = X[0].size
     return dict(u=np.zeros((3, N)), T=benchmark_Theta0(*X, ri, ro).reshape(N),
                 B=benchmark_B0(*X, ri, ro).reshape(3, N), P=np.zeros(N), Pb=np.zeros(N))
+
+
+def _edge_sequences(n, sizes):
+    """All ordered sequences of edges from `sizes` summing to n, grouped by length."""
+    out = {}
+
+    def rec(rem, seq):
+        if rem == 0:
+            out.setdefault(len(seq), []).append(tuple(seq))
+            return
+        for s in sizes:
+            if s <= rem:
+                rec(rem - s, seq + [s])
+    rec(n, [])
+    return out
+
+
+def uneven_boxes(Ns, Nr, sizes=(8, 12, 16, 24), target=None, seed=0):
+    """An uneven decomposition of every panel into boxes with edges from `sizes`.
+
+    Each panel's (i, j) square is cut along i and along j into seeded random edge
+    sequences (Ns must be a sum of edges from `sizes`); every resulting rectangle's
+    radial column is cut into its own random edge sequence.  With `target`, the
+    number of radial pieces per rectangle is chosen so that the total box count is
+    exactly `target`.  Returns owned boxes (panel, i0, i1, j0, j1, k0, k1) that
+    tile the shell.  Input synthesis only."""
+    rng = np.random.default_rng(seed)
+    hseq = _edge_sequences(Ns, sizes)
+    rseq = _edge_sequences(Nr, sizes)
+    hlens = sorted(hseq)
+    rects = []
+    for p in range(6):
+        li, lj = int(rng.choice(hlens)), int(rng.choice(hlens))
+        ei = hseq[li][int(rng.integers(len(hseq[li])))]
+        ej = hseq[lj][int(rng.integers(len(hseq[lj])))]
+        ci, cj = np.concatenate([[0], np.cumsum(ei)]), np.concatenate([[0], np.cumsum(ej)])
+        rects += [(p, int(ci[a]), int(ci[a + 1]), int(cj[b]), int(cj[b + 1]))
+                  for a in range(len(ei)) for b in range(len(ej))]
+    rlens = sorted(rseq)
+    if target is None:
+        counts = [int(rng.choice(rlens)) for _ in rects]
+    else:
+        lo, hi = rlens[0], rlens[-1]
+        if not lo * len(rects) <= target <= hi * len(rects):
+            raise ValueError('target %d not reachable with %d rectangles' % (target, len(rects)))
+        counts = [lo] * len(rects)
+        extra = target - lo * len(rects)
+        order = rng.permutation(len(rects))
+        while extra > 0:
+            for r in order:
+                if extra == 0:
+                    break
+                nxt = [c for c in rlens if c > counts[r]]
+                if nxt and nxt[0] - counts[r] <= extra:
+                    extra -= nxt[0] - counts[r]
+                    counts[r] = nxt[0]
+    boxes = []
+    for (p, i0, i1, j0, j1), c in zip(rects, counts):
+        seq = rseq[c][int(rng.integers(len(rseq[c])))]
+        ck = np.concatenate([[0], np.cumsum(seq)])
+        boxes += [(p, i0, i1, j0, j1, int(ck[q]), int(ck[q + 1])) for q in range(len(seq))]
+    return boxes

@@ -170,7 +170,7 @@ def test_mixed_precision_solve_reaches_fp64_residual(fv, kind, levels):
     g = fv.fv_build_grid(Ns, Nr)
     s64 = fv.fv_assemble_system(g, kind, **PH, p=parts, overlap=1, levels=levels)
     s32 = fv.fv_assemble_system(g, kind, **PH, p=parts, overlap=1, levels=levels, precision=fv.FV_PREC_FP32,
-                                inner_rtol=1e-3, inner_restart=30, inner_maxit=30)
+                                inner_maxit=6, coarse_maxit=8)
     x64 = torch.zeros(A.shape[0], dtype=torch.float64, device='cuda')
     x32 = torch.zeros_like(x64)
     st64 = fv.fv_gmres_solve(s64, _dev(b), x64, rtol=1e-8)
@@ -197,7 +197,7 @@ def test_mixed_precision_time_step_matches_oracle(fv):
     st_o = Stepper(Grid(Ns, Nr), Physics(**PH), SolverOptions(parts=parts, delta=1, ppbe_levels=2, rtol=1e-10))
     ref, _ = st_o.step(dict(s0, first=True))
     g = fv.fv_build_grid(Ns, Nr)
-    mp = dict(precision=fv.FV_PREC_FP32, inner_rtol=1e-3, inner_restart=30, inner_maxit=30)
+    mp = dict(precision=fv.FV_PREC_FP32, inner_maxit=6, coarse_maxit=8)
     V = fv.fv_assemble_system(g, 0, **PH, p=parts, overlap=1, **mp)
     P = fv.fv_assemble_system(g, 1, **PH, p=parts, overlap=1, levels=2, **mp)
     st = fv.fv_state_create(g, _dev(init), **PH)
@@ -207,5 +207,14 @@ def test_mixed_precision_time_step_matches_oracle(fv):
     assert _rel(out[:3 * N], ref['u'].ravel()) < 1e-7
     assert _rel(out[3 * N:4 * N], ref['T']) < 1e-7
     assert _rel(out[4 * N:7 * N], ref['B'].ravel()) < 1e-7
+    # second and third steps replay the captured inner-solve graphs
+    ref2 = ref
+    for _ in range(2):
+        ref2, _ = st_o.step(ref2)
+    stats = fv.fv_time_step(st, V, P, nsteps=2, rtol=1e-10)
+    assert all(s.converged for s in stats)
+    out = fv.fv_state_get(st, torch.empty(9 * N, dtype=torch.float64, device='cuda')).cpu().numpy()
+    assert _rel(out[:3 * N], ref2['u'].ravel()) < 1e-7
+    assert _rel(out[4 * N:7 * N], ref2['B'].ravel()) < 1e-7
     for h, f in ((st, fv.fv_free_state), (V, fv.fv_free_system), (P, fv.fv_free_system), (g, fv.fv_free_grid)):
         f(h)
