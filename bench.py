@@ -174,12 +174,15 @@ def batch_workload(args, fv, torch, rank, ws):
         e1.record(stream)
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
-    # the same 32 right-hand sides one at a time (the unbatched reference on the GPU)
+    # the same 32 right-hand sides one at a time (batches of one: same preconditioner, no sharing)
+    x1 = torch.zeros(1, n, dtype=torch.float64, device='cuda')
+    fv.fv_gmres_solve_batch(s, Bd[:1].contiguous(), x1, restart=c['restart'], rtol=c['rtol'])  # tune G for nrhs = 1
     e0.record(stream)
     its1 = []
     for r in range(c['nrhs']):
-        x = torch.zeros(n, dtype=torch.float64, device='cuda')
-        its1.append(fv.fv_gmres_solve(s, Bd[r].contiguous(), x, restart=c['restart'], rtol=c['rtol']).iters)
+        x1.zero_()
+        its1.append(fv.fv_gmres_solve_batch(s, Bd[r:r + 1].contiguous(), x1, restart=c['restart'],
+                                            rtol=c['rtol'])[0].iters)
     e1.record(stream)
     torch.cuda.synchronize()
     ms1 = e0.elapsed_time(e1)
