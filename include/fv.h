@@ -161,6 +161,8 @@ typedef struct {
   int converged;
   double r0, rfinal;     /* ||b - A x0||, ||b - A x|| (true residuals) */
   double time_ms;        /* wall time of the call */
+  int fallback;          /* 1: a learned coarse correction (fv_net.h) failed and the
+                            plain coarse solve finished the call */
 } fv_solve_stats;
 
 fv_status fv_gmres_solve(const fv_system* s, const double* b, double* x, const fv_gmres_opts* opts,
@@ -222,6 +224,8 @@ fv_status fv_time_step(fv_state* st, const fv_system* vtbe, const fv_system* ppb
 #define FV_K_PHASE_PC_I 11
 #define FV_K_RAS_FWD_PPBE 12
 #define FV_K_RAS_BWD_PPBE 13
+#define FV_K_NET_FWD 14     /* learned coarse correction: inference (fv_net.h) */
+#define FV_K_NET_TRAIN 15   /* learned coarse correction: loss, backward pass, Adam */
 #define FV_K_COARSE 16
 #define FV_K_FP32 32
 #define FV_K_COUNT 64

@@ -124,3 +124,30 @@ def loss_and_grads(params, r, e):
     _, gw, gb = conv_backward(st['x'], params['c1'][0], g)
     grads['c1'] = (gw, gb)
     return L, grads
+
+
+def flatten(params):
+    """Flat parameter vector: layer by layer, W[co][ci][dz][dy][dx] then b[co]."""
+    return np.concatenate([np.concatenate([params[k][0].ravel(), params[k][1].ravel()]) for k, _, _ in LAYERS])
+
+
+def unflatten(flat, C):
+    params, off = {}, 0
+    for name, (ci, co) in shapes(C).items():
+        n = co * ci * 27
+        w = np.asarray(flat[off:off + n], dtype=np.float64).reshape(co, ci, 3, 3, 3)
+        off += n
+        params[name] = (w, np.asarray(flat[off:off + co], dtype=np.float64))
+        off += co
+    assert off == len(flat)
+    return params
+
+
+def adam_step(w, g, m, v, t, lr, beta1, beta2, eps):
+    """One Adam update (Kingma & Ba 2015, Algorithm 1) of flat arrays; t is the new step count (>= 1).
+    Returns (w, m, v)."""
+    m = beta1 * m + (1.0 - beta1) * g
+    v = beta2 * v + (1.0 - beta2) * g * g
+    mhat = m / (1.0 - beta1 ** t)
+    vhat = v / (1.0 - beta2 ** t)
+    return w - lr * mhat / (np.sqrt(vhat) + eps), m, v

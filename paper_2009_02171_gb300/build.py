@@ -38,7 +38,7 @@ def build(force=False):
     os.makedirs(BUILD, exist_ok=True)
     srcs = sources()
     deps = srcs + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(('.h', '.cuh'))]
-    deps.append(os.path.join(HERE, '..', 'include', 'fv.h'))
+    deps += [os.path.join(HERE, '..', 'include', h) for h in ('fv.h', 'fv_net.h')]
     if not force and os.path.exists(OUT) and os.path.getmtime(OUT) > max(os.path.getmtime(d) for d in deps):
         return OUT
     with cf.ThreadPoolExecutor(max_workers=len(srcs)) as ex:

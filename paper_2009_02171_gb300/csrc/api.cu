@@ -3,6 +3,7 @@
 #include <string>
 #include <vector>
 
+#include "../../include/fv_net.h"
 #include "fv_internal.h"
 
 namespace fv {
@@ -174,6 +175,49 @@ fv_status fv_gmres_solve(const fv_system* s, const double* b, double* x, const f
                          fv_solve_stats* stats, void* stream) {
   if (!s || !b || !x || !opts || b == x) return set_error("fv_gmres_solve: bad argument"), FV_EINVAL;
   return gmres(s, b, x, opts, stats, (cudaStream_t)stream, false);
+}
+
+fv_status fv_coarse_system(const fv_system* s, const fv_system** coarse) {
+  if (!s || !coarse) return set_error("fv_coarse_system: null argument"), FV_EINVAL;
+  if (!s->coarse) return set_error("fv_coarse_system: the system has one level"), FV_EINVAL;
+  *coarse = s->coarse;
+  return FV_OK;
+}
+
+fv_status fv_restrict_coarse(const fv_system* s, const double* x, double* xc, void* stream) {
+  if (!s || !x || !xc) return set_error("fv_restrict_coarse: null argument"), FV_EINVAL;
+  if (!s->coarse) return set_error("fv_restrict_coarse: the system has one level"), FV_EINVAL;
+  return restrict_coarse(s, x, xc, (cudaStream_t)stream);
+}
+
+fv_status fv_pc_set_learned(fv_system* s, fv_net* net, int coarse_its, int flags) {
+  if (!s) return set_error("fv_pc_set_learned: null system"), FV_EINVAL;
+  if (!net) {
+    set_learned_active(s, 0);
+    s->net = nullptr;
+    return FV_OK;
+  }
+  if (s->kind != FV_PPBE || !s->coarse) return set_error("fv_pc_set_learned: needs a two-level PPBE system"), FV_EINVAL;
+  if (!net_matches(net, s->coarse->grid))
+    return set_error("fv_pc_set_learned: the network's grid differs from the coarse grid"), FV_EINVAL;
+  if (coarse_its < 0 || coarse_its > 31 || (flags & ~FV_LEARN_GUESS))
+    return set_error("fv_pc_set_learned: coarse_its must be in [0, 31], flags in {0, FV_LEARN_GUESS}"), FV_EINVAL;
+  if (!s->xbak) {
+    if (cudaMalloc(&s->xbak, s->n * sizeof(double)) != cudaSuccess)
+      return set_error("fv_pc_set_learned: allocation failed"), FV_ENOMEM;
+    s->allocs.push_back(s->xbak);
+  }
+  if (s->prec32 && !s->tc32) {
+    const size_t nc = (size_t)s->coarse->n;
+    if (cudaMalloc(&s->tc32, nc * sizeof(float)) != cudaSuccess) return set_error("fv_pc_set_learned: allocation failed"), FV_ENOMEM;
+    s->allocs.push_back(s->tc32);
+    if (cudaMalloc(&s->dc32, nc * sizeof(float)) != cudaSuccess) return set_error("fv_pc_set_learned: allocation failed"), FV_ENOMEM;
+    s->allocs.push_back(s->dc32);
+  }
+  set_learned_active(s, 0);
+  s->net = net, s->learned_its = coarse_its, s->learned_flags = flags;
+  set_learned_active(s, 1);
+  return FV_OK;
 }
 
 }  // extern "C"

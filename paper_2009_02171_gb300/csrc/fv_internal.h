@@ -67,6 +67,8 @@ struct BatchWork;
 
 }  // namespace fv
 
+struct fv_net;
+
 struct fv_grid {
   fv::GridHost h;
   fv::Geo geo;                 // device pointers (FP64 tables)
@@ -138,6 +140,12 @@ struct fv_system {
   fv::BatchWork* batch = nullptr;  // fv_gmres_solve_batch workspace
   mutable int last_inner = 0;
   int level = 0;               // 0 fine, 1 coarse (kernel timing category offset)
+  // learned coarse correction (fv_net.h), borrowed network
+  fv_net* net = nullptr;
+  int learned_its = 0, learned_flags = 0;
+  int learned_on = 0;          // 0 while a failed learned solve is finished by the plain one
+  double* xbak = nullptr;      // [n] x0 of the top-level solve (fallback after NaN)
+  float *tc32 = nullptr, *dc32 = nullptr;  // [coarse n] FP32 residual / correction of the coarse iterations
   std::vector<void*> allocs;
 };
 
@@ -191,6 +199,14 @@ fv_status precond_apply32(const fv_system* s, const float* r, float* z, cudaStre
 fv_status ras_apply(const fv_system* s, const double* r, double* z, cudaStream_t st);
 fv_status restrict_mean(const fv_grid* g, int d, const double* x, double* xc, cudaStream_t st);
 fv_status prolong_inject(const fv_grid* g, int d, const double* xc, double* x, cudaStream_t st);
+fv_status restrict_coarse(const fv_system* s, const double* x, double* xc, cudaStream_t st);
+void set_learned_active(fv_system* s, int on);
+fv_status learned_guess(const fv_system* s, const double* b, double* x, cudaStream_t st);
+
+// nn.cu: learned coarse correction (one sample, coarse vectors in the system layout)
+fv_status net_forward64(fv_net* n, const double* r, double* e, cudaStream_t st);
+fv_status net_forward32(fv_net* n, const float* r, float* e, cudaStream_t st);
+bool net_matches(const fv_net* n, const fv_grid* coarse);
 
 // krylov.cu
 fv_status gmres(const fv_system* s, const double* b, double* x, const fv_gmres_opts* o, fv_solve_stats* stats,

@@ -22,6 +22,7 @@
 #include <utility>
 #include <vector>
 
+#include "../../include/fv_net.h"
 #include "fv_internal.h"
 
 namespace fv {
@@ -573,6 +574,7 @@ static fv_status gmres_t(const fv_system* s, const T* b, T* x, const fv_gmres_op
   const bool conv = !nan && beta <= target;
   if (stats) {
     stats->iters = its;
+    stats->fallback = 0;
     stats->inner_iters = s->last_inner;
     stats->converged = conv ? 1 : 0;
     stats->r0 = r0;
@@ -584,8 +586,52 @@ static fv_status gmres_t(const fv_system* s, const T* b, T* x, const fv_gmres_op
   return FV_OK;
 }
 
+// Top-level solves of a system with a learned coarse correction: optional
+// learned initial guess, then FGMRES; if that ends without convergence, the
+// plain coarse solve finishes from the last finite iterate with the original
+// absolute target max(atol, rtol ||b - A x0||).
+static fv_status gmres_learned(const fv_system* s, const double* b, double* x, const fv_gmres_opts* o,
+                               fv_solve_stats* stats, cudaStream_t st) {
+  fv_system* sm = const_cast<fv_system*>(s);
+  const size_t bytes = (size_t)s->n * sizeof(double);
+  FV_CUDA(cudaMemcpyAsync(s->xbak, x, bytes, cudaMemcpyDeviceToDevice, st));
+  fv_solve_stats s1{};
+  fv_status rc = FV_OK;
+  double r0 = -1.0;
+  if (s->learned_flags & FV_LEARN_GUESS) {
+    // the tolerance stays relative to the caller's x0
+    const fv_gmres_opts o0{o->restart, 0, o->atol, o->rtol};
+    fv_status rr = gmres_t<double>(s, b, x, &o0, &s1, st, false);
+    if (rr && rr != FV_ENOCONV && rr != FV_ENAN) return rr;
+    r0 = s1.r0;
+    if ((rc = learned_guess(s, b, x, st))) return rc;
+  }
+  fv_gmres_opts o1 = *o;
+  if (r0 >= 0.0) o1.atol = std::max(o->atol, o->rtol * r0), o1.rtol = 0.0;
+  rc = gmres_t<double>(s, b, x, &o1, &s1, st, false);
+  int inner = s->last_inner;
+  if (r0 >= 0.0) s1.r0 = r0;
+  if (rc == FV_ENOCONV || rc == FV_ENAN) {
+    if (rc == FV_ENAN) FV_CUDA(cudaMemcpyAsync(x, s->xbak, bytes, cudaMemcpyDeviceToDevice, st));
+    fv_gmres_opts o2 = *o;
+    o2.atol = std::max(o->atol, o->rtol * s1.r0), o2.rtol = 0.0;
+    fv_solve_stats s2{};
+    set_learned_active(sm, 0);
+    rc = gmres_t<double>(s, b, x, &o2, &s2, st, false);
+    set_learned_active(sm, 1);
+    inner += s->last_inner;
+    s1.iters += s2.iters, s1.converged = s2.converged, s1.rfinal = s2.rfinal, s1.time_ms += s2.time_ms;
+    s1.fallback = 1;
+  }
+  s->last_inner = inner;
+  s1.inner_iters = inner;
+  if (stats) *stats = s1;
+  return rc;
+}
+
 fv_status gmres(const fv_system* s, const double* b, double* x, const fv_gmres_opts* o, fv_solve_stats* stats,
                 cudaStream_t st, bool inner) {
+  if (!inner && s->net) return gmres_learned(s, b, x, o, stats, st);
   return gmres_t<double>(s, b, x, o, stats, st, inner);
 }
 

@@ -948,11 +948,18 @@ fv_status precond_apply(const fv_system* s, const double* r, double* z, cudaStre
   }
   {
     ProfScope ph(FV_K_PHASE_PC_C, st);
-    fv_gmres_opts o{s->pc.coarse_restart, s->pc.coarse_maxit, 0.0, s->pc.coarse_rtol};
-    fv_solve_stats cs{};
-    rc = gmres(c, s->xc, s->ec, &o, &cs, st, true);
-    if (rc && rc != FV_ENOCONV) return rc;
-    s->last_inner += cs.iters;
+    int its = s->pc.coarse_maxit;
+    if (s->net && s->learned_on) {  // learned e_c = N(r_c), then learned_its iterations from it
+      if ((rc = net_forward64(s->net, s->xc, s->ec, st))) return rc;
+      its = s->learned_its;
+    }
+    if (its > 0) {
+      fv_gmres_opts o{s->pc.coarse_restart, its, 0.0, s->pc.coarse_rtol};
+      fv_solve_stats cs{};
+      rc = gmres(c, s->xc, s->ec, &o, &cs, st, true);
+      if (rc && rc != FV_ENOCONV) return rc;
+      s->last_inner += cs.iters;
+    }
   }
   {
     ProfScope ph(FV_K_PHASE_PC_I, st);
@@ -982,7 +989,18 @@ fv_status precond_apply32(const fv_system* s, const float* r, float* z, cudaStre
   }
   {
     ProfScope ph(FV_K_PHASE_PC_C, st);
-    if ((rc = gmres_fixed32(c, s->xc32, s->ec32, s->pc.coarse_maxit, st))) return rc;
+    if (s->net && s->learned_on) {
+      // learned e_c = N(r_c), then learned_its iterations on the residual r_c - A_c e_c
+      if ((rc = net_forward32(s->net, s->xc32, s->ec32, st))) return rc;
+      if (s->learned_its > 0) {
+        if ((rc = apply_op32(c, s->ec32, s->tc32, st)) || (rc = axpby32(c->n, 1.0, s->xc32, -1.0, s->tc32, s->tc32, st)) ||
+            (rc = gmres_fixed32(c, s->tc32, s->dc32, s->learned_its, st)) ||
+            (rc = axpby32(c->n, 1.0, s->ec32, 1.0, s->dc32, s->ec32, st)))
+          return rc;
+      }
+    } else if ((rc = gmres_fixed32(c, s->xc32, s->ec32, s->pc.coarse_maxit, st))) {
+      return rc;
+    }
   }
   {
     ProfScope ph(FV_K_PHASE_PC_I, st);
@@ -996,6 +1014,35 @@ fv_status precond_apply32(const fv_system* s, const float* r, float* z, cudaStre
   }
   ProfScope ph(FV_K_PHASE_PC_I, st);
   return axpby32(s->n, 1.0, z, 1.0, s->w32, z, st);
+}
+
+// the coarse right-hand side of the two-level preconditioner (restriction and,
+// for the Neumann pressure, the volume-weighted mean removal)
+fv_status restrict_coarse(const fv_system* s, const double* x, double* xc, cudaStream_t st) {
+  fv_status rc = restrict_mean(s->grid, s->d, x, xc, st);
+  if (rc) return rc;
+  if (s->kind == FV_PPBE) return weighted_mean_remove(s->coarse->grid, xc, st, s->red, s->red + 32 * 304);
+  return FV_OK;
+}
+
+// switch the learned coarse correction on or off; the captured inner solve of
+// mixed precision contains the coarse solve, so it is captured again
+void set_learned_active(fv_system* s, int on) {
+  if (s->learned_on == on) return;
+  s->learned_on = on;
+  if (s->inner_graph) cudaGraphExecDestroy(s->inner_graph);
+  s->inner_graph = nullptr;
+  s->inner_warm = 0;
+}
+
+// x <- x + I_c^f N(r_c(b - A x)): the learned initial-guess correction
+fv_status learned_guess(const fv_system* s, const double* b, double* x, cudaStream_t st) {
+  fv_status rc;
+  if ((rc = apply_op(s, x, s->t, st)) || (rc = axpby(s->n, 1.0, b, -1.0, s->t, s->t, st)) ||
+      (rc = restrict_coarse(s, s->t, s->xc, st)) || (rc = net_forward64(s->net, s->xc, s->ec, st)) ||
+      (rc = prolong_inject(s->grid, s->d, s->ec, s->w, st)))
+    return rc;
+  return axpby(s->n, 1.0, x, 1.0, s->w, x, st);
 }
 
 }  // namespace fv

@@ -1,4 +1,4 @@
-"""Thin ctypes binding of libfv.so (the C ABI of include/fv.h).
+"""Thin ctypes binding of libfv.so (the C ABI of include/fv.h and include/fv_net.h).
 
 Argument marshalling only: every step of the solve runs in the CUDA library.
 Vectors are torch CUDA float64 tensors (contiguous, component-major
@@ -48,7 +48,21 @@ class fv_gmres_opts(ctypes.Structure):
 
 class fv_solve_stats(ctypes.Structure):
     _fields_ = [('iters', ctypes.c_int), ('inner_iters', ctypes.c_int), ('converged', ctypes.c_int),
-                ('r0', ctypes.c_double), ('rfinal', ctypes.c_double), ('time_ms', ctypes.c_double)]
+                ('r0', ctypes.c_double), ('rfinal', ctypes.c_double), ('time_ms', ctypes.c_double),
+                ('fallback', ctypes.c_int)]
+
+
+class fv_net_desc(ctypes.Structure):
+    _fields_ = [('C', ctypes.c_int), ('Ns', ctypes.c_int), ('Nr', ctypes.c_int), ('max_batch', ctypes.c_int)]
+
+
+class fv_adam_opts(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ('lr', 'beta1', 'beta2', 'eps')]
+
+
+class fv_train_opts(ctypes.Structure):
+    _fields_ = [('epochs', ctypes.c_int), ('batch', ctypes.c_int), ('seed', ctypes.c_ulonglong),
+                ('adam', fv_adam_opts)]
 
 
 # (name, argtypes) of every symbol include/fv.h declares
@@ -73,7 +87,21 @@ SIGNATURES = {
     'fv_profile_enable': [ctypes.c_int],
     'fv_profile_read': [ctypes.c_int, _P(ctypes.c_longlong), _P(ctypes.c_double)],
     'fv_last_error': [],
+    # include/fv_net.h
+    'fv_net_create': [_P(fv_net_desc), _P(_VP)],
+    'fv_net_free': [_VP],
+    'fv_net_param_count': [_VP, _P(ctypes.c_longlong)],
+    'fv_net_set_params': [_VP, _VP],
+    'fv_net_get_params': [_VP, _VP],
+    'fv_net_forward': [_VP, ctypes.c_int, _DP, _DP, _VP],
+    'fv_net_loss_grad': [_VP, ctypes.c_int, _DP, _DP, _P(ctypes.c_double), _VP, _VP],
+    'fv_net_adam_step': [_VP, _VP, _P(fv_adam_opts)],
+    'fv_net_train': [_VP, ctypes.c_int, _DP, _DP, _P(fv_train_opts), _VP, _VP],
+    'fv_coarse_system': [_VP, _P(_VP)],
+    'fv_restrict_coarse': [_VP, _DP, _DP, _VP],
+    'fv_pc_set_learned': [_VP, _VP, ctypes.c_int, ctypes.c_int],
 }
+FV_LEARN_GUESS = 1
 
 
 def _load():
@@ -217,7 +245,7 @@ def fv_free_state(h):
 
 K_NAMES = {0: 'ghost', 1: 'apply_vtbe', 2: 'apply_ppbe', 3: 'ras_fwd_vtbe', 4: 'ras_bwd_vtbe', 5: 'cgs', 6: 'vec',
            7: 'glue', 8: 'transfer', 9: 'phase_pc_c', 10: 'phase_pc_f', 11: 'phase_pc_i', 12: 'ras_fwd_ppbe',
-           13: 'ras_bwd_ppbe'}
+           13: 'ras_bwd_ppbe', 14: 'net_fwd', 15: 'net_train'}
 K_COARSE, K_FP32, K_COUNT = 16, 32, 64
 
 
@@ -237,3 +265,86 @@ def fv_profile_read(category):
 
 def fv_last_error():
     return lib.fv_last_error().decode()
+
+
+# ---------------------------------------------------------------- learned coarse correction (include/fv_net.h)
+def _fptr(a, n):
+    """Host float32 numpy array of n values -> pointer."""
+    import numpy as np
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float32 and a.flags.c_contiguous and a.size == n):
+        raise ValueError('expected a contiguous float32 numpy array of %d values' % n)
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def fv_net_create(C, Ns, Nr, max_batch=1):
+    h = ctypes.c_void_p()
+    _check(lib.fv_net_create(ctypes.byref(fv_net_desc(C, Ns, Nr, max_batch)), ctypes.byref(h)))
+    return h
+
+
+def fv_net_free(net):
+    _check(lib.fv_net_free(net))
+
+
+def fv_net_param_count(net):
+    n = ctypes.c_longlong()
+    _check(lib.fv_net_param_count(net, ctypes.byref(n)))
+    return n.value
+
+
+def fv_net_set_params(net, params):
+    _check(lib.fv_net_set_params(net, _fptr(params, fv_net_param_count(net))))
+
+
+def fv_net_get_params(net):
+    import numpy as np
+    out = np.empty(fv_net_param_count(net), dtype=np.float32)
+    _check(lib.fv_net_get_params(net, ctypes.c_void_p(out.ctypes.data)))
+    return out
+
+
+def fv_net_forward(net, nb, r, e):
+    _check(lib.fv_net_forward(net, nb, _ptr(r), _ptr(e), _stream()))
+    return e
+
+
+def fv_net_loss_grad(net, nb, r, e, want_grads=True):
+    """(mean squared error, FP32 numpy gradient or None)."""
+    import numpy as np
+    loss = ctypes.c_double()
+    g = np.empty(fv_net_param_count(net), dtype=np.float32) if want_grads else None
+    _check(lib.fv_net_loss_grad(net, nb, _ptr(r), _ptr(e), ctypes.byref(loss),
+                                ctypes.c_void_p(g.ctypes.data) if want_grads else None, _stream()))
+    return loss.value, g
+
+
+def fv_net_adam_step(net, grads, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    _check(lib.fv_net_adam_step(net, _fptr(grads, fv_net_param_count(net)),
+                                ctypes.byref(fv_adam_opts(lr, beta1, beta2, eps))))
+
+
+def fv_net_train(net, R, E, epochs=1, batch=1, seed=0, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    """Train on the rows of R, E (npairs x 2*6*Ns^2*Nr CUDA float64); returns the mean loss of each epoch."""
+    import numpy as np
+    if R.dim() != 2 or E.shape != R.shape:
+        raise ValueError('R and E must be (npairs, coarse n)')
+    losses = np.zeros(max(epochs, 1), dtype=np.float64)
+    o = fv_train_opts(epochs, batch, seed, fv_adam_opts(lr, beta1, beta2, eps))
+    _check(lib.fv_net_train(net, R.shape[0], _ptr(R), _ptr(E), ctypes.byref(o),
+                            ctypes.c_void_p(losses.ctypes.data), _stream()))
+    return losses[:epochs]
+
+
+def fv_coarse_system(system):
+    h = ctypes.c_void_p()
+    _check(lib.fv_coarse_system(system, ctypes.byref(h)))
+    return h
+
+
+def fv_restrict_coarse(system, x, xc):
+    _check(lib.fv_restrict_coarse(system, _ptr(x), _ptr(xc), _stream()))
+    return xc
+
+
+def fv_pc_set_learned(system, net, coarse_its=0, flags=0):
+    _check(lib.fv_pc_set_learned(system, net, coarse_its, flags))

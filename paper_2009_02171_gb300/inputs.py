@@ -214,3 +214,23 @@ def uneven_boxes(Ns, Nr, sizes=(8, 12, 16, 24), target=None, seed=0):
         ck = np.concatenate([[0], np.cumsum(seq)])
         boxes += [(p, i0, i1, j0, j1, int(ck[q]), int(ck[q + 1])) for q in range(len(seq))]
     return boxes
+
+
+def multiscale_fields(Ns, Nr, nsamples, seed, d=2, smooth=(0, 1, 2, 4, 8, 16)):
+    """nsamples random d-component fields on a 6 x Ns x Ns x Nr grid, each row of the
+    result one sample laid out [c][p][k][j][i]: white noise smoothed, per sample, m
+    times (m drawn from `smooth`) by the 3-point filter (1, 2, 1)/4 along each panel
+    axis (edge values repeated), then scaled to unit RMS.  Training and test inputs
+    of the learned coarse correction."""
+    rng = np.random.default_rng(seed)
+    out = np.empty((nsamples, d * 6 * Nr * Ns * Ns))
+    for s in range(nsamples):
+        f = rng.standard_normal((d, 6, Nr, Ns, Ns))
+        for _ in range(int(rng.choice(smooth))):
+            for ax in (2, 3, 4):
+                g = np.concatenate([np.take(f, [0], axis=ax), f, np.take(f, [-1], axis=ax)], axis=ax)
+                n = f.shape[ax]
+                f = 0.25 * (np.take(g, range(0, n), axis=ax) + 2 * np.take(g, range(1, n + 1), axis=ax) +
+                            np.take(g, range(2, n + 2), axis=ax))
+        out[s] = (f / np.sqrt((f * f).mean())).ravel()
+    return out
