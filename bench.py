@@ -397,9 +397,11 @@ def box_cells(Ns, Nr, p, delta):
 def algorithmic_bytes(cat, c, N, es):
     """Algorithmic HBM bytes of one launch of a timing category: what it must read and write.
 
-    apply: read x, write y.  RAS forward (gather + L sweep): per box cell read r, write and read
-    the local vector, read the L factors (5 d off-diagonal + d(d-1)/2 diagonal-block entries),
-    write the result; backward (U sweep + scatter) likewise with the U factors (5 d + d(d+1)/2)."""
+    apply: read x, write y (d values per cell).  RAS forward sweep (gather fused): per box cell
+    read r and the cell map (8 bytes), read the L factors (5 d off-diagonal + d(d-1)/2
+    diagonal-block entries), write the local vector; backward sweep (scatter fused): per box
+    cell read the local vector, the cell map and owner flag (9 bytes) and the U factors
+    (5 d + d(d+1)/2), and write z once per grid cell (d values)."""
     es = 4 if cat.endswith('_fp32') else 8
     base = cat.replace('_fp32', '')
     coarse = base.endswith('_coarse')
@@ -415,8 +417,8 @@ def algorithmic_bytes(cat, c, N, es):
         else:
             cells = box_cells(c['Ns'], c['Nr'], c['p'], c['overlap'])
         if base.startswith('ras_fwd'):
-            return cells * es * (4 * d + 5 * d + d * (d - 1) // 2)
-        return cells * es * (4 * d + 5 * d + d * (d + 1) // 2)
+            return cells * (es * (2 * d + 5 * d + d * (d - 1) // 2) + 8)
+        return cells * (es * (d + 5 * d + d * (d + 1) // 2) + 9) + ncell * d * es
     return None
 
 

@@ -106,7 +106,8 @@ struct Subdomains {
   void* ring = nullptr;           // global 4-plane ring per CTA when it does not fit in shared memory
   int fp32 = 0;                   // 1: factors and sweeps in FP32
   int max_cols = 0;               // max nx * ny
-  int threads = 0;                // CTA size of the sweeps
+  int threads = 0;                // CTA size of the column-mapped d = 2 sweeps
+  int dense_threads = 0;          // CTA size of the level-mapped generic sweeps
   size_t smem = 0;                // dynamic shared memory of the sweeps
   int ring_in_smem = 0;
 };

@@ -325,6 +325,8 @@ __global__ void repack_kernel(int d, int count, const long long* __restrict__ ce
   }
 }
 
+constexpr int DENSE_THREADS = 512;  // CTA size bound of the generic sweeps (registers per thread)
+
 static size_t table_bytes(int levels, int ny) { return (size_t)(levels + 1 + levels * ny) * sizeof(int); }
 
 fv_status prepare_sweeps(fv_system* s, int fp32) {
@@ -355,10 +357,18 @@ fv_status prepare_sweeps(fv_system* s, int fp32) {
   std::vector<int> dims(3 * S.count);
   FV_CUDA(cudaMemcpy(dims.data(), S.dims, dims.size() * sizeof(int), cudaMemcpyDeviceToHost));
   size_t tab = 0;
+  int widest = 1;  // most cells in one wavefront step of any box
   for (int sd = 0; sd < S.count; ++sd) {
     const int nx = dims[3 * sd], ny = dims[3 * sd + 1], nz = dims[3 * sd + 2];
-    tab = std::max(tab, table_bytes((nx - 1) + 2 * (ny - 1) + (nz - 1) + 1, ny));
+    const int levels = (nx - 1) + 2 * (ny - 1) + (nz - 1) + 1;
+    tab = std::max(tab, table_bytes(levels, ny));
+    for (int L = 0; L < levels; ++L) {
+      int cnt = 0;
+      for (int j = 0; j < ny; ++j) cnt += std::max(0, std::min(nx - 1, L - 2 * j) - std::max(0, L - 2 * j - (nz - 1)) + 1);
+      widest = std::max(widest, cnt);
+    }
   }
+  S.dense_threads = std::min(DENSE_THREADS, (widest + 31) / 32 * 32);
   const size_t ring = 4 * (size_t)S.max_cols * d * es;
   const size_t ring_al = (ring + 15) / 16 * 16;
   S.ring_in_smem = ring_al + tab <= 200 * 1024;
@@ -372,34 +382,6 @@ fv_status prepare_sweeps(fv_system* s, int fp32) {
 }
 
 // ------------------------------------------------------------------ RAS apply
-// gather R_i^delta r into the packed sweep vector (zero past cube corners)
-template <class T, class V>
-__global__ void gather_kernel(int d, long long N, const long long* __restrict__ cell_off,
-                              const long long* __restrict__ gmap_p, const V* __restrict__ r, T* __restrict__ loc) {
-  const int sd = blockIdx.x;
-  const long long base = cell_off[sd], nc = cell_off[sd + 1] - base;
-  for (long long e = blockIdx.y * (long long)blockDim.x + threadIdx.x; e < nc * d; e += (long long)gridDim.y * blockDim.x) {
-    const int a = (int)(e / nc);
-    const long long pos = e - a * nc;
-    const long long g = gmap_p[base + pos];
-    loc[base * d + e] = g >= 0 ? (T)r[a * N + g] : (T)0;
-  }
-}
-
-// scatter the owned cells, (R_i^0)^T
-template <class T, class V>
-__global__ void scatter_kernel(int d, long long N, const long long* __restrict__ cell_off,
-                               const long long* __restrict__ gmap_p, const unsigned char* __restrict__ owned_p,
-                               const T* __restrict__ loc, V* __restrict__ z) {
-  const int sd = blockIdx.x;
-  const long long base = cell_off[sd], nc = cell_off[sd + 1] - base;
-  for (long long e = blockIdx.y * (long long)blockDim.x + threadIdx.x; e < nc * d; e += (long long)gridDim.y * blockDim.x) {
-    const int a = (int)(e / nc);
-    const long long pos = e - a * nc;
-    if (owned_p[base + pos]) z[a * N + gmap_p[base + pos]] = (V)loc[base * d + e];
-  }
-}
-
 // Wavefront sweeps: thread <-> (i, j) column; at step L the column's cell is k = L - i - 2j.
 // In-plane neighbours and the own column's previous cell are read from a ring of 4 planes
 // indexed by k mod 4 (a neighbour of level L-1..L-3 is never overwritten before it is read).
@@ -437,11 +419,33 @@ __device__ __forceinline__ void build_tables(const SweepBox& b, int* lvl, int* r
   __syncthreads();
 }
 
-template <class T, int D>
-__global__ void __launch_bounds__(704) ras_fwd_kernel(long long N, const long long* __restrict__ cell_off,
-                                                       const int* __restrict__ dims, const int* __restrict__ lpt,
-                                                       const T* __restrict__ F, T* __restrict__ loc, T* ring_g,
-                                                       int ring_in_smem, int max_cols) {
+// Generic sweeps (d = 7, and d = 2 boxes too wide for the column-prefetching kernels below):
+// at wavefront step L the thread with local index t takes the t-th cell of the level in
+// wavefront order (row j by binary search in the level's row offsets), so every active
+// lane does work; at most DENSE_THREADS threads leave each thread enough registers to
+// keep all of a cell's factor loads in flight at once.  The forward sweep gathers
+// R_i^delta r itself; the backward sweep scatters the owned cells, (R_i^0)^T.
+__device__ __forceinline__ void level_cell(const SweepBox& b, const int* rowoff, int L, int t, int& i, int& j,
+                                           int& k) {
+  const int* ro = rowoff + L * b.ny;
+  int lo = 0, hi = b.ny - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (ro[mid] <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  j = lo;
+  i = t - ro[j] + max(0, L - 2 * j - (b.nz - 1));
+  k = L - i - 2 * j;
+}
+
+template <class T, int D, class V>
+__global__ void __launch_bounds__(DENSE_THREADS) ras_fwd_kernel(const long long* __restrict__ cell_off,
+                                                                 const int* __restrict__ dims, const int* __restrict__ lpt,
+                                                                 const T* __restrict__ F, T* __restrict__ loc, T* ring_g,
+                                                                 int ring_in_smem, int max_cols, long long N,
+                                                                 const long long* __restrict__ gmap_p,
+                                                                 const V* __restrict__ r) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int sd = lpt[blockIdx.x];
   const SweepBox b = sweep_box(cell_off, dims, sd);
@@ -453,18 +457,22 @@ __global__ void __launch_bounds__(704) ras_fwd_kernel(long long N, const long lo
   constexpr int Q = 10 * D + D * D;
   const T* Fb = F + b.base * Q;
   T* Lb = loc + b.base * D;
+  const long long* gm = gmap_p + b.base;
   const long long nc = b.nc;
   for (int L = 0; L < b.levels; ++L) {
-    for (int col = threadIdx.x; col < b.ncols; col += blockDim.x) {
-      const int j = col / b.nx, i = col - j * b.nx, k = L - i - 2 * j;
-      if (k < 0 || k >= b.nz) continue;
-      const long long pos = lvl[L] + rowoff[L * b.ny + j] + i - max(0, L - 2 * j - (b.nz - 1));
+    const int cnt = lvl[L + 1] - lvl[L];
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+      int i, j, k;
+      level_cell(b, rowoff, L, t, i, j, k);
+      const int col = j * b.nx + i;
+      const long long pos = lvl[L] + t;
       const int pk = k & 3;
       T* rp = ring + (size_t)(pk * b.ncols) * D;
       const T* r0 = ring + (size_t)(((k - 1) & 3) * b.ncols + col) * D;
+      const long long g = gm[pos];
       T y[D];
 #pragma unroll
-      for (int a = 0; a < D; ++a) y[a] = Lb[a * nc + pos];
+      for (int a = 0; a < D; ++a) y[a] = g >= 0 ? (T)r[a * N + g] : T(0);
       if constexpr (sizeof(T) == 4 || D < 7) {
         // every factor slot exists (zero where the neighbour is outside the box): load them all
         // unconditionally so they are in flight together; only the neighbour reads are guarded
@@ -507,11 +515,14 @@ __global__ void __launch_bounds__(704) ras_fwd_kernel(long long N, const long lo
   }
 }
 
-template <class T, int D>
-__global__ void __launch_bounds__(704) ras_bwd_kernel(long long N, const long long* __restrict__ cell_off,
-                                                       const int* __restrict__ dims, const int* __restrict__ lpt,
-                                                       const T* __restrict__ F, T* __restrict__ loc, T* ring_g,
-                                                       int ring_in_smem, int max_cols) {
+template <class T, int D, class V>
+__global__ void __launch_bounds__(DENSE_THREADS) ras_bwd_kernel(const long long* __restrict__ cell_off,
+                                                                 const int* __restrict__ dims, const int* __restrict__ lpt,
+                                                                 const T* __restrict__ F, const T* __restrict__ loc,
+                                                                 T* ring_g, int ring_in_smem, int max_cols, long long N,
+                                                                 const long long* __restrict__ gmap_p,
+                                                                 const unsigned char* __restrict__ owned_p,
+                                                                 V* __restrict__ z) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int sd = lpt[blockIdx.x];
   const SweepBox b = sweep_box(cell_off, dims, sd);
@@ -522,13 +533,17 @@ __global__ void __launch_bounds__(704) ras_bwd_kernel(long long N, const long lo
   build_tables(b, lvl, rowoff);
   constexpr int Q = 10 * D + D * D;
   const T* Fb = F + b.base * Q;
-  T* Lb = loc + b.base * D;
+  const T* Lb = loc + b.base * D;
+  const long long* gm = gmap_p + b.base;
+  const unsigned char* ow = owned_p + b.base;
   const long long nc = b.nc;
   for (int L = b.levels - 1; L >= 0; --L) {
-    for (int col = threadIdx.x; col < b.ncols; col += blockDim.x) {
-      const int j = col / b.nx, i = col - j * b.nx, k = L - i - 2 * j;
-      if (k < 0 || k >= b.nz) continue;
-      const long long pos = lvl[L] + rowoff[L * b.ny + j] + i - max(0, L - 2 * j - (b.nz - 1));
+    const int cnt = lvl[L + 1] - lvl[L];
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+      int i, j, k;
+      level_cell(b, rowoff, L, t, i, j, k);
+      const int col = j * b.nx + i;
+      const long long pos = lvl[L] + t;
       T* rp = ring + (size_t)((k & 3) * b.ncols) * D;
       const T* r1 = ring + (size_t)(((k + 1) & 3) * b.ncols + col) * D;
       constexpr int U = 5 * D + D * D;
@@ -569,9 +584,11 @@ __global__ void __launch_bounds__(704) ras_bwd_kernel(long long N, const long lo
         }
       }
 #pragma unroll
-      for (int a = 0; a < D; ++a) {
-        rp[col * D + a] = x[a];
-        Lb[a * nc + pos] = x[a];
+      for (int a = 0; a < D; ++a) rp[col * D + a] = x[a];
+      if (ow[pos]) {
+        const long long g = gm[pos];
+#pragma unroll
+        for (int a = 0; a < D; ++a) z[a * N + g] = (V)x[a];
       }
     }
     __syncthreads();
@@ -736,7 +753,6 @@ static fv_status ras_apply_t(const fv_system* s, const V* r, V* z, cudaStream_t 
   const Subdomains& S = s->subs;
   const long long N = s->grid->geo.N;
   T* loc = (T*)S.loc;
-  const dim3 gs(S.count, 4);
   const int mc = (D == 2 && S.max_cols <= S.threads && S.threads <= 1024) ? 1
                  : (D == 2 && S.max_cols <= 2 * S.threads && S.threads <= 704) ? 2
                                                                                  : 0;
@@ -752,11 +768,10 @@ static fv_status ras_apply_t(const fv_system* s, const V* r, V* z, cudaStream_t 
     else if (mc == 2)
       ras_fwd2_kernel<T, 2, V><<<S.count, S.threads, S.smem, st>>>(S.cell_off, S.dims, S.lpt, (const T*)S.F, loc,
                                                                    (T*)S.ring, S.ring_in_smem, S.max_cols, N, S.gmap_p, r);
-    else {
-      gather_kernel<T, V><<<gs, 256, 0, st>>>(D, N, S.cell_off, S.gmap_p, r, loc);
-      ras_fwd_kernel<T, D><<<S.count, S.threads, S.smem, st>>>(N, S.cell_off, S.dims, S.lpt, (const T*)S.F, loc,
-                                                               (T*)S.ring, S.ring_in_smem, S.max_cols);
-    }
+    else
+      ras_fwd_kernel<T, D, V><<<S.count, S.dense_threads, S.smem, st>>>(S.cell_off, S.dims, S.lpt, (const T*)S.F, loc,
+                                                                       (T*)S.ring, S.ring_in_smem, S.max_cols, N,
+                                                                       S.gmap_p, r);
   }
   FV_CUDA(cudaGetLastError());
   {
@@ -769,11 +784,10 @@ static fv_status ras_apply_t(const fv_system* s, const V* r, V* z, cudaStream_t 
       ras_bwd2_kernel<T, 2, V><<<S.count, S.threads, S.smem, st>>>(S.cell_off, S.dims, S.lpt, (const T*)S.F, loc,
                                                                    (T*)S.ring, S.ring_in_smem, S.max_cols, N, S.gmap_p,
                                                                    S.owned_p, z);
-    else {
-      ras_bwd_kernel<T, D><<<S.count, S.threads, S.smem, st>>>(N, S.cell_off, S.dims, S.lpt, (const T*)S.F, loc,
-                                                               (T*)S.ring, S.ring_in_smem, S.max_cols);
-      scatter_kernel<T, V><<<gs, 256, 0, st>>>(D, N, S.cell_off, S.gmap_p, S.owned_p, loc, z);
-    }
+    else
+      ras_bwd_kernel<T, D, V><<<S.count, S.dense_threads, S.smem, st>>>(S.cell_off, S.dims, S.lpt, (const T*)S.F, loc,
+                                                                       (T*)S.ring, S.ring_in_smem, S.max_cols, N,
+                                                                       S.gmap_p, S.owned_p, z);
   }
   FV_CUDA(cudaGetLastError());
   return FV_OK;
@@ -783,8 +797,8 @@ static fv_status ras_apply_t(const fv_system* s, const V* r, V* z, cudaStream_t 
 // raise it to the device's opt-in maximum (never lower it for a smaller system).
 template <class T, int D>
 static fv_status set_smem_attr(int limit) {
-  FV_CUDA(cudaFuncSetAttribute(ras_fwd_kernel<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
-  FV_CUDA(cudaFuncSetAttribute(ras_bwd_kernel<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+  FV_CUDA(cudaFuncSetAttribute(ras_fwd_kernel<T, D, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+  FV_CUDA(cudaFuncSetAttribute(ras_bwd_kernel<T, D, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
   if (D == 2) {
     FV_CUDA(cudaFuncSetAttribute(ras_fwd2_kernel<T, 1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
     FV_CUDA(cudaFuncSetAttribute(ras_fwd2_kernel<T, 2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));

@@ -216,21 +216,23 @@ def uneven_boxes(Ns, Nr, sizes=(8, 12, 16, 24), target=None, seed=0):
     return boxes
 
 
-def multiscale_fields(Ns, Nr, nsamples, seed, d=2, smooth=(0, 1, 2, 4, 8, 16)):
+def multiscale_fields(Ns, Nr, nsamples, seed, d=2, widths=(0.0, 0.5, 1.0, 2.0, 4.0, 8.0)):
     """nsamples random d-component fields on a 6 x Ns x Ns x Nr grid, each row of the
-    result one sample laid out [c][p][k][j][i]: white noise smoothed, per sample, m
-    times (m drawn from `smooth`) by the 3-point filter (1, 2, 1)/4 along each panel
-    axis (edge values repeated), then scaled to unit RMS.  Training and test inputs
-    of the learned coarse correction."""
+    result one sample laid out [c][p][k][j][i]: per sample, white noise on every
+    (component, panel) block filtered by the Gaussian of a width (in cells) drawn from
+    `widths` (periodic FFT filter over the block, 0 = white), scaled to unit RMS.
+    Training and test inputs of the learned coarse correction."""
     rng = np.random.default_rng(seed)
     out = np.empty((nsamples, d * 6 * Nr * Ns * Ns))
+    kz = np.fft.fftfreq(Nr)[:, None, None]
+    ky = np.fft.fftfreq(Ns)[None, :, None]
+    kx = np.fft.rfftfreq(Ns)[None, None, :]
+    k2 = (2 * np.pi) ** 2 * (kz * kz + ky * ky + kx * kx)
     for s in range(nsamples):
         f = rng.standard_normal((d, 6, Nr, Ns, Ns))
-        for _ in range(int(rng.choice(smooth))):
-            for ax in (2, 3, 4):
-                g = np.concatenate([np.take(f, [0], axis=ax), f, np.take(f, [-1], axis=ax)], axis=ax)
-                n = f.shape[ax]
-                f = 0.25 * (np.take(g, range(0, n), axis=ax) + 2 * np.take(g, range(1, n + 1), axis=ax) +
-                            np.take(g, range(2, n + 2), axis=ax))
+        w = float(rng.choice(widths))
+        if w > 0:
+            f = np.fft.irfftn(np.fft.rfftn(f, axes=(2, 3, 4)) * np.exp(-0.5 * w * w * k2), s=(Nr, Ns, Ns),
+                              axes=(2, 3, 4))
         out[s] = (f / np.sqrt((f * f).mean())).ravel()
     return out
