@@ -325,7 +325,7 @@ __global__ void repack_kernel(int d, int count, const long long* __restrict__ ce
   }
 }
 
-constexpr int DENSE_THREADS = 512;  // CTA size bound of the generic sweeps (registers per thread)
+constexpr int DENSE_THREADS = 384;  // CTA size bound of the generic sweeps (170 registers per thread)
 
 static size_t table_bytes(int levels, int ny) { return (size_t)(levels + 1 + levels * ny) * sizeof(int); }
 
@@ -440,7 +440,7 @@ __device__ __forceinline__ void level_cell(const SweepBox& b, const int* rowoff,
 }
 
 template <class T, int D, class V>
-__global__ void __launch_bounds__(DENSE_THREADS) ras_fwd_kernel(const long long* __restrict__ cell_off,
+__global__ void __launch_bounds__(DENSE_THREADS, 1) ras_fwd_kernel(const long long* __restrict__ cell_off,
                                                                  const int* __restrict__ dims, const int* __restrict__ lpt,
                                                                  const T* __restrict__ F, T* __restrict__ loc, T* ring_g,
                                                                  int ring_in_smem, int max_cols, long long N,
@@ -459,6 +459,9 @@ __global__ void __launch_bounds__(DENSE_THREADS) ras_fwd_kernel(const long long*
   T* Lb = loc + b.base * D;
   const long long* gm = gmap_p + b.base;
   const long long nc = b.nc;
+  // the cell map entry of each thread's first cell of the next step is loaded before the
+  // barrier, so a step issues its right-hand-side and factor loads together
+  long long gnext = threadIdx.x < lvl[1] ? gm[threadIdx.x] : -1;
   for (int L = 0; L < b.levels; ++L) {
     const int cnt = lvl[L + 1] - lvl[L];
     for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
@@ -469,7 +472,7 @@ __global__ void __launch_bounds__(DENSE_THREADS) ras_fwd_kernel(const long long*
       const int pk = k & 3;
       T* rp = ring + (size_t)(pk * b.ncols) * D;
       const T* r0 = ring + (size_t)(((k - 1) & 3) * b.ncols + col) * D;
-      const long long g = gm[pos];
+      const long long g = t == threadIdx.x ? gnext : gm[pos];
       T y[D];
 #pragma unroll
       for (int a = 0; a < D; ++a) y[a] = g >= 0 ? (T)r[a * N + g] : T(0);
@@ -511,12 +514,13 @@ __global__ void __launch_bounds__(DENSE_THREADS) ras_fwd_kernel(const long long*
         Lb[a * nc + pos] = y[a];
       }
     }
+    if (L + 1 < b.levels && threadIdx.x < lvl[L + 2] - lvl[L + 1]) gnext = gm[lvl[L + 1] + threadIdx.x];
     __syncthreads();
   }
 }
 
 template <class T, int D, class V>
-__global__ void __launch_bounds__(DENSE_THREADS) ras_bwd_kernel(const long long* __restrict__ cell_off,
+__global__ void __launch_bounds__(DENSE_THREADS, 1) ras_bwd_kernel(const long long* __restrict__ cell_off,
                                                                  const int* __restrict__ dims, const int* __restrict__ lpt,
                                                                  const T* __restrict__ F, const T* __restrict__ loc,
                                                                  T* ring_g, int ring_in_smem, int max_cols, long long N,
