@@ -624,20 +624,29 @@ __global__ void __launch_bounds__(MC == 1 ? 1024 : 704) ras_fwd2_kernel(const lo
   const long long nc = b.nc;
   int ci[MC], cj[MC];
   T f[MC][NF], y0[MC][D];
-  long long ps[MC];
+  long long ps[MC], gn[MC];
 #pragma unroll
   for (int m = 0; m < MC; ++m) {
     const int col = threadIdx.x + m * blockDim.x;
     cj[m] = col < b.ncols ? col / b.nx : -1;
     ci[m] = col < b.ncols ? col - cj[m] * b.nx : 0;
   }
-  auto fetch = [&](int L, int m) {
+  auto cellpos = [&](int L, int m) -> long long {
     const int i = ci[m], j = cj[m], k = L - i - 2 * j;
-    ps[m] = -1;
-    if (j < 0 || k < 0 || k >= b.nz || L >= b.levels) return;
-    const long long pos = lvl[L] + rowoff[L * b.ny + j] + i - max(0, L - 2 * j - (b.nz - 1));
+    if (j < 0 || k < 0 || k >= b.nz || L >= b.levels) return -1;
+    return lvl[L] + rowoff[L * b.ny + j] + i - max(0, L - 2 * j - (b.nz - 1));
+  };
+  // the cell map entry is loaded two steps ahead, the gathered r and the factors one step
+  // ahead: nothing a step's critical path waits for is loaded in that step
+  auto fetch_g = [&](int L, int m) {
+    const long long pos = cellpos(L, m);
+    gn[m] = pos >= 0 ? gmap_p[b.base + pos] : -1;
+  };
+  auto fetch = [&](int L, int m) {
+    const long long pos = cellpos(L, m);
     ps[m] = pos;
-    const long long g = gmap_p[b.base + pos];  // R_i^delta r gathered here (zero past cube corners)
+    if (pos < 0) return;
+    const long long g = gn[m];  // R_i^delta r gathered here (zero past cube corners)
 #pragma unroll
     for (int a = 0; a < D; ++a) y0[m][a] = g >= 0 ? (T)r[a * N + g] : T(0);
 #pragma unroll
@@ -645,7 +654,7 @@ __global__ void __launch_bounds__(MC == 1 ? 1024 : 704) ras_fwd2_kernel(const lo
     f[m][5 * D] = Fb[(5 * D + 1 * D + 0) * nc + pos];  // diagonal block entry (1, 0)
   };
 #pragma unroll
-  for (int m = 0; m < MC; ++m) fetch(0, m);
+  for (int m = 0; m < MC; ++m) fetch_g(0, m), fetch(0, m), fetch_g(1, m);
   for (int L = 0; L < b.levels; ++L) {
 #pragma unroll
     for (int m = 0; m < MC; ++m) {
@@ -669,7 +678,7 @@ __global__ void __launch_bounds__(MC == 1 ? 1024 : 704) ras_fwd2_kernel(const lo
       for (int a = 0; a < D; ++a) w[a] = y[a], Lb[a * nc + ps[m]] = y[a];
     }
 #pragma unroll
-    for (int m = 0; m < MC; ++m) fetch(L + 1, m);
+    for (int m = 0; m < MC; ++m) fetch(L + 1, m), fetch_g(L + 2, m);
     __syncthreads();
   }
 }
@@ -696,7 +705,7 @@ __global__ void __launch_bounds__(MC == 1 ? 1024 : 704) ras_bwd2_kernel(const lo
   const long long nc = b.nc;
   int ci[MC], cj[MC];
   T f[MC][NF], x0[MC][D];
-  long long ps[MC];
+  long long ps[MC], go[MC];  // go: cell map entry of an owned cell, else -1 (fetched with the factors)
 #pragma unroll
   for (int m = 0; m < MC; ++m) {
     const int col = threadIdx.x + m * blockDim.x;
@@ -716,6 +725,8 @@ __global__ void __launch_bounds__(MC == 1 ? 1024 : 704) ras_bwd2_kernel(const lo
     f[m][5 * D] = Fb[(5 * D + 0 * D + 1) * nc + pos];      // diag (0, 1)
     f[m][5 * D + 1] = Fb[(5 * D + 0 * D + 0) * nc + pos];  // diag (0, 0)
     f[m][5 * D + 2] = Fb[(5 * D + 1 * D + 1) * nc + pos];  // diag (1, 1)
+    const long long g = gmap_p[b.base + pos];
+    go[m] = owned_p[b.base + pos] ? g : -1;
   };
 #pragma unroll
   for (int m = 0; m < MC; ++m) fetch(b.levels - 1, m);
@@ -740,10 +751,9 @@ __global__ void __launch_bounds__(MC == 1 ? 1024 : 704) ras_bwd2_kernel(const lo
       T* w = ring + (size_t)((k & 3) * b.ncols + col) * D;
 #pragma unroll
       for (int a = 0; a < D; ++a) w[a] = x[a];
-      if (owned_p[b.base + ps[m]]) {  // (R_i^0)^T: scatter the owned cells
-        const long long g = gmap_p[b.base + ps[m]];
+      if (go[m] >= 0) {  // (R_i^0)^T: scatter the owned cells
 #pragma unroll
-        for (int a = 0; a < D; ++a) z[a * N + g] = (V)x[a];
+        for (int a = 0; a < D; ++a) z[a * N + go[m]] = (V)x[a];
       }
     }
 #pragma unroll
