@@ -9,20 +9,23 @@
  * coarse GMRES stays the fallback: a solve whose learned preconditioner fails
  * to converge is finished with the plain one.
  *
- * Network (per cubed-sphere panel; panels never exchange data inside it):
- *   s  = ||r_c||_2 over the whole coarse vector (N(a r) = a N(r))
- *   a1 = relu(conv(r_c/s; 2 -> C))      a2 = relu(conv(a1; C -> C))
- *   p  = 2x2x2 mean pooling of a2
- *   a3 = relu(conv(p; C -> 2C))         a4 = relu(conv(a3; 2C -> 2C))
- *   a5 = relu(conv([a2, upsample(a4)]; 3C -> C))   (nearest upsampling, concat)
- *   e_c = s conv(a5; C -> 2)
- * conv = 3x3x3 cross-correlation with zero padding 1 inside each panel plus a
- * bias, over the panel's (k, j, i) = (radial, eta, xi) cells.  Parameters are
- * FP32 masters, flat, layer by layer: W[co][ci][dz][dy][dx] then b[co]
- * (~71k parameters for C = 16, ~284k for C = 32).  Activations, weights and
- * gradients are stored as BF16; products accumulate in FP32 on the tensor
- * cores.  Training minimises the mean squared error of N(r)/s against e/s
- * with Adam (Kingma & Ba, 2015) on FP32 masters.
+ * Network: a U-Net with `levels` poolings and width C on the cubed sphere.
+ * Before every 3x3x3 convolution each panel is padded by one cell in (eta, xi)
+ * with the neighbouring panel's cells across each edge (the cell sharing the
+ * edge face; zero at the ring corners) and by zeros radially.
+ *   s = ||r_c||_2 over the whole coarse vector (N(a r) = a N(r))
+ *   level l = 0..L: input r_c/s (l = 0) or the 2x2x2 mean pooling of E_{l-1};
+ *                   A_l = relu(conv(input)), E_l = relu(conv(A_l))
+ *   D_L = E_L; l = L-1..0: D_l = relu(conv([E_l, upsample(D_{l+1})]))
+ *   e_c = s conv(D_0; C -> 2)
+ * conv = 3x3x3 cross-correlation plus a bias over the panel's (k, j, i) =
+ * (radial, eta, xi) cells (input channels: 2 for the first, 2C for the
+ * decoder, else C).  Parameters are FP32 masters, flat, layer by layer (e0a,
+ * e0b, ..., eLa, eLb, d(L-1), ..., d0, out): W[co][ci][dz][dy][dx] then b[co]
+ * (C = 32, L = 3: 363,234 parameters).  Activations, weights and gradients are
+ * stored as BF16; products accumulate in FP32 on the tensor cores.  Training
+ * minimises the mean squared error of N(r)/s against e/s with Adam (Kingma &
+ * Ba, 2015) on FP32 masters.
  *
  * Vectors follow fv.h: caller-owned device FP64, a coarse PPBE vector is
  * [comp = P, P_b][panel][k][j][i] on the coarse grid (2 * 6 Ns^2 Nr values);
@@ -40,12 +43,13 @@ extern "C" {
 typedef struct fv_net fv_net;
 
 /* Network on a grid of 6 panels x Ns x Ns x Nr cells (the coarse grid of the
- * system it serves).  C in {16, 32}; Ns, Nr even and >= 2; max_batch >= 1
- * samples per forward / training step (activation memory scales with it:
- * about 700 bytes per cell and sample at C = 32).  Weights start at zero:
- * set them with fv_net_set_params. */
+ * system it serves).  C in {16, 32}; levels in [0, 4]; Ns, Nr >= 1 and
+ * divisible by 2^levels; max_batch >= 1 samples per forward / training step
+ * (activation memory scales with it: about 600 bytes per cell and sample at
+ * C = 32, twice that while training).  Weights start at zero: set them with
+ * fv_net_set_params. */
 typedef struct {
-  int C, Ns, Nr, max_batch;
+  int C, levels, Ns, Nr, max_batch;
 } fv_net_desc;
 
 fv_status fv_net_create(const fv_net_desc* desc, fv_net** out);

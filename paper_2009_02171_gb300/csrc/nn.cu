@@ -1,17 +1,22 @@
-// Learned coarse correction: a panel-wise 3-D convolutional U-Net on the coarse
-// grid of the two-level preconditioner (declared in include/fv_net.h; not in the
-// paper, it stands in for the coarse solve of eqn:coarsesolve).
+// Learned coarse correction: a cubed-sphere U-Net on the coarse grid of the
+// two-level preconditioner (declared in include/fv_net.h; not in the paper, it
+// stands in for the coarse solve of eqn:coarsesolve).
 //
 // Data layout: activations and gradients are BF16, channels last, one voxel per
-// coarse cell: [panel][k][j][i][channel] with panel = sample * 6 + cubed-sphere
-// panel.  A convolution is an implicit GEMM (M = voxels, N = output channels,
-// K = 27 taps x input channels) on the tensor cores (mma.sync m16n8k16, BF16 x
-// BF16 -> FP32): one CTA computes a 4 x 4 x 8 brick of output voxels from a
-// (6 x 6 x 10)-voxel halo of its input staged in shared memory (channel stride
-// padded by 8 so ldmatrix rows fall in distinct banks).  The backward data pass
-// is the same kernel with flipped, transposed weights; the weight gradient is a
-// GEMM over voxels (M = input channels, N = output channels) split over
-// (tap, voxel range) CTAs with FP32 atomics into the master gradient.
+// cell of a pyramid level, each panel padded by a one-cell ring in (eta, xi):
+// [panel][k][j + 1][i + 1][channel], (Ns_l + 2)^2 voxels a plane, panel = sample
+// * 6 + cubed-sphere panel.  The ring holds the neighbouring panel's cells across
+// each edge (halo_fill); ring corners stay zero.  A convolution is an implicit
+// GEMM (M = voxels, N = output channels, K = 27 taps x input channels) on the
+// tensor cores (mma.sync m16n8k16, BF16 x BF16 -> FP32): one CTA computes a
+// 4 x 4 x 8 brick of output voxels from a (6 x 6 x 10)-voxel halo of its input
+// staged in shared memory (channel stride padded by 8 so ldmatrix rows fall in
+// distinct banks).  The backward data pass is the same kernel with flipped,
+// transposed weights over the whole padded plane (the gradient of the ring
+// included), followed by halo_adjoint (ring gradients added to the neighbour
+// cells they were copied from); the weight gradient is a GEMM over voxels
+// (M = input channels, N = output channels) split over (tap, voxel range) CTAs
+// with FP32 atomics into the master gradient.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -30,21 +35,31 @@ using bf16 = __nv_bfloat16;
 constexpr int BZ = 4, BY = 4, BX = 8;  // output brick of one convolution CTA (128 voxels, 4 warps)
 constexpr int HY = BY + 2, HX = BX + 2, HV = (BZ + 2) * HY * HX;
 constexpr int CONV_THREADS = 128;
+constexpr int MAX_CIN = 64;            // widest convolution input (2C, C <= 32)
 constexpr int WK = 64;                 // voxels per weight-gradient chunk
 constexpr int RED_THREADS = 256;
 
-enum { EPI_RELU = 0, EPI_RAW = 1, EPI_MASK = 2, EPI_FINAL = 3 };
+enum { EPI_RELU = 0, EPI_RAW = 1, EPI_FINAL = 2 };
+
+// one pyramid level: Z x Y x X cells a panel, stored with the (Y + 2) x (X + 2) ring plane
+struct Lvl {
+  int Z, Y, X;
+  __host__ __device__ long long vox(int P) const { return (long long)P * Z * (Y + 2) * (X + 2); }
+  __host__ __device__ long long cells(int P) const { return (long long)P * Z * Y * X; }
+};
 
 struct ConvArgs {
-  const bf16* s0;     // full-resolution input, c0 channels
-  const bf16* s1;     // half-resolution input read through nearest upsampling, c1 channels (or null)
+  const bf16* s0;     // input at the output's level, c0 channels (padded)
+  const bf16* s1;     // input one level coarser read through nearest upsampling, c1 channels (or null)
   const bf16* w;      // [27][coutN][cin], tap = dz * 9 + dy * 3 + dx, input voxel = output + (dz, dy, dx) - 1
   const float* bias;  // [cout] (RELU, FINAL)
-  const bf16* mask;   // [voxel][cout] (MASK): output kept where mask > 0
-  bf16* out;          // [voxel][cout]
-  float* y;           // [voxel][cout] FP32 (FINAL)
+  bf16* out;          // [padded voxel][cout]
+  float* y;           // [cell][cout] FP32 (FINAL)
   int c0, c1, cin, coutN, cout;
-  int P, Z, Y, X;
+  int P;
+  Lvl L;
+  int o0, On;         // output region per plane axis in padded coordinates: [o0, o0 + On) (1, Y: interior; 0, Y + 2: all)
+  int i0, i1;         // valid input region per plane axis in padded coordinates, zero outside
   int mode;
 };
 
@@ -66,15 +81,17 @@ __device__ __forceinline__ void mma16816(float* c, const uint32_t* a, uint32_t b
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// Load one 16-byte channel group q (8 channels) of the (possibly concatenated)
-// input at voxel (p, z, y, x); zero outside the panel.
-__device__ __forceinline__ uint4 load_in(const bf16* s0, int c0, const bf16* s1, int c1, int q, int p, int z,
-                                         int y, int x, int Z, int Y, int X) {
-  if (z < 0 || z >= Z || y < 0 || y >= Y || x < 0 || x >= X) return make_uint4(0, 0, 0, 0);
-  if (q * 8 < c0) return *reinterpret_cast<const uint4*>(s0 + ((((long long)p * Z + z) * Y + y) * X + x) * c0 + q * 8);
-  const int Zh = Z >> 1, Yh = Y >> 1, Xh = X >> 1;
-  return *reinterpret_cast<const uint4*>(
-      s1 + ((((long long)p * Zh + (z >> 1)) * Yh + (y >> 1)) * Xh + (x >> 1)) * c1 + (q * 8 - c0));
+// One 16-byte channel group q (8 channels) of the (possibly concatenated) input at
+// padded voxel (p, z, y, x) of level L; zero outside the valid region [i0, i1) and radially.
+__device__ __forceinline__ uint4 load_in(const bf16* s0, int c0, const bf16* s1, int c1, int q, int p, int z, int y,
+                                         int x, const Lvl& L, int i0, int i1) {
+  if (z < 0 || z >= L.Z || y < i0 || y >= i1 || x < i0 || x >= i1) return make_uint4(0, 0, 0, 0);
+  const int Yp = L.Y + 2, Xp = L.X + 2;
+  if (q * 8 < c0) return *reinterpret_cast<const uint4*>(s0 + ((((long long)p * L.Z + z) * Yp + y) * Xp + x) * c0 + q * 8);
+  const int Zh = L.Z >> 1, Yh = (L.Y >> 1) + 2, Xh = (L.X >> 1) + 2;
+  const int yh = ((y - 1) >> 1) + 1, xh = ((x - 1) >> 1) + 1;  // parent in padded coordinates (ring -> ring)
+  return *reinterpret_cast<const uint4*>(s1 + ((((long long)p * Zh + (z >> 1)) * Yh + yh) * Xh + xh) * c1 +
+                                         (q * 8 - c0));
 }
 
 template <int NT>
@@ -82,7 +99,7 @@ __global__ void __launch_bounds__(CONV_THREADS) conv_kernel(ConvArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   bf16* hs = reinterpret_cast<bf16*>(smem_raw);
   const int cs = a.cin + 8;
-  const int nbx = (a.X + BX - 1) / BX, nby = (a.Y + BY - 1) / BY, nbz = (a.Z + BZ - 1) / BZ;
+  const int nbx = (a.On + BX - 1) / BX, nby = (a.On + BY - 1) / BY, nbz = (a.L.Z + BZ - 1) / BZ;
   int blk = blockIdx.x;
   const int bx = blk % nbx;
   blk /= nbx;
@@ -90,13 +107,13 @@ __global__ void __launch_bounds__(CONV_THREADS) conv_kernel(ConvArgs a) {
   blk /= nby;
   const int bz = blk % nbz;
   const int p = blk / nbz;
-  const int x0 = bx * BX, y0 = by * BY, z0 = bz * BZ;
+  const int x0 = a.o0 + bx * BX, y0 = a.o0 + by * BY, z0 = bz * BZ;  // padded coordinates of the brick origin
 
   const int qn = a.cin >> 3;
   for (int it = threadIdx.x; it < HV * qn; it += CONV_THREADS) {
     const int hv = it / qn, q = it - hv * qn;
     const int hx = hv % HX, hy = (hv / HX) % HY, hz = hv / (HX * HY);
-    const uint4 v = load_in(a.s0, a.c0, a.s1, a.c1, q, p, z0 - 1 + hz, y0 - 1 + hy, x0 - 1 + hx, a.Z, a.Y, a.X);
+    const uint4 v = load_in(a.s0, a.c0, a.s1, a.c1, q, p, z0 - 1 + hz, y0 - 1 + hy, x0 - 1 + hx, a.L, a.i0, a.i1);
     *reinterpret_cast<uint4*>(hs + hv * cs + q * 8) = v;
   }
   __syncthreads();
@@ -138,47 +155,218 @@ __global__ void __launch_bounds__(CONV_THREADS) conv_kernel(ConvArgs a) {
 
   // epilogue: accumulator e of tile (mt, nt): row (lane >> 2) + 8 (e >> 1), column nt*8 + (lane & 3)*2 + (e & 1)
   const int z = z0 + warp;
+  const int Yp = a.L.Y + 2, Xp = a.L.X + 2;
 #pragma unroll
   for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int row = (lane >> 2) + 8 * h;
       const int y = y0 + 2 * mt + (row >> 3), x = x0 + (row & 7);
-      if (z >= a.Z || y >= a.Y || x >= a.X) continue;
-      const long long v = (((long long)p * a.Z + z) * a.Y + y) * a.X + x;
+      if (z >= a.L.Z || y >= a.o0 + a.On || x >= a.o0 + a.On) continue;
+      const long long v = (((long long)p * a.L.Z + z) * Yp + y) * Xp + x;
 #pragma unroll
       for (int nt = 0; nt < NT; ++nt) {
         const int col = nt * 8 + (lane & 3) * 2;
         float u0 = acc[mt][nt][2 * h], u1 = acc[mt][nt][2 * h + 1];
-        if (a.mode == EPI_FINAL) {
-          if (col < a.cout) a.y[v * a.cout + col] = u0 + a.bias[col];
-          if (col + 1 < a.cout) a.y[v * a.cout + col + 1] = u1 + a.bias[col + 1];
+        if (a.mode == EPI_FINAL) {  // interior cell index (y, x >= 1 here)
+          const long long c = (((long long)p * a.L.Z + z) * a.L.Y + (y - 1)) * a.L.X + (x - 1);
+          if (col < a.cout) a.y[c * a.cout + col] = u0 + a.bias[col];
+          if (col + 1 < a.cout) a.y[c * a.cout + col + 1] = u1 + a.bias[col + 1];
           continue;
         }
         if (col >= a.cout) continue;
         if (a.mode == EPI_RELU) {
           u0 = fmaxf(u0 + a.bias[col], 0.f);
           u1 = fmaxf(u1 + a.bias[col + 1], 0.f);
-        } else if (a.mode == EPI_MASK) {
-          const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162*>(a.mask + v * a.cout + col);
-          if (!(__bfloat162float(m.x) > 0.f)) u0 = 0.f;
-          if (!(__bfloat162float(m.y) > 0.f)) u1 = 0.f;
         }
         *reinterpret_cast<__nv_bfloat162*>(a.out + v * a.cout + col) = __floats2bfloat162_rn(u0, u1);
       }
     }
 }
 
-// Weight gradient of one convolution: gw[co][ci][tap] += sum over voxels v of
-// in[v + tap offset][ci] * g[v][co].  CTA (chunk group, tap); warp pairs
-// (16 input channels) x (16 output channels) accumulate over WK-voxel chunks.
+// Cubed-sphere ring: the ring voxel beyond `side` of panel p at tangential index t takes
+// the value of panel q[p][side]'s cell next to its side s[p][side] at tangential index
+// t (flip: n - 1 - t).  Sides: 0 xi-min, 1 xi-max, 2 eta-min, 3 eta-max.
+struct Halo {
+  int q[24], s[24], flip[24];
+};
+
+// (y, x) of the cell next to `side` at tangential index t (padded coordinates); ring = outside
+__device__ __forceinline__ void side_cell(int side, int t, int n, bool ring, int& y, int& x) {
+  const int lo = ring ? 0 : 1, hi = ring ? n + 1 : n;
+  if (side == 0) y = t + 1, x = lo;
+  else if (side == 1) y = t + 1, x = hi;
+  else if (side == 2) y = lo, x = t + 1;
+  else y = hi, x = t + 1;
+}
+
+__global__ void halo_fill_kernel(bf16* __restrict__ a, int C, int P, Lvl L, Halo H) {
+  const int n = L.Y, qn = C / 8;
+  const long long total = (long long)P * 4 * n * L.Z * qn;
+  const int Yp = L.Y + 2, Xp = L.X + 2;
+  for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total; it += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(it % qn);
+    long long t = it / qn;
+    const int z = (int)(t % L.Z);
+    t /= L.Z;
+    const int tt = (int)(t % n);
+    t /= n;
+    const int side = (int)(t % 4);
+    const int pp = (int)(t / 4), p = pp % 6, base = pp - p;
+    const int e = p * 4 + side;
+    int yd, xd, ys, xs;
+    side_cell(side, tt, n, true, yd, xd);
+    side_cell(H.s[e], H.flip[e] ? n - 1 - tt : tt, n, false, ys, xs);
+    const long long src = (((long long)(base + H.q[e]) * L.Z + z) * Yp + ys) * Xp + xs;
+    const long long dst = (((long long)pp * L.Z + z) * Yp + yd) * Xp + xd;
+    *reinterpret_cast<uint4*>(a + dst * C + q * 8) = *reinterpret_cast<const uint4*>(a + src * C + q * 8);
+  }
+}
+
+// Adjoint of halo_fill on a gradient over the whole padded plane: every edge cell gets
+// the ring gradients copied from it added (1 side, 2 at a panel corner, 4 when n = 1).
+// Ring values are left in place (consumers read interior cells only).
+__global__ void halo_adjoint_kernel(bf16* __restrict__ g, int C, int P, Lvl L, Halo H) {
+  const int n = L.Y;
+  const int ne = n > 1 ? 4 * n - 4 : 1;  // edge cells of a plane
+  const long long total = (long long)P * L.Z * ne * C;
+  const int Yp = L.Y + 2, Xp = L.X + 2;
+  for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total; it += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(it % C);
+    long long t = it / C;
+    const int ec = (int)(t % ne);
+    t /= ne;
+    const int z = (int)(t % L.Z);
+    const int pp = (int)(t / L.Z), p = pp % 6, base = pp - p;
+    // edge cell ec -> (j, i): bottom row, top row, then the left and right columns without corners
+    int j, i;
+    if (n == 1) j = 0, i = 0;
+    else if (ec < n) j = 0, i = ec;
+    else if (ec < 2 * n) j = n - 1, i = ec - n;
+    else if (ec < 3 * n - 2) j = ec - 2 * n + 1, i = 0;
+    else j = ec - (3 * n - 2) + 1, i = n - 1;
+    const long long dst = ((((long long)pp * L.Z + z) * Yp + j + 1) * Xp + i + 1) * C + c;
+    float acc = __bfloat162float(g[dst]);
+    for (int sq = 0; sq < 4; ++sq) {
+      const bool on = sq == 0 ? i == 0 : sq == 1 ? i == n - 1 : sq == 2 ? j == 0 : j == n - 1;
+      if (!on) continue;
+      const int e = p * 4 + sq;                    // the neighbour across side sq of this panel
+      const int tq = sq < 2 ? j : i;               // tangential index on this side
+      const int tp = H.flip[e] ? n - 1 - tq : tq;  // ... on the neighbour's side
+      int yr, xr;
+      side_cell(H.s[e], tp, n, true, yr, xr);
+      acc += __bfloat162float(g[((((long long)(base + H.q[e]) * L.Z + z) * Yp + yr) * Xp + xr) * C + c]);
+    }
+    g[dst] = __float2bfloat16_rn(acc);
+  }
+}
+
+// g <- g * (a > 0) on interior cells, 0 on the ring (padded tensors of C channels)
+__global__ void mask_kernel(bf16* __restrict__ g, const bf16* __restrict__ a, int C, int P, Lvl L) {
+  const long long total = L.vox(P) * C;
+  const int Yp = L.Y + 2, Xp = L.X + 2;
+  for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total; it += (long long)gridDim.x * blockDim.x) {
+    const long long v = it / C;
+    const int x = (int)(v % Xp), y = (int)((v / Xp) % Yp);
+    const bool in = x >= 1 && x <= L.X && y >= 1 && y <= L.Y;
+    g[it] = (in && __bfloat162float(a[it]) > 0.f) ? g[it] : __float2bfloat16_rn(0.f);
+  }
+}
+
+// interior cell index -> padded voxel index
+__device__ __forceinline__ long long padded(long long cell, const Lvl& L) {
+  const int x = (int)(cell % L.X);
+  long long t = cell / L.X;
+  const int y = (int)(t % L.Y);
+  t /= L.Y;  // p * Z + z
+  return (t * (L.Y + 2) + y + 1) * (L.X + 2) + x + 1;
+}
+
+// 2x2x2 mean pooling of the interior of a (level l) into the interior of out (level l + 1 = Lc)
+__global__ void pool_kernel(const bf16* __restrict__ a, bf16* __restrict__ out, int C, int P, Lvl Lc) {
+  const Lvl L{Lc.Z * 2, Lc.Y * 2, Lc.X * 2};
+  const int qn = C / 8;
+  const long long total = Lc.cells(P) * qn;
+  for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total; it += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(it % qn);
+    const long long cell = it / qn;
+    const int x = (int)(cell % Lc.X), y = (int)((cell / Lc.X) % Lc.Y);
+    const long long pz = cell / ((long long)Lc.X * Lc.Y);  // p * Zc + z
+    const int z = (int)(pz % Lc.Z);
+    const long long p = pz / Lc.Z;
+    float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int c = 0; c < 8; ++c) {
+      const long long v = (((p * L.Z + 2 * z + (c >> 2)) * (L.Y + 2) + 2 * y + ((c >> 1) & 1) + 1) * (L.X + 2) + 2 * x +
+                           (c & 1) + 1);
+      const uint4 u = *reinterpret_cast<const uint4*>(a + v * C + q * 8);
+      const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+      for (int k = 0; k < 4; ++k) {
+        s[2 * k] += __bfloat162float(h[k].x);
+        s[2 * k + 1] += __bfloat162float(h[k].y);
+      }
+    }
+    uint4 o;
+    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&o);
+    for (int k = 0; k < 4; ++k) h[k] = __floats2bfloat162_rn(0.125f * s[2 * k], 0.125f * s[2 * k + 1]);
+    *reinterpret_cast<uint4*>(out + padded(cell, Lc) * C + q * 8) = o;
+  }
+}
+
+// decoder backward split of gcat (2C channels, level l, interior after halo_adjoint):
+// gE[child][c] = gcat[child][c] (skip), gnext[parent][c] = sum over children of
+// gcat[child][C + c], times (mask[parent][c] > 0) when a mask is given
+__global__ void split_kernel(const bf16* __restrict__ gcat, bf16* __restrict__ gE, bf16* __restrict__ gnext,
+                             const bf16* __restrict__ mask, int C, int P, Lvl Lc) {
+  const Lvl L{Lc.Z * 2, Lc.Y * 2, Lc.X * 2};
+  const long long total = Lc.cells(P) * C;
+  for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total; it += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(it % C);
+    const long long cell = it / C;
+    const int x = (int)(cell % Lc.X), y = (int)((cell / Lc.X) % Lc.Y);
+    const long long pz = cell / ((long long)Lc.X * Lc.Y);
+    const int z = (int)(pz % Lc.Z);
+    const long long p = pz / Lc.Z;
+    float s = 0.f;
+    for (int k = 0; k < 8; ++k) {
+      const long long v = (((p * L.Z + 2 * z + (k >> 2)) * (L.Y + 2) + 2 * y + ((k >> 1) & 1) + 1) * (L.X + 2) + 2 * x +
+                           (k & 1) + 1);
+      gE[v * C + c] = gcat[v * 2 * C + c];
+      s += __bfloat162float(gcat[v * 2 * C + C + c]);
+    }
+    const long long pv = padded(cell, Lc) * C + c;
+    if (mask && !(__bfloat162float(mask[pv]) > 0.f)) s = 0.f;
+    gnext[pv] = __float2bfloat16_rn(s);
+  }
+}
+
+// encoder backward through the pooling: gE[child] += g[parent] / 8 (interiors; Lc = parent level)
+__global__ void unpool_add_kernel(const bf16* __restrict__ g, bf16* __restrict__ gE, int C, int P, Lvl Lc) {
+  const Lvl L{Lc.Z * 2, Lc.Y * 2, Lc.X * 2};
+  const long long total = L.cells(P) * C;
+  for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total; it += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(it % C);
+    const long long cell = it / C;
+    const int x = (int)(cell % L.X), y = (int)((cell / L.X) % L.Y);
+    const long long pz = cell / ((long long)L.X * L.Y);
+    const int z = (int)(pz % L.Z);
+    const long long p = pz / L.Z;
+    const long long pc = ((p * Lc.Z + z / 2) * Lc.Y + y / 2) * Lc.X + x / 2;
+    const long long v = padded(cell, L) * C + c;
+    gE[v] = __float2bfloat16_rn(__bfloat162float(gE[v]) + 0.125f * __bfloat162float(g[padded(pc, Lc) * C + c]));
+  }
+}
+
+// Weight gradient of one convolution: gw[co][ci][tap] += sum over interior output cells v of
+// in[v + tap offset][ci] * g[v][co].  CTA (chunk group, tap); warp pairs (16 input channels) x
+// (16 output channels) accumulate over WK-cell chunks.
 struct WGradArgs {
   const bf16* s0;
   const bf16* s1;
   const bf16* g;
   float* gw;
   int c0, c1, cin, gc, ci, co;
-  int P, Z, Y, X;
+  int P;
+  Lvl L;
   long long chunks_per_cta;
 };
 
@@ -191,7 +379,7 @@ __global__ void __launch_bounds__(CONV_THREADS) wgrad_kernel(WGradArgs a) {
   bf16* gs = xs + WK * xsn;
   const int tap = blockIdx.y;
   const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-  const long long V = (long long)a.P * a.Z * a.Y * a.X;
+  const long long V = a.L.cells(a.P);
   const long long nchunk = (V + WK - 1) / WK;
   const long long c_begin = blockIdx.x * a.chunks_per_cta;
   const long long c_end = nchunk < c_begin + a.chunks_per_cta ? nchunk : c_begin + a.chunks_per_cta;
@@ -215,20 +403,21 @@ __global__ void __launch_bounds__(CONV_THREADS) wgrad_kernel(WGradArgs a) {
       uint4 val = make_uint4(0, 0, 0, 0);
       if (v < V) {
         long long t = v;
-        const int x = (int)(t % a.X);
-        t /= a.X;
-        const int y = (int)(t % a.Y);
-        t /= a.Y;
-        const int z = (int)(t % a.Z);
-        const int p = (int)(t / a.Z);
-        val = load_in(a.s0, a.c0, a.s1, a.c1, qq, p, z + dz, y + dy, x + dx, a.Z, a.Y, a.X);
+        const int x = (int)(t % a.L.X);
+        t /= a.L.X;
+        const int y = (int)(t % a.L.Y);
+        t /= a.L.Y;
+        const int z = (int)(t % a.L.Z);
+        const int p = (int)(t / a.L.Z);
+        val = load_in(a.s0, a.c0, a.s1, a.c1, qq, p, z + dz, y + 1 + dy, x + 1 + dx, a.L, 0, a.L.Y + 2);
       }
       *reinterpret_cast<uint4*>(xs + k * xsn + qq * 8) = val;
     }
     for (int it = threadIdx.x; it < WK * qg; it += CONV_THREADS) {
       const int k = it / qg, qq = it - k * qg;
       const long long v = ch * WK + k;
-      const uint4 val = v < V ? *reinterpret_cast<const uint4*>(a.g + v * a.gc + qq * 8) : make_uint4(0, 0, 0, 0);
+      const uint4 val =
+          v < V ? *reinterpret_cast<const uint4*>(a.g + padded(v, a.L) * a.gc + qq * 8) : make_uint4(0, 0, 0, 0);
       *reinterpret_cast<uint4*>(gs + k * gsn + qq * 8) = val;
     }
     __syncthreads();
@@ -260,102 +449,26 @@ __global__ void __launch_bounds__(CONV_THREADS) wgrad_kernel(WGradArgs a) {
       for (int e = 0; e < 4; ++e) {
         const int m = mt * 16 + (lane >> 2) + 8 * (e >> 1);
         const int n = nt * 16 + h * 8 + (lane & 3) * 2 + (e & 1);
-        if (m < a.ci && n < a.co) atomicAdd(a.gw + ((long long)n * a.ci + m) * 27 + (blockIdx.y), acc[i][h][e]);
+        if (m < a.ci && n < a.co) atomicAdd(a.gw + ((long long)n * a.ci + m) * 27 + tap, acc[i][h][e]);
       }
   }
 }
 
-// bias gradient: gb[c] += sum over voxels of g[v][c]
-__global__ void bgrad_kernel(const bf16* __restrict__ g, int gc, int co, long long V, float* gb) {
+// bias gradient: gb[c] += sum over interior cells of g[v][c]
+__global__ void bgrad_kernel(const bf16* __restrict__ g, int gc, int co, int P, Lvl L, float* gb) {
   __shared__ float part[RED_THREADS];
   const int rows = RED_THREADS / gc;  // gc divides RED_THREADS (16, 32, 64)
   const int c = threadIdx.x % gc, r = threadIdx.x / gc;
+  const long long V = L.cells(P);
   float s = 0.f;
-  if (r < rows)
-    for (long long v = (long long)blockIdx.x * rows + r; v < V; v += (long long)gridDim.x * rows)
-      s += __bfloat162float(g[v * gc + c]);
+  for (long long v = (long long)blockIdx.x * rows + r; v < V; v += (long long)gridDim.x * rows)
+    s += __bfloat162float(g[padded(v, L) * gc + c]);
   part[threadIdx.x] = s;
   __syncthreads();
   if (threadIdx.x < gc) {
     float t = 0.f;
     for (int k = 0; k < rows; ++k) t += part[k * gc + threadIdx.x];
     if (threadIdx.x < co) atomicAdd(gb + threadIdx.x, t);
-  }
-}
-
-// 2x2x2 mean pooling (forward) of a [voxel][C] BF16 tensor
-__global__ void pool_kernel(const bf16* __restrict__ a, bf16* __restrict__ p, int C, int P, int Z, int Y, int X) {
-  const int Zh = Z / 2, Yh = Y / 2, Xh = X / 2, qn = C / 8;
-  const long long n = (long long)P * Zh * Yh * Xh * qn;
-  for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < n; it += (long long)gridDim.x * blockDim.x) {
-    const int q = (int)(it % qn);
-    long long t = it / qn;
-    const int x = (int)(t % Xh);
-    t /= Xh;
-    const int y = (int)(t % Yh);
-    t /= Yh;
-    const int z = (int)(t % Zh);
-    const int pp = (int)(t / Zh);
-    float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int c = 0; c < 8; ++c) {
-      const long long v = (((long long)pp * Z + 2 * z + (c >> 2)) * Y + 2 * y + ((c >> 1) & 1)) * X + 2 * x + (c & 1);
-      const uint4 u = *reinterpret_cast<const uint4*>(a + v * C + q * 8);
-      const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
-      for (int k = 0; k < 4; ++k) {
-        s[2 * k] += __bfloat162float(h[k].x);
-        s[2 * k + 1] += __bfloat162float(h[k].y);
-      }
-    }
-    uint4 o;
-    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&o);
-    for (int k = 0; k < 4; ++k) h[k] = __floats2bfloat162_rn(0.125f * s[2 * k], 0.125f * s[2 * k + 1]);
-    *reinterpret_cast<uint4*>(p + (it / qn) * C + q * 8) = o;
-  }
-}
-
-// backward through upsample + concat + ReLU of a4:
-// g4[pv][c] = (sum over the 8 children of gcat[child][C + c]) * (a4[pv][c] > 0),  c < 2C
-__global__ void g4_kernel(const bf16* __restrict__ gcat, const bf16* __restrict__ a4, bf16* __restrict__ g4, int C,
-                          int P, int Z, int Y, int X) {
-  const int Zh = Z / 2, Yh = Y / 2, Xh = X / 2, C2 = 2 * C;
-  const long long n = (long long)P * Zh * Yh * Xh * C2;
-  for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < n; it += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(it % C2);
-    long long t = it / C2;
-    const int x = (int)(t % Xh);
-    t /= Xh;
-    const int y = (int)(t % Yh);
-    t /= Yh;
-    const int z = (int)(t % Zh);
-    const int pp = (int)(t / Zh);
-    float s = 0.f;
-    for (int k = 0; k < 8; ++k) {
-      const long long v = (((long long)pp * Z + 2 * z + (k >> 2)) * Y + 2 * y + ((k >> 1) & 1)) * X + 2 * x + (k & 1);
-      s += __bfloat162float(gcat[v * 3 * C + C + c]);
-    }
-    g4[it] = __float2bfloat16_rn(__bfloat162float(a4[it]) > 0.f ? s : 0.f);
-  }
-}
-
-// backward through the skip path and the pooling into a2:
-// g2[v][c] = (gcat[v][c] + gp[parent][c] / 8) * (a2[v][c] > 0),  c < C
-__global__ void g2_kernel(const bf16* __restrict__ gcat, const bf16* __restrict__ gp, const bf16* __restrict__ a2,
-                          bf16* __restrict__ g2, int C, int P, int Z, int Y, int X) {
-  const long long n = (long long)P * Z * Y * X * C;
-  const int Zh = Z / 2, Yh = Y / 2, Xh = X / 2;
-  for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < n; it += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(it % C);
-    long long t = it / C;
-    const long long v = t;
-    const int x = (int)(t % X);
-    t /= X;
-    const int y = (int)(t % Y);
-    t /= Y;
-    const int z = (int)(t % Z);
-    const int pp = (int)(t / Z);
-    const long long pv = (((long long)pp * Zh + z / 2) * Yh + y / 2) * Xh + x / 2;
-    const float s = __bfloat162float(gcat[v * 3 * C + c]) + 0.125f * __bfloat162float(gp[pv * C + c]);
-    g2[it] = __float2bfloat16_rn(__bfloat162float(a2[it]) > 0.f ? s : 0.f);
   }
 }
 
@@ -378,9 +491,9 @@ __global__ void sumsq_kernel(const T* __restrict__ r, long long n1, double* ss) 
   if (threadIdx.x == 0) atomicAdd(ss + blockIdx.y, part[0]);
 }
 
-// x[v][0..15] = (r_P, r_Pb) / s, zero channels 2..15
+// x interior [cell][0..15] = (r_P, r_Pb) / s, zero channels 2..15 (cells sample-major)
 template <class T>
-__global__ void pack_kernel(const T* __restrict__ r, const double* __restrict__ ss, long long V1, int nb,
+__global__ void pack_kernel(const T* __restrict__ r, const double* __restrict__ ss, long long V1, int nb, Lvl L,
                             bf16* __restrict__ x) {
   const long long n = V1 * nb;
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
@@ -390,13 +503,13 @@ __global__ void pack_kernel(const T* __restrict__ r, const double* __restrict__ 
     uint4 o[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
     __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(o);
     h[0] = __floats2bfloat162_rn((float)r[b * 2 * V1 + vl] * inv, (float)r[b * 2 * V1 + V1 + vl] * inv);
-    uint4* dst = reinterpret_cast<uint4*>(x + v * 16);
+    uint4* dst = reinterpret_cast<uint4*>(x + padded(v, L) * 16);
     dst[0] = o[0];
     dst[1] = o[1];
   }
 }
 
-// e[b][c][vl] = s_b * y[v][c]
+// e[b][c][vl] = s_b * y[cell][c]
 template <class T>
 __global__ void unpack_kernel(const float* __restrict__ y, const double* __restrict__ ss, long long V1, int nb,
                               T* __restrict__ e) {
@@ -409,9 +522,10 @@ __global__ void unpack_kernel(const float* __restrict__ y, const double* __restr
   }
 }
 
-// loss = sum over entries of (y - e/s)^2 (accumulated), gy = 2 (y - e/s) / ntot (channels 0, 1 of 16)
+// loss = sum over entries of (y - e/s)^2 (accumulated); gy interior = 2 (y - e/s) / ntot in
+// channels 0, 1 of 16 (the ring of gy stays zero)
 __global__ void loss_kernel(const float* __restrict__ y, const double* __restrict__ e, const double* __restrict__ ss,
-                            long long V1, int nb, double inv_ntot, bf16* __restrict__ gy, double* loss) {
+                            long long V1, int nb, Lvl L, double inv_ntot, bf16* __restrict__ gy, double* loss) {
   __shared__ double part[RED_THREADS];
   const long long n = V1 * nb;
   double acc = 0.0;
@@ -425,7 +539,7 @@ __global__ void loss_kernel(const float* __restrict__ y, const double* __restric
     uint4 o[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
     reinterpret_cast<__nv_bfloat162*>(o)[0] =
         __floats2bfloat162_rn((float)(2.0 * d0 * inv_ntot), (float)(2.0 * d1 * inv_ntot));
-    uint4* dst = reinterpret_cast<uint4*>(gy + v * 16);
+    uint4* dst = reinterpret_cast<uint4*>(gy + padded(v, L) * 16);
     dst[0] = o[0];
     dst[1] = o[1];
   }
@@ -476,30 +590,35 @@ int gridsz(long long n, int threads) { return (int)std::max(1LL, std::min((n + t
 }  // namespace
 
 struct NetLayer {
-  int ci, co;            // logical channels
+  int ci, co;              // logical channels
   int ciK, coN, ciN, coK;  // padded: forward input (x16), forward output tile (x8), backward output, backward input
-  long long woff, boff;  // offsets of W and b in the flat parameters
+  long long woff, boff;    // offsets of W and b in the flat parameters
   bf16 *wf = nullptr, *wb = nullptr;
 };
+
+constexpr int MAX_LEVELS = 4;
 
 }  // namespace fv
 
 struct fv_net {
-  int C = 0, Ns = 0, Nr = 0, nbmax = 0;
-  int Z = 0, Y = 0, X = 0;
+  int C = 0, Ns = 0, Nr = 0, nbmax = 0, levels = 0;
+  fv::Lvl lv[fv::MAX_LEVELS + 1];
   long long V1 = 0;       // coarse cells of one sample (6 Ns^2 Nr)
   long long nparam = 0;
-  fv::NetLayer L[6];
+  int nlayer = 0;
+  fv::NetLayer L[3 * fv::MAX_LEVELS + 3];  // e0a e0b ... eLa eLb, d(L-1) .. d0, out
+  fv::Halo halo{};
   float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;  // FP32 masters, gradient, Adam moments
   long long t = 0;        // Adam step counter
   double* ss = nullptr;   // [nbmax] per-sample sum of squares
   double* loss = nullptr; // [1]
-  // activations (BF16, channels last)
-  fv::bf16 *x = nullptr, *a1 = nullptr, *a2 = nullptr, *p = nullptr, *a3 = nullptr, *a4 = nullptr, *a5 = nullptr;
-  float* y = nullptr;
-  // gradients (allocated on first training call)
-  fv::bf16 *gy = nullptr, *g5 = nullptr, *gcat = nullptr, *g4 = nullptr, *g3 = nullptr, *gp = nullptr,
-           *g2 = nullptr, *g1 = nullptr;
+  // activations (BF16, channels last, padded planes)
+  fv::bf16* x0 = nullptr;
+  fv::bf16 *A[fv::MAX_LEVELS + 1] = {}, *E[fv::MAX_LEVELS + 1] = {}, *In[fv::MAX_LEVELS + 1] = {},
+           *D[fv::MAX_LEVELS + 1] = {};
+  float* y = nullptr;     // [cell][2] of level 0
+  // gradients (allocated on the first training call)
+  fv::bf16 *gy = nullptr, *T = nullptr, *gE[fv::MAX_LEVELS + 1] = {}, *gD[fv::MAX_LEVELS + 1] = {};
   double *rb = nullptr, *eb = nullptr;  // training batch staging
   std::vector<void*> allocs;
 };
@@ -512,14 +631,21 @@ fv_status nalloc(fv_net* n, T** p, size_t count) {
   if (cudaMalloc(p, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess)
     return set_error("fv_net: device allocation failed"), FV_ENOMEM;
   n->allocs.push_back(*p);
+  if (cudaMemset(*p, 0, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess)
+    return set_error("fv_net: device memset failed"), FV_ECUDA;
   return FV_OK;
 }
+
+int eA(int l) { return 2 * l; }
+int eB(int l) { return 2 * l + 1; }
+int dL(const fv_net* n, int l) { return 2 * (n->levels + 1) + (n->levels - 1 - l); }
+int outL(const fv_net* n) { return 2 * (n->levels + 1) + n->levels; }
 
 template <int NT>
 fv_status conv_launch_nt(const ConvArgs& a, int blocks, size_t smem, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    FV_CUDA(cudaFuncSetAttribute(conv_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, HV * (96 + 8) * 2));
+    FV_CUDA(cudaFuncSetAttribute(conv_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, HV * (MAX_CIN + 8) * 2));
     attr = true;
   }
   conv_kernel<NT><<<blocks, CONV_THREADS, smem, st>>>(a);
@@ -527,48 +653,67 @@ fv_status conv_launch_nt(const ConvArgs& a, int blocks, size_t smem, cudaStream_
 }
 
 fv_status conv(const ConvArgs& a, cudaStream_t st) {
-  const int blocks = a.P * ((a.Z + BZ - 1) / BZ) * ((a.Y + BY - 1) / BY) * ((a.X + BX - 1) / BX);
+  const int blocks = a.P * ((a.L.Z + BZ - 1) / BZ) * ((a.On + BY - 1) / BY) * ((a.On + BX - 1) / BX);
   const size_t smem = (size_t)HV * (a.cin + 8) * 2;
-  if (a.cin % 16 || a.c0 % 8 || a.cin > 96 || a.coutN % 8) return set_error("fv_net: bad convolution shape"), FV_EINVAL;
+  if (a.cin % 16 || a.c0 % 8 || a.cin > MAX_CIN || a.coutN % 8) return set_error("fv_net: bad convolution shape"), FV_EINVAL;
   switch (a.coutN / 8) {
     case 1: return conv_launch_nt<1>(a, blocks, smem, st);
     case 2: return conv_launch_nt<2>(a, blocks, smem, st);
     case 4: return conv_launch_nt<4>(a, blocks, smem, st);
-    case 6: return conv_launch_nt<6>(a, blocks, smem, st);
     case 8: return conv_launch_nt<8>(a, blocks, smem, st);
-    case 12: return conv_launch_nt<12>(a, blocks, smem, st);
     default: return set_error("fv_net: unsupported output channel count"), FV_EINVAL;
   }
 }
 
-ConvArgs cargs(const bf16* s0, int c0, const bf16* s1, int c1, const bf16* w, int coutN, int cout, int P, int Z,
-               int Y, int X, int mode) {
+// forward convolution: output interior, input with its ring
+ConvArgs fwd_args(const bf16* s0, int c0, const bf16* s1, int c1, const NetLayer& ly, int P, const Lvl& L, int mode) {
   ConvArgs a{};
-  a.s0 = s0, a.c0 = c0, a.s1 = s1, a.c1 = c1, a.cin = c0 + c1, a.w = w, a.coutN = coutN, a.cout = cout;
-  a.P = P, a.Z = Z, a.Y = Y, a.X = X, a.mode = mode;
+  a.s0 = s0, a.c0 = c0, a.s1 = s1, a.c1 = c1, a.cin = c0 + c1, a.w = ly.wf, a.coutN = ly.coN, a.cout = ly.co;
+  a.P = P, a.L = L, a.o0 = 1, a.On = L.Y, a.i0 = 0, a.i1 = L.Y + 2, a.mode = mode;
   return a;
 }
 
-fv_status wgrad(const fv_net* n, const bf16* s0, int c0, const bf16* s1, int c1, const bf16* g, int gc, int li,
-                int P, int Z, int Y, int X, cudaStream_t st) {
+// backward data: gradient with respect to the whole padded input plane from an interior-only g
+ConvArgs bwd_args(const bf16* g, const NetLayer& ly, bf16* out, int P, const Lvl& L) {
+  ConvArgs a{};
+  a.s0 = g, a.c0 = ly.coK, a.s1 = nullptr, a.c1 = 0, a.cin = ly.coK, a.w = ly.wb, a.coutN = ly.ciN, a.cout = ly.ciN;
+  a.P = P, a.L = L, a.o0 = 0, a.On = L.Y + 2, a.i0 = 1, a.i1 = L.Y + 1, a.mode = EPI_RAW, a.out = out;
+  return a;
+}
+
+fv_status wgrad(fv_net* n, const bf16* s0, int c0, const bf16* s1, int c1, const bf16* g, int gc, int li, int P,
+                const Lvl& L, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    FV_CUDA(cudaFuncSetAttribute(wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, WK * (96 + 8 + 64 + 8) * 2));
+    FV_CUDA(cudaFuncSetAttribute(wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, WK * (MAX_CIN + 8 + 64 + 8) * 2));
     attr = true;
   }
   WGradArgs a{};
   a.s0 = s0, a.c0 = c0, a.s1 = s1, a.c1 = c1, a.cin = c0 + c1, a.g = g, a.gc = gc;
   a.ci = n->L[li].ci, a.co = n->L[li].co, a.gw = n->g + n->L[li].woff;
-  a.P = P, a.Z = Z, a.Y = Y, a.X = X;
+  a.P = P, a.L = L;
   if ((a.cin / 16) * (gc / 16) > 4 * WG_PAIRS) return set_error("fv_net: weight-gradient tile too large"), FV_EINVAL;
-  const long long V = (long long)P * Z * Y * X, nchunk = (V + WK - 1) / WK;
+  const long long V = L.cells(P), nchunk = (V + WK - 1) / WK;
   const long long groups = std::min<long long>(nchunk, 48);
   a.chunks_per_cta = (nchunk + groups - 1) / groups;
   const dim3 grid((unsigned)((nchunk + a.chunks_per_cta - 1) / a.chunks_per_cta), 27);
   wgrad_kernel<<<grid, CONV_THREADS, (size_t)WK * (a.cin + 8 + gc + 8) * 2, st>>>(a);
   const int rows = RED_THREADS / gc;
-  bgrad_kernel<<<gridsz(V, rows) / 4 + 1, RED_THREADS, 0, st>>>(g, gc, a.co, V, n->g + n->L[li].boff);
+  bgrad_kernel<<<gridsz(V, rows) / 4 + 1, RED_THREADS, 0, st>>>(g, gc, a.co, P, L, n->g + n->L[li].boff);
   return FV_OK;
+}
+
+void halo(fv_net* n, bf16* a, int C, int P, const Lvl& L, cudaStream_t st) {
+  halo_fill_kernel<<<gridsz((long long)P * 4 * L.Y * L.Z * (C / 8), 256), 256, 0, st>>>(a, C, P, L, n->halo);
+}
+
+void halo_adj(fv_net* n, bf16* g, int C, int P, const Lvl& L, cudaStream_t st) {
+  const long long ne = L.Y > 1 ? 4 * L.Y - 4 : 1;
+  halo_adjoint_kernel<<<gridsz((long long)P * L.Z * ne * C, 256), 256, 0, st>>>(g, C, P, L, n->halo);
+}
+
+void mask(bf16* g, const bf16* a, int C, int P, const Lvl& L, cudaStream_t st) {
+  mask_kernel<<<gridsz(L.vox(P) * C, 256), 256, 0, st>>>(g, a, C, P, L);
 }
 
 fv_status check_nb(const fv_net* n, int nb) {
@@ -579,35 +724,45 @@ fv_status check_nb(const fv_net* n, int nb) {
 // forward pass of nb samples; leaves all activations and y in the network
 template <class T>
 fv_status forward_t(fv_net* n, int nb, const T* r, cudaStream_t st) {
-  const int C = n->C, P = 6 * nb, Z = n->Z, Y = n->Y, X = n->X;
-  const long long V = n->V1 * nb;
+  const int C = n->C, P = 6 * nb, Lv = n->levels;
   FV_CUDA(cudaMemsetAsync(n->ss, 0, nb * sizeof(double), st));
   sumsq_kernel<T><<<dim3(gridsz(2 * n->V1, RED_THREADS) / 8 + 1, nb), RED_THREADS, 0, st>>>(r, 2 * n->V1, n->ss);
-  pack_kernel<T><<<gridsz(V, 256), 256, 0, st>>>(r, n->ss, n->V1, nb, n->x);
+  pack_kernel<T><<<gridsz(n->V1 * nb, 256), 256, 0, st>>>(r, n->ss, n->V1, nb, n->lv[0], n->x0);
+  halo(n, n->x0, 16, P, n->lv[0], st);
   fv_status rc;
-  ConvArgs a = cargs(n->x, 16, nullptr, 0, n->L[0].wf, C, C, P, Z, Y, X, EPI_RELU);
-  a.bias = n->w + n->L[0].boff, a.out = n->a1;
-  if ((rc = conv(a, st))) return rc;
-  a = cargs(n->a1, C, nullptr, 0, n->L[1].wf, C, C, P, Z, Y, X, EPI_RELU);
-  a.bias = n->w + n->L[1].boff, a.out = n->a2;
-  if ((rc = conv(a, st))) return rc;
-  pool_kernel<<<gridsz(V / 8 * (C / 8), 256), 256, 0, st>>>(n->a2, n->p, C, P, Z, Y, X);
-  a = cargs(n->p, C, nullptr, 0, n->L[2].wf, 2 * C, 2 * C, P, Z / 2, Y / 2, X / 2, EPI_RELU);
-  a.bias = n->w + n->L[2].boff, a.out = n->a3;
-  if ((rc = conv(a, st))) return rc;
-  a = cargs(n->a3, 2 * C, nullptr, 0, n->L[3].wf, 2 * C, 2 * C, P, Z / 2, Y / 2, X / 2, EPI_RELU);
-  a.bias = n->w + n->L[3].boff, a.out = n->a4;
-  if ((rc = conv(a, st))) return rc;
-  a = cargs(n->a2, C, n->a4, 2 * C, n->L[4].wf, C, C, P, Z, Y, X, EPI_RELU);
-  a.bias = n->w + n->L[4].boff, a.out = n->a5;
-  if ((rc = conv(a, st))) return rc;
-  a = cargs(n->a5, C, nullptr, 0, n->L[5].wf, 8, 2, P, Z, Y, X, EPI_FINAL);
-  a.bias = n->w + n->L[5].boff, a.y = n->y;
+  for (int l = 0; l <= Lv; ++l) {
+    const Lvl& L = n->lv[l];
+    const bf16* in = n->x0;
+    int cin = 16;
+    if (l > 0) {
+      pool_kernel<<<gridsz(L.cells(P) * (C / 8), 256), 256, 0, st>>>(n->E[l - 1], n->In[l], C, P, L);
+      halo(n, n->In[l], C, P, L, st);
+      in = n->In[l], cin = C;
+    }
+    ConvArgs a = fwd_args(in, cin, nullptr, 0, n->L[eA(l)], P, L, EPI_RELU);
+    a.bias = n->w + n->L[eA(l)].boff, a.out = n->A[l];
+    if ((rc = conv(a, st))) return rc;
+    halo(n, n->A[l], C, P, L, st);
+    a = fwd_args(n->A[l], C, nullptr, 0, n->L[eB(l)], P, L, EPI_RELU);
+    a.bias = n->w + n->L[eB(l)].boff, a.out = n->E[l];
+    if ((rc = conv(a, st))) return rc;
+    halo(n, n->E[l], C, P, L, st);
+  }
+  for (int l = Lv - 1; l >= 0; --l) {
+    const bf16* up = l + 1 == Lv ? n->E[Lv] : n->D[l + 1];
+    ConvArgs a = fwd_args(n->E[l], C, up, C, n->L[dL(n, l)], P, n->lv[l], EPI_RELU);
+    a.bias = n->w + n->L[dL(n, l)].boff, a.out = n->D[l];
+    if ((rc = conv(a, st))) return rc;
+    halo(n, n->D[l], C, P, n->lv[l], st);
+  }
+  const bf16* last = Lv > 0 ? n->D[0] : n->E[0];
+  ConvArgs a = fwd_args(last, C, nullptr, 0, n->L[outL(n)], P, n->lv[0], EPI_FINAL);
+  a.bias = n->w + n->L[outL(n)].boff, a.y = n->y;
   return conv(a, st);
 }
 
 fv_status pack_weights(fv_net* n, cudaStream_t st) {
-  for (int l = 0; l < 6; ++l) {
+  for (int l = 0; l < n->nlayer; ++l) {
     const NetLayer& L = n->L[l];
     const int tot = 27 * L.coN * L.ciK + (L.wb ? 27 * L.ciN * L.coK : 0);
     packw_kernel<<<gridsz(tot, 256), 256, 0, st>>>(n->w + L.woff, L.ci, L.co, L.ciK, L.coN, L.ciN, L.coK, L.wf, L.wb);
@@ -618,16 +773,16 @@ fv_status pack_weights(fv_net* n, cudaStream_t st) {
 
 fv_status ensure_train(fv_net* n) {
   if (n->gy) return FV_OK;
-  const long long V = n->V1 * n->nbmax, Vh = V / 8;
-  const int C = n->C;
+  const int C = n->C, P = 6 * n->nbmax;
   fv_status rc;
-  if ((rc = nalloc(n, &n->gy, V * 16)) || (rc = nalloc(n, &n->g5, V * C)) || (rc = nalloc(n, &n->gcat, V * 3 * C)) ||
-      (rc = nalloc(n, &n->g4, Vh * 2 * C)) || (rc = nalloc(n, &n->g3, Vh * 2 * C)) || (rc = nalloc(n, &n->gp, Vh * C)) ||
-      (rc = nalloc(n, &n->g2, V * C)) || (rc = nalloc(n, &n->g1, V * C)) ||
+  if ((rc = nalloc(n, &n->gy, n->lv[0].vox(P) * 16)) || (rc = nalloc(n, &n->T, n->lv[0].vox(P) * 2 * C)) ||
       (rc = nalloc(n, &n->rb, 2 * n->V1 * n->nbmax)) || (rc = nalloc(n, &n->eb, 2 * n->V1 * n->nbmax)))
     return rc;
-  for (int l = 1; l < 6; ++l) {
+  for (int l = 0; l <= n->levels; ++l)
+    if ((rc = nalloc(n, &n->gE[l], n->lv[l].vox(P) * C)) || (rc = nalloc(n, &n->gD[l], n->lv[l].vox(P) * C))) return rc;
+  for (int l = 0; l < n->nlayer; ++l) {
     NetLayer& L = n->L[l];
+    if (l == eA(0)) continue;  // the gradient with respect to the input is not needed
     if ((rc = nalloc(n, &L.wb, (size_t)27 * L.ciN * L.coK))) return rc;
   }
   if ((rc = pack_weights(n, 0))) return rc;
@@ -635,41 +790,57 @@ fv_status ensure_train(fv_net* n) {
   return FV_OK;
 }
 
-
 // loss (device n->loss, sum of squares) and the full parameter gradient into n->g
 fv_status loss_grad_dev(fv_net* n, int nb, const double* r, const double* e, cudaStream_t st) {
   fv_status rc;
   if ((rc = forward_t<double>(n, nb, r, st))) return rc;
-  const int C = n->C, P = 6 * nb, Z = n->Z, Y = n->Y, X = n->X, Zh = Z / 2, Yh = Y / 2, Xh = X / 2;
-  const long long V = n->V1 * nb, Vh = V / 8;
+  const int C = n->C, P = 6 * nb, Lv = n->levels;
+  const Lvl& L0 = n->lv[0];
   FV_CUDA(cudaMemsetAsync(n->loss, 0, sizeof(double), st));
   FV_CUDA(cudaMemsetAsync(n->g, 0, n->nparam * sizeof(float), st));
-  loss_kernel<<<gridsz(V, RED_THREADS) / 4 + 1, RED_THREADS, 0, st>>>(n->y, e, n->ss, n->V1, nb,
-                                                                       1.0 / (2.0 * (double)V), n->gy, n->loss);
-  // c6: gy -> g5 (mask a5), weight grad from a5
-  ConvArgs a = cargs(n->gy, 16, nullptr, 0, n->L[5].wb, C, C, P, Z, Y, X, EPI_MASK);
-  a.mask = n->a5, a.out = n->g5;
-  if ((rc = conv(a, st)) || (rc = wgrad(n, n->a5, C, nullptr, 0, n->gy, 16, 5, P, Z, Y, X, st))) return rc;
-  // c5: g5 -> gcat (raw), weight grad from [a2, up(a4)]
-  a = cargs(n->g5, C, nullptr, 0, n->L[4].wb, 3 * C, 3 * C, P, Z, Y, X, EPI_RAW);
-  a.out = n->gcat;
-  if ((rc = conv(a, st)) || (rc = wgrad(n, n->a2, C, n->a4, 2 * C, n->g5, C, 4, P, Z, Y, X, st))) return rc;
-  g4_kernel<<<gridsz(Vh * 2 * C, 256), 256, 0, st>>>(n->gcat, n->a4, n->g4, C, P, Z, Y, X);
-  // c4: g4 -> g3 (mask a3)
-  a = cargs(n->g4, 2 * C, nullptr, 0, n->L[3].wb, 2 * C, 2 * C, P, Zh, Yh, Xh, EPI_MASK);
-  a.mask = n->a3, a.out = n->g3;
-  if ((rc = conv(a, st)) || (rc = wgrad(n, n->a3, 2 * C, nullptr, 0, n->g4, 2 * C, 3, P, Zh, Yh, Xh, st))) return rc;
-  // c3: g3 -> gp (raw)
-  a = cargs(n->g3, 2 * C, nullptr, 0, n->L[2].wb, C, C, P, Zh, Yh, Xh, EPI_RAW);
-  a.out = n->gp;
-  if ((rc = conv(a, st)) || (rc = wgrad(n, n->p, C, nullptr, 0, n->g3, 2 * C, 2, P, Zh, Yh, Xh, st))) return rc;
-  g2_kernel<<<gridsz(V * C, 256), 256, 0, st>>>(n->gcat, n->gp, n->a2, n->g2, C, P, Z, Y, X);
-  // c2: g2 -> g1 (mask a1)
-  a = cargs(n->g2, C, nullptr, 0, n->L[1].wb, C, C, P, Z, Y, X, EPI_MASK);
-  a.mask = n->a1, a.out = n->g1;
-  if ((rc = conv(a, st)) || (rc = wgrad(n, n->a1, C, nullptr, 0, n->g2, C, 1, P, Z, Y, X, st))) return rc;
-  // c1: weight grad only
-  if ((rc = wgrad(n, n->x, 16, nullptr, 0, n->g1, C, 0, P, Z, Y, X, st))) return rc;
+  loss_kernel<<<gridsz(n->V1 * nb, RED_THREADS) / 4 + 1, RED_THREADS, 0, st>>>(
+      n->y, e, n->ss, n->V1, nb, L0, 1.0 / (2.0 * (double)(n->V1 * nb)), n->gy, n->loss);
+  // output convolution: gradient of its input, D_0 (or E_0 without levels)
+  const bf16* last = Lv > 0 ? n->D[0] : n->E[0];
+  if ((rc = conv(bwd_args(n->gy, n->L[outL(n)], n->T, P, L0), st)) ||
+      (rc = wgrad(n, last, C, nullptr, 0, n->gy, 16, outL(n), P, L0, st)))
+    return rc;
+  halo_adj(n, n->T, C, P, L0, st);
+  FV_CUDA(cudaMemcpyAsync(Lv > 0 ? n->gD[0] : n->gE[0], n->T, L0.vox(P) * C * sizeof(bf16), cudaMemcpyDeviceToDevice,
+                          st));
+  if (Lv > 0) mask(n->gD[0], n->D[0], C, P, L0, st);
+  // decoder, in reverse order of the forward pass
+  for (int l = 0; l < Lv; ++l) {
+    const Lvl& L = n->lv[l];
+    const bf16* up = l + 1 == Lv ? n->E[Lv] : n->D[l + 1];
+    if ((rc = conv(bwd_args(n->gD[l], n->L[dL(n, l)], n->T, P, L), st)) ||
+        (rc = wgrad(n, n->E[l], C, up, C, n->gD[l], C, dL(n, l), P, L, st)))
+      return rc;
+    halo_adj(n, n->T, 2 * C, P, L, st);
+    bf16* gnext = l + 1 == Lv ? n->gE[Lv] : n->gD[l + 1];
+    const bf16* mk = l + 1 == Lv ? nullptr : n->D[l + 1];
+    split_kernel<<<gridsz(n->lv[l + 1].cells(P) * C, 256), 256, 0, st>>>(n->T, n->gE[l], gnext, mk, C, P, n->lv[l + 1]);
+  }
+  // encoder, from the bottom level up
+  for (int l = Lv; l >= 0; --l) {
+    const Lvl& L = n->lv[l];
+    mask(n->gE[l], n->E[l], C, P, L, st);
+    if ((rc = conv(bwd_args(n->gE[l], n->L[eB(l)], n->T, P, L), st)) ||
+        (rc = wgrad(n, n->A[l], C, nullptr, 0, n->gE[l], C, eB(l), P, L, st)))
+      return rc;
+    halo_adj(n, n->T, C, P, L, st);
+    bf16* gA = n->gD[l];  // free at this point: holds the gradient of A_l's pre-activation
+    FV_CUDA(cudaMemcpyAsync(gA, n->T, L.vox(P) * C * sizeof(bf16), cudaMemcpyDeviceToDevice, st));
+    mask(gA, n->A[l], C, P, L, st);
+    const bf16* in = l > 0 ? n->In[l] : n->x0;
+    const int cin = l > 0 ? C : 16;
+    if ((rc = wgrad(n, in, cin, nullptr, 0, gA, C, eA(l), P, L, st))) return rc;
+    if (l > 0) {
+      if ((rc = conv(bwd_args(gA, n->L[eA(l)], n->T, P, L), st))) return rc;
+      halo_adj(n, n->T, C, P, L, st);
+      unpool_add_kernel<<<gridsz(n->lv[l - 1].cells(P) * C, 256), 256, 0, st>>>(n->T, n->gE[l - 1], C, P, L);
+    }
+  }
   FV_CUDA(cudaGetLastError());
   return FV_OK;
 }
@@ -718,43 +889,58 @@ extern "C" {
 
 fv_status fv_net_create(const fv_net_desc* d, fv_net** out) {
   if (!d || !out) return set_error("fv_net_create: null argument"), FV_EINVAL;
-  if ((d->C != 16 && d->C != 32) || d->Ns < 2 || d->Nr < 2 || d->Ns % 2 || d->Nr % 2 || d->max_batch < 1)
-    return set_error("fv_net_create: need C in {16, 32}, even Ns, Nr >= 2 and max_batch >= 1"), FV_EINVAL;
+  const int Lv = d->levels;
+  const int k = 1 << std::max(0, std::min(Lv, MAX_LEVELS));
+  if ((d->C != 16 && d->C != 32) || Lv < 0 || Lv > MAX_LEVELS || d->Ns < 1 || d->Nr < 1 || d->Ns % k || d->Nr % k ||
+      d->max_batch < 1)
+    return set_error("fv_net_create: need C in {16, 32}, levels in [0, 4], Ns and Nr >= 1 divisible by 2^levels, "
+                     "max_batch >= 1"),
+           FV_EINVAL;
+  // panel adjacency from the grid's own edge tables: neighbour panel, its side, orientation
+  fv_grid* g = nullptr;
+  const fv_grid_desc gd{4, 2, 0.5, 1.5};
+  fv_status rc = build_grid(&gd, &g);
+  if (rc) return rc;
   fv_net* n = new fv_net();
-  n->C = d->C, n->Ns = d->Ns, n->Nr = d->Nr, n->nbmax = d->max_batch;
-  n->Z = d->Nr, n->Y = d->Ns, n->X = d->Ns;
+  for (int e = 0; e < 24; ++e) {
+    n->halo.q[e] = g->h.pq[e], n->halo.s[e] = g->h.psq[e];
+    n->halo.flip[e] = g->h.ptmap[e * 4 + 0] != 0;
+  }
+  free_grid(g);
+  n->C = d->C, n->Ns = d->Ns, n->Nr = d->Nr, n->nbmax = d->max_batch, n->levels = Lv;
+  for (int l = 0; l <= Lv; ++l) n->lv[l] = Lvl{d->Nr >> l, d->Ns >> l, d->Ns >> l};
   n->V1 = 6LL * d->Ns * d->Ns * d->Nr;
   const int C = d->C;
-  const int io[6][2] = {{2, C}, {C, C}, {C, 2 * C}, {2 * C, 2 * C}, {3 * C, C}, {C, 2}};
+  n->nlayer = 2 * (Lv + 1) + Lv + 1;
   long long off = 0;
-  for (int l = 0; l < 6; ++l) {
+  for (int l = 0; l < n->nlayer; ++l) {
     NetLayer& L = n->L[l];
-    L.ci = io[l][0], L.co = io[l][1];
+    if (l < 2 * (Lv + 1)) L.ci = (l == 0 ? 2 : C), L.co = C;
+    else if (l < 2 * (Lv + 1) + Lv) L.ci = 2 * C, L.co = C;
+    else L.ci = C, L.co = 2;
     L.ciK = r16(L.ci), L.coN = r8(L.co), L.ciN = r8(L.ci), L.coK = r16(L.co);
     L.woff = off, off += 27LL * L.ci * L.co;
     L.boff = off, off += L.co;
   }
   n->nparam = off;
-  const long long V = n->V1 * n->nbmax, Vh = V / 8;
-  fv_status rc;
+  const int P = 6 * n->nbmax;
   if ((rc = nalloc(n, &n->w, off)) || (rc = nalloc(n, &n->g, off)) || (rc = nalloc(n, &n->m, off)) ||
       (rc = nalloc(n, &n->v, off)) || (rc = nalloc(n, &n->ss, n->nbmax)) || (rc = nalloc(n, &n->loss, 1)) ||
-      (rc = nalloc(n, &n->x, V * 16)) || (rc = nalloc(n, &n->a1, V * C)) || (rc = nalloc(n, &n->a2, V * C)) ||
-      (rc = nalloc(n, &n->p, Vh * C)) || (rc = nalloc(n, &n->a3, Vh * 2 * C)) || (rc = nalloc(n, &n->a4, Vh * 2 * C)) ||
-      (rc = nalloc(n, &n->a5, V * C)) || (rc = nalloc(n, &n->y, V * 2))) {
+      (rc = nalloc(n, &n->x0, n->lv[0].vox(P) * 16)) || (rc = nalloc(n, &n->y, n->V1 * n->nbmax * 2))) {
     fv_net_free(n);
     return rc;
   }
-  for (int l = 0; l < 6; ++l)
-    if ((rc = nalloc(n, &n->L[l].wf, (size_t)27 * n->L[l].coN * n->L[l].ciK))) {
-      fv_net_free(n);
-      return rc;
-    }
-  if (cudaMemset(n->w, 0, off * sizeof(float)) != cudaSuccess || cudaMemset(n->m, 0, off * sizeof(float)) != cudaSuccess ||
-      cudaMemset(n->v, 0, off * sizeof(float)) != cudaSuccess || pack_weights(n, 0) != FV_OK ||
-      cudaDeviceSynchronize() != cudaSuccess) {
+  for (int l = 0; l <= Lv && !rc; ++l) {
+    const long long vx = n->lv[l].vox(P) * C;
+    rc = nalloc(n, &n->A[l], vx);
+    if (!rc) rc = nalloc(n, &n->E[l], vx);
+    if (!rc && l > 0) rc = nalloc(n, &n->In[l], vx);
+    if (!rc && l < Lv) rc = nalloc(n, &n->D[l], vx);
+  }
+  for (int l = 0; l < n->nlayer && !rc; ++l) rc = nalloc(n, &n->L[l].wf, (size_t)27 * n->L[l].coN * n->L[l].ciK);
+  if (rc || pack_weights(n, 0) != FV_OK || cudaDeviceSynchronize() != cudaSuccess) {
     fv_net_free(n);
-    return set_error("fv_net_create: initialisation failed"), FV_ECUDA;
+    return rc ? rc : (set_error("fv_net_create: initialisation failed"), FV_ECUDA);
   }
   *out = n;
   return FV_OK;

@@ -53,7 +53,8 @@ class fv_solve_stats(ctypes.Structure):
 
 
 class fv_net_desc(ctypes.Structure):
-    _fields_ = [('C', ctypes.c_int), ('Ns', ctypes.c_int), ('Nr', ctypes.c_int), ('max_batch', ctypes.c_int)]
+    _fields_ = [('C', ctypes.c_int), ('levels', ctypes.c_int), ('Ns', ctypes.c_int), ('Nr', ctypes.c_int),
+                ('max_batch', ctypes.c_int)]
 
 
 class fv_adam_opts(ctypes.Structure):
@@ -276,9 +277,9 @@ def _fptr(a, n):
     return ctypes.c_void_p(a.ctypes.data)
 
 
-def fv_net_create(C, Ns, Nr, max_batch=1):
+def fv_net_create(C, Ns, Nr, levels=3, max_batch=1):
     h = ctypes.c_void_p()
-    _check(lib.fv_net_create(ctypes.byref(fv_net_desc(C, Ns, Nr, max_batch)), ctypes.byref(h)))
+    _check(lib.fv_net_create(ctypes.byref(fv_net_desc(C, levels, Ns, Nr, max_batch)), ctypes.byref(h)))
     return h
 
 

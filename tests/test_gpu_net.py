@@ -36,73 +36,73 @@ def bf16(a):
     return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
-def _params(C, seed):
-    p = unet.init(C, normals(seed, 27 * 20 * C * C + 100))
+def _params(C, levels, seed):
+    p = unet.init(C, levels, normals(seed, 27 * C * C * (3 * levels + 3) * 2))
     for i, k in enumerate(p):
         p[k] = (p[k][0], 0.05 * normals(seed + 100 + i, p[k][1].size))
     flat = unet.flatten(p).astype(np.float32)
-    ref = unet.unflatten(flat.astype(np.float64), C)
+    ref = unet.unflatten(flat.astype(np.float64), C, levels)
     ref = {k: (bf16(w), b) for k, (w, b) in ref.items()}  # the GPU multiplies BF16 weights
     return flat, ref
 
 
 def _to_oracle(v, Ns, Nr):
-    return v.reshape(2, 6, Nr, Ns, Ns).transpose(1, 0, 2, 3, 4)
+    """Rows of samples laid out [c][p][k][j][i] -> oracle panels [6 nb][c][k][j][i]."""
+    v = np.asarray(v).reshape(-1, 2, 6, Nr, Ns, Ns)
+    return v.transpose(0, 2, 1, 3, 4, 5).reshape(-1, 2, Nr, Ns, Ns)
 
 
-def _from_oracle(a):
-    return a.transpose(1, 0, 2, 3, 4).ravel()
+def _from_oracle(a, nb):
+    return a.reshape(nb, 6, 2, *a.shape[2:]).transpose(0, 2, 1, 3, 4, 5).reshape(nb, -1)
 
 
 def _rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
-# ragged bricks (12 = 8 + 4, 10 = 4 + 4 + 2) and an odd pooled depth (5)
-NS, NR, C = 12, 10, 16
+# (C, Ns, Nr, levels): ragged bricks in every pass (padded planes 10 = 8 + 2 and 6 = 4 + 2,
+# radial 2 and 1 below a 4-deep brick) and a one-cell panel at the bottom level
+CASES = [(16, 8, 8, 3), (32, 8, 4, 2)]
 
 
-def test_forward_matches_oracle(fv):
-    flat, ref = _params(C, 11)
-    net = fv.fv_net_create(C, NS, NR, max_batch=3)
+@pytest.mark.parametrize('C,Ns,Nr,levels', CASES)
+def test_forward_matches_oracle(fv, C, Ns, Nr, levels):
+    flat, ref = _params(C, levels, 11)
+    net = fv.fv_net_create(C, Ns, Nr, levels=levels, max_batch=3)
     fv.fv_net_set_params(net, flat)
-    n1 = 2 * 6 * NS * NS * NR
-    r = multiscale_fields(NS, NR, 3, seed=3)
+    n1 = 2 * 6 * Ns * Ns * Nr
+    r = multiscale_fields(Ns, Nr, 3, seed=3)
     r[1] *= 1e3       # each sample is normalised by its own norm
     r[2] = 0.0        # zero input -> zero output
     e = fv.fv_net_forward(net, 3, _dev(r.ravel()), torch.empty(3 * n1, dtype=torch.float64, device='cuda'))
     e = e.cpu().numpy().reshape(3, n1)
+    want = _from_oracle(unet.forward(ref, _to_oracle(r[:2], Ns, Nr), levels), 2)
     for s in range(2):
-        want = _from_oracle(unet.forward(ref, _to_oracle(r[s], NS, NR)))
-        assert _rel(e[s], want) < 2e-2, (s, _rel(e[s], want))
+        assert _rel(e[s], want[s]) < 2e-2, (s, _rel(e[s], want[s]))
     assert np.all(e[2] == 0.0)
     fv.fv_net_free(net)
 
 
-def test_gradients_match_oracle(fv):
-    flat, ref = _params(C, 12)
-    net = fv.fv_net_create(C, NS, NR, max_batch=2)
+@pytest.mark.parametrize('C,Ns,Nr,levels', CASES)
+def test_gradients_match_oracle(fv, C, Ns, Nr, levels):
+    flat, ref = _params(C, levels, 12)
+    net = fv.fv_net_create(C, Ns, Nr, levels=levels, max_batch=2)
     fv.fv_net_set_params(net, flat)
-    r = multiscale_fields(NS, NR, 2, seed=5)
-    e = multiscale_fields(NS, NR, 2, seed=6) * np.array([[0.3], [2.0]])
+    r = multiscale_fields(Ns, Nr, 2, seed=5)
+    e = multiscale_fields(Ns, Nr, 2, seed=6) * np.array([[0.3], [2.0]])
     loss, g = fv.fv_net_loss_grad(net, 2, _dev(r.ravel()), _dev(e.ravel()))
-    Ls, Gs = [], []
-    for s in range(2):
-        L, gr = unet.loss_and_grads(ref, _to_oracle(r[s], NS, NR), _to_oracle(e[s], NS, NR))
-        Ls.append(L)
-        Gs.append(unet.flatten(gr))
-    assert abs(loss - np.mean(Ls)) < 1e-2 * np.mean(Ls)
-    want = unet.unflatten(0.5 * (Gs[0] + Gs[1]), C)
-    got = unet.unflatten(g.astype(np.float64), C)
-    for k in want:
-        assert _rel(got[k][0], want[k][0]) < 5e-2, (k, 'W', _rel(got[k][0], want[k][0]))
-        assert _rel(got[k][1], want[k][1]) < 5e-2, (k, 'b', _rel(got[k][1], want[k][1]))
+    L, gr = unet.loss_and_grads(ref, _to_oracle(r, Ns, Nr), _to_oracle(e, Ns, Nr), levels)
+    assert abs(loss - L) < 1e-2 * L
+    got = unet.unflatten(g.astype(np.float64), C, levels)
+    for k in gr:
+        assert _rel(got[k][0], gr[k][0]) < 5e-2, (k, 'W', _rel(got[k][0], gr[k][0]))
+        assert _rel(got[k][1], gr[k][1]) < 5e-2, (k, 'b', _rel(got[k][1], gr[k][1]))
     fv.fv_net_free(net)
 
 
 def test_adam_matches_oracle(fv):
-    flat, _ = _params(16, 13)
-    net = fv.fv_net_create(16, 8, 8)
+    flat, _ = _params(16, 2, 13)
+    net = fv.fv_net_create(16, 8, 8, levels=2)
     fv.fv_net_set_params(net, flat)
     w, m, v = flat.astype(np.float64), np.zeros(flat.size), np.zeros(flat.size)
     for t in range(1, 4):
@@ -115,8 +115,8 @@ def test_adam_matches_oracle(fv):
 
 
 def test_training_reduces_the_loss(fv):
-    flat, _ = _params(16, 14)
-    net = fv.fv_net_create(16, 8, 8, max_batch=4)
+    flat, _ = _params(16, 2, 14)
+    net = fv.fv_net_create(16, 8, 8, levels=2, max_batch=4)
     fv.fv_net_set_params(net, flat)
     R = _dev(multiscale_fields(8, 8, 16, seed=7))
     losses = fv.fv_net_train(net, R, R.clone(), epochs=25, batch=4, seed=1, lr=3e-3)
@@ -141,8 +141,8 @@ def ppbe(fv):
     for i in range(0, 48, 16):
         st = fv.fv_gmres_solve_batch(c, Rc[i:i + 16].contiguous(), Ec[i:i + 16], rtol=1e-6)
         assert all(t.converged for t in st)
-    net = fv.fv_net_create(16, Ns // 2, Nr // 2, max_batch=8)
-    fv.fv_net_set_params(net, _params(16, 15)[0])
+    net = fv.fv_net_create(16, Ns // 2, Nr // 2, levels=3, max_batch=8)
+    fv.fv_net_set_params(net, _params(16, 3, 15)[0])
     losses = fv.fv_net_train(net, Rc, Ec, epochs=40, batch=8, seed=2, lr=2e-3)
     yield fv, s, net, n, losses
     fv.fv_pc_set_learned(s, None)
@@ -183,7 +183,7 @@ def test_learned_preconditioner_converges_and_reports_gain(fv, ppbe):
 def test_plain_fallback_finishes_a_failed_learned_solve(fv, ppbe, bad):
     fv, s, _, n, _ = ppbe
     plain, _ = _solve(fv, s, n, 32)
-    net = fv.fv_net_create(16, 8, 8)
+    net = fv.fv_net_create(16, 8, 8, levels=3)
     k = fv.fv_net_param_count(net)
     fv.fv_net_set_params(net, np.zeros(k, np.float32) if bad == 'zero' else np.full(k, np.nan, np.float32))
     fv.fv_pc_set_learned(s, net, coarse_its=0)
@@ -199,8 +199,8 @@ def test_learned_mixed_precision_inner_solve(fv):
     g = fv.fv_build_grid(Ns, Nr)
     s = fv.fv_assemble_system(g, 1, **PH, p=(2, 2, 2), overlap=1, levels=2, overlap_coarse=1,
                               precision=fv.FV_PREC_FP32, inner_maxit=8, coarse_maxit=8)
-    net = fv.fv_net_create(16, 8, 8)
-    fv.fv_net_set_params(net, _params(16, 16)[0])
+    net = fv.fv_net_create(16, 8, 8, levels=3)
+    fv.fv_net_set_params(net, _params(16, 3, 16)[0])
     n = fv.fv_system_size(s)
     for its in (0, 3):
         fv.fv_pc_set_learned(s, net, coarse_its=its)
