@@ -13,7 +13,7 @@
  * Before every 3x3x3 convolution each panel is padded by one cell in (eta, xi)
  * with the neighbouring panel's cells across each edge (the cell sharing the
  * edge face; zero at the ring corners) and by zeros radially.
- *   s = ||r_c||_2 over the whole coarse vector (N(a r) = a N(r))
+ *   s = RMS of r_c over the whole coarse vector (N(a r) = a N(r) for a > 0)
  *   level l = 0..L: input r_c/s (l = 0) or the 2x2x2 mean pooling of E_{l-1};
  *                   A_l = relu(conv(input)), E_l = relu(conv(A_l))
  *   D_L = E_L; l = L-1..0: D_l = relu(conv([E_l, upsample(D_{l+1})]))
@@ -64,7 +64,7 @@ fv_status fv_net_get_params(const fv_net* net, float* params);
 fv_status fv_net_forward(fv_net* net, int nb, const double* r, double* e, void* stream);
 
 /* Mean squared error L = mean over all nb * 2 * 6 Ns^2 Nr entries of
- * (N(r)/s - e/s)^2 (s per sample) and its gradient with respect to the
+ * (N(r)/s - e/s)^2 (s the RMS of each sample's r) and its gradient with respect to the
  * parameters.  loss: host, may be NULL; grads: HOST FP32 array of
  * fv_net_param_count values, may be NULL.  Synchronizes the stream. */
 fv_status fv_net_loss_grad(fv_net* net, int nb, const double* r, const double* e, double* loss, float* grads,

@@ -13,7 +13,7 @@ a valid cross-correlation in (eta, xi) and a zero-padded one radially, plus a
 bias.  Weights W[co][ci][dz][dy][dx], bias b[co].
 
 Network with `levels` = L poolings and width C:
-  s = ||r_c||_2;  a = r_c / s
+  s = RMS of r_c (per sample of 6 panels);  a = r_c / s
   level l = 0..L:  (l > 0: a = 2x2x2 mean pooling of E_{l-1})
                    A_l = relu(conv_{e l a}(pad a));  E_l = relu(conv_{e l b}(pad A_l))
   D_L = E_L;  level l = L-1..0:  D_l = relu(conv_{d l}(pad [E_l, up(D_{l+1})]))
@@ -186,7 +186,7 @@ def _down_sum(g):
 def forward(params, r, levels, keep=False):
     """e_c = N(r_c) per sample of 6 panels (r: [6 nb][2][Z][n][n]); keep=True also returns the cache."""
     P = r.shape[0]
-    s = np.sqrt((r.reshape(P // 6, -1) ** 2).sum(axis=1))             # per sample
+    s = np.sqrt((r.reshape(P // 6, -1) ** 2).mean(axis=1))            # RMS per sample
     sp = np.repeat(s, 6)[:, None, None, None, None]
     x = np.where(sp > 0, r / np.where(sp > 0, sp, 1.0), 0.0)
     c = {'s': sp, 'in': [], 'A': [], 'E': [], 'cat': [], 'D': {}}

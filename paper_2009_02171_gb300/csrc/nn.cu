@@ -491,7 +491,8 @@ __global__ void sumsq_kernel(const T* __restrict__ r, long long n1, double* ss) 
   if (threadIdx.x == 0) atomicAdd(ss + blockIdx.y, part[0]);
 }
 
-// x interior [cell][0..15] = (r_P, r_Pb) / s, zero channels 2..15 (cells sample-major)
+// x interior [cell][0..15] = (r_P, r_Pb) / s, zero channels 2..15 (cells sample-major), with
+// s the RMS of the sample (ss = its sum of squares over 2 V1 values): O(1) activations
 template <class T>
 __global__ void pack_kernel(const T* __restrict__ r, const double* __restrict__ ss, long long V1, int nb, Lvl L,
                             bf16* __restrict__ x) {
@@ -499,7 +500,7 @@ __global__ void pack_kernel(const T* __restrict__ r, const double* __restrict__ 
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
     const long long b = v / V1, vl = v - b * V1;
     const double s2 = ss[b];
-    const float inv = s2 > 0.0 ? (float)(1.0 / sqrt(s2)) : 0.f;
+    const float inv = s2 > 0.0 ? (float)sqrt(2.0 * (double)V1 / s2) : 0.f;
     uint4 o[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
     __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(o);
     h[0] = __floats2bfloat162_rn((float)r[b * 2 * V1 + vl] * inv, (float)r[b * 2 * V1 + V1 + vl] * inv);
@@ -509,14 +510,14 @@ __global__ void pack_kernel(const T* __restrict__ r, const double* __restrict__ 
   }
 }
 
-// e[b][c][vl] = s_b * y[cell][c]
+// e[b][c][vl] = s_b * y[cell][c] (s_b the RMS of sample b)
 template <class T>
 __global__ void unpack_kernel(const float* __restrict__ y, const double* __restrict__ ss, long long V1, int nb,
                               T* __restrict__ e) {
   const long long n = V1 * nb;
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
     const long long b = v / V1, vl = v - b * V1;
-    const double s = sqrt(ss[b]);
+    const double s = sqrt(ss[b] / (2.0 * (double)V1));
     e[b * 2 * V1 + vl] = (T)(s * (double)y[2 * v]);
     e[b * 2 * V1 + V1 + vl] = (T)(s * (double)y[2 * v + 1]);
   }
@@ -532,7 +533,7 @@ __global__ void loss_kernel(const float* __restrict__ y, const double* __restric
   for (long long v = blockIdx.x * (long long)RED_THREADS + threadIdx.x; v < n; v += (long long)gridDim.x * RED_THREADS) {
     const long long b = v / V1, vl = v - b * V1;
     const double s2 = ss[b];
-    const double inv = s2 > 0.0 ? 1.0 / sqrt(s2) : 0.0;
+    const double inv = s2 > 0.0 ? sqrt(2.0 * (double)V1 / s2) : 0.0;
     const double d0 = (double)y[2 * v] - e[b * 2 * V1 + vl] * inv;
     const double d1 = (double)y[2 * v + 1] - e[b * 2 * V1 + V1 + vl] * inv;
     acc += d0 * d0 + d1 * d1;
