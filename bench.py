@@ -6,9 +6,13 @@ list): 6 x 64^2 x 64 cells (1,572,864), E = 1e-3, Pm = 5, Ra = 100, Pr = 1,
 dt = 1e-4, seeded synthetic fields (seed 1 + rank).  One step = the paper's
 predictor-corrector time step (Sec. 3.1): nonlinear terms, VTBE solve
 (FGMRES(30), one-level RAS, 96 subdomains = 6 x (2 x 2 x 4), overlap 2),
-PPBE solve (FGMRES(30), hybrid two-level RAS, coarse 32^3 x 6 with overlap 1
-and inner GMRES to 0.1), projection; both systems to a 1e-8 relative
-residual, FP64 throughout.
+PPBE solve (FGMRES(30), hybrid two-level RAS, coarse 32^3 x 6 with overlap 1),
+projection; both systems to a 1e-8 relative FP64 residual.  Three arms, all
+timed on the same steps: fp64 (FP64 throughout, coarse inner GMRES to 0.1),
+mixed (FP32 inner FGMRES in FP64 outer FGMRES, 10 coarse iterations) and the
+headline learned (mixed, with the coarse solve replaced by a BF16 cubed-sphere
+U-Net followed by 6 coarse iterations; its training on seeded pairs from the
+plain coarse solver is setup, reported in `learned`).
 
 value       -- ms per time step (max over ranks; one independent shell per GPU)
 e2e         -- the same through the C ABI with the state copied host->device
@@ -32,7 +36,11 @@ CFG = dict(Ns=64, Nr=64, p=(2, 2, 4), overlap=2, overlap_coarse=1, levels=2, E=1
            dt=1e-4, rtol=1e-8, restart=30, seed=1, vtbe_inner=4, ppbe_inner=8, coarse_its=10)
 WORKLOAD = ('shell 6x64^2x64 (1.57M cells), time step: VTBE one-level RAS + PPBE two-level RAS, '
             '96 subdomains overlap 2, FGMRES(30) to 1e-8 relative FP64 residual; mixed precision = FP32 inner '
-            'FGMRES (operator, ILU(0) sweeps, coarse level) inside FP64 outer FGMRES')
+            'FGMRES (operator, ILU(0) sweeps, coarse level) inside FP64 outer FGMRES; learned = mixed with the '
+            'PPBE coarse solve replaced by a BF16 cubed-sphere U-Net followed by 6 coarse FGMRES iterations')
+# learned coarse correction of the headline arm: network and training (seeded synthetic pairs from the plain
+# coarse solver; data generation and training are counted in setup_s)
+LEARN = dict(C=16, levels=3, pairs=256, epochs=40, batch=8, lr=3e-4, coarse_its=6)
 METRIC = 'wall time per time step at 1e-8 residual'
 # oracle sample: the same step on 6 x 32^2 x 32 (1/8 of the cells), scaled by the cell ratio
 ORACLE_NS = 32
@@ -45,8 +53,9 @@ def parse():
     ap.add_argument('--warmup', type=int, default=3)
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
     ap.add_argument('--no-cpu-baseline', action='store_true')
-    ap.add_argument('--precision', default='mixed', choices=['mixed', 'fp64'],
-                    help='headline arm; the other one is timed beside it with the same steps')
+    ap.add_argument('--precision', default='learned', choices=['learned', 'mixed', 'fp64'],
+                    help='headline arm (learned = mixed precision with the learned coarse correction); the other '
+                         'arms are timed beside it with the same steps')
     ap.add_argument('--single', action='store_true', help='time the headline arm only (profiling runs)')
     ap.add_argument('--ns', type=int, default=0, help='override Ns = Nr (small profiling cases)')
     ap.add_argument('--workload', default='step', choices=['step', 'batch'],
@@ -234,25 +243,37 @@ def main():
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
-    def build(mixed):
+    def build(mode):
+        """(handles, setup seconds, learned-correction info) for arm mode in {fp64, mixed, learned}."""
         t = time.perf_counter()
+        mixed = mode != 'fp64'
         g = fv.fv_build_grid(c['Ns'], c['Nr'])
         mv = dict(precision=fv.FV_PREC_FP32, inner_maxit=c['vtbe_inner']) if mixed else {}
         mpp = dict(precision=fv.FV_PREC_FP32, inner_maxit=c['ppbe_inner'], coarse_maxit=c['coarse_its']) if mixed else {}
         V = fv.fv_assemble_system(g, fv.FV_VTBE, **ph, p=c['p'], overlap=c['overlap'], levels=1, **mv)
         P = fv.fv_assemble_system(g, fv.FV_PPBE, **ph, p=c['p'], overlap=c['overlap'], levels=c['levels'],
                                   overlap_coarse=c['overlap_coarse'], **mpp)
+        net, info = None, None
+        if mode == 'learned':
+            from paper_2009_02171_gb300.learned import train_learned_correction
+            L = LEARN
+            net, info = train_learned_correction(P, c['Ns'], c['Nr'], C=L['C'], levels=L['levels'],
+                                                 npairs=L['pairs'], epochs=L['epochs'], batch=L['batch'],
+                                                 lr=L['lr'], coarse_its=L['coarse_its'])
         st = fv.fv_state_create(g, torch.tensor(host, device='cuda'), **ph)
         torch.cuda.synchronize()
-        return (g, V, P, st), time.perf_counter() - t
+        return (g, V, P, st, net), time.perf_counter() - t, info
 
     def free(h):
-        g, V, P, st = h
+        g, V, P, st, net = h
+        if net is not None:
+            fv.fv_pc_set_learned(P, None)
+            fv.fv_net_free(net)
         for x, f in ((st, fv.fv_free_state), (V, fv.fv_free_system), (P, fv.fv_free_system), (g, fv.fv_free_grid)):
             f(x)
 
     def timed(h, steps, warmup, profile):
-        g, V, P, st = h
+        g, V, P, st, _ = h
         for _ in range(warmup):
             fv.fv_time_step(st, V, P, 1, **opts)
         iters = []
@@ -277,18 +298,22 @@ def main():
             ms = float(t.item())
         return ms, iters, clk.summary()
 
-    mixed = args.precision == 'mixed'
-    # the other arm first (same steps), then the headline arm with kernel timing
-    if args.single:
-        ms_other, it_other, t_other = float('nan'), [], 0.0
-    else:
-        other, t_other = build(not mixed)
-        ms_other, it_other, _ = timed(other, args.steps, args.warmup, False)
-        free(other)
-    h, t_setup = build(mixed)
-    g, V, P, st = h
+    head = args.precision
+    others = {}
+    # the other arms first (same steps), then the headline arm, then its kernel breakdown:
+    # the same number of steps again with CUDA-event timing on (eager launches)
+    if not args.single:
+        for mode in [m for m in ('fp64', 'mixed', 'learned') if m != head]:
+            other, t_other, info_o = build(mode)
+            ms_o, it_o, _ = timed(other, args.steps, args.warmup, False)
+            others[mode] = {'ms_per_step': round(ms_o, 3), 'iterations_vtbe_ppbe': [(i[0], i[1]) for i in it_o],
+                            'setup_s': round(t_other, 2)}
+            if info_o:
+                others[mode]['learned'] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in info_o.items()}
+            free(other)
+    h, t_setup, info = build(head)
+    g, V, P, st, net = h
     ms, iters, clocks = timed(h, args.steps, args.warmup, False)
-    # kernel breakdown: the same number of steps again with CUDA-event timing on (eager launches)
     ms_prof, _, _ = timed(h, args.steps, 0, True)
     kern = {}
     for cat in range(fv.K_COUNT):
@@ -352,11 +377,13 @@ def main():
         print(json.dumps({
             'metric': METRIC, 'value': round(ms, 3), 'unit': 'ms/step', 'n_gpus': ws, 'steps': args.steps,
             'warmup': args.warmup, 'ms_per_step': round(ms, 3), 'higher_is_better': False, 'scaling': 'weak',
-            'vs_baseline': None, 'dtype': 'f32 inner / f64 outer' if mixed else 'f64', 'data': 'synthetic',
-            'precision': args.precision,
-            ('fp64' if mixed else 'mixed'): {'ms_per_step': round(ms_other, 3),
-                                             'iterations_vtbe_ppbe': [(i[0], i[1]) for i in it_other],
-                                             'setup_s': round(t_other, 2)},
+            'vs_baseline': None,
+            'dtype': {'fp64': 'f64', 'mixed': 'f32 inner / f64 outer',
+                      'learned': 'f32 inner / f64 outer, bf16 network'}[head],
+            'data': 'synthetic',
+            'precision': head,
+            'arms': others,
+            'learned': ({k: (round(v, 4) if isinstance(v, float) else v) for k, v in info.items()} if info else None),
             'config': {'workload': WORKLOAD if not args.ns else WORKLOAD.replace('64', str(args.ns)),
                        'cells': 6 * c['Ns'] ** 2 * c['Nr'], 'subdomains': 6 * 16,
                        'overlap': c['overlap'], 'ppbe_levels': c['levels'], 'rtol': c['rtol'],

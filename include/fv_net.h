@@ -58,6 +58,11 @@ fv_status fv_net_param_count(const fv_net* net, long long* n);
 /* params: HOST FP32 array of fv_net_param_count values, layout above. */
 fv_status fv_net_set_params(fv_net* net, const float* params);
 fv_status fv_net_get_params(const fv_net* net, float* params);
+/* He initialisation: every weight of a layer with ci input channels drawn from
+ * N(0, 2 / (27 ci)) (Box-Muller on 53-bit uniforms of the splitmix64 stream
+ * started at `seed`, layer by layer in parameter order), biases zero; resets
+ * Adam's state like fv_net_set_params. */
+fv_status fv_net_init(fv_net* net, unsigned long long seed);
 
 /* e = N(r) for nb <= max_batch samples.  r, e: device FP64 (layout above);
  * a sample with r = 0 gives e = 0. */

@@ -972,6 +972,32 @@ fv_status fv_net_set_params(fv_net* n, const float* params) {
   return FV_OK;
 }
 
+fv_status fv_net_init(fv_net* n, unsigned long long seed) {
+  if (!n) return set_error("fv_net_init: null network"), FV_EINVAL;
+  // He initialisation: W ~ N(0, 2 / (27 ci)), b = 0.  Normals by Box-Muller from
+  // 53-bit uniforms in (0, 1) of the splitmix64 stream started at `seed`.
+  std::vector<float> w(n->nparam, 0.f);
+  unsigned long long state = seed;
+  auto next = [&state]() {
+    unsigned long long z = (state += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+  };
+  auto uniform = [&]() { return ((double)(next() >> 11) + 0.5) / 9007199254740992.0; };
+  for (int l = 0; l < n->nlayer; ++l) {
+    const NetLayer& L = n->L[l];
+    const double sd = std::sqrt(2.0 / (27.0 * L.ci));
+    const long long cnt = 27LL * L.ci * L.co;
+    for (long long i = 0; i < cnt; i += 2) {
+      const double r = std::sqrt(-2.0 * std::log(uniform())), t = 2.0 * M_PI * uniform();
+      w[L.woff + i] = (float)(sd * r * std::cos(t));
+      if (i + 1 < cnt) w[L.woff + i + 1] = (float)(sd * r * std::sin(t));
+    }
+  }
+  return fv_net_set_params(n, w.data());
+}
+
 fv_status fv_net_get_params(const fv_net* n, float* params) {
   if (!n || !params) return set_error("fv_net_get_params: null argument"), FV_EINVAL;
   FV_CUDA(cudaDeviceSynchronize());

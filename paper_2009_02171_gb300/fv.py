@@ -94,6 +94,7 @@ SIGNATURES = {
     'fv_net_param_count': [_VP, _P(ctypes.c_longlong)],
     'fv_net_set_params': [_VP, _VP],
     'fv_net_get_params': [_VP, _VP],
+    'fv_net_init': [_VP, ctypes.c_ulonglong],
     'fv_net_forward': [_VP, ctypes.c_int, _DP, _DP, _VP],
     'fv_net_loss_grad': [_VP, ctypes.c_int, _DP, _DP, _P(ctypes.c_double), _VP, _VP],
     'fv_net_adam_step': [_VP, _VP, _P(fv_adam_opts)],
@@ -295,6 +296,10 @@ def fv_net_param_count(net):
 
 def fv_net_set_params(net, params):
     _check(lib.fv_net_set_params(net, _fptr(params, fv_net_param_count(net))))
+
+
+def fv_net_init(net, seed=0):
+    _check(lib.fv_net_init(net, seed))
 
 
 def fv_net_get_params(net):

@@ -106,6 +106,19 @@ def test_gradients_match_oracle(fv, C, Ns, Nr, levels):
     fv.fv_net_free(net)
 
 
+def test_he_initialisation(fv):
+    net = fv.fv_net_create(32, 8, 8, levels=3)
+    fv.fv_net_init(net, 7)
+    w = fv.fv_net_get_params(net).astype(np.float64)
+    fv.fv_net_init(net, 7)
+    assert np.array_equal(fv.fv_net_get_params(net), w.astype(np.float32))
+    for k, (W, b) in unet.unflatten(w, 32, 3).items():
+        ci = W.shape[1]
+        assert np.all(b == 0)
+        assert abs(W.std() / np.sqrt(2.0 / (27 * ci)) - 1) < 0.1 and abs(W.mean()) < 0.1 * W.std(), k
+    fv.fv_net_free(net)
+
+
 def test_adam_matches_oracle(fv):
     flat, _ = _params(16, 2, 13)
     net = fv.fv_net_create(16, 8, 8, levels=2)
