@@ -10,8 +10,8 @@
 // GEMM (M = voxels, N = output channels, K = 27 taps x input channels) on the
 // tensor cores (mma.sync m16n8k16, BF16 x BF16 -> FP32): one CTA computes a
 // 4 x 4 x 8 brick of output voxels from a (6 x 6 x 10)-voxel halo of its input
-// staged in shared memory (channel stride padded by 8 so ldmatrix rows fall in
-// distinct banks).  The backward data pass is the same kernel with flipped,
+// and all 27 taps' weights, both staged in shared memory (row stride padded by 8
+// channels so ldmatrix rows fall in distinct banks).  The backward data pass is the same kernel with flipped,
 // transposed weights over the whole padded plane (the gradient of the ring
 // included), followed by halo_adjoint (ring gradients added to the neighbour
 // cells they were copied from); the weight gradient is a GEMM over voxels
@@ -116,6 +116,13 @@ __global__ void __launch_bounds__(CONV_THREADS) conv_kernel(ConvArgs a) {
     const uint4 v = load_in(a.s0, a.c0, a.s1, a.c1, q, p, z0 - 1 + hz, y0 - 1 + hy, x0 - 1 + hx, a.L, a.i0, a.i1);
     *reinterpret_cast<uint4*>(hs + hv * cs + q * 8) = v;
   }
+  // all 27 taps' weights, rows (tap, n) of cin values, staged once: the tap loop then reads the B
+  // fragments from shared memory instead of waiting on global loads
+  bf16* ws = hs + HV * cs;
+  for (int it = threadIdx.x; it < 27 * a.coutN * qn; it += CONV_THREADS) {
+    const int row = it / qn, q = it - row * qn;
+    *reinterpret_cast<uint4*>(ws + row * cs + q * 8) = __ldg(reinterpret_cast<const uint4*>(a.w + (size_t)row * a.cin + q * 8));
+  }
   __syncthreads();
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -133,22 +140,26 @@ __global__ void __launch_bounds__(CONV_THREADS) conv_kernel(ConvArgs a) {
   int hv0[2];
 #pragma unroll
   for (int mt = 0; mt < 2; ++mt) hv0[mt] = (warp * HY + 2 * mt + (r >> 3)) * HX + (r & 7);
-  const int nq = lane >> 2, kq = (lane & 3) * 2;
+  // B rows: lanes 0-7 / 8-15 give n-tile 2j's rows at k halves 0 / 1, lanes 16-31 n-tile 2j + 1's
+  const uint32_t wbase = sbase + (uint32_t)(HV * cs * 2);
+  const int brow = ((lane >> 4) * 8 + (lane & 7)), bk = ((lane >> 3) & 1) * 8;
   for (int tap = 0; tap < 27; ++tap) {
     const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
     const int toff = (dz * HY + dy) * HX + dx;
-    const bf16* wt = a.w + (size_t)tap * a.coutN * a.cin + (size_t)nq * a.cin + kq;
     for (int kc = 0; kc < a.cin; kc += 16) {
       uint32_t af[2][4];
 #pragma unroll
       for (int mt = 0; mt < 2; ++mt) ldsm4(sbase + (uint32_t)(((hv0[mt] + toff) * cs + kc + kh * 8) * 2), af[mt]);
 #pragma unroll
-      for (int nt = 0; nt < NT; ++nt) {
-        const bf16* wp = wt + (size_t)nt * 8 * a.cin + kc;
-        const uint32_t b0 = __ldg(reinterpret_cast<const unsigned int*>(wp));
-        const uint32_t b1 = __ldg(reinterpret_cast<const unsigned int*>(wp + 8));
+      for (int np = 0; np < (NT + 1) / 2; ++np) {
+        uint32_t bf[4];
+        const int row = tap * a.coutN + np * 16 + (NT == 1 ? (lane & 7) : brow);
+        ldsm4(wbase + (uint32_t)((row * cs + kc + bk) * 2), bf);
 #pragma unroll
-        for (int mt = 0; mt < 2; ++mt) mma16816(acc[mt][nt], af[mt], b0, b1);
+        for (int mt = 0; mt < 2; ++mt) {
+          mma16816(acc[mt][2 * np], af[mt], bf[0], bf[1]);
+          if (2 * np + 1 < NT) mma16816(acc[mt][2 * np + 1], af[mt], bf[2], bf[3]);
+        }
       }
     }
   }
@@ -646,7 +657,7 @@ template <int NT>
 fv_status conv_launch_nt(const ConvArgs& a, int blocks, size_t smem, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    FV_CUDA(cudaFuncSetAttribute(conv_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, HV * (MAX_CIN + 8) * 2));
+    FV_CUDA(cudaFuncSetAttribute(conv_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr = true;
   }
   conv_kernel<NT><<<blocks, CONV_THREADS, smem, st>>>(a);
@@ -655,8 +666,9 @@ fv_status conv_launch_nt(const ConvArgs& a, int blocks, size_t smem, cudaStream_
 
 fv_status conv(const ConvArgs& a, cudaStream_t st) {
   const int blocks = a.P * ((a.L.Z + BZ - 1) / BZ) * ((a.On + BY - 1) / BY) * ((a.On + BX - 1) / BX);
-  const size_t smem = (size_t)HV * (a.cin + 8) * 2;
-  if (a.cin % 16 || a.c0 % 8 || a.cin > MAX_CIN || a.coutN % 8) return set_error("fv_net: bad convolution shape"), FV_EINVAL;
+  const size_t smem = (size_t)(HV + 27 * a.coutN) * (a.cin + 8) * 2;  // halo + the staged weights
+  if (a.cin % 16 || a.c0 % 8 || a.cin > MAX_CIN || a.coutN % 8 || smem > 200 * 1024)
+    return set_error("fv_net: bad convolution shape"), FV_EINVAL;
   switch (a.coutN / 8) {
     case 1: return conv_launch_nt<1>(a, blocks, smem, st);
     case 2: return conv_launch_nt<2>(a, blocks, smem, st);
