@@ -58,7 +58,7 @@ def parse():
                          'arms are timed beside it with the same steps')
     ap.add_argument('--single', action='store_true', help='time the headline arm only (profiling runs)')
     ap.add_argument('--ns', type=int, default=0, help='override Ns = Nr (small profiling cases)')
-    ap.add_argument('--workload', default='step', choices=['step', 'batch'],
+    ap.add_argument('--workload', default='step', choices=['step', 'batch', 'net'],
                     help='step: the time step (headline); batch: 32 right-hand sides on uneven subdomains')
     return ap.parse_args()
 
@@ -210,6 +210,59 @@ def batch_workload(args, fv, torch, rank, ws):
     fv.fv_free_grid(g)
 
 
+def net_workload(args, fv, torch, rank, ws):
+    """The learned correction's network alone on the bench's coarse grid (6 x 32^3, C = 16, 3 levels):
+    forward of one sample (as inside the preconditioner) and one training step of a batch of 8."""
+    from paper_2009_02171_gb300.inputs import multiscale_fields
+    c = dict(CFG)
+    if args.ns:
+        c['Ns'] = c['Nr'] = args.ns
+    ns, nr, L = c['Ns'] // 2, c['Nr'] // 2, LEARN
+    net = fv.fv_net_create(L['C'], ns, nr, levels=L['levels'], max_batch=L['batch'])
+    fv.fv_net_init(net, 1)
+    R = torch.tensor(multiscale_fields(ns, nr, L['batch'], seed=1), device='cuda')
+    E = torch.empty_like(R)
+    r0, e_0 = R[0].contiguous(), E[0].contiguous()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(args.warmup):
+        fv.fv_net_forward(net, 1, r0, e_0)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        fv.fv_net_forward(net, 1, r0, e_0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_f = e0.elapsed_time(e1) / args.steps
+    fv.fv_net_train(net, R, R.clone(), epochs=max(1, args.warmup), batch=L['batch'], seed=1, lr=L['lr'])
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fv.fv_net_train(net, R, R.clone(), epochs=args.steps, batch=L['batch'], seed=2, lr=L['lr'])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_t = e0.elapsed_time(e1) / args.steps
+    flops = network_flops(c)
+    peaks = json.load(open(os.path.join(ROOT, 'MEASURED_PEAKS.json'))) if os.path.exists(
+        os.path.join(ROOT, 'MEASURED_PEAKS.json')) else {}
+    pk = peaks.get('bf16_tflops', 1869.0)
+    ach = flops / (ms_f * 1e-3) / 1e12
+    if rank == 0:
+        print(json.dumps({'metric': 'learned-correction network forward time (one sample)', 'value': round(ms_f, 4),
+                          'unit': 'ms/forward', 'n_gpus': ws, 'steps': args.steps, 'warmup': args.warmup,
+                          'higher_is_better': False, 'scaling': 'weak', 'dtype': 'bf16 x bf16 -> f32',
+                          'data': 'synthetic', 'config': {'workload': 'cubed-sphere U-Net C=%d, %d levels, grid 6x%d^2x%d'
+                                                          % (L['C'], L['levels'], ns, nr)},
+                          'train_step_ms_batch8': round(ms_t, 3),
+                          # per forward: sumsq, pack, ring; per level 2 convolutions + 2 rings (+ pool and its
+                          # ring below level 0); per decoder level 1 convolution + 1 ring; output conv; unpack
+                          'gpu_launches': args.steps * (9 + 8 * L['levels']),
+                          'roofline': {'kernel': 'net_fwd', 'bound': 'tensor', 'achieved': round(ach, 2), 'peak': pk,
+                                       'unit': 'TFLOP/s', 'frac': round(ach / pk, 4), 'traffic': None,
+                                       'flops_per_launch': flops,
+                                       'peak_source': 'MEASURED_PEAKS.json bf16_tflops (of measured; timed alone)'}}))
+    fv.fv_net_free(net)
+
+
 def main():
     args = parse()
     if args.impl == 'reference':
@@ -226,8 +279,8 @@ def main():
     torch.cuda.set_device(local)
     from paper_2009_02171_gb300 import fv
     from paper_2009_02171_gb300.inputs import initial_state
-    if args.workload == 'batch':
-        batch_workload(args, fv, torch, rank, ws)
+    if args.workload in ('batch', 'net'):
+        (batch_workload if args.workload == 'batch' else net_workload)(args, fv, torch, rank, ws)
         if ws > 1:
             dist.destroy_process_group()
         return
@@ -272,7 +325,7 @@ def main():
         for x, f in ((st, fv.fv_free_state), (V, fv.fv_free_system), (P, fv.fv_free_system), (g, fv.fv_free_grid)):
             f(x)
 
-    def timed(h, steps, warmup, profile):
+    def timed(h, steps, warmup, profile, label=None):
         g, V, P, st, _ = h
         for _ in range(warmup):
             fv.fv_time_step(st, V, P, 1, **opts)
@@ -283,11 +336,15 @@ def main():
             torch.cuda.synchronize()
             if profile:
                 fv.fv_profile_enable(True)
+            if label:  # NVTX range: ncu --nvtx --nvtx-include <label>/ captures exactly these launches
+                torch.cuda.nvtx.range_push(label)
             e0.record(stream)
             for _ in range(steps):
                 s = fv.fv_time_step(st, V, P, 1, **opts)
                 iters.append((s[0].iters, s[1].iters, s[0].inner_iters, s[1].inner_iters))
             e1.record(stream)
+            if label:
+                torch.cuda.nvtx.range_pop()
             torch.cuda.synchronize()
             if ws > 1:
                 dist.barrier()
@@ -313,7 +370,7 @@ def main():
             free(other)
     h, t_setup, info = build(head)
     g, V, P, st, net = h
-    ms, iters, clocks = timed(h, args.steps, args.warmup, False)
+    ms, iters, clocks = timed(h, args.steps, args.warmup, False, label='timed_steps')
     ms_prof, _, _ = timed(h, args.steps, 0, True)
     kern = {}
     for cat in range(fv.K_COUNT):
