@@ -81,18 +81,27 @@ __device__ __forceinline__ void mma16816(float* c, const uint32_t* a, uint32_t b
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// One 16-byte channel group q (8 channels) of the (possibly concatenated) input at
-// padded voxel (p, z, y, x) of level L; zero outside the valid region [i0, i1) and radially.
-__device__ __forceinline__ uint4 load_in(const bf16* s0, int c0, const bf16* s1, int c1, int q, int p, int z, int y,
-                                         int x, const Lvl& L, int i0, int i1) {
-  if (z < 0 || z >= L.Z || y < i0 || y >= i1 || x < i0 || x >= i1) return make_uint4(0, 0, 0, 0);
+// Address of the 16-byte channel group q (8 channels) of the (possibly concatenated) input at
+// padded voxel (p, z, y, x) of level L, or null (value zero) outside the valid region [i0, i1)
+// and radially.
+__device__ __forceinline__ const bf16* src_in(const bf16* s0, int c0, const bf16* s1, int c1, int q, int p, int z,
+                                              int y, int x, const Lvl& L, int i0, int i1) {
+  if (z < 0 || z >= L.Z || y < i0 || y >= i1 || x < i0 || x >= i1) return nullptr;
   const int Yp = L.Y + 2, Xp = L.X + 2;
-  if (q * 8 < c0) return *reinterpret_cast<const uint4*>(s0 + ((((long long)p * L.Z + z) * Yp + y) * Xp + x) * c0 + q * 8);
+  if (q * 8 < c0) return s0 + ((((long long)p * L.Z + z) * Yp + y) * Xp + x) * c0 + q * 8;
   const int Zh = L.Z >> 1, Yh = (L.Y >> 1) + 2, Xh = (L.X >> 1) + 2;
-  const int yh = ((y - 1) >> 1) + 1, xh = ((x - 1) >> 1) + 1;  // parent in padded coordinates (ring -> ring)
-  return *reinterpret_cast<const uint4*>(s1 + ((((long long)p * Zh + (z >> 1)) * Yh + yh) * Xh + xh) * c1 +
-                                         (q * 8 - c0));
+  const int yh = ((y - 1) >> 1) + 1, xh = ((x - 1) >> 1) + 1;
+  return s1 + ((((long long)p * Zh + (z >> 1)) * Yh + yh) * Xh + xh) * c1 + (q * 8 - c0);
 }
+
+// asynchronous 16-byte global -> shared copy (zero fill when src is null): a thread's copies are
+// all in flight together instead of one round trip per loaded value
+__device__ __forceinline__ void cp16(void* dst, const void* src, const void* any) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int n = src ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src ? src : any), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 template <int NT>
 __global__ void __launch_bounds__(CONV_THREADS) conv_kernel(ConvArgs a) {
@@ -113,16 +122,17 @@ __global__ void __launch_bounds__(CONV_THREADS) conv_kernel(ConvArgs a) {
   for (int it = threadIdx.x; it < HV * qn; it += CONV_THREADS) {
     const int hv = it / qn, q = it - hv * qn;
     const int hx = hv % HX, hy = (hv / HX) % HY, hz = hv / (HX * HY);
-    const uint4 v = load_in(a.s0, a.c0, a.s1, a.c1, q, p, z0 - 1 + hz, y0 - 1 + hy, x0 - 1 + hx, a.L, a.i0, a.i1);
-    *reinterpret_cast<uint4*>(hs + hv * cs + q * 8) = v;
+    cp16(hs + hv * cs + q * 8,
+         src_in(a.s0, a.c0, a.s1, a.c1, q, p, z0 - 1 + hz, y0 - 1 + hy, x0 - 1 + hx, a.L, a.i0, a.i1), a.w);
   }
   // all 27 taps' weights, rows (tap, n) of cin values, staged once: the tap loop then reads the B
   // fragments from shared memory instead of waiting on global loads
   bf16* ws = hs + HV * cs;
   for (int it = threadIdx.x; it < 27 * a.coutN * qn; it += CONV_THREADS) {
     const int row = it / qn, q = it - row * qn;
-    *reinterpret_cast<uint4*>(ws + row * cs + q * 8) = __ldg(reinterpret_cast<const uint4*>(a.w + (size_t)row * a.cin + q * 8));
+    cp16(ws + row * cs + q * 8, a.w + (size_t)row * a.cin + q * 8, a.w);
   }
+  cp_wait_all();
   __syncthreads();
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -411,7 +421,7 @@ __global__ void __launch_bounds__(CONV_THREADS) wgrad_kernel(WGradArgs a) {
     for (int it = threadIdx.x; it < WK * qx; it += CONV_THREADS) {
       const int k = it / qx, qq = it - k * qx;
       const long long v = ch * WK + k;
-      uint4 val = make_uint4(0, 0, 0, 0);
+      const bf16* src = nullptr;
       if (v < V) {
         long long t = v;
         const int x = (int)(t % a.L.X);
@@ -420,17 +430,16 @@ __global__ void __launch_bounds__(CONV_THREADS) wgrad_kernel(WGradArgs a) {
         t /= a.L.Y;
         const int z = (int)(t % a.L.Z);
         const int p = (int)(t / a.L.Z);
-        val = load_in(a.s0, a.c0, a.s1, a.c1, qq, p, z + dz, y + 1 + dy, x + 1 + dx, a.L, 0, a.L.Y + 2);
+        src = src_in(a.s0, a.c0, a.s1, a.c1, qq, p, z + dz, y + 1 + dy, x + 1 + dx, a.L, 0, a.L.Y + 2);
       }
-      *reinterpret_cast<uint4*>(xs + k * xsn + qq * 8) = val;
+      cp16(xs + k * xsn + qq * 8, src, a.g);
     }
     for (int it = threadIdx.x; it < WK * qg; it += CONV_THREADS) {
       const int k = it / qg, qq = it - k * qg;
       const long long v = ch * WK + k;
-      const uint4 val =
-          v < V ? *reinterpret_cast<const uint4*>(a.g + padded(v, a.L) * a.gc + qq * 8) : make_uint4(0, 0, 0, 0);
-      *reinterpret_cast<uint4*>(gs + k * gsn + qq * 8) = val;
+      cp16(gs + k * gsn + qq * 8, v < V ? a.g + padded(v, a.L) * a.gc + qq * 8 : nullptr, a.g);
     }
+    cp_wait_all();
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < WK / 16; ++kk) {
