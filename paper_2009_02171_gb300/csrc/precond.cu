@@ -369,6 +369,7 @@ fv_status prepare_sweeps(fv_system* s, int fp32) {
     }
   }
   S.dense_threads = std::min(DENSE_THREADS, (widest + 31) / 32 * 32);
+  S.dense_single = widest <= S.dense_threads;  // one cell per thread and step: the pipelined sweeps
   const size_t ring = 4 * (size_t)S.max_cols * d * es;
   const size_t ring_al = (ring + 15) / 16 * 16;
   S.ring_in_smem = ring_al + tab <= 200 * 1024;
@@ -600,6 +601,158 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_bwd_kernel(const long lo
 }
 
 
+// Level-mapped sweeps with every thread holding at most one cell a step (the widest step fits the
+// CTA): the next step's factors and right-hand side are loaded into registers before the barrier
+// (they do not depend on this step's results) and the cell map two steps ahead, so a step's
+// critical path is the barrier, shared-memory ring reads and arithmetic.
+template <class T, int D, class V>
+__global__ void __launch_bounds__(DENSE_THREADS, 1) ras_fwd_pipe_kernel(const long long* __restrict__ cell_off,
+                                                                      const int* __restrict__ dims,
+                                                                      const int* __restrict__ lpt,
+                                                                      const T* __restrict__ F, T* __restrict__ loc,
+                                                                      T* ring_g, int ring_in_smem, int max_cols,
+                                                                      long long N, const long long* __restrict__ gmap_p,
+                                                                      const V* __restrict__ r) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int sd = lpt[blockIdx.x];
+  const SweepBox b = sweep_box(cell_off, dims, sd);
+  const size_t ring_bytes = ring_in_smem ? ((4 * (size_t)max_cols * D * sizeof(T) + 15) / 16 * 16) : 0;
+  T* ring = ring_in_smem ? (T*)smem : ring_g + (size_t)blockIdx.x * 4 * max_cols * D;
+  int* lvl = (int*)(smem + ring_bytes);
+  int* rowoff = lvl + b.levels + 1;
+  build_tables(b, lvl, rowoff);
+  constexpr int Q = 10 * D + D * D;
+  const T* Fb = F + b.base * Q;
+  T* Lb = loc + b.base * D;
+  const long long* gm = gmap_p + b.base;
+  const long long nc = b.nc;
+  const int t = threadIdx.x;
+  auto cnt_of = [&](int L) { return L < b.levels ? lvl[L + 1] - lvl[L] : 0; };
+  long long gn = t < cnt_of(0) ? gm[t] : -1;  // cell map entry of the next fetch
+  T y0[D], fl[5 * D], fd[D * D];
+  int ci = 0, cj = 0, ck = 0;
+  long long cp = -1;
+  auto fetch = [&](int L) {
+    cp = -1;
+    if (t >= cnt_of(L)) return;
+    level_cell(b, rowoff, L, t, ci, cj, ck);
+    cp = lvl[L] + t;
+    const long long g = gn;
+#pragma unroll
+    for (int a = 0; a < D; ++a) y0[a] = g >= 0 ? (T)r[a * N + g] : T(0);
+#pragma unroll
+    for (int q = 0; q < 5 * D; ++q) fl[q] = Fb[q * nc + cp];
+#pragma unroll
+    for (int a = 1; a < D; ++a)
+#pragma unroll
+      for (int c = 0; c < a; ++c) fd[a * D + c] = Fb[(5 * D + a * D + c) * nc + cp];
+  };
+  fetch(0);
+  gn = t < cnt_of(1) ? gm[lvl[1] + t] : -1;
+  for (int L = 0; L < b.levels; ++L) {
+    if (cp >= 0) {
+      const int i = ci, j = cj, k = ck, col = j * b.nx + i;
+      T* rp = ring + (size_t)((k & 3) * b.ncols) * D;
+      const T* r0 = ring + (size_t)(((k - 1) & 3) * b.ncols + col) * D;
+      T y[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        y[a] = y0[a];
+        if (k > 0) y[a] -= fl[0 * D + a] * r0[a];
+        if (i > 0 && j > 0) y[a] -= fl[1 * D + a] * rp[(col - b.nx - 1) * D + a];
+        if (j > 0) y[a] -= fl[2 * D + a] * rp[(col - b.nx) * D + a];
+        if (j > 0 && i + 1 < b.nx) y[a] -= fl[3 * D + a] * rp[(col - b.nx + 1) * D + a];
+        if (i > 0) y[a] -= fl[4 * D + a] * rp[(col - 1) * D + a];
+#pragma unroll
+        for (int c = 0; c < a; ++c) y[a] -= fd[a * D + c] * y[c];
+      }
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        rp[col * D + a] = y[a];
+        Lb[a * nc + cp] = y[a];
+      }
+    }
+    fetch(L + 1);
+    if (L + 2 < b.levels) gn = t < cnt_of(L + 2) ? gm[lvl[L + 2] + t] : -1;
+    __syncthreads();
+  }
+}
+
+template <class T, int D, class V>
+__global__ void __launch_bounds__(DENSE_THREADS, 1) ras_bwd_pipe_kernel(const long long* __restrict__ cell_off,
+                                                                      const int* __restrict__ dims,
+                                                                      const int* __restrict__ lpt,
+                                                                      const T* __restrict__ F, const T* __restrict__ loc,
+                                                                      T* ring_g, int ring_in_smem, int max_cols,
+                                                                      long long N, const long long* __restrict__ gmap_p,
+                                                                      const unsigned char* __restrict__ owned_p,
+                                                                      V* __restrict__ z) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int sd = lpt[blockIdx.x];
+  const SweepBox b = sweep_box(cell_off, dims, sd);
+  const size_t ring_bytes = ring_in_smem ? ((4 * (size_t)max_cols * D * sizeof(T) + 15) / 16 * 16) : 0;
+  T* ring = ring_in_smem ? (T*)smem : ring_g + (size_t)blockIdx.x * 4 * max_cols * D;
+  int* lvl = (int*)(smem + ring_bytes);
+  int* rowoff = lvl + b.levels + 1;
+  build_tables(b, lvl, rowoff);
+  constexpr int Q = 10 * D + D * D, U = 5 * D + D * D;
+  const T* Fb = F + b.base * Q;
+  const T* Lb = loc + b.base * D;
+  const long long* gm = gmap_p + b.base;
+  const unsigned char* ow = owned_p + b.base;
+  const long long nc = b.nc;
+  const int t = threadIdx.x;
+  T x0[D], fu[5 * D], fd[D * D];
+  int ci = 0, cj = 0, ck = 0;
+  long long cp = -1, go = -1;  // go: cell map entry of an owned cell, else -1
+  auto fetch = [&](int L) {
+    cp = -1;
+    if (L < 0 || t >= lvl[L + 1] - lvl[L]) return;
+    level_cell(b, rowoff, L, t, ci, cj, ck);
+    cp = lvl[L] + t;
+#pragma unroll
+    for (int a = 0; a < D; ++a) x0[a] = Lb[a * nc + cp];
+#pragma unroll
+    for (int q = 0; q < 5 * D; ++q) fu[q] = Fb[(U + q) * nc + cp];
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int c = a; c < D; ++c) fd[a * D + c] = Fb[(5 * D + a * D + c) * nc + cp];
+    const long long g = gm[cp];
+    go = ow[cp] ? g : -1;
+  };
+  fetch(b.levels - 1);
+  for (int L = b.levels - 1; L >= 0; --L) {
+    if (cp >= 0) {
+      const int i = ci, j = cj, k = ck, col = j * b.nx + i;
+      T* rp = ring + (size_t)((k & 3) * b.ncols) * D;
+      const T* r1 = ring + (size_t)(((k + 1) & 3) * b.ncols + col) * D;
+      T x[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) x[a] = x0[a];
+#pragma unroll
+      for (int a = D - 1; a >= 0; --a) {
+#pragma unroll
+        for (int c = a + 1; c < D; ++c) x[a] -= fd[a * D + c] * x[c];
+        if (i + 1 < b.nx) x[a] -= fu[0 * D + a] * rp[(col + 1) * D + a];
+        if (i > 0 && j + 1 < b.ny) x[a] -= fu[1 * D + a] * rp[(col + b.nx - 1) * D + a];
+        if (j + 1 < b.ny) x[a] -= fu[2 * D + a] * rp[(col + b.nx) * D + a];
+        if (i + 1 < b.nx && j + 1 < b.ny) x[a] -= fu[3 * D + a] * rp[(col + b.nx + 1) * D + a];
+        if (k + 1 < b.nz) x[a] -= fu[4 * D + a] * r1[a];
+        x[a] /= fd[a * D + a];
+      }
+#pragma unroll
+      for (int a = 0; a < D; ++a) rp[col * D + a] = x[a];
+      if (go >= 0) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) z[a * N + go] = (V)x[a];
+      }
+    }
+    fetch(L - 1);
+    __syncthreads();
+  }
+}
+
 // D = 2 sweeps with the next wavefront step's factors and vector entries loaded into
 // registers before the barrier (their latency overlaps the barrier and this step's work).
 // At most MC columns per thread.
@@ -782,10 +935,19 @@ static fv_status ras_apply_t(const fv_system* s, const V* r, V* z, cudaStream_t 
     else if (mc == 2)
       ras_fwd2_kernel<T, 2, V><<<S.count, S.threads, S.smem, st>>>(S.cell_off, S.dims, S.lpt, (const T*)S.F, loc,
                                                                    (T*)S.ring, S.ring_in_smem, S.max_cols, N, S.gmap_p, r);
-    else
-      ras_fwd_kernel<T, D, V><<<S.count, S.dense_threads, S.smem, st>>>(S.cell_off, S.dims, S.lpt, (const T*)S.F, loc,
-                                                                       (T*)S.ring, S.ring_in_smem, S.max_cols, N,
-                                                                       S.gmap_p, r);
+    else {
+      bool piped = false;
+      if constexpr (sizeof(T) == 4 || D < 7) {
+        if (S.dense_single) {
+          ras_fwd_pipe_kernel<T, D, V><<<S.count, S.dense_threads, S.smem, st>>>(
+              S.cell_off, S.dims, S.lpt, (const T*)S.F, loc, (T*)S.ring, S.ring_in_smem, S.max_cols, N, S.gmap_p, r);
+          piped = true;
+        }
+      }
+      if (!piped)
+        ras_fwd_kernel<T, D, V><<<S.count, S.dense_threads, S.smem, st>>>(
+            S.cell_off, S.dims, S.lpt, (const T*)S.F, loc, (T*)S.ring, S.ring_in_smem, S.max_cols, N, S.gmap_p, r);
+    }
   }
   FV_CUDA(cudaGetLastError());
   {
@@ -798,10 +960,21 @@ static fv_status ras_apply_t(const fv_system* s, const V* r, V* z, cudaStream_t 
       ras_bwd2_kernel<T, 2, V><<<S.count, S.threads, S.smem, st>>>(S.cell_off, S.dims, S.lpt, (const T*)S.F, loc,
                                                                    (T*)S.ring, S.ring_in_smem, S.max_cols, N, S.gmap_p,
                                                                    S.owned_p, z);
-    else
-      ras_bwd_kernel<T, D, V><<<S.count, S.dense_threads, S.smem, st>>>(S.cell_off, S.dims, S.lpt, (const T*)S.F, loc,
-                                                                       (T*)S.ring, S.ring_in_smem, S.max_cols, N,
-                                                                       S.gmap_p, S.owned_p, z);
+    else {
+      bool piped = false;
+      if constexpr (sizeof(T) == 4 || D < 7) {
+        if (S.dense_single) {
+          ras_bwd_pipe_kernel<T, D, V><<<S.count, S.dense_threads, S.smem, st>>>(
+              S.cell_off, S.dims, S.lpt, (const T*)S.F, loc, (T*)S.ring, S.ring_in_smem, S.max_cols, N, S.gmap_p,
+              S.owned_p, z);
+          piped = true;
+        }
+      }
+      if (!piped)
+        ras_bwd_kernel<T, D, V><<<S.count, S.dense_threads, S.smem, st>>>(
+            S.cell_off, S.dims, S.lpt, (const T*)S.F, loc, (T*)S.ring, S.ring_in_smem, S.max_cols, N, S.gmap_p,
+            S.owned_p, z);
+    }
   }
   FV_CUDA(cudaGetLastError());
   return FV_OK;
@@ -813,6 +986,10 @@ template <class T, int D>
 static fv_status set_smem_attr(int limit) {
   FV_CUDA(cudaFuncSetAttribute(ras_fwd_kernel<T, D, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
   FV_CUDA(cudaFuncSetAttribute(ras_bwd_kernel<T, D, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+  if constexpr (sizeof(T) == 4 || D < 7) {
+    FV_CUDA(cudaFuncSetAttribute(ras_fwd_pipe_kernel<T, D, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    FV_CUDA(cudaFuncSetAttribute(ras_bwd_pipe_kernel<T, D, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+  }
   if (D == 2) {
     FV_CUDA(cudaFuncSetAttribute(ras_fwd2_kernel<T, 1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
     FV_CUDA(cudaFuncSetAttribute(ras_fwd2_kernel<T, 2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
