@@ -89,6 +89,10 @@ class ClockSampler:
                                          stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+        # let nvidia-smi finish initialising (its driver calls can stall CUDA calls) before timing starts
+        deadline = time.time() + 5.0
+        while self.proc and time.time() < deadline and os.path.getsize(self.path) == 0:
+            time.sleep(0.05)
         return self
 
     def __exit__(self, *a):
@@ -426,6 +430,9 @@ def main():
         bytes_per = algorithmic_bytes(top, c, N, 8)
         if not bytes_per:
             return None
+        bwd = top.replace('ras_fwd', 'ras_bwd')
+        if top.startswith('ras_fwd') and bwd not in kern:  # sweeps fused into one launch: both counted
+            bytes_per += algorithmic_bytes(bwd, c, N, 8)
         ach = bytes_per / (per_launch_ms * 1e-3) / 1e9
         return dict(common, bound='hbm', achieved=round(ach, 1), peak=hbm, unit='GB/s', frac=round(ach / hbm, 4),
                     bytes_per_launch=bytes_per, peak_source='MEASURED_PEAKS.json hbm_gbs (of measured)')
@@ -529,9 +536,9 @@ def algorithmic_bytes(cat, c, N, es):
             cells = box_cells(c['Ns'] // 2, c['Nr'] // 2, c['p'], c['overlap_coarse'])
         else:
             cells = box_cells(c['Ns'], c['Nr'], c['p'], c['overlap'])
-        if base.startswith('ras_fwd'):
-            return cells * (es * (2 * d + 5 * d + d * (d - 1) // 2) + 8)
-        return cells * (es * (d + 5 * d + d * (d + 1) // 2) + 9) + ncell * d * es
+        fwd = cells * (es * (2 * d + 5 * d + d * (d - 1) // 2) + 8)
+        bwd = cells * (es * (d + 5 * d + d * (d + 1) // 2) + 9) + ncell * d * es
+        return fwd if base.startswith('ras_fwd') else bwd
     return None
 
 

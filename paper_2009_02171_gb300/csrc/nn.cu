@@ -377,21 +377,25 @@ __global__ void unpool_add_kernel(const bf16* __restrict__ g, bf16* __restrict__
   }
 }
 
-// Weight gradient of one convolution: gw[co][ci][tap] += sum over interior output cells v of
+// Weight gradient of one convolution: gw[co][ci][tap] = sum over interior output cells v of
 // in[v + tap offset][ci] * g[v][co].  CTA (chunk group, tap); warp pairs (16 input channels) x
-// (16 output channels) accumulate over WK-cell chunks.
+// (16 output channels) accumulate over WK-cell chunks; each CTA stores its partial tile and
+// wsum_kernel adds the groups' tiles in a fixed order (bitwise reproducible training).
 struct WGradArgs {
   const bf16* s0;
   const bf16* s1;
   const bf16* g;
-  float* gw;
+  float* part;  // [CTA group][tap][co][ci] partial sums (summed in a fixed order: deterministic)
   int c0, c1, cin, gc, ci, co;
   int P;
   Lvl L;
   long long chunks_per_cta;
 };
 
-constexpr int WG_PAIRS = 4;  // (16 x 16) output tiles per warp: cin/16 * gc/16 <= 16
+constexpr int WG_PAIRS = 4;     // (16 x 16) output tiles per warp: cin/16 * gc/16 <= 16
+constexpr int WG_GROUPS = 48;   // voxel-range groups of the weight gradient (partial tiles)
+constexpr int BG_BLOCKS = 640;  // blocks of the bias gradient (partial sums)
+constexpr int SS_BLOCKS = 320;  // blocks per sample of the sum of squares
 
 __global__ void __launch_bounds__(CONV_THREADS) wgrad_kernel(WGradArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -469,13 +473,24 @@ __global__ void __launch_bounds__(CONV_THREADS) wgrad_kernel(WGradArgs a) {
       for (int e = 0; e < 4; ++e) {
         const int m = mt * 16 + (lane >> 2) + 8 * (e >> 1);
         const int n = nt * 16 + h * 8 + (lane & 3) * 2 + (e & 1);
-        if (m < a.ci && n < a.co) atomicAdd(a.gw + ((long long)n * a.ci + m) * 27 + tap, acc[i][h][e]);
+        if (m < a.ci && n < a.co) a.part[((long long)blockIdx.x * 27 + tap) * a.ci * a.co + n * a.ci + m] = acc[i][h][e];
       }
   }
 }
 
-// bias gradient: gb[c] += sum over interior cells of g[v][c]
-__global__ void bgrad_kernel(const bf16* __restrict__ g, int gc, int co, int P, Lvl L, float* gb) {
+// gw[co][ci][tap] = sum over the groups (in order) of the partial tiles
+__global__ void wsum_kernel(const float* __restrict__ part, int groups, int ci, int co, float* __restrict__ gw) {
+  const int n = 27 * ci * co;
+  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < n; it += gridDim.x * blockDim.x) {
+    const int tap = it % 27, m = (it / 27) % ci, o = it / (27 * ci);
+    float s = 0.f;
+    for (int g = 0; g < groups; ++g) s += part[((long long)g * 27 + tap) * ci * co + o * ci + m];
+    gw[it] = s;
+  }
+}
+
+// bias gradient, per block: bpart[block][c] = sum over the block's interior cells of g[v][c]
+__global__ void bgrad_kernel(const bf16* __restrict__ g, int gc, int co, int P, Lvl L, float* bpart) {
   __shared__ float part[RED_THREADS];
   const int rows = RED_THREADS / gc;  // gc divides RED_THREADS (16, 32, 64)
   const int c = threadIdx.x % gc, r = threadIdx.x / gc;
@@ -488,13 +503,22 @@ __global__ void bgrad_kernel(const bf16* __restrict__ g, int gc, int co, int P, 
   if (threadIdx.x < gc) {
     float t = 0.f;
     for (int k = 0; k < rows; ++k) t += part[k * gc + threadIdx.x];
-    if (threadIdx.x < co) atomicAdd(gb + threadIdx.x, t);
+    if (threadIdx.x < co) bpart[blockIdx.x * co + threadIdx.x] = t;
   }
 }
 
-// per-sample sum of squares of a coarse vector batch (sample b: 2 * V1 values)
+// gb[c] = sum over blocks (in order) of bpart[block][c]
+__global__ void bsum_kernel(const float* __restrict__ bpart, int blocks, int co, float* __restrict__ gb) {
+  if (threadIdx.x >= co) return;
+  float s = 0.f;
+  for (int b = 0; b < blocks; ++b) s += bpart[b * co + threadIdx.x];
+  gb[threadIdx.x] = s;
+}
+
+// per-sample sum of squares of a coarse vector batch (sample b: 2 * V1 values): block partials
+// sspart[b][block], added in order by sssum_kernel (the scale s is bitwise reproducible)
 template <class T>
-__global__ void sumsq_kernel(const T* __restrict__ r, long long n1, double* ss) {
+__global__ void sumsq_kernel(const T* __restrict__ r, long long n1, double* sspart) {
   __shared__ double part[RED_THREADS];
   const T* rb = r + blockIdx.y * n1;
   double s = 0.0;
@@ -508,7 +532,15 @@ __global__ void sumsq_kernel(const T* __restrict__ r, long long n1, double* ss) 
     if (threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x == 0) atomicAdd(ss + blockIdx.y, part[0]);
+  if (threadIdx.x == 0) sspart[blockIdx.y * gridDim.x + blockIdx.x] = part[0];
+}
+
+__global__ void sssum_kernel(const double* __restrict__ sspart, int blocks, int nb, double* ss) {
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < blocks; ++b) s += sspart[i * blocks + b];
+    ss[i] = s;
+  }
 }
 
 // x interior [cell][0..15] = (r_P, r_Pb) / s, zero channels 2..15 (cells sample-major), with
@@ -632,6 +664,8 @@ struct fv_net {
   float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;  // FP32 masters, gradient, Adam moments
   long long t = 0;        // Adam step counter
   double* ss = nullptr;   // [nbmax] per-sample sum of squares
+  double* sspart = nullptr;  // [nbmax][SS_BLOCKS] its block partials
+  float *wpart = nullptr, *bpart = nullptr;  // weight- and bias-gradient partials (training)
   double* loss = nullptr; // [1]
   // activations (BF16, channels last, padded planes)
   fv::bf16* x0 = nullptr;
@@ -712,16 +746,18 @@ fv_status wgrad(fv_net* n, const bf16* s0, int c0, const bf16* s1, int c1, const
   }
   WGradArgs a{};
   a.s0 = s0, a.c0 = c0, a.s1 = s1, a.c1 = c1, a.cin = c0 + c1, a.g = g, a.gc = gc;
-  a.ci = n->L[li].ci, a.co = n->L[li].co, a.gw = n->g + n->L[li].woff;
+  a.ci = n->L[li].ci, a.co = n->L[li].co, a.part = n->wpart;
   a.P = P, a.L = L;
   if ((a.cin / 16) * (gc / 16) > 4 * WG_PAIRS) return set_error("fv_net: weight-gradient tile too large"), FV_EINVAL;
   const long long V = L.cells(P), nchunk = (V + WK - 1) / WK;
-  const long long groups = std::min<long long>(nchunk, 48);
+  const long long groups = std::min<long long>(nchunk, WG_GROUPS);
   a.chunks_per_cta = (nchunk + groups - 1) / groups;
-  const dim3 grid((unsigned)((nchunk + a.chunks_per_cta - 1) / a.chunks_per_cta), 27);
-  wgrad_kernel<<<grid, CONV_THREADS, (size_t)WK * (a.cin + 8 + gc + 8) * 2, st>>>(a);
-  const int rows = RED_THREADS / gc;
-  bgrad_kernel<<<gridsz(V, rows) / 4 + 1, RED_THREADS, 0, st>>>(g, gc, a.co, P, L, n->g + n->L[li].boff);
+  const int ng = (int)((nchunk + a.chunks_per_cta - 1) / a.chunks_per_cta);
+  wgrad_kernel<<<dim3(ng, 27), CONV_THREADS, (size_t)WK * (a.cin + 8 + gc + 8) * 2, st>>>(a);
+  wsum_kernel<<<gridsz(27LL * a.ci * a.co, 256), 256, 0, st>>>(n->wpart, ng, a.ci, a.co, n->g + n->L[li].woff);
+  const int rows = RED_THREADS / gc, nbk = std::min(gridsz(V, rows) / 4 + 1, BG_BLOCKS);
+  bgrad_kernel<<<nbk, RED_THREADS, 0, st>>>(g, gc, a.co, P, L, n->bpart);
+  bsum_kernel<<<1, 64, 0, st>>>(n->bpart, nbk, a.co, n->g + n->L[li].boff);
   return FV_OK;
 }
 
@@ -747,8 +783,9 @@ fv_status check_nb(const fv_net* n, int nb) {
 template <class T>
 fv_status forward_t(fv_net* n, int nb, const T* r, cudaStream_t st) {
   const int C = n->C, P = 6 * nb, Lv = n->levels;
-  FV_CUDA(cudaMemsetAsync(n->ss, 0, nb * sizeof(double), st));
-  sumsq_kernel<T><<<dim3(gridsz(2 * n->V1, RED_THREADS) / 8 + 1, nb), RED_THREADS, 0, st>>>(r, 2 * n->V1, n->ss);
+  const int sblk = std::min(gridsz(2 * n->V1, RED_THREADS) / 8 + 1, SS_BLOCKS);
+  sumsq_kernel<T><<<dim3(sblk, nb), RED_THREADS, 0, st>>>(r, 2 * n->V1, n->sspart);
+  sssum_kernel<<<1, 128, 0, st>>>(n->sspart, sblk, nb, n->ss);
   pack_kernel<T><<<gridsz(n->V1 * nb, 256), 256, 0, st>>>(r, n->ss, n->V1, nb, n->lv[0], n->x0);
   halo(n, n->x0, 16, P, n->lv[0], st);
   fv_status rc;
@@ -798,6 +835,8 @@ fv_status ensure_train(fv_net* n) {
   const int C = n->C, P = 6 * n->nbmax;
   fv_status rc;
   if ((rc = nalloc(n, &n->gy, n->lv[0].vox(P) * 16)) || (rc = nalloc(n, &n->T, n->lv[0].vox(P) * 2 * C)) ||
+      (rc = nalloc(n, &n->wpart, (size_t)WG_GROUPS * 27 * MAX_CIN * 64)) ||
+      (rc = nalloc(n, &n->bpart, (size_t)BG_BLOCKS * 64)) ||
       (rc = nalloc(n, &n->rb, 2 * n->V1 * n->nbmax)) || (rc = nalloc(n, &n->eb, 2 * n->V1 * n->nbmax)))
     return rc;
   for (int l = 0; l <= n->levels; ++l)
@@ -948,6 +987,7 @@ fv_status fv_net_create(const fv_net_desc* d, fv_net** out) {
   const int P = 6 * n->nbmax;
   if ((rc = nalloc(n, &n->w, off)) || (rc = nalloc(n, &n->g, off)) || (rc = nalloc(n, &n->m, off)) ||
       (rc = nalloc(n, &n->v, off)) || (rc = nalloc(n, &n->ss, n->nbmax)) || (rc = nalloc(n, &n->loss, 1)) ||
+      (rc = nalloc(n, &n->sspart, (size_t)n->nbmax * SS_BLOCKS)) ||
       (rc = nalloc(n, &n->x0, n->lv[0].vox(P) * 16)) || (rc = nalloc(n, &n->y, n->V1 * n->nbmax * 2))) {
     fv_net_free(n);
     return rc;

@@ -755,9 +755,10 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_bwd_pipe_kernel(const lo
 
 // D = 2 sweeps with the next wavefront step's factors and vector entries loaded into
 // registers before the barrier (their latency overlaps the barrier and this step's work).
-// At most MC columns per thread.
+// At most MC columns per thread.  Device functions: one kernel runs a box's forward sweep,
+// a block barrier, and its backward sweep (the two depend only on that box's data).
 template <class T, int MC, class V>
-__global__ void __launch_bounds__(MC == 1 ? 1024 : 704) ras_fwd2_kernel(const long long* __restrict__ cell_off,
+__device__ __forceinline__ void fwd2_sweep(const long long* __restrict__ cell_off,
                                                         const int* __restrict__ dims, const int* __restrict__ lpt,
                                                         const T* __restrict__ F, T* __restrict__ loc, T* ring_g,
                                                         int ring_in_smem, int max_cols, long long N,
@@ -837,7 +838,7 @@ __global__ void __launch_bounds__(MC == 1 ? 1024 : 704) ras_fwd2_kernel(const lo
 }
 
 template <class T, int MC, class V>
-__global__ void __launch_bounds__(MC == 1 ? 1024 : 704) ras_bwd2_kernel(const long long* __restrict__ cell_off,
+__device__ __forceinline__ void bwd2_sweep(const long long* __restrict__ cell_off,
                                                         const int* __restrict__ dims, const int* __restrict__ lpt,
                                                         const T* __restrict__ F, T* __restrict__ loc, T* ring_g,
                                                         int ring_in_smem, int max_cols, long long N,
@@ -915,6 +916,33 @@ __global__ void __launch_bounds__(MC == 1 ? 1024 : 704) ras_bwd2_kernel(const lo
   }
 }
 
+template <class T, int MC, class V>
+__global__ void __launch_bounds__(MC == 1 ? 1024 : 704) ras_fwd2_kernel(
+    const long long* __restrict__ cell_off, const int* __restrict__ dims, const int* __restrict__ lpt,
+    const T* __restrict__ F, T* __restrict__ loc, T* ring_g, int ring_in_smem, int max_cols, long long N,
+    const long long* __restrict__ gmap_p, const V* __restrict__ r) {
+  fwd2_sweep<T, MC, V>(cell_off, dims, lpt, F, loc, ring_g, ring_in_smem, max_cols, N, gmap_p, r);
+}
+
+template <class T, int MC, class V>
+__global__ void __launch_bounds__(MC == 1 ? 1024 : 704) ras_bwd2_kernel(
+    const long long* __restrict__ cell_off, const int* __restrict__ dims, const int* __restrict__ lpt,
+    const T* __restrict__ F, T* __restrict__ loc, T* ring_g, int ring_in_smem, int max_cols, long long N,
+    const long long* __restrict__ gmap_p, const unsigned char* __restrict__ owned_p, V* __restrict__ z) {
+  bwd2_sweep<T, MC, V>(cell_off, dims, lpt, F, loc, ring_g, ring_in_smem, max_cols, N, gmap_p, owned_p, z);
+}
+
+template <class T, int MC, class V>
+__global__ void __launch_bounds__(MC == 1 ? 1024 : 704) ras_sweep2_kernel(
+    const long long* __restrict__ cell_off, const int* __restrict__ dims, const int* __restrict__ lpt,
+    const T* __restrict__ F, T* __restrict__ loc, T* ring_g, int ring_in_smem, int max_cols, long long N,
+    const long long* __restrict__ gmap_p, const unsigned char* __restrict__ owned_p, const V* __restrict__ r,
+    V* __restrict__ z) {
+  fwd2_sweep<T, MC, V>(cell_off, dims, lpt, F, loc, ring_g, ring_in_smem, max_cols, N, gmap_p, r);
+  __syncthreads();  // the box's local vector, written above, is read by the backward sweep
+  bwd2_sweep<T, MC, V>(cell_off, dims, lpt, F, loc, ring_g, ring_in_smem, max_cols, N, gmap_p, owned_p, z);
+}
+
 template <class T, int D, class V>
 static fv_status ras_apply_t(const fv_system* s, const V* r, V* z, cudaStream_t st) {
   const Subdomains& S = s->subs;
@@ -927,15 +955,34 @@ static fv_status ras_apply_t(const fv_system* s, const V* r, V* z, cudaStream_t 
                  FV_K_FP32 * S.fp32;
   const int pb = (s->kind == FV_VTBE ? FV_K_RAS_BWD_VTBE : FV_K_RAS_BWD_PPBE) + FV_K_COARSE * s->level +
                  FV_K_FP32 * S.fp32;
+  if constexpr (D == 2) {
+    if (mc == 1) {  // one column a thread: forward and backward in one launch (timed as the forward category)
+      ProfScope ps(pf, st);
+      ras_sweep2_kernel<T, 1, V><<<S.count, S.threads, S.smem, st>>>(S.cell_off, S.dims, S.lpt, (const T*)S.F, loc,
+                                                                     (T*)S.ring, S.ring_in_smem, S.max_cols, N,
+                                                                     S.gmap_p, S.owned_p, r, z);
+      FV_CUDA(cudaGetLastError());
+      return FV_OK;
+    }
+    if (mc == 2) {  // two columns a thread: separate launches (the fused kernel spills registers)
+      {
+        ProfScope ps(pf, st);
+        ras_fwd2_kernel<T, 2, V><<<S.count, S.threads, S.smem, st>>>(S.cell_off, S.dims, S.lpt, (const T*)S.F, loc,
+                                                                     (T*)S.ring, S.ring_in_smem, S.max_cols, N,
+                                                                     S.gmap_p, r);
+      }
+      FV_CUDA(cudaGetLastError());
+      ProfScope ps(pb, st);
+      ras_bwd2_kernel<T, 2, V><<<S.count, S.threads, S.smem, st>>>(S.cell_off, S.dims, S.lpt, (const T*)S.F, loc,
+                                                                   (T*)S.ring, S.ring_in_smem, S.max_cols, N,
+                                                                   S.gmap_p, S.owned_p, z);
+      FV_CUDA(cudaGetLastError());
+      return FV_OK;
+    }
+  }
   {
     ProfScope ps(pf, st);
-    if (mc == 1)
-      ras_fwd2_kernel<T, 1, V><<<S.count, S.threads, S.smem, st>>>(S.cell_off, S.dims, S.lpt, (const T*)S.F, loc,
-                                                                   (T*)S.ring, S.ring_in_smem, S.max_cols, N, S.gmap_p, r);
-    else if (mc == 2)
-      ras_fwd2_kernel<T, 2, V><<<S.count, S.threads, S.smem, st>>>(S.cell_off, S.dims, S.lpt, (const T*)S.F, loc,
-                                                                   (T*)S.ring, S.ring_in_smem, S.max_cols, N, S.gmap_p, r);
-    else {
+    {
       bool piped = false;
       if constexpr (sizeof(T) == 4 || D < 7) {
         if (S.dense_single) {
@@ -952,15 +999,7 @@ static fv_status ras_apply_t(const fv_system* s, const V* r, V* z, cudaStream_t 
   FV_CUDA(cudaGetLastError());
   {
     ProfScope ps(pb, st);
-    if (mc == 1)
-      ras_bwd2_kernel<T, 1, V><<<S.count, S.threads, S.smem, st>>>(S.cell_off, S.dims, S.lpt, (const T*)S.F, loc,
-                                                                   (T*)S.ring, S.ring_in_smem, S.max_cols, N, S.gmap_p,
-                                                                   S.owned_p, z);
-    else if (mc == 2)
-      ras_bwd2_kernel<T, 2, V><<<S.count, S.threads, S.smem, st>>>(S.cell_off, S.dims, S.lpt, (const T*)S.F, loc,
-                                                                   (T*)S.ring, S.ring_in_smem, S.max_cols, N, S.gmap_p,
-                                                                   S.owned_p, z);
-    else {
+    {
       bool piped = false;
       if constexpr (sizeof(T) == 4 || D < 7) {
         if (S.dense_single) {
@@ -991,9 +1030,8 @@ static fv_status set_smem_attr(int limit) {
     FV_CUDA(cudaFuncSetAttribute(ras_bwd_pipe_kernel<T, D, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
   }
   if (D == 2) {
-    FV_CUDA(cudaFuncSetAttribute(ras_fwd2_kernel<T, 1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    FV_CUDA(cudaFuncSetAttribute(ras_sweep2_kernel<T, 1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
     FV_CUDA(cudaFuncSetAttribute(ras_fwd2_kernel<T, 2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
-    FV_CUDA(cudaFuncSetAttribute(ras_bwd2_kernel<T, 1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
     FV_CUDA(cudaFuncSetAttribute(ras_bwd2_kernel<T, 2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
   }
   return FV_OK;

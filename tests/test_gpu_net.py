@@ -133,6 +133,21 @@ def test_adam_matches_oracle(fv):
     fv.fv_net_free(net)
 
 
+def test_training_is_bitwise_reproducible(fv):
+    """Gradients are summed in a fixed order (no floating-point atomics): the same data, seed and
+    initialisation give the same weights bit for bit."""
+    R = _dev(multiscale_fields(8, 8, 8, seed=9))
+    E = _dev(multiscale_fields(8, 8, 8, seed=10))
+    out = []
+    for _ in range(2):
+        net = fv.fv_net_create(16, 8, 8, levels=3, max_batch=4)
+        fv.fv_net_init(net, 3)
+        fv.fv_net_train(net, R, E, epochs=3, batch=4, seed=1, lr=1e-3)
+        out.append(fv.fv_net_get_params(net))
+        fv.fv_net_free(net)
+    assert np.array_equal(out[0], out[1])
+
+
 def test_training_reduces_the_loss(fv):
     flat, _ = _params(16, 2, 14)
     net = fv.fv_net_create(16, 8, 8, levels=2, max_batch=4)
