@@ -33,10 +33,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 CFG = dict(Ns=64, Nr=64, p=(2, 2, 4), overlap=2, overlap_coarse=1, levels=2, E=1e-3, Ra=100.0, Pr=1.0, Pm=5.0,
-           dt=1e-4, rtol=1e-8, restart=30, seed=1, vtbe_inner=4, ppbe_inner=8, coarse_its=10)
+           dt=1e-4, rtol=1e-8, restart=30, seed=1, vtbe_inner=4, ppbe_inner=8, coarse_its=10, inner_gs=1)
 WORKLOAD = ('shell 6x64^2x64 (1.57M cells), time step: VTBE one-level RAS + PPBE two-level RAS, '
             '96 subdomains overlap 2, FGMRES(30) to 1e-8 relative FP64 residual; mixed precision = FP32 inner '
-            'FGMRES (operator, ILU(0) sweeps, coarse level) inside FP64 outer FGMRES; learned = mixed with the '
+            'FGMRES (operator, ILU(0) sweeps, coarse level; one Gram-Schmidt pass) inside FP64 outer FGMRES '
+            '(two passes); learned = mixed with the '
             'PPBE coarse solve replaced by a BF16 cubed-sphere U-Net followed by 6 coarse FGMRES iterations')
 # learned coarse correction of the headline arm: network and training (seeded synthetic pairs from the plain
 # coarse solver; data generation and training are counted in setup_s)
@@ -305,8 +306,9 @@ def main():
         t = time.perf_counter()
         mixed = mode != 'fp64'
         g = fv.fv_build_grid(c['Ns'], c['Nr'])
-        mv = dict(precision=fv.FV_PREC_FP32, inner_maxit=c['vtbe_inner']) if mixed else {}
-        mpp = dict(precision=fv.FV_PREC_FP32, inner_maxit=c['ppbe_inner'], coarse_maxit=c['coarse_its']) if mixed else {}
+        mv = dict(precision=fv.FV_PREC_FP32, inner_maxit=c['vtbe_inner'], inner_gs_passes=c['inner_gs']) if mixed else {}
+        mpp = dict(precision=fv.FV_PREC_FP32, inner_maxit=c['ppbe_inner'], coarse_maxit=c['coarse_its'],
+                   inner_gs_passes=c['inner_gs']) if mixed else {}
         V = fv.fv_assemble_system(g, fv.FV_VTBE, **ph, p=c['p'], overlap=c['overlap'], levels=1, **mv)
         P = fv.fv_assemble_system(g, fv.FV_PPBE, **ph, p=c['p'], overlap=c['overlap'], levels=c['levels'],
                                   overlap_coarse=c['overlap_coarse'], **mpp)

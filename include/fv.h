@@ -106,6 +106,10 @@ typedef struct {
    * even; the coarse level uses the halved boxes.  Read during the call only. */
   int nboxes;
   const int* boxes;
+  /* Gram-Schmidt passes of the FP32 fixed-iteration inner solves (mixed
+   * precision only): 2 (classical Gram-Schmidt twice, the default; 0 means 2)
+   * or 1 (once).  The FP64 outer FGMRES always uses two passes. */
+  int inner_gs_passes;
 } fv_pc_desc;
 #define FV_PREC_FP64 0
 #define FV_PREC_FP32 1

@@ -28,6 +28,8 @@ static void free_system(fv_system* s) {
 }
 
 static fv_status make_system(const fv_grid* g, int kind, const fv_phys* ph, const fv_pc_desc* pc, fv_system** out) {
+  if (pc->inner_gs_passes < 0 || pc->inner_gs_passes > 2)
+    return set_error("fv_assemble_system: inner_gs_passes must be 0, 1 or 2"), FV_EINVAL;
   fv_system* s = new fv_system();
   s->grid = g, s->kind = kind, s->d = kind == FV_VTBE ? 7 : 2;
   s->n = s->d * g->h.N;

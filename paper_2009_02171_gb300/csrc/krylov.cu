@@ -442,8 +442,10 @@ static fv_status gmres_fixed_t(const fv_system* s, const T* b, T* x, int m, cuda
   KrylovT<T>& k = kt<T>(s->kry);
   const long long n = s->n;
   const int lvl = FV_K_COARSE * s->level + (sizeof(T) == 4 ? FV_K_FP32 : 0);
+  const bool once = s->pc.inner_gs_passes == 1;
   {
     ProfScope ps(FV_K_CGS + lvl, st);
+    if (once) FV_CUDA(cudaMemsetAsync(k.h + KMAX, 0, KMAX * sizeof(double), st));
     cgs_launch<T>(0, n, b, nullptr, const_cast<T*>(b), k.part, 2, st);
     start_kernel<<<1, 32, 0, st>>>(k.part, RBLOCKS, k.ad);
     dscale_kernel<T><<<vblocks(n), 256, 0, st>>>(n, b, &k.ad->scale, k.V);
@@ -459,10 +461,15 @@ static fv_status gmres_fixed_t(const fv_system* s, const T* b, T* x, int m, cuda
     f.ticket = k.ticket;
     f.out = k.h;
     cgs_launch<T>(nv, n, k.V, nullptr, k.w, k.part, 0, st, f);
-    f.out = k.h + KMAX;
-    cgs_launch<T>(nv, n, k.V, k.h, k.w, k.part, 1, st, f);
-    f.out = k.h + 2 * KMAX, f.ad = k.ad, f.gj = j, f.hg = k.h;
-    cgs_launch<T>(nv, n, k.V, k.h + KMAX, k.w, k.part, 2, st, f);
+    if (once) {  // one pass: w -= V h1 with the norm; the second coefficients stay zero
+      f.out = k.h + 2 * KMAX, f.ad = k.ad, f.gj = j, f.hg = k.h;
+      cgs_launch<T>(nv, n, k.V, k.h, k.w, k.part, 2, st, f);
+    } else {
+      f.out = k.h + KMAX;
+      cgs_launch<T>(nv, n, k.V, k.h, k.w, k.part, 1, st, f);
+      f.out = k.h + 2 * KMAX, f.ad = k.ad, f.gj = j, f.hg = k.h;
+      cgs_launch<T>(nv, n, k.V, k.h + KMAX, k.w, k.part, 2, st, f);
+    }
     if (j + 1 < m) dscale_kernel<T><<<vblocks(n), 256, 0, st>>>(n, k.w, &k.ad->scale, k.V + (size_t)(j + 1) * n);
   }
   ProfScope ps(FV_K_VEC, st);

@@ -159,8 +159,8 @@ def test_bad_arguments_raise(fv):
     fv.fv_free_grid(g)
 
 
-@pytest.mark.parametrize('kind,levels', [(0, 1), (1, 2)])
-def test_mixed_precision_solve_reaches_fp64_residual(fv, kind, levels):
+@pytest.mark.parametrize('kind,levels,gs', [(0, 1, 2), (1, 2, 2), (0, 1, 1), (1, 2, 1)])
+def test_mixed_precision_solve_reaches_fp64_residual(fv, kind, levels, gs):
     """FP32 inner FGMRES (FP32 operator, FP32 ILU(0) sweeps, FP32 coarse level) as the
     preconditioner of the FP64 outer FGMRES: the true FP64 residual (oracle matrix) reaches
     1e-8 and the solution matches the FP64 solution to the conditioning-limited accuracy."""
@@ -173,7 +173,7 @@ def test_mixed_precision_solve_reaches_fp64_residual(fv, kind, levels):
     g = fv.fv_build_grid(Ns, Nr)
     s64 = fv.fv_assemble_system(g, kind, **PH, p=parts, overlap=1, levels=levels)
     s32 = fv.fv_assemble_system(g, kind, **PH, p=parts, overlap=1, levels=levels, precision=fv.FV_PREC_FP32,
-                                inner_maxit=6, coarse_maxit=8)
+                                inner_maxit=6, coarse_maxit=8, inner_gs_passes=gs)
     x64 = torch.zeros(A.shape[0], dtype=torch.float64, device='cuda')
     x32 = torch.zeros_like(x64)
     st64 = fv.fv_gmres_solve(s64, _dev(b), x64, rtol=1e-8)
