@@ -64,6 +64,15 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(value, device):
+    """The largest of the ranks' values (the job's time is its slowest rank's); every rank gets it."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_setup(backend):
     import torch.distributed as dist
     ws = int(os.environ.get('WORLD_SIZE', '1'))
@@ -356,9 +365,7 @@ def main():
                 dist.barrier()
         ms = e0.elapsed_time(e1) / steps
         if ws > 1:
-            t = torch.tensor([ms], device='cuda')
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+            ms = max_over_ranks(ms, 'cuda')
         return ms, iters, clk.summary()
 
     head = args.precision
@@ -408,9 +415,7 @@ def main():
     torch.cuda.synchronize()
     ms_e2e = e0.elapsed_time(e1) / ke
     if ws > 1:
-        t = torch.tensor([ms_e2e], device='cuda')
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
+        ms_e2e = max_over_ranks(ms_e2e, 'cuda')
 
     # roofline of the dominant kernel category (measured live over the timed region)
     peaks = json.load(open(os.path.join(ROOT, 'MEASURED_PEAKS.json'))) if os.path.exists(
