@@ -113,9 +113,10 @@ fv_status fv_restrict_coarse(const fv_system* s, const double* x, double* xc, vo
  * fixed-iteration inner solve under mixed precision).  flags: FV_LEARN_GUESS
  * also corrects the initial guess of each top-level solve,
  * x0 <- x0 + I_c^f N(r_c(b - A x0)).  The system borrows the network: keep
- * it alive while attached.  A top-level solve that ends without convergence
- * (FV_ENOCONV or FV_ENAN) under the learned preconditioner continues with the
- * plain coarse GMRES for the remaining iterations (stats->fallback = 1). */
+ * it alive while attached.  A top-level solve that has not converged within
+ * one restart cycle (opts->restart iterations) under the learned
+ * preconditioner, or meets a NaN, continues with the plain coarse GMRES for
+ * the remaining iterations (stats->fallback = 1). */
 #define FV_LEARN_GUESS 1
 fv_status fv_pc_set_learned(fv_system* s, fv_net* net, int coarse_its, int flags);
 

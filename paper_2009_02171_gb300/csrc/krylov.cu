@@ -594,9 +594,10 @@ static fv_status gmres_t(const fv_system* s, const T* b, T* x, const fv_gmres_op
 }
 
 // Top-level solves of a system with a learned coarse correction: optional
-// learned initial guess, then FGMRES; if that ends without convergence, the
-// plain coarse solve finishes from the last finite iterate with the original
-// absolute target max(atol, rtol ||b - A x0||).
+// learned initial guess, then FGMRES for at most one restart cycle; if that
+// ends without convergence, the plain coarse solve finishes from the last
+// finite iterate with the original absolute target max(atol, rtol ||b - A x0||)
+// and the iterations left.
 static fv_status gmres_learned(const fv_system* s, const double* b, double* x, const fv_gmres_opts* o,
                                fv_solve_stats* stats, cudaStream_t st) {
   fv_system* sm = const_cast<fv_system*>(s);
@@ -615,12 +616,16 @@ static fv_status gmres_learned(const fv_system* s, const double* b, double* x, c
   }
   fv_gmres_opts o1 = *o;
   if (r0 >= 0.0) o1.atol = std::max(o->atol, o->rtol * r0), o1.rtol = 0.0;
+  // the learned preconditioner gets one restart cycle; a solve it has not finished by then
+  // (a stall, or a network that does not fit this problem) goes on with the plain one
+  o1.max_it = std::min(o->max_it, o->restart);
   rc = gmres_t<double>(s, b, x, &o1, &s1, st, false);
   int inner = s->last_inner;
   if (r0 >= 0.0) s1.r0 = r0;
   if (rc == FV_ENOCONV || rc == FV_ENAN) {
     if (rc == FV_ENAN) FV_CUDA(cudaMemcpyAsync(x, s->xbak, bytes, cudaMemcpyDeviceToDevice, st));
     fv_gmres_opts o2 = *o;
+    o2.max_it = std::max(0, o->max_it - s1.iters);
     o2.atol = std::max(o->atol, o->rtol * s1.r0), o2.rtol = 0.0;
     fv_solve_stats s2{};
     set_learned_active(sm, 0);

@@ -223,7 +223,7 @@ def test_plain_fallback_finishes_a_failed_learned_solve(fv, ppbe, bad):
     k = fv.fv_net_param_count(net)
     fv.fv_net_set_params(net, np.zeros(k, np.float32) if bad == 'zero' else np.full(k, np.nan, np.float32))
     fv.fv_pc_set_learned(s, net, coarse_its=0)
-    st, res = _solve(fv, s, n, 32, max_it=plain.iters + 1, raise_on_noconv=False)
+    st, res = _solve(fv, s, n, 32, restart=plain.iters + 1, max_it=100, raise_on_noconv=False)
     fv.fv_pc_set_learned(s, None)
     fv.fv_net_free(net)
     assert st.fallback == 1 and st.converged and res < 1.0001e-8
