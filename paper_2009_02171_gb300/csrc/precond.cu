@@ -347,13 +347,7 @@ fv_status prepare_sweeps(fv_system* s, int fp32) {
   release(s, S.off), release(s, S.diag), release(s, S.perm);
   S.off = S.diag = nullptr;
   S.perm = nullptr;
-  // CTA shape: one thread per (i, j) column, at most 1024 threads (columns loop); the
-  // register-prefetching d = 2 sweeps take up to 2 columns per thread on at most 704 threads
-  // (the generic kernels, used for d = 7 and for very wide d = 2 boxes, take at most 704 threads)
-  S.threads = std::min(704, ((S.max_cols + 31) / 32) * 32);
-  if (d == 2 && S.max_cols <= 1024) S.threads = ((S.max_cols + 31) / 32) * 32;
-  if (d == 2 && S.max_cols > 1024 && S.max_cols <= 1408) S.threads = ((S.max_cols + 1) / 2 + 31) / 32 * 32;
-  // the widest box's level table; the 4-plane ring in shared memory when it fits
+  // the widest box's level table and wavefront step; the 4-plane ring in shared memory when it fits
   std::vector<int> dims(3 * S.count);
   FV_CUDA(cudaMemcpy(dims.data(), S.dims, dims.size() * sizeof(int), cudaMemcpyDeviceToHost));
   size_t tab = 0;
@@ -383,9 +377,9 @@ fv_status prepare_sweeps(fv_system* s, int fp32) {
 }
 
 // ------------------------------------------------------------------ RAS apply
-// Wavefront sweeps: thread <-> (i, j) column; at step L the column's cell is k = L - i - 2j.
-// In-plane neighbours and the own column's previous cell are read from a ring of 4 planes
-// indexed by k mod 4 (a neighbour of level L-1..L-3 is never overwritten before it is read).
+// Wavefront sweeps: step L updates the box cells with i + 2j + k = L.  A cell's in-plane
+// neighbours and its own column's previous cell are read from a ring of 4 planes indexed by
+// k mod 4 (a neighbour of level L-1..L-3 is never overwritten before it is read).
 struct SweepBox {
   int nx, ny, nz, levels, ncols;
   long long base, nc;
@@ -753,233 +747,15 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_bwd_pipe_kernel(const lo
   }
 }
 
-// D = 2 sweeps with the next wavefront step's factors and vector entries loaded into
-// registers before the barrier (their latency overlaps the barrier and this step's work).
-// At most MC columns per thread.  Device functions: one kernel runs a box's forward sweep,
-// a block barrier, and its backward sweep (the two depend only on that box's data).
-template <class T, int MC, class V>
-__device__ __forceinline__ void fwd2_sweep(const long long* __restrict__ cell_off,
-                                                        const int* __restrict__ dims, const int* __restrict__ lpt,
-                                                        const T* __restrict__ F, T* __restrict__ loc, T* ring_g,
-                                                        int ring_in_smem, int max_cols, long long N,
-                                                        const long long* __restrict__ gmap_p,
-                                                        const V* __restrict__ r) {
-  constexpr int D = 2, NF = 5 * D + 1;  // lower slots + the diagonal block's lower entry
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int sd = lpt[blockIdx.x];
-  const SweepBox b = sweep_box(cell_off, dims, sd);
-  const size_t ring_bytes = ring_in_smem ? ((4 * (size_t)max_cols * D * sizeof(T) + 15) / 16 * 16) : 0;
-  T* ring = ring_in_smem ? (T*)smem : ring_g + (size_t)blockIdx.x * 4 * max_cols * D;
-  int* lvl = (int*)(smem + ring_bytes);
-  int* rowoff = lvl + b.levels + 1;
-  build_tables(b, lvl, rowoff);
-  const T* Fb = F + b.base * (10 * D + D * D);
-  T* Lb = loc + b.base * D;
-  const long long nc = b.nc;
-  int ci[MC], cj[MC];
-  T f[MC][NF], y0[MC][D];
-  long long ps[MC], gn[MC];
-#pragma unroll
-  for (int m = 0; m < MC; ++m) {
-    const int col = threadIdx.x + m * blockDim.x;
-    cj[m] = col < b.ncols ? col / b.nx : -1;
-    ci[m] = col < b.ncols ? col - cj[m] * b.nx : 0;
-  }
-  auto cellpos = [&](int L, int m) -> long long {
-    const int i = ci[m], j = cj[m], k = L - i - 2 * j;
-    if (j < 0 || k < 0 || k >= b.nz || L >= b.levels) return -1;
-    return lvl[L] + rowoff[L * b.ny + j] + i - max(0, L - 2 * j - (b.nz - 1));
-  };
-  // the cell map entry is loaded two steps ahead, the gathered r and the factors one step
-  // ahead: nothing a step's critical path waits for is loaded in that step
-  auto fetch_g = [&](int L, int m) {
-    const long long pos = cellpos(L, m);
-    gn[m] = pos >= 0 ? gmap_p[b.base + pos] : -1;
-  };
-  auto fetch = [&](int L, int m) {
-    const long long pos = cellpos(L, m);
-    ps[m] = pos;
-    if (pos < 0) return;
-    const long long g = gn[m];  // R_i^delta r gathered here (zero past cube corners)
-#pragma unroll
-    for (int a = 0; a < D; ++a) y0[m][a] = g >= 0 ? (T)r[a * N + g] : T(0);
-#pragma unroll
-    for (int q = 0; q < 5 * D; ++q) f[m][q] = Fb[q * nc + pos];
-    f[m][5 * D] = Fb[(5 * D + 1 * D + 0) * nc + pos];  // diagonal block entry (1, 0)
-  };
-#pragma unroll
-  for (int m = 0; m < MC; ++m) fetch_g(0, m), fetch(0, m), fetch_g(1, m);
-  for (int L = 0; L < b.levels; ++L) {
-#pragma unroll
-    for (int m = 0; m < MC; ++m) {
-      if (ps[m] < 0) continue;
-      const int i = ci[m], j = cj[m], k = L - i - 2 * j, col = j * b.nx + i;
-      const T* rp = ring + (size_t)((k & 3) * b.ncols) * D;
-      const T* r0 = ring + (size_t)(((k - 1) & 3) * b.ncols + col) * D;
-      T y[D];
-#pragma unroll
-      for (int a = 0; a < D; ++a) {
-        y[a] = y0[m][a];
-        if (k > 0) y[a] -= f[m][0 * D + a] * r0[a];
-        if (i > 0 && j > 0) y[a] -= f[m][1 * D + a] * rp[(col - b.nx - 1) * D + a];
-        if (j > 0) y[a] -= f[m][2 * D + a] * rp[(col - b.nx) * D + a];
-        if (j > 0 && i + 1 < b.nx) y[a] -= f[m][3 * D + a] * rp[(col - b.nx + 1) * D + a];
-        if (i > 0) y[a] -= f[m][4 * D + a] * rp[(col - 1) * D + a];
-      }
-      y[1] -= f[m][5 * D] * y[0];
-      T* w = ring + (size_t)((k & 3) * b.ncols + col) * D;
-#pragma unroll
-      for (int a = 0; a < D; ++a) w[a] = y[a], Lb[a * nc + ps[m]] = y[a];
-    }
-#pragma unroll
-    for (int m = 0; m < MC; ++m) fetch(L + 1, m), fetch_g(L + 2, m);
-    __syncthreads();
-  }
-}
-
-template <class T, int MC, class V>
-__device__ __forceinline__ void bwd2_sweep(const long long* __restrict__ cell_off,
-                                                        const int* __restrict__ dims, const int* __restrict__ lpt,
-                                                        const T* __restrict__ F, T* __restrict__ loc, T* ring_g,
-                                                        int ring_in_smem, int max_cols, long long N,
-                                                        const long long* __restrict__ gmap_p,
-                                                        const unsigned char* __restrict__ owned_p,
-                                                        V* __restrict__ z) {
-  constexpr int D = 2, U = 5 * D + D * D, NF = 5 * D + 3;  // upper slots + diag (0,1), (0,0), (1,1)
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int sd = lpt[blockIdx.x];
-  const SweepBox b = sweep_box(cell_off, dims, sd);
-  const size_t ring_bytes = ring_in_smem ? ((4 * (size_t)max_cols * D * sizeof(T) + 15) / 16 * 16) : 0;
-  T* ring = ring_in_smem ? (T*)smem : ring_g + (size_t)blockIdx.x * 4 * max_cols * D;
-  int* lvl = (int*)(smem + ring_bytes);
-  int* rowoff = lvl + b.levels + 1;
-  build_tables(b, lvl, rowoff);
-  const T* Fb = F + b.base * (10 * D + D * D);
-  T* Lb = loc + b.base * D;
-  const long long nc = b.nc;
-  int ci[MC], cj[MC];
-  T f[MC][NF], x0[MC][D];
-  long long ps[MC], go[MC];  // go: cell map entry of an owned cell, else -1 (fetched with the factors)
-#pragma unroll
-  for (int m = 0; m < MC; ++m) {
-    const int col = threadIdx.x + m * blockDim.x;
-    cj[m] = col < b.ncols ? col / b.nx : -1;
-    ci[m] = col < b.ncols ? col - cj[m] * b.nx : 0;
-  }
-  auto fetch = [&](int L, int m) {
-    const int i = ci[m], j = cj[m], k = L - i - 2 * j;
-    ps[m] = -1;
-    if (j < 0 || L < 0 || k < 0 || k >= b.nz) return;
-    const long long pos = lvl[L] + rowoff[L * b.ny + j] + i - max(0, L - 2 * j - (b.nz - 1));
-    ps[m] = pos;
-#pragma unroll
-    for (int a = 0; a < D; ++a) x0[m][a] = Lb[a * nc + pos];
-#pragma unroll
-    for (int q = 0; q < 5 * D; ++q) f[m][q] = Fb[(U + q) * nc + pos];
-    f[m][5 * D] = Fb[(5 * D + 0 * D + 1) * nc + pos];      // diag (0, 1)
-    f[m][5 * D + 1] = Fb[(5 * D + 0 * D + 0) * nc + pos];  // diag (0, 0)
-    f[m][5 * D + 2] = Fb[(5 * D + 1 * D + 1) * nc + pos];  // diag (1, 1)
-    const long long g = gmap_p[b.base + pos];
-    go[m] = owned_p[b.base + pos] ? g : -1;
-  };
-#pragma unroll
-  for (int m = 0; m < MC; ++m) fetch(b.levels - 1, m);
-  for (int L = b.levels - 1; L >= 0; --L) {
-#pragma unroll
-    for (int m = 0; m < MC; ++m) {
-      if (ps[m] < 0) continue;
-      const int i = ci[m], j = cj[m], k = L - i - 2 * j, col = j * b.nx + i;
-      const T* rp = ring + (size_t)((k & 3) * b.ncols) * D;
-      const T* r1 = ring + (size_t)(((k + 1) & 3) * b.ncols + col) * D;
-      T x[D] = {x0[m][0], x0[m][1]};
-#pragma unroll
-      for (int a = D - 1; a >= 0; --a) {
-        if (a == 0) x[0] -= f[m][5 * D] * x[1];
-        if (i + 1 < b.nx) x[a] -= f[m][0 * D + a] * rp[(col + 1) * D + a];
-        if (i > 0 && j + 1 < b.ny) x[a] -= f[m][1 * D + a] * rp[(col + b.nx - 1) * D + a];
-        if (j + 1 < b.ny) x[a] -= f[m][2 * D + a] * rp[(col + b.nx) * D + a];
-        if (i + 1 < b.nx && j + 1 < b.ny) x[a] -= f[m][3 * D + a] * rp[(col + b.nx + 1) * D + a];
-        if (k + 1 < b.nz) x[a] -= f[m][4 * D + a] * r1[a];
-        x[a] /= f[m][5 * D + 1 + a];
-      }
-      T* w = ring + (size_t)((k & 3) * b.ncols + col) * D;
-#pragma unroll
-      for (int a = 0; a < D; ++a) w[a] = x[a];
-      if (go[m] >= 0) {  // (R_i^0)^T: scatter the owned cells
-#pragma unroll
-        for (int a = 0; a < D; ++a) z[a * N + go[m]] = (V)x[a];
-      }
-    }
-#pragma unroll
-    for (int m = 0; m < MC; ++m) fetch(L - 1, m);
-    __syncthreads();
-  }
-}
-
-template <class T, int MC, class V>
-__global__ void __launch_bounds__(MC == 1 ? 1024 : 704) ras_fwd2_kernel(
-    const long long* __restrict__ cell_off, const int* __restrict__ dims, const int* __restrict__ lpt,
-    const T* __restrict__ F, T* __restrict__ loc, T* ring_g, int ring_in_smem, int max_cols, long long N,
-    const long long* __restrict__ gmap_p, const V* __restrict__ r) {
-  fwd2_sweep<T, MC, V>(cell_off, dims, lpt, F, loc, ring_g, ring_in_smem, max_cols, N, gmap_p, r);
-}
-
-template <class T, int MC, class V>
-__global__ void __launch_bounds__(MC == 1 ? 1024 : 704) ras_bwd2_kernel(
-    const long long* __restrict__ cell_off, const int* __restrict__ dims, const int* __restrict__ lpt,
-    const T* __restrict__ F, T* __restrict__ loc, T* ring_g, int ring_in_smem, int max_cols, long long N,
-    const long long* __restrict__ gmap_p, const unsigned char* __restrict__ owned_p, V* __restrict__ z) {
-  bwd2_sweep<T, MC, V>(cell_off, dims, lpt, F, loc, ring_g, ring_in_smem, max_cols, N, gmap_p, owned_p, z);
-}
-
-template <class T, int MC, class V>
-__global__ void __launch_bounds__(MC == 1 ? 1024 : 704) ras_sweep2_kernel(
-    const long long* __restrict__ cell_off, const int* __restrict__ dims, const int* __restrict__ lpt,
-    const T* __restrict__ F, T* __restrict__ loc, T* ring_g, int ring_in_smem, int max_cols, long long N,
-    const long long* __restrict__ gmap_p, const unsigned char* __restrict__ owned_p, const V* __restrict__ r,
-    V* __restrict__ z) {
-  fwd2_sweep<T, MC, V>(cell_off, dims, lpt, F, loc, ring_g, ring_in_smem, max_cols, N, gmap_p, r);
-  __syncthreads();  // the box's local vector, written above, is read by the backward sweep
-  bwd2_sweep<T, MC, V>(cell_off, dims, lpt, F, loc, ring_g, ring_in_smem, max_cols, N, gmap_p, owned_p, z);
-}
-
 template <class T, int D, class V>
 static fv_status ras_apply_t(const fv_system* s, const V* r, V* z, cudaStream_t st) {
   const Subdomains& S = s->subs;
   const long long N = s->grid->geo.N;
   T* loc = (T*)S.loc;
-  const int mc = (D == 2 && S.max_cols <= S.threads && S.threads <= 1024) ? 1
-                 : (D == 2 && S.max_cols <= 2 * S.threads && S.threads <= 704) ? 2
-                                                                                 : 0;
   const int pf = (s->kind == FV_VTBE ? FV_K_RAS_FWD_VTBE : FV_K_RAS_FWD_PPBE) + FV_K_COARSE * s->level +
                  FV_K_FP32 * S.fp32;
   const int pb = (s->kind == FV_VTBE ? FV_K_RAS_BWD_VTBE : FV_K_RAS_BWD_PPBE) + FV_K_COARSE * s->level +
                  FV_K_FP32 * S.fp32;
-  if constexpr (D == 2) {
-    if (mc == 1) {  // one column a thread: forward and backward in one launch (timed as the forward category)
-      ProfScope ps(pf, st);
-      ras_sweep2_kernel<T, 1, V><<<S.count, S.threads, S.smem, st>>>(S.cell_off, S.dims, S.lpt, (const T*)S.F, loc,
-                                                                     (T*)S.ring, S.ring_in_smem, S.max_cols, N,
-                                                                     S.gmap_p, S.owned_p, r, z);
-      FV_CUDA(cudaGetLastError());
-      return FV_OK;
-    }
-    if (mc == 2) {  // two columns a thread: separate launches (the fused kernel spills registers)
-      {
-        ProfScope ps(pf, st);
-        ras_fwd2_kernel<T, 2, V><<<S.count, S.threads, S.smem, st>>>(S.cell_off, S.dims, S.lpt, (const T*)S.F, loc,
-                                                                     (T*)S.ring, S.ring_in_smem, S.max_cols, N,
-                                                                     S.gmap_p, r);
-      }
-      FV_CUDA(cudaGetLastError());
-      ProfScope ps(pb, st);
-      ras_bwd2_kernel<T, 2, V><<<S.count, S.threads, S.smem, st>>>(S.cell_off, S.dims, S.lpt, (const T*)S.F, loc,
-                                                                   (T*)S.ring, S.ring_in_smem, S.max_cols, N,
-                                                                   S.gmap_p, S.owned_p, z);
-      FV_CUDA(cudaGetLastError());
-      return FV_OK;
-    }
-  }
   {
     ProfScope ps(pf, st);
     {
@@ -1028,11 +804,6 @@ static fv_status set_smem_attr(int limit) {
   if constexpr (sizeof(T) == 4 || D < 7) {
     FV_CUDA(cudaFuncSetAttribute(ras_fwd_pipe_kernel<T, D, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
     FV_CUDA(cudaFuncSetAttribute(ras_bwd_pipe_kernel<T, D, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
-  }
-  if (D == 2) {
-    FV_CUDA(cudaFuncSetAttribute(ras_sweep2_kernel<T, 1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
-    FV_CUDA(cudaFuncSetAttribute(ras_fwd2_kernel<T, 2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
-    FV_CUDA(cudaFuncSetAttribute(ras_bwd2_kernel<T, 2, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
   }
   return FV_OK;
 }

@@ -52,11 +52,12 @@ def test_apply_matches_oracle(fv, kind, Ns, Nr):
     fv.fv_free_grid(g)
 
 
-# d = 2 boxes up to 1024 columns take the column-prefetching sweeps (18 x 18 x 12 among them);
-# 42 x 42 x 6 (wider than 1408 columns) the level-mapped generic sweeps
+# boxes whose widest wavefront step fits the CTA (<= 384 cells) take the pipelined level-mapped
+# sweeps; 42 x 42 x 24 (504 cells in a step) the level-mapped sweeps with several cells a thread
 @pytest.mark.parametrize('kind,Ns,Nr,parts,delta', [(0, 8, 6, (2, 2, 2), 1), (1, 10, 8, (3, 2, 2), 2),
                                                      (1, 8, 8, (1, 1, 1), 1), (0, 9, 5, (2, 3, 1), 2),
-                                                     (1, 16, 12, (1, 1, 1), 1), (1, 40, 4, (1, 1, 1), 1)])
+                                                     (1, 16, 12, (1, 1, 1), 1), (1, 40, 4, (1, 1, 1), 1),
+                                                     (1, 40, 24, (1, 1, 1), 1)])
 def test_one_level_ras_matches_oracle(fv, kind, Ns, Nr, parts, delta):
     """z = M_one^{-1} r (level-scheduled ILU(0) sweeps) vs the oracle's sequential ILU(0)."""
     A, d, _ = _oracle_matrix(kind, Ns, Nr)
