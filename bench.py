@@ -267,9 +267,9 @@ def net_workload(args, fv, torch, rank, ws):
                           'data': 'synthetic', 'config': {'workload': 'cubed-sphere U-Net C=%d, %d levels, grid 6x%d^2x%d'
                                                           % (L['C'], L['levels'], ns, nr)},
                           'train_step_ms_batch8': round(ms_t, 3),
-                          # per forward: sumsq, pack, ring; per level 2 convolutions + 2 rings (+ pool and its
-                          # ring below level 0); per decoder level 1 convolution + 1 ring; output conv; unpack
-                          'gpu_launches': args.steps * (9 + 8 * L['levels']),
+                          # per forward: sumsq + ordered sum, pack, ring; per level 2 convolutions (+ pool and its
+                          # ring below level 0); per decoder level 1 convolution; output conv; unpack
+                          'gpu_launches': args.steps * (8 + 5 * L['levels']),
                           'roofline': {'kernel': 'net_fwd', 'bound': 'tensor', 'achieved': round(ach, 2), 'peak': pk,
                                        'unit': 'TFLOP/s', 'frac': round(ach / pk, 4), 'traffic': None,
                                        'flops_per_launch': flops,

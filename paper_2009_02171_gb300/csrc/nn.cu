@@ -6,7 +6,8 @@
 // cell of a pyramid level, each panel padded by a one-cell ring in (eta, xi):
 // [panel][k][j + 1][i + 1][channel], (Ns_l + 2)^2 voxels a plane, panel = sample
 // * 6 + cubed-sphere panel.  The ring holds the neighbouring panel's cells across
-// each edge (halo_fill); ring corners stay zero.  A convolution is an implicit
+// each edge (written by the producing convolution's epilogue, or by halo_fill for the
+// input and the pooled tensors); ring corners stay zero.  A convolution is an implicit
 // GEMM (M = voxels, N = output channels, K = 27 taps x input channels) on the
 // tensor cores (mma.sync m16n8k16, BF16 x BF16 -> FP32): one CTA computes a
 // 4 x 4 x 8 brick of output voxels from a (6 x 6 x 10)-voxel halo of its input
@@ -48,6 +49,22 @@ struct Lvl {
   __host__ __device__ long long cells(int P) const { return (long long)P * Z * Y * X; }
 };
 
+// Cubed-sphere ring: the ring voxel beyond `side` of panel p at tangential index t takes
+// the value of panel q[p][side]'s cell next to its side s[p][side] at tangential index
+// t (flip: n - 1 - t).  Sides: 0 xi-min, 1 xi-max, 2 eta-min, 3 eta-max.
+struct Halo {
+  int q[24], s[24], flip[24];
+};
+
+// (y, x) of the cell next to `side` at tangential index t (padded coordinates); ring = outside
+__device__ __forceinline__ void side_cell(int side, int t, int n, bool ring, int& y, int& x) {
+  const int lo = ring ? 0 : 1, hi = ring ? n + 1 : n;
+  if (side == 0) y = t + 1, x = lo;
+  else if (side == 1) y = t + 1, x = hi;
+  else if (side == 2) y = lo, x = t + 1;
+  else y = hi, x = t + 1;
+}
+
 struct ConvArgs {
   const bf16* s0;     // input at the output's level, c0 channels (padded)
   const bf16* s1;     // input one level coarser read through nearest upsampling, c1 channels (or null)
@@ -61,6 +78,8 @@ struct ConvArgs {
   int o0, On;         // output region per plane axis in padded coordinates: [o0, o0 + On) (1, Y: interior; 0, Y + 2: all)
   int i0, i1;         // valid input region per plane axis in padded coordinates, zero outside
   int mode;
+  int ring;           // RELU: also write panel-edge outputs into the neighbouring panels' rings
+  Halo H;
 };
 
 __device__ __forceinline__ void ldsm4(uint32_t addr, uint32_t* r) {
@@ -200,25 +219,23 @@ __global__ void __launch_bounds__(CONV_THREADS) conv_kernel(ConvArgs a) {
           u0 = fmaxf(u0 + a.bias[col], 0.f);
           u1 = fmaxf(u1 + a.bias[col + 1], 0.f);
         }
-        *reinterpret_cast<__nv_bfloat162*>(a.out + v * a.cout + col) = __floats2bfloat162_rn(u0, u1);
+        const __nv_bfloat162 o = __floats2bfloat162_rn(u0, u1);
+        *reinterpret_cast<__nv_bfloat162*>(a.out + v * a.cout + col) = o;
+        if (a.ring) {  // the cell is the source of the ring voxel across each panel edge it touches
+          const int n = a.L.Y, jj = y - 1, ii = x - 1, pl = p % 6, base = p - pl;
+#pragma unroll
+          for (int sd = 0; sd < 4; ++sd) {
+            const bool on = sd == 0 ? ii == 0 : sd == 1 ? ii == n - 1 : sd == 2 ? jj == 0 : jj == n - 1;
+            if (!on) continue;
+            const int e = pl * 4 + sd, t = sd < 2 ? jj : ii;
+            int yr, xr;
+            side_cell(a.H.s[e], a.H.flip[e] ? n - 1 - t : t, n, true, yr, xr);
+            const long long rv = (((long long)(base + a.H.q[e]) * a.L.Z + z) * Yp + yr) * Xp + xr;
+            *reinterpret_cast<__nv_bfloat162*>(a.out + rv * a.cout + col) = o;
+          }
+        }
       }
     }
-}
-
-// Cubed-sphere ring: the ring voxel beyond `side` of panel p at tangential index t takes
-// the value of panel q[p][side]'s cell next to its side s[p][side] at tangential index
-// t (flip: n - 1 - t).  Sides: 0 xi-min, 1 xi-max, 2 eta-min, 3 eta-max.
-struct Halo {
-  int q[24], s[24], flip[24];
-};
-
-// (y, x) of the cell next to `side` at tangential index t (padded coordinates); ring = outside
-__device__ __forceinline__ void side_cell(int side, int t, int n, bool ring, int& y, int& x) {
-  const int lo = ring ? 0 : 1, hi = ring ? n + 1 : n;
-  if (side == 0) y = t + 1, x = lo;
-  else if (side == 1) y = t + 1, x = hi;
-  else if (side == 2) y = lo, x = t + 1;
-  else y = hi, x = t + 1;
 }
 
 __global__ void halo_fill_kernel(bf16* __restrict__ a, int C, int P, Lvl L, Halo H) {
@@ -799,20 +816,17 @@ fv_status forward_t(fv_net* n, int nb, const T* r, cudaStream_t st) {
       in = n->In[l], cin = C;
     }
     ConvArgs a = fwd_args(in, cin, nullptr, 0, n->L[eA(l)], P, L, EPI_RELU);
-    a.bias = n->w + n->L[eA(l)].boff, a.out = n->A[l];
+    a.bias = n->w + n->L[eA(l)].boff, a.out = n->A[l], a.ring = 1, a.H = n->halo;
     if ((rc = conv(a, st))) return rc;
-    halo(n, n->A[l], C, P, L, st);
     a = fwd_args(n->A[l], C, nullptr, 0, n->L[eB(l)], P, L, EPI_RELU);
-    a.bias = n->w + n->L[eB(l)].boff, a.out = n->E[l];
+    a.bias = n->w + n->L[eB(l)].boff, a.out = n->E[l], a.ring = 1, a.H = n->halo;
     if ((rc = conv(a, st))) return rc;
-    halo(n, n->E[l], C, P, L, st);
   }
   for (int l = Lv - 1; l >= 0; --l) {
     const bf16* up = l + 1 == Lv ? n->E[Lv] : n->D[l + 1];
     ConvArgs a = fwd_args(n->E[l], C, up, C, n->L[dL(n, l)], P, n->lv[l], EPI_RELU);
-    a.bias = n->w + n->L[dL(n, l)].boff, a.out = n->D[l];
+    a.bias = n->w + n->L[dL(n, l)].boff, a.out = n->D[l], a.ring = 1, a.H = n->halo;
     if ((rc = conv(a, st))) return rc;
-    halo(n, n->D[l], C, P, n->lv[l], st);
   }
   const bf16* last = Lv > 0 ? n->D[0] : n->E[0];
   ConvArgs a = fwd_args(last, C, nullptr, 0, n->L[outL(n)], P, n->lv[0], EPI_FINAL);

@@ -64,38 +64,32 @@ fv_status fill_ghosts(const fv_system* s, const double* x, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------- apply
-// Two launches cover every row: the interior kernel maps threads onto the (Ns-2)^2
-// interior of each panel layer (no warp touches a panel edge, so no warp diverges into
-// the out-of-line edge path), the edge kernel onto the 4 (Ns-1) cells of each layer's
-// boundary ring.  grid.y = k, grid.z = comp * 6 + panel; 32-bit index math.
-template <int KIND, class T, class GT>
-__global__ void __launch_bounds__(256) apply_interior_kernel(GT G, Coefs<typename GT::real> cf,
-                                                             const T* __restrict__ x, const T* __restrict__ gh,
-                                                             T* __restrict__ y) {
-  const int ni = G.Ns - 2;
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= ni * ni) return;
-  const int i = 1 + q % ni, j = 1 + q / ni, k = blockIdx.y;
-  const int a = blockIdx.z / 6, p = blockIdx.z - 6 * a;
-  ApplyAcc<T, typename GT::real> acc(G, x, gh);
-  if (KIND == FV_VTBE) vtbe_row(G, cf, acc, p, k, j, i, a);
-  else ppbe_row(G, cf, acc, p, k, j, i, a);
-  y[(long long)a * G.N + ((long long)(p * G.Nr + k) * G.Ns + j) * G.Ns + i] = (T)acc.sum;
-}
+// One launch covers every row: the first blocks map threads onto the (Ns-2)^2 interior of
+// each panel layer (no warp touches a panel edge, so none diverges into the out-of-line edge
+// path), the remaining blocks onto the 4 (Ns-1) cells of each layer's boundary ring, so the
+// edge rows run beside the interior ones.  grid.y = k, grid.z = comp * 6 + panel; 32-bit index math.
+constexpr int APPLY_THREADS = 256;
 
 template <int KIND, class T, class GT>
-__global__ void __launch_bounds__(128) apply_edge_kernel(GT G, Coefs<typename GT::real> cf, const T* __restrict__ x,
-                                                         const T* __restrict__ gh, T* __restrict__ y) {
-  const int Ns = G.Ns, ring = 4 * (Ns - 1);
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= ring) return;
-  // walk the boundary ring: j = 0 row, i = Ns-1 column, j = Ns-1 row, i = 0 column
-  const int s = q / (Ns - 1), t = q % (Ns - 1);
+__global__ void __launch_bounds__(APPLY_THREADS) apply_kernel(GT G, Coefs<typename GT::real> cf,
+                                                              const T* __restrict__ x, const T* __restrict__ gh,
+                                                              T* __restrict__ y) {
+  const int Ns = G.Ns, ni = Ns - 2;
+  const int nib = (ni * ni + APPLY_THREADS - 1) / APPLY_THREADS;  // interior blocks
   int i, j;
-  if (s == 0) i = t, j = 0;
-  else if (s == 1) i = Ns - 1, j = t;
-  else if (s == 2) i = Ns - 1 - t, j = Ns - 1;
-  else i = 0, j = Ns - 1 - t;
+  if ((int)blockIdx.x < nib) {
+    const int q = blockIdx.x * APPLY_THREADS + threadIdx.x;
+    if (q >= ni * ni) return;
+    i = 1 + q % ni, j = 1 + q / ni;
+  } else {  // walk the boundary ring: j = 0 row, i = Ns-1 column, j = Ns-1 row, i = 0 column
+    const int q = (blockIdx.x - nib) * APPLY_THREADS + threadIdx.x;
+    if (q >= 4 * (Ns - 1)) return;
+    const int s = q / (Ns - 1), t = q % (Ns - 1);
+    if (s == 0) i = t, j = 0;
+    else if (s == 1) i = Ns - 1, j = t;
+    else if (s == 2) i = Ns - 1 - t, j = Ns - 1;
+    else i = 0, j = Ns - 1 - t;
+  }
   const int k = blockIdx.y, a = blockIdx.z / 6, p = blockIdx.z - 6 * a;
   ApplyAcc<T, typename GT::real> acc(G, x, gh);
   if (KIND == FV_VTBE) vtbe_row(G, cf, acc, p, k, j, i, a);
@@ -107,8 +101,8 @@ template <int KIND, class T, class GT>
 static void launch_apply(const GT& G, const Coefs<typename GT::real>& cf, int d, const T* x, const T* gh, T* y,
                          cudaStream_t st) {
   const int ni = G.Ns - 2;
-  apply_interior_kernel<KIND, T, GT><<<dim3((ni * ni + 255) / 256, G.Nr, 6 * d), 256, 0, st>>>(G, cf, x, gh, y);
-  apply_edge_kernel<KIND, T, GT><<<dim3((4 * (G.Ns - 1) + 127) / 128, G.Nr, 6 * d), 128, 0, st>>>(G, cf, x, gh, y);
+  const int blocks = (ni * ni + APPLY_THREADS - 1) / APPLY_THREADS + (4 * (G.Ns - 1) + APPLY_THREADS - 1) / APPLY_THREADS;
+  apply_kernel<KIND, T, GT><<<dim3(blocks, G.Nr, 6 * d), APPLY_THREADS, 0, st>>>(G, cf, x, gh, y);
 }
 
 fv_status apply_op(const fv_system* s, const double* x, double* y, cudaStream_t st) {
