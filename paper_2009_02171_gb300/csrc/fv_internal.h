@@ -100,6 +100,7 @@ struct Subdomains {
   // order (level i + 2j + k, then j, then i), structure of arrays
   int* perm = nullptr;            // [total_cells] natural local index -> packed position (setup only)
   long long* gmap_p = nullptr;    // [total_cells] packed: global cell or -1
+  int* ijk = nullptr;             // [total_cells] packed: box cell (i | j << 10 | k << 20)
   unsigned char* owned_p = nullptr;
   void* F = nullptr;              // [cell_off * Q + q * ncell + pos], Q = 10 d + d^2, element type per `fp32`
   void* loc = nullptr;            // [cell_off * d + a * ncell + pos] sweep vector

@@ -364,6 +364,25 @@ fv_status prepare_sweeps(fv_system* s, int fp32) {
   }
   S.dense_threads = std::min(DENSE_THREADS, (widest + 31) / 32 * 32);
   S.dense_single = widest <= S.dense_threads;  // one cell per thread and step: the pipelined sweeps
+  // (i, j, k) of every packed position (wavefront order: step, then j, then i), so the pipelined
+  // sweeps load a cell's coordinates with its factors instead of searching the step's rows
+  {
+    std::vector<long long> off(S.count + 1);
+    FV_CUDA(cudaMemcpy(off.data(), S.cell_off, off.size() * sizeof(long long), cudaMemcpyDeviceToHost));
+    std::vector<int> ijk(S.total_cells);
+    for (int sd = 0; sd < S.count; ++sd) {
+      const int nx = dims[3 * sd], ny = dims[3 * sd + 1], nz = dims[3 * sd + 2];
+      if (nx >= 1024 || ny >= 1024 || nz >= 1024) return set_error("fv_assemble_system: subdomain too large"), FV_EINVAL;
+      long long pos = off[sd];
+      for (int L = 0; L < nx - 1 + 2 * (ny - 1) + nz; ++L)
+        for (int j = 0; j < ny; ++j)
+          for (int i = std::max(0, L - 2 * j - (nz - 1)); i <= std::min(nx - 1, L - 2 * j); ++i)
+            ijk[pos++] = i | j << 10 | (L - i - 2 * j) << 20;
+    }
+    S.ijk = dalloc<int>(s, S.total_cells);
+    if (!S.ijk) return set_error("fv_assemble_system: allocation of the sweep cell table failed"), FV_ENOMEM;
+    FV_CUDA(cudaMemcpy(S.ijk, ijk.data(), ijk.size() * sizeof(int), cudaMemcpyHostToDevice));
+  }
   const size_t ring = 4 * (size_t)S.max_cols * d * es;
   const size_t ring_al = (ring + 15) / 16 * 16;
   S.ring_in_smem = ring_al + tab <= 200 * 1024;
@@ -606,6 +625,7 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_fwd_pipe_kernel(const lo
                                                                       const T* __restrict__ F, T* __restrict__ loc,
                                                                       T* ring_g, int ring_in_smem, int max_cols,
                                                                       long long N, const long long* __restrict__ gmap_p,
+                                                                      const int* __restrict__ ijk,
                                                                       const V* __restrict__ r) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int sd = lpt[blockIdx.x];
@@ -626,11 +646,13 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_fwd_pipe_kernel(const lo
   T y0[D], fl[5 * D], fd[D * D];
   int ci = 0, cj = 0, ck = 0;
   long long cp = -1;
+  const int* cells = ijk + b.base;
   auto fetch = [&](int L) {
     cp = -1;
     if (t >= cnt_of(L)) return;
-    level_cell(b, rowoff, L, t, ci, cj, ck);
     cp = lvl[L] + t;
+    const int c = cells[cp];
+    ci = c & 1023, cj = (c >> 10) & 1023, ck = c >> 20;
     const long long g = gn;
 #pragma unroll
     for (int a = 0; a < D; ++a) y0[a] = g >= 0 ? (T)r[a * N + g] : T(0);
@@ -680,6 +702,7 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_bwd_pipe_kernel(const lo
                                                                       T* ring_g, int ring_in_smem, int max_cols,
                                                                       long long N, const long long* __restrict__ gmap_p,
                                                                       const unsigned char* __restrict__ owned_p,
+                                                                      const int* __restrict__ ijk,
                                                                       V* __restrict__ z) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int sd = lpt[blockIdx.x];
@@ -690,6 +713,7 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_bwd_pipe_kernel(const lo
   int* rowoff = lvl + b.levels + 1;
   build_tables(b, lvl, rowoff);
   constexpr int Q = 10 * D + D * D, U = 5 * D + D * D;
+  const int* cells = ijk + b.base;
   const T* Fb = F + b.base * Q;
   const T* Lb = loc + b.base * D;
   const long long* gm = gmap_p + b.base;
@@ -702,8 +726,9 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_bwd_pipe_kernel(const lo
   auto fetch = [&](int L) {
     cp = -1;
     if (L < 0 || t >= lvl[L + 1] - lvl[L]) return;
-    level_cell(b, rowoff, L, t, ci, cj, ck);
     cp = lvl[L] + t;
+    const int c = cells[cp];
+    ci = c & 1023, cj = (c >> 10) & 1023, ck = c >> 20;
 #pragma unroll
     for (int a = 0; a < D; ++a) x0[a] = Lb[a * nc + cp];
 #pragma unroll
@@ -763,7 +788,8 @@ static fv_status ras_apply_t(const fv_system* s, const V* r, V* z, cudaStream_t 
       if constexpr (sizeof(T) == 4 || D < 7) {
         if (S.dense_single) {
           ras_fwd_pipe_kernel<T, D, V><<<S.count, S.dense_threads, S.smem, st>>>(
-              S.cell_off, S.dims, S.lpt, (const T*)S.F, loc, (T*)S.ring, S.ring_in_smem, S.max_cols, N, S.gmap_p, r);
+              S.cell_off, S.dims, S.lpt, (const T*)S.F, loc, (T*)S.ring, S.ring_in_smem, S.max_cols, N, S.gmap_p,
+              S.ijk, r);
           piped = true;
         }
       }
@@ -781,7 +807,7 @@ static fv_status ras_apply_t(const fv_system* s, const V* r, V* z, cudaStream_t 
         if (S.dense_single) {
           ras_bwd_pipe_kernel<T, D, V><<<S.count, S.dense_threads, S.smem, st>>>(
               S.cell_off, S.dims, S.lpt, (const T*)S.F, loc, (T*)S.ring, S.ring_in_smem, S.max_cols, N, S.gmap_p,
-              S.owned_p, z);
+              S.owned_p, S.ijk, z);
           piped = true;
         }
       }
