@@ -242,10 +242,12 @@ def net_workload(args, fv, torch, rank, ws):
     for _ in range(args.warmup):
         fv.fv_net_forward(net, 1, r0, e_0)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push('net_forward')  # ncu --nvtx --nvtx-include net_forward/: the timed forwards
     e0.record(stream)
     for _ in range(args.steps):
         fv.fv_net_forward(net, 1, r0, e_0)
     e1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     ms_f = e0.elapsed_time(e1) / args.steps
     fv.fv_net_train(net, R, R.clone(), epochs=max(1, args.warmup), batch=L['batch'], seed=1, lr=L['lr'])
