@@ -43,6 +43,10 @@ WORKLOAD = ('shell 6x64^2x64 (1.57M cells), time step: VTBE one-level RAS + PPBE
 # coarse solver; data generation and training are counted in setup_s)
 LEARN = dict(C=16, levels=3, pairs=256, epochs=40, batch=8, lr=3e-4, coarse_its=6)
 METRIC = 'wall time per time step at 1e-8 residual'
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a kernel category at the default
+# workload, from the ncu capture in the file named beside it; a category leaves this table when its kernels
+# change, until they are captured again
+TRAFFIC = {'net_fwd': (51663360, 'profiles/launches_net_forward_c16_coarse32.md')}
 # oracle sample: the same step on 6 x 32^2 x 32 (1/8 of the cells), scaled by the cell ratio
 ORACLE_NS = 32
 
@@ -273,7 +277,9 @@ def net_workload(args, fv, torch, rank, ws):
                           # ring below level 0); per decoder level 1 convolution; output conv; unpack
                           'gpu_launches': args.steps * (8 + 5 * L['levels']),
                           'roofline': {'kernel': 'net_fwd', 'bound': 'tensor', 'achieved': round(ach, 2), 'peak': pk,
-                                       'unit': 'TFLOP/s', 'frac': round(ach / pk, 4), 'traffic': None,
+                                       'unit': 'TFLOP/s', 'frac': round(ach / pk, 4),
+                                       'traffic': TRAFFIC['net_fwd'][0] if not args.ns else None,
+                                       'traffic_source': TRAFFIC['net_fwd'][1] if not args.ns else None,
                                        'flops_per_launch': flops,
                                        'peak_source': 'MEASURED_PEAKS.json bf16_tflops (of measured; timed alone)'}}))
     fv.fv_net_free(net)
@@ -427,7 +433,9 @@ def main():
 
     def roof_of(top):
         per_launch_ms = kern[top]['ms_total'] / kern[top]['launches']
-        common = {'kernel': top, 'ms_per_launch': round(per_launch_ms, 4), 'traffic': None,
+        tr = TRAFFIC.get(top) if not args.ns else None
+        common = {'kernel': top, 'ms_per_launch': round(per_launch_ms, 4), 'traffic': tr[0] if tr else None,
+                  'traffic_source': tr[1] if tr else None,
                   'share_of_step': round(kern[top]['ms_total'] / (ms * args.steps), 3), 'top_kernel': ranked[-1][1]}
         if top.startswith('net_fwd'):
             flops = network_flops(c)
@@ -472,7 +480,9 @@ def main():
             'precision': head,
             'arms': others,
             'learned': ({k: (round(v, 4) if isinstance(v, float) else v) for k, v in info.items()} if info else None),
-            'config': {'workload': WORKLOAD if not args.ns else WORKLOAD.replace('64', str(args.ns)),
+            'config': {'workload': WORKLOAD if not args.ns else WORKLOAD.replace(
+                           'shell 6x64^2x64 (1.57M cells)', 'shell 6x%d^2x%d (%d cells)' % (args.ns, args.ns, 6 * args.ns ** 3)).replace(
+                           'coarse 32', 'coarse %d' % (args.ns // 2)),
                        'cells': 6 * c['Ns'] ** 2 * c['Nr'], 'subdomains': 6 * 16,
                        'overlap': c['overlap'], 'ppbe_levels': c['levels'], 'rtol': c['rtol'],
                        'restart': c['restart'], 'l2': 'working set > L2 (no flush needed)',

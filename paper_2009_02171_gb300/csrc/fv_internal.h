@@ -111,6 +111,10 @@ struct Subdomains {
   int dense_single = 0;           // 1: no step is wider than the CTA (the pipelined sweeps apply)
   size_t smem = 0;                // dynamic shared memory of the sweeps
   int ring_in_smem = 0;
+  int stage = 0;                  // d = 2: depth of the shared-memory staged sweeps (8 or 4), 0 = not used
+  size_t stage_off = 0;           // offset of the stage ring in dynamic shared memory
+  size_t stage_smem = 0;          // dynamic shared memory of the staged sweeps
+  long long* go = nullptr;        // [total_cells] packed: grid cell of an owned cell, else -1 (staged sweeps)
 };
 
 }  // namespace fv

@@ -325,6 +325,13 @@ __global__ void repack_kernel(int d, int count, const long long* __restrict__ ce
   }
 }
 
+// scatter target of every packed position: the grid cell when the box owns it, else -1
+__global__ void scatter_target_kernel(long long n, const long long* __restrict__ gmap_p,
+                                      const unsigned char* __restrict__ owned_p, long long* __restrict__ go) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
+    go[c] = owned_p[c] ? gmap_p[c] : -1;
+}
+
 constexpr int DENSE_THREADS = 384;  // CTA size bound of the generic sweeps (170 registers per thread)
 
 static size_t table_bytes(int levels, int ny) { return (size_t)(levels + 1 + levels * ny) * sizeof(int); }
@@ -391,6 +398,26 @@ fv_status prepare_sweeps(fv_system* s, int fp32) {
     S.ring = fp32 ? (void*)dalloc<float>(s, (size_t)S.count * 4 * S.max_cols * d)
                   : (void*)dalloc<double>(s, (size_t)S.count * 4 * S.max_cols * d);
     if (!S.ring) return set_error("fv_assemble_system: allocation of the sweep ring failed"), FV_ENOMEM;
+  }
+  // d = 2 boxes whose steps fit the CTA: the shared-memory staged sweeps, 8 (else 4) steps deep when
+  // the stage ring fits beside the 4-plane ring and the tables (per thread and slot: the forward's
+  // 11 or the backward's 13 factors, d vector values, an 8-byte cell map entry, packed (i, j, k))
+  S.stage = 0;
+  if (d == 2 && S.dense_single) {
+    const size_t per = (size_t)S.dense_threads * ((5 * d + d * (d + 1) / 2) * es + d * es + 8 + 4);
+    const size_t off = (S.smem + 15) / 16 * 16;
+    for (int sg : {8, 4})
+      if (off + sg * per <= 200 * 1024) {
+        S.stage = sg, S.stage_off = off, S.stage_smem = off + sg * per;
+        break;
+      }
+    if (S.stage) {
+      S.go = dalloc<long long>(s, S.total_cells);
+      if (!S.go) return set_error("fv_assemble_system: allocation of the sweep scatter map failed"), FV_ENOMEM;
+      scatter_target_kernel<<<blocks, 256>>>(S.total_cells, S.gmap_p, S.owned_p, S.go);
+      FV_CUDA(cudaGetLastError());
+      FV_CUDA(cudaDeviceSynchronize());
+    }
   }
   return FV_OK;
 }
@@ -772,6 +799,200 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_bwd_pipe_kernel(const lo
   }
 }
 
+// Shared-memory staged sweeps (d = 2 boxes whose widest step fits the CTA): every thread copies
+// its own cell's factors, right-hand side and packed coordinates for the step SG - 1 ahead into
+// a slot of an SG-deep ring with cp.async (one commit group a step) and reads them back after
+// waiting for that step's group, so SG - 1 steps of load latency overlap the step in progress at
+// no register cost.  A thread reads only what it copied itself: the wait orders it, no barrier.
+// Slot element e of thread t sits at [(slot * n + e) * blockDim + t] (no bank conflicts).
+template <int B>
+__device__ __forceinline__ void cp_async(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const size_t g = __cvta_generic_to_global(src);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(g), "n"(B) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <class T, int D, class V, int SG>
+__global__ void __launch_bounds__(DENSE_THREADS, 1) ras_fwd_stage_kernel(const long long* __restrict__ cell_off,
+                                                                       const int* __restrict__ dims,
+                                                                       const int* __restrict__ lpt,
+                                                                       const T* __restrict__ F, T* __restrict__ loc,
+                                                                       T* ring_g, int ring_in_smem, int max_cols,
+                                                                       long long N, const long long* __restrict__ gmap_p,
+                                                                       const int* __restrict__ ijk,
+                                                                       const V* __restrict__ r, int stage_off) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int sd = lpt[blockIdx.x];
+  const SweepBox b = sweep_box(cell_off, dims, sd);
+  const size_t ring_bytes = ring_in_smem ? ((4 * (size_t)max_cols * D * sizeof(T) + 15) / 16 * 16) : 0;
+  T* ring = ring_in_smem ? (T*)smem : ring_g + (size_t)blockIdx.x * 4 * max_cols * D;
+  int* lvl = (int*)(smem + ring_bytes);
+  int* rowoff = lvl + b.levels + 1;
+  build_tables(b, lvl, rowoff);
+  constexpr int Q = 10 * D + D * D, NF = 5 * D + D * (D - 1) / 2;
+  const int Tn = blockDim.x, t = threadIdx.x;
+  T* sF = (T*)(smem + stage_off);                         // [SG][NF][Tn] lower factors
+  V* sY = (V*)(sF + (size_t)SG * NF * Tn);                // [SG][D][Tn] gathered right-hand side
+  long long* sG = (long long*)(sY + (size_t)SG * D * Tn); // [SG][Tn] cell map entry SG - 1 steps later
+  int* sI = (int*)(sG + (size_t)SG * Tn);                 // [SG][Tn] packed (i, j, k)
+  const T* Fb = F + b.base * Q;
+  T* Lb = loc + b.base * D;
+  const long long* gm = gmap_p + b.base;
+  const int* cells = ijk + b.base;
+  const long long nc = b.nc;
+  auto cnt_of = [&](int L) { return L < b.levels ? lvl[L + 1] - lvl[L] : 0; };
+  // step g into slot g % SG (gg: this thread's cell map entry in step g), and the cell map entry of
+  // step g + SG - 1, which the copies of that step need for the gather
+  auto issue = [&](int g, long long gg) {
+    const int s = g % SG;
+    if (t < cnt_of(g)) {
+      const long long cp = lvl[g] + t;
+      cp_async<4>(sI + s * Tn + t, cells + cp);
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        if (gg >= 0) cp_async<sizeof(V)>(sY + (s * D + a) * Tn + t, r + a * N + gg);
+        else sY[(s * D + a) * Tn + t] = V(0);
+      }
+#pragma unroll
+      for (int q = 0; q < 5 * D; ++q) cp_async<sizeof(T)>(sF + (s * NF + q) * Tn + t, Fb + q * nc + cp);
+#pragma unroll
+      for (int a = 1; a < D; ++a)
+#pragma unroll
+        for (int c = 0; c < a; ++c)
+          cp_async<sizeof(T)>(sF + (s * NF + 5 * D + a * (a - 1) / 2 + c) * Tn + t, Fb + (5 * D + a * D + c) * nc + cp);
+    }
+    const int h = g + SG - 1;
+    if (t < cnt_of(h)) cp_async<8>(sG + s * Tn + t, gm + lvl[h] + t);
+    cp_commit();
+  };
+  for (int g = 0; g < SG - 1; ++g) issue(g, t < cnt_of(g) ? gm[lvl[g] + t] : -1);
+  for (int L = 0; L < b.levels; ++L) {
+    cp_wait<SG - 2>();  // step L's group has landed (the SG - 2 later ones may be in flight)
+    const int s = L % SG;
+    issue(L + SG - 1, t < cnt_of(L + SG - 1) ? sG[s * Tn + t] : -1);  // into the slot step L - 1 used
+    if (t < cnt_of(L)) {
+      const int c = sI[s * Tn + t];
+      const int i = c & 1023, j = (c >> 10) & 1023, k = c >> 20, col = j * b.nx + i;
+      const long long cp = lvl[L] + t;
+      T* rp = ring + (size_t)((k & 3) * b.ncols) * D;
+      const T* r0 = ring + (size_t)(((k - 1) & 3) * b.ncols + col) * D;
+      const T* f = sF + s * NF * Tn + t;
+      T y[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        y[a] = (T)sY[(s * D + a) * Tn + t];
+        if (k > 0) y[a] -= f[(0 * D + a) * Tn] * r0[a];
+        if (i > 0 && j > 0) y[a] -= f[(1 * D + a) * Tn] * rp[(col - b.nx - 1) * D + a];
+        if (j > 0) y[a] -= f[(2 * D + a) * Tn] * rp[(col - b.nx) * D + a];
+        if (j > 0 && i + 1 < b.nx) y[a] -= f[(3 * D + a) * Tn] * rp[(col - b.nx + 1) * D + a];
+        if (i > 0) y[a] -= f[(4 * D + a) * Tn] * rp[(col - 1) * D + a];
+#pragma unroll
+        for (int c2 = 0; c2 < a; ++c2) y[a] -= f[(5 * D + a * (a - 1) / 2 + c2) * Tn] * y[c2];
+      }
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        rp[col * D + a] = y[a];
+        Lb[a * nc + cp] = y[a];
+      }
+    }
+    __syncthreads();
+  }
+  cp_wait<0>();
+}
+
+// Backward sweep of the staged pair: steps in reverse, each thread's x0 (the forward result),
+// upper factors, coordinates and scatter target (grid cell of an owned cell, else -1) copied
+// SG - 1 steps ahead.  Nothing a copy needs depends on a staged value, so a step's copies are
+// issued before it waits.
+template <class T, int D, class V, int SG>
+__global__ void __launch_bounds__(DENSE_THREADS, 1) ras_bwd_stage_kernel(const long long* __restrict__ cell_off,
+                                                                       const int* __restrict__ dims,
+                                                                       const int* __restrict__ lpt,
+                                                                       const T* __restrict__ F, const T* __restrict__ loc,
+                                                                       T* ring_g, int ring_in_smem, int max_cols,
+                                                                       long long N, const long long* __restrict__ go_p,
+                                                                       const int* __restrict__ ijk, V* __restrict__ z,
+                                                                       int stage_off) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int sd = lpt[blockIdx.x];
+  const SweepBox b = sweep_box(cell_off, dims, sd);
+  const size_t ring_bytes = ring_in_smem ? ((4 * (size_t)max_cols * D * sizeof(T) + 15) / 16 * 16) : 0;
+  T* ring = ring_in_smem ? (T*)smem : ring_g + (size_t)blockIdx.x * 4 * max_cols * D;
+  int* lvl = (int*)(smem + ring_bytes);
+  int* rowoff = lvl + b.levels + 1;
+  build_tables(b, lvl, rowoff);
+  constexpr int Q = 10 * D + D * D, U = 5 * D + D * D, NB = 5 * D + D * (D + 1) / 2;
+  const int Tn = blockDim.x, t = threadIdx.x;
+  T* sF = (T*)(smem + stage_off);                         // [SG][NB][Tn] upper factors, then U's diagonal block
+  T* sX = sF + (size_t)SG * NB * Tn;                      // [SG][D][Tn] forward result
+  long long* sG = (long long*)(sX + (size_t)SG * D * Tn); // [SG][Tn] scatter target
+  int* sI = (int*)(sG + (size_t)SG * Tn);                 // [SG][Tn] packed (i, j, k)
+  const T* Fb = F + b.base * Q;
+  const T* Lb = loc + b.base * D;
+  const long long* go = go_p + b.base;
+  const int* cells = ijk + b.base;
+  const long long nc = b.nc;
+  // (a, c >= a) of the d x d upper block -> its slot after the 5 d off-diagonal ones
+  auto uslot = [](int a, int c) { return 5 * D + a * D - a * (a - 1) / 2 + (c - a); };
+  auto issue = [&](int n) {  // n-th step of the backward order (level levels - 1 - n) into slot n % SG
+    const int L = b.levels - 1 - n, s = n % SG;
+    if (L >= 0 && t < lvl[L + 1] - lvl[L]) {
+      const long long cp = lvl[L] + t;
+      cp_async<4>(sI + s * Tn + t, cells + cp);
+      cp_async<8>(sG + s * Tn + t, go + cp);
+#pragma unroll
+      for (int a = 0; a < D; ++a) cp_async<sizeof(T)>(sX + (s * D + a) * Tn + t, Lb + a * nc + cp);
+#pragma unroll
+      for (int q = 0; q < 5 * D; ++q) cp_async<sizeof(T)>(sF + (s * NB + q) * Tn + t, Fb + (U + q) * nc + cp);
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int c = a; c < D; ++c)
+          cp_async<sizeof(T)>(sF + (s * NB + uslot(a, c)) * Tn + t, Fb + (5 * D + a * D + c) * nc + cp);
+    }
+    cp_commit();
+  };
+  for (int n = 0; n < SG - 1; ++n) issue(n);
+  for (int n = 0; n < b.levels; ++n) {
+    issue(n + SG - 1);  // into the slot step n - 1 used
+    cp_wait<SG - 1>();  // step n's group has landed
+    const int L = b.levels - 1 - n, s = n % SG;
+    if (t < lvl[L + 1] - lvl[L]) {
+      const int c = sI[s * Tn + t];
+      const int i = c & 1023, j = (c >> 10) & 1023, k = c >> 20, col = j * b.nx + i;
+      T* rp = ring + (size_t)((k & 3) * b.ncols) * D;
+      const T* r1 = ring + (size_t)(((k + 1) & 3) * b.ncols + col) * D;
+      const T* f = sF + s * NB * Tn + t;
+      T x[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) x[a] = sX[(s * D + a) * Tn + t];
+#pragma unroll
+      for (int a = D - 1; a >= 0; --a) {
+#pragma unroll
+        for (int c2 = a + 1; c2 < D; ++c2) x[a] -= f[uslot(a, c2) * Tn] * x[c2];
+        if (i + 1 < b.nx) x[a] -= f[(0 * D + a) * Tn] * rp[(col + 1) * D + a];
+        if (i > 0 && j + 1 < b.ny) x[a] -= f[(1 * D + a) * Tn] * rp[(col + b.nx - 1) * D + a];
+        if (j + 1 < b.ny) x[a] -= f[(2 * D + a) * Tn] * rp[(col + b.nx) * D + a];
+        if (i + 1 < b.nx && j + 1 < b.ny) x[a] -= f[(3 * D + a) * Tn] * rp[(col + b.nx + 1) * D + a];
+        if (k + 1 < b.nz) x[a] -= f[(4 * D + a) * Tn] * r1[a];
+        x[a] /= f[uslot(a, a) * Tn];
+      }
+#pragma unroll
+      for (int a = 0; a < D; ++a) rp[col * D + a] = x[a];
+      const long long g = sG[s * Tn + t];
+      if (g >= 0) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) z[a * N + g] = (V)x[a];
+      }
+    }
+    __syncthreads();
+  }
+  cp_wait<0>();
+}
+
 template <class T, int D, class V>
 static fv_status ras_apply_t(const fv_system* s, const V* r, V* z, cudaStream_t st) {
   const Subdomains& S = s->subs;
@@ -785,8 +1006,20 @@ static fv_status ras_apply_t(const fv_system* s, const V* r, V* z, cudaStream_t 
     ProfScope ps(pf, st);
     {
       bool piped = false;
+      if constexpr (D == 2) {
+        const int so = (int)S.stage_off;
+        if (S.stage == 8)
+          ras_fwd_stage_kernel<T, D, V, 8><<<S.count, S.dense_threads, S.stage_smem, st>>>(
+              S.cell_off, S.dims, S.lpt, (const T*)S.F, loc, (T*)S.ring, S.ring_in_smem, S.max_cols, N, S.gmap_p,
+              S.ijk, r, so);
+        else if (S.stage == 4)
+          ras_fwd_stage_kernel<T, D, V, 4><<<S.count, S.dense_threads, S.stage_smem, st>>>(
+              S.cell_off, S.dims, S.lpt, (const T*)S.F, loc, (T*)S.ring, S.ring_in_smem, S.max_cols, N, S.gmap_p,
+              S.ijk, r, so);
+        piped = S.stage != 0;
+      }
       if constexpr (sizeof(T) == 4 || D < 7) {
-        if (S.dense_single) {
+        if (S.dense_single && !piped) {
           ras_fwd_pipe_kernel<T, D, V><<<S.count, S.dense_threads, S.smem, st>>>(
               S.cell_off, S.dims, S.lpt, (const T*)S.F, loc, (T*)S.ring, S.ring_in_smem, S.max_cols, N, S.gmap_p,
               S.ijk, r);
@@ -803,8 +1036,20 @@ static fv_status ras_apply_t(const fv_system* s, const V* r, V* z, cudaStream_t 
     ProfScope ps(pb, st);
     {
       bool piped = false;
+      if constexpr (D == 2) {
+        const int so = (int)S.stage_off;
+        if (S.stage == 8)
+          ras_bwd_stage_kernel<T, D, V, 8><<<S.count, S.dense_threads, S.stage_smem, st>>>(
+              S.cell_off, S.dims, S.lpt, (const T*)S.F, loc, (T*)S.ring, S.ring_in_smem, S.max_cols, N, S.go, S.ijk,
+              z, so);
+        else if (S.stage == 4)
+          ras_bwd_stage_kernel<T, D, V, 4><<<S.count, S.dense_threads, S.stage_smem, st>>>(
+              S.cell_off, S.dims, S.lpt, (const T*)S.F, loc, (T*)S.ring, S.ring_in_smem, S.max_cols, N, S.go, S.ijk,
+              z, so);
+        piped = S.stage != 0;
+      }
       if constexpr (sizeof(T) == 4 || D < 7) {
-        if (S.dense_single) {
+        if (S.dense_single && !piped) {
           ras_bwd_pipe_kernel<T, D, V><<<S.count, S.dense_threads, S.smem, st>>>(
               S.cell_off, S.dims, S.lpt, (const T*)S.F, loc, (T*)S.ring, S.ring_in_smem, S.max_cols, N, S.gmap_p,
               S.owned_p, S.ijk, z);
@@ -831,6 +1076,12 @@ static fv_status set_smem_attr(int limit) {
     FV_CUDA(cudaFuncSetAttribute(ras_fwd_pipe_kernel<T, D, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
     FV_CUDA(cudaFuncSetAttribute(ras_bwd_pipe_kernel<T, D, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
   }
+  if constexpr (D == 2) {
+    FV_CUDA(cudaFuncSetAttribute(ras_fwd_stage_kernel<T, D, T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    FV_CUDA(cudaFuncSetAttribute(ras_bwd_stage_kernel<T, D, T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    FV_CUDA(cudaFuncSetAttribute(ras_fwd_stage_kernel<T, D, T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    FV_CUDA(cudaFuncSetAttribute(ras_bwd_stage_kernel<T, D, T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+  }
   return FV_OK;
 }
 
@@ -839,7 +1090,8 @@ fv_status sweeps_smem_attr(const fv_system* s) {
   int dev = 0, limit = 0;
   FV_CUDA(cudaGetDevice(&dev));
   FV_CUDA(cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  if (S.smem > (size_t)limit) return set_error("fv_assemble_system: sweep tables exceed shared memory"), FV_EINVAL;
+  if (S.smem > (size_t)limit || S.stage_smem > (size_t)limit)
+    return set_error("fv_assemble_system: sweep tables exceed shared memory"), FV_EINVAL;
   if (S.d == 2) return S.fp32 ? set_smem_attr<float, 2>(limit) : set_smem_attr<double, 2>(limit);
   return S.fp32 ? set_smem_attr<float, 7>(limit) : set_smem_attr<double, 7>(limit);
 }

@@ -52,12 +52,15 @@ def test_apply_matches_oracle(fv, kind, Ns, Nr):
     fv.fv_free_grid(g)
 
 
-# boxes whose widest wavefront step fits the CTA (<= 384 cells) take the pipelined level-mapped
-# sweeps; 42 x 42 x 24 (504 cells in a step) the level-mapped sweeps with several cells a thread
+# Sweep variants: VTBE (kind 0) boxes whose widest wavefront step fits the CTA (<= 384 cells) take the
+# register-pipelined level-mapped sweeps.  PPBE boxes of that kind take the shared-memory staged sweeps,
+# 8 steps deep (the small cases) or 4 (40 x 4: 42 x 42 x 4 boxes, 96 threads), or the register-pipelined
+# ones when no 4-deep stage ring fits (32 x 12 with overlap 2: 36 x 36 x 12 boxes, 224 threads, 218 KB).
+# 42 x 42 x 24 (504 cells in a step) takes the level-mapped sweeps with several cells a thread.
 @pytest.mark.parametrize('kind,Ns,Nr,parts,delta', [(0, 8, 6, (2, 2, 2), 1), (1, 10, 8, (3, 2, 2), 2),
                                                      (1, 8, 8, (1, 1, 1), 1), (0, 9, 5, (2, 3, 1), 2),
                                                      (1, 16, 12, (1, 1, 1), 1), (1, 40, 4, (1, 1, 1), 1),
-                                                     (1, 40, 24, (1, 1, 1), 1)])
+                                                     (1, 32, 12, (1, 1, 1), 2), (1, 40, 24, (1, 1, 1), 1)])
 def test_one_level_ras_matches_oracle(fv, kind, Ns, Nr, parts, delta):
     """z = M_one^{-1} r (level-scheduled ILU(0) sweeps) vs the oracle's sequential ILU(0)."""
     A, d, _ = _oracle_matrix(kind, Ns, Nr)
