@@ -114,7 +114,8 @@ struct Subdomains {
   int stage = 0;                  // d = 2: depth of the shared-memory staged sweeps (8 or 4), 0 = not used
   size_t stage_off = 0;           // offset of the stage ring in dynamic shared memory
   size_t stage_smem = 0;          // dynamic shared memory of the staged sweeps
-  long long* go = nullptr;        // [total_cells] packed: grid cell of an owned cell, else -1 (staged sweeps)
+  void* blk_f = nullptr;          // [total_cells] staged sweeps: forward operand block per packed position
+  void* blk_b = nullptr;          // [total_cells] staged sweeps: backward operand block per packed position
 };
 
 }  // namespace fv

@@ -325,11 +325,49 @@ __global__ void repack_kernel(int d, int count, const long long* __restrict__ ce
   }
 }
 
-// scatter target of every packed position: the grid cell when the box owns it, else -1
-__global__ void scatter_target_kernel(long long n, const long long* __restrict__ gmap_p,
-                                      const unsigned char* __restrict__ owned_p, long long* __restrict__ go) {
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
-    go[c] = owned_p[c] ? gmap_p[c] : -1;
+// Per-cell operand blocks of the staged d = 2 sweeps (packed position order, 16-byte multiples so a
+// thread stages its cell's block with 16-byte copies).  Forward: the 5 d lower off-diagonal slots
+// (slot s, component a at s d + a), then L's strictly lower diagonal-block entry (1, 0), then the packed
+// (i, j, k).  Backward: the 5 d upper slots, then U's diagonal block (0,0), (0,1), (1,1), the packed
+// (i, j, k) and the scatter target (grid cell of an owned cell, else -1).
+template <class T>
+struct alignas(16) FwdBlk {
+  T f[11];
+  int ijk;
+};
+template <class T>
+struct alignas(16) BwdBlk {
+  T f[13];
+  int ijk;
+  long long go;
+};
+static_assert(sizeof(FwdBlk<float>) == 48 && sizeof(BwdBlk<float>) == 64, "block layout");
+static_assert(sizeof(FwdBlk<double>) == 96 && sizeof(BwdBlk<double>) == 128, "block layout");
+
+template <class T>
+__global__ void stage_pack_kernel(int count, const long long* __restrict__ cell_off, const T* __restrict__ F,
+                                  const int* __restrict__ ijk, const long long* __restrict__ gmap_p,
+                                  const unsigned char* __restrict__ owned_p, FwdBlk<T>* __restrict__ bf,
+                                  BwdBlk<T>* __restrict__ bb) {
+  constexpr int D = 2, Q = 10 * D + D * D, U = 5 * D + D * D;
+  const long long total = cell_off[count];
+  for (long long C = blockIdx.x * (long long)blockDim.x + threadIdx.x; C < total;
+       C += (long long)gridDim.x * blockDim.x) {
+    const int sd = find_subdomain(cell_off, count, C);
+    const long long base = cell_off[sd], nc = cell_off[sd + 1] - base;
+    const T* Fs = F + base * Q + (C - base);
+    FwdBlk<T> f{};
+    BwdBlk<T> g{};
+    for (int q = 0; q < 5 * D; ++q) f.f[q] = Fs[q * nc], g.f[q] = Fs[(U + q) * nc];
+    f.f[5 * D] = Fs[(5 * D + 1 * D + 0) * nc];
+    g.f[5 * D + 0] = Fs[(5 * D + 0 * D + 0) * nc];
+    g.f[5 * D + 1] = Fs[(5 * D + 0 * D + 1) * nc];
+    g.f[5 * D + 2] = Fs[(5 * D + 1 * D + 1) * nc];
+    f.ijk = g.ijk = ijk[C];
+    g.go = owned_p[C] ? gmap_p[C] : -1;
+    bf[C] = f;
+    bb[C] = g;
+  }
 }
 
 constexpr int DENSE_THREADS = 384;  // CTA size bound of the generic sweeps (170 registers per thread)
@@ -400,11 +438,13 @@ fv_status prepare_sweeps(fv_system* s, int fp32) {
     if (!S.ring) return set_error("fv_assemble_system: allocation of the sweep ring failed"), FV_ENOMEM;
   }
   // d = 2 boxes whose steps fit the CTA: the shared-memory staged sweeps, 8 (else 4) steps deep when
-  // the stage ring fits beside the 4-plane ring and the tables (per thread and slot: the forward's
-  // 11 or the backward's 13 factors, d vector values, an 8-byte cell map entry, packed (i, j, k))
+  // the stage ring fits beside the 4-plane ring and the tables (per thread and slot: the forward's block,
+  // d right-hand side values and an 8-byte cell map entry, or the backward's block and d values)
   S.stage = 0;
-  if (d == 2 && S.dense_single) {
-    const size_t per = (size_t)S.dense_threads * ((5 * d + d * (d + 1) / 2) * es + d * es + 8 + 4);
+  if (d == 2 && S.dense_single && S.ring_in_smem) {
+    const size_t fwd = (fp32 ? sizeof(FwdBlk<float>) : sizeof(FwdBlk<double>)) + d * es + 8;
+    const size_t bwd = (fp32 ? sizeof(BwdBlk<float>) : sizeof(BwdBlk<double>)) + d * es;
+    const size_t per = (size_t)S.dense_threads * std::max(fwd, bwd);
     const size_t off = (S.smem + 15) / 16 * 16;
     for (int sg : {8, 4})
       if (off + sg * per <= 200 * 1024) {
@@ -412,9 +452,18 @@ fv_status prepare_sweeps(fv_system* s, int fp32) {
         break;
       }
     if (S.stage) {
-      S.go = dalloc<long long>(s, S.total_cells);
-      if (!S.go) return set_error("fv_assemble_system: allocation of the sweep scatter map failed"), FV_ENOMEM;
-      scatter_target_kernel<<<blocks, 256>>>(S.total_cells, S.gmap_p, S.owned_p, S.go);
+      if (fp32) {
+        S.blk_f = dalloc<FwdBlk<float>>(s, S.total_cells), S.blk_b = dalloc<BwdBlk<float>>(s, S.total_cells);
+        if (S.blk_f && S.blk_b)
+          stage_pack_kernel<float><<<blocks, 256>>>(S.count, S.cell_off, (const float*)S.F, S.ijk, S.gmap_p,
+                                                    S.owned_p, (FwdBlk<float>*)S.blk_f, (BwdBlk<float>*)S.blk_b);
+      } else {
+        S.blk_f = dalloc<FwdBlk<double>>(s, S.total_cells), S.blk_b = dalloc<BwdBlk<double>>(s, S.total_cells);
+        if (S.blk_f && S.blk_b)
+          stage_pack_kernel<double><<<blocks, 256>>>(S.count, S.cell_off, (const double*)S.F, S.ijk, S.gmap_p,
+                                                     S.owned_p, (FwdBlk<double>*)S.blk_f, (BwdBlk<double>*)S.blk_b);
+      }
+      if (!S.blk_f || !S.blk_b) return set_error("fv_assemble_system: allocation of the sweep blocks failed"), FV_ENOMEM;
       FV_CUDA(cudaGetLastError());
       FV_CUDA(cudaDeviceSynchronize());
     }
@@ -441,21 +490,32 @@ __device__ __forceinline__ SweepBox sweep_box(const long long* cell_off, const i
   return b;
 }
 
-// level start offsets and per-(level, row) offsets of the wavefront order
+// level start offsets and per-(level, row) offsets of the wavefront order (rowoff == nullptr: levels only)
 __device__ __forceinline__ void build_tables(const SweepBox& b, int* lvl, int* rowoff) {
   for (int L = threadIdx.x; L < b.levels; L += blockDim.x) {
     int cnt = 0;
     for (int j = 0; j < b.ny; ++j) {
-      rowoff[L * b.ny + j] = cnt;
+      if (rowoff) rowoff[L * b.ny + j] = cnt;
       const int lo = max(0, L - 2 * j - (b.nz - 1)), hi = min(b.nx - 1, L - 2 * j);
       if (hi >= lo) cnt += hi - lo + 1;
     }
     lvl[L + 1] = cnt;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    lvl[0] = 0;
-    for (int L = 0; L < b.levels; ++L) lvl[L + 1] += lvl[L];
+  if (threadIdx.x < 32) {  // prefix sum of the step sizes by warp 0, each lane over a contiguous chunk
+    const int lane = threadIdx.x, per = (b.levels + 31) / 32;
+    const int lo = min(b.levels, lane * per), hi = min(b.levels, lo + per);
+    int sum = 0;
+    for (int L = lo; L < hi; ++L) sum += lvl[L + 1];
+    int inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += v;
+    }
+    int run = inc - sum;
+    for (int L = lo; L < hi; ++L) lvl[L + 1] = run += lvl[L + 1];
+    if (lane == 0) lvl[0] = 0;
   }
   __syncthreads();
 }
@@ -660,8 +720,7 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_fwd_pipe_kernel(const lo
   const size_t ring_bytes = ring_in_smem ? ((4 * (size_t)max_cols * D * sizeof(T) + 15) / 16 * 16) : 0;
   T* ring = ring_in_smem ? (T*)smem : ring_g + (size_t)blockIdx.x * 4 * max_cols * D;
   int* lvl = (int*)(smem + ring_bytes);
-  int* rowoff = lvl + b.levels + 1;
-  build_tables(b, lvl, rowoff);
+  build_tables(b, lvl, nullptr);
   constexpr int Q = 10 * D + D * D;
   const T* Fb = F + b.base * Q;
   T* Lb = loc + b.base * D;
@@ -737,8 +796,7 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_bwd_pipe_kernel(const lo
   const size_t ring_bytes = ring_in_smem ? ((4 * (size_t)max_cols * D * sizeof(T) + 15) / 16 * 16) : 0;
   T* ring = ring_in_smem ? (T*)smem : ring_g + (size_t)blockIdx.x * 4 * max_cols * D;
   int* lvl = (int*)(smem + ring_bytes);
-  int* rowoff = lvl + b.levels + 1;
-  build_tables(b, lvl, rowoff);
+  build_tables(b, lvl, nullptr);
   constexpr int Q = 10 * D + D * D, U = 5 * D + D * D;
   const int* cells = ijk + b.base;
   const T* Fb = F + b.base * Q;
@@ -799,103 +857,110 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_bwd_pipe_kernel(const lo
   }
 }
 
-// Shared-memory staged sweeps (d = 2 boxes whose widest step fits the CTA): every thread copies
-// its own cell's factors, right-hand side and packed coordinates for the step SG - 1 ahead into
-// a slot of an SG-deep ring with cp.async (one commit group a step) and reads them back after
-// waiting for that step's group, so SG - 1 steps of load latency overlap the step in progress at
-// no register cost.  A thread reads only what it copied itself: the wait orders it, no barrier.
-// Slot element e of thread t sits at [(slot * n + e) * blockDim + t] (no bank conflicts).
+// Shared-memory staged sweeps (d = 2 boxes whose widest step fits the CTA): every thread copies its
+// own cell's operand block (FwdBlk / BwdBlk) and vector values for the step SG - 1 ahead into a slot
+// of an SG-deep ring with cp.async (one commit group a step) and reads them back after waiting for
+// that step's group, so SG - 1 steps of load latency overlap the step in progress at no register
+// cost, with a few 16-byte copies a cell.  A thread reads only what it copied itself: the wait orders
+// it, and the step keeps one barrier (for the 4-plane ring).  Chunk c of thread t's block in slot s
+// sits at 16-byte element (s * nchunks + c) * blockDim + t (no bank conflicts); the forward result
+// is kept per cell, [cell][d], so the backward sweep stages it with one copy.
 template <int B>
 __device__ __forceinline__ void cp_async(void* dst, const void* src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
   const size_t g = __cvta_generic_to_global(src);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(g), "n"(B) : "memory");
+  if constexpr (B == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(g) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(g), "n"(B) : "memory");
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-template <class T, int D, class V, int SG>
+template <class Blk>
+union StagedBlk {
+  Blk b;
+  uint4 u[sizeof(Blk) / 16];
+};
+
+template <class T, class V, int SG>
 __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_fwd_stage_kernel(const long long* __restrict__ cell_off,
                                                                        const int* __restrict__ dims,
                                                                        const int* __restrict__ lpt,
-                                                                       const T* __restrict__ F, T* __restrict__ loc,
-                                                                       T* ring_g, int ring_in_smem, int max_cols,
-                                                                       long long N, const long long* __restrict__ gmap_p,
-                                                                       const int* __restrict__ ijk,
+                                                                       const FwdBlk<T>* __restrict__ blk,
+                                                                       T* __restrict__ loc, int max_cols, long long N,
+                                                                       const long long* __restrict__ gmap_p,
                                                                        const V* __restrict__ r, int stage_off) {
+  constexpr int D = 2, NC = sizeof(FwdBlk<T>) / 16;
   extern __shared__ __align__(16) unsigned char smem[];
   const int sd = lpt[blockIdx.x];
   const SweepBox b = sweep_box(cell_off, dims, sd);
-  const size_t ring_bytes = ring_in_smem ? ((4 * (size_t)max_cols * D * sizeof(T) + 15) / 16 * 16) : 0;
-  T* ring = ring_in_smem ? (T*)smem : ring_g + (size_t)blockIdx.x * 4 * max_cols * D;
+  const int ring_bytes = (4 * max_cols * D * (int)sizeof(T) + 15) / 16 * 16;
+  T* ring = (T*)smem;  // the 4-plane ring: the staged sweeps run only where it fits in shared memory
   int* lvl = (int*)(smem + ring_bytes);
-  int* rowoff = lvl + b.levels + 1;
-  build_tables(b, lvl, rowoff);
-  constexpr int Q = 10 * D + D * D, NF = 5 * D + D * (D - 1) / 2;
+  build_tables(b, lvl, nullptr);
   const int Tn = blockDim.x, t = threadIdx.x;
-  T* sF = (T*)(smem + stage_off);                         // [SG][NF][Tn] lower factors
-  V* sY = (V*)(sF + (size_t)SG * NF * Tn);                // [SG][D][Tn] gathered right-hand side
+  uint4* sB = (uint4*)(smem + stage_off);                 // [SG][NC][Tn] operand blocks
+  V* sY = (V*)(sB + (size_t)SG * NC * Tn);                // [SG][D][Tn] gathered right-hand side
   long long* sG = (long long*)(sY + (size_t)SG * D * Tn); // [SG][Tn] cell map entry SG - 1 steps later
-  int* sI = (int*)(sG + (size_t)SG * Tn);                 // [SG][Tn] packed (i, j, k)
-  const T* Fb = F + b.base * Q;
+  const FwdBlk<T>* Bb = blk + b.base;
   T* Lb = loc + b.base * D;
   const long long* gm = gmap_p + b.base;
-  const int* cells = ijk + b.base;
-  const long long nc = b.nc;
   auto cnt_of = [&](int L) { return L < b.levels ? lvl[L + 1] - lvl[L] : 0; };
   // step g into slot g % SG (gg: this thread's cell map entry in step g), and the cell map entry of
   // step g + SG - 1, which the copies of that step need for the gather
   auto issue = [&](int g, long long gg) {
     const int s = g % SG;
     if (t < cnt_of(g)) {
-      const long long cp = lvl[g] + t;
-      cp_async<4>(sI + s * Tn + t, cells + cp);
+      const uint4* src = reinterpret_cast<const uint4*>(Bb + lvl[g] + t);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) cp_async<16>(sB + (s * NC + c) * Tn + t, src + c);
 #pragma unroll
       for (int a = 0; a < D; ++a) {
         if (gg >= 0) cp_async<sizeof(V)>(sY + (s * D + a) * Tn + t, r + a * N + gg);
         else sY[(s * D + a) * Tn + t] = V(0);
       }
-#pragma unroll
-      for (int q = 0; q < 5 * D; ++q) cp_async<sizeof(T)>(sF + (s * NF + q) * Tn + t, Fb + q * nc + cp);
-#pragma unroll
-      for (int a = 1; a < D; ++a)
-#pragma unroll
-        for (int c = 0; c < a; ++c)
-          cp_async<sizeof(T)>(sF + (s * NF + 5 * D + a * (a - 1) / 2 + c) * Tn + t, Fb + (5 * D + a * D + c) * nc + cp);
     }
     const int h = g + SG - 1;
     if (t < cnt_of(h)) cp_async<8>(sG + s * Tn + t, gm + lvl[h] + t);
     cp_commit();
   };
-  for (int g = 0; g < SG - 1; ++g) issue(g, t < cnt_of(g) ? gm[lvl[g] + t] : -1);
+  {  // the first SG - 1 steps' cell map entries, loaded together before any copy is issued
+    long long g0[SG - 1];
+#pragma unroll
+    for (int g = 0; g < SG - 1; ++g) g0[g] = t < cnt_of(g) ? gm[lvl[g] + t] : -1;
+#pragma unroll
+    for (int g = 0; g < SG - 1; ++g) issue(g, g0[g]);
+  }
   for (int L = 0; L < b.levels; ++L) {
     cp_wait<SG - 2>();  // step L's group has landed (the SG - 2 later ones may be in flight)
     const int s = L % SG;
     issue(L + SG - 1, t < cnt_of(L + SG - 1) ? sG[s * Tn + t] : -1);  // into the slot step L - 1 used
     if (t < cnt_of(L)) {
-      const int c = sI[s * Tn + t];
-      const int i = c & 1023, j = (c >> 10) & 1023, k = c >> 20, col = j * b.nx + i;
-      const long long cp = lvl[L] + t;
-      T* rp = ring + (size_t)((k & 3) * b.ncols) * D;
-      const T* r0 = ring + (size_t)(((k - 1) & 3) * b.ncols + col) * D;
-      const T* f = sF + s * NF * Tn + t;
+      StagedBlk<FwdBlk<T>> q;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) q.u[c] = sB[(s * NC + c) * Tn + t];
+      const T* f = q.b.f;
+      const int i = q.b.ijk & 1023, j = (q.b.ijk >> 10) & 1023, k = q.b.ijk >> 20, col = j * b.nx + i;
+      T* rp = ring + ((k & 3) * b.ncols) * D;
+      const T* r0 = ring + (((k - 1) & 3) * b.ncols + col) * D;
       T y[D];
 #pragma unroll
       for (int a = 0; a < D; ++a) {
         y[a] = (T)sY[(s * D + a) * Tn + t];
-        if (k > 0) y[a] -= f[(0 * D + a) * Tn] * r0[a];
-        if (i > 0 && j > 0) y[a] -= f[(1 * D + a) * Tn] * rp[(col - b.nx - 1) * D + a];
-        if (j > 0) y[a] -= f[(2 * D + a) * Tn] * rp[(col - b.nx) * D + a];
-        if (j > 0 && i + 1 < b.nx) y[a] -= f[(3 * D + a) * Tn] * rp[(col - b.nx + 1) * D + a];
-        if (i > 0) y[a] -= f[(4 * D + a) * Tn] * rp[(col - 1) * D + a];
-#pragma unroll
-        for (int c2 = 0; c2 < a; ++c2) y[a] -= f[(5 * D + a * (a - 1) / 2 + c2) * Tn] * y[c2];
+        if (k > 0) y[a] -= f[0 * D + a] * r0[a];
+        if (i > 0 && j > 0) y[a] -= f[1 * D + a] * rp[(col - b.nx - 1) * D + a];
+        if (j > 0) y[a] -= f[2 * D + a] * rp[(col - b.nx) * D + a];
+        if (j > 0 && i + 1 < b.nx) y[a] -= f[3 * D + a] * rp[(col - b.nx + 1) * D + a];
+        if (i > 0) y[a] -= f[4 * D + a] * rp[(col - 1) * D + a];
       }
+      y[1] -= f[5 * D] * y[0];
+      const long long cp = lvl[L] + t;
 #pragma unroll
       for (int a = 0; a < D; ++a) {
         rp[col * D + a] = y[a];
-        Lb[a * nc + cp] = y[a];
+        Lb[cp * D + a] = y[a];
       }
     }
     __syncthreads();
@@ -903,55 +968,38 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_fwd_stage_kernel(const l
   cp_wait<0>();
 }
 
-// Backward sweep of the staged pair: steps in reverse, each thread's x0 (the forward result),
-// upper factors, coordinates and scatter target (grid cell of an owned cell, else -1) copied
-// SG - 1 steps ahead.  Nothing a copy needs depends on a staged value, so a step's copies are
-// issued before it waits.
-template <class T, int D, class V, int SG>
+// Backward sweep of the staged pair: steps in reverse; each thread's block and its cell's forward
+// result are copied SG - 1 steps ahead.  Nothing a copy needs depends on a staged value, so a step's
+// copies are issued before it waits.
+template <class T, class V, int SG>
 __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_bwd_stage_kernel(const long long* __restrict__ cell_off,
                                                                        const int* __restrict__ dims,
                                                                        const int* __restrict__ lpt,
-                                                                       const T* __restrict__ F, const T* __restrict__ loc,
-                                                                       T* ring_g, int ring_in_smem, int max_cols,
-                                                                       long long N, const long long* __restrict__ go_p,
-                                                                       const int* __restrict__ ijk, V* __restrict__ z,
-                                                                       int stage_off) {
+                                                                       const BwdBlk<T>* __restrict__ blk,
+                                                                       const T* __restrict__ loc, int max_cols,
+                                                                       long long N,
+                                                                       V* __restrict__ z, int stage_off) {
+  constexpr int D = 2, NC = sizeof(BwdBlk<T>) / 16;
   extern __shared__ __align__(16) unsigned char smem[];
   const int sd = lpt[blockIdx.x];
   const SweepBox b = sweep_box(cell_off, dims, sd);
-  const size_t ring_bytes = ring_in_smem ? ((4 * (size_t)max_cols * D * sizeof(T) + 15) / 16 * 16) : 0;
-  T* ring = ring_in_smem ? (T*)smem : ring_g + (size_t)blockIdx.x * 4 * max_cols * D;
+  const int ring_bytes = (4 * max_cols * D * (int)sizeof(T) + 15) / 16 * 16;
+  T* ring = (T*)smem;  // the 4-plane ring: the staged sweeps run only where it fits in shared memory
   int* lvl = (int*)(smem + ring_bytes);
-  int* rowoff = lvl + b.levels + 1;
-  build_tables(b, lvl, rowoff);
-  constexpr int Q = 10 * D + D * D, U = 5 * D + D * D, NB = 5 * D + D * (D + 1) / 2;
+  build_tables(b, lvl, nullptr);
   const int Tn = blockDim.x, t = threadIdx.x;
-  T* sF = (T*)(smem + stage_off);                         // [SG][NB][Tn] upper factors, then U's diagonal block
-  T* sX = sF + (size_t)SG * NB * Tn;                      // [SG][D][Tn] forward result
-  long long* sG = (long long*)(sX + (size_t)SG * D * Tn); // [SG][Tn] scatter target
-  int* sI = (int*)(sG + (size_t)SG * Tn);                 // [SG][Tn] packed (i, j, k)
-  const T* Fb = F + b.base * Q;
+  uint4* sB = (uint4*)(smem + stage_off);  // [SG][NC][Tn] operand blocks
+  T* sX = (T*)(sB + (size_t)SG * NC * Tn); // [SG][Tn][D] forward result
+  const BwdBlk<T>* Bb = blk + b.base;
   const T* Lb = loc + b.base * D;
-  const long long* go = go_p + b.base;
-  const int* cells = ijk + b.base;
-  const long long nc = b.nc;
-  // (a, c >= a) of the d x d upper block -> its slot after the 5 d off-diagonal ones
-  auto uslot = [](int a, int c) { return 5 * D + a * D - a * (a - 1) / 2 + (c - a); };
   auto issue = [&](int n) {  // n-th step of the backward order (level levels - 1 - n) into slot n % SG
     const int L = b.levels - 1 - n, s = n % SG;
     if (L >= 0 && t < lvl[L + 1] - lvl[L]) {
       const long long cp = lvl[L] + t;
-      cp_async<4>(sI + s * Tn + t, cells + cp);
-      cp_async<8>(sG + s * Tn + t, go + cp);
+      const uint4* src = reinterpret_cast<const uint4*>(Bb + cp);
 #pragma unroll
-      for (int a = 0; a < D; ++a) cp_async<sizeof(T)>(sX + (s * D + a) * Tn + t, Lb + a * nc + cp);
-#pragma unroll
-      for (int q = 0; q < 5 * D; ++q) cp_async<sizeof(T)>(sF + (s * NB + q) * Tn + t, Fb + (U + q) * nc + cp);
-#pragma unroll
-      for (int a = 0; a < D; ++a)
-#pragma unroll
-        for (int c = a; c < D; ++c)
-          cp_async<sizeof(T)>(sF + (s * NB + uslot(a, c)) * Tn + t, Fb + (5 * D + a * D + c) * nc + cp);
+      for (int c = 0; c < NC; ++c) cp_async<16>(sB + (s * NC + c) * Tn + t, src + c);
+      cp_async<D * sizeof(T)>(sX + ((size_t)s * Tn + t) * D, Lb + cp * D);
     }
     cp_commit();
   };
@@ -961,31 +1009,32 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_bwd_stage_kernel(const l
     cp_wait<SG - 1>();  // step n's group has landed
     const int L = b.levels - 1 - n, s = n % SG;
     if (t < lvl[L + 1] - lvl[L]) {
-      const int c = sI[s * Tn + t];
-      const int i = c & 1023, j = (c >> 10) & 1023, k = c >> 20, col = j * b.nx + i;
-      T* rp = ring + (size_t)((k & 3) * b.ncols) * D;
-      const T* r1 = ring + (size_t)(((k + 1) & 3) * b.ncols + col) * D;
-      const T* f = sF + s * NB * Tn + t;
+      StagedBlk<BwdBlk<T>> q;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) q.u[c] = sB[(s * NC + c) * Tn + t];
+      const T* f = q.b.f;
+      const int i = q.b.ijk & 1023, j = (q.b.ijk >> 10) & 1023, k = q.b.ijk >> 20, col = j * b.nx + i;
+      T* rp = ring + ((k & 3) * b.ncols) * D;
+      const T* r1 = ring + (((k + 1) & 3) * b.ncols + col) * D;
       T x[D];
 #pragma unroll
-      for (int a = 0; a < D; ++a) x[a] = sX[(s * D + a) * Tn + t];
+      for (int a = 0; a < D; ++a) x[a] = sX[((size_t)s * Tn + t) * D + a];
+      // U's diagonal block at f[5 d + 0, 1, 2] = (0,0), (0,1), (1,1)
 #pragma unroll
       for (int a = D - 1; a >= 0; --a) {
-#pragma unroll
-        for (int c2 = a + 1; c2 < D; ++c2) x[a] -= f[uslot(a, c2) * Tn] * x[c2];
-        if (i + 1 < b.nx) x[a] -= f[(0 * D + a) * Tn] * rp[(col + 1) * D + a];
-        if (i > 0 && j + 1 < b.ny) x[a] -= f[(1 * D + a) * Tn] * rp[(col + b.nx - 1) * D + a];
-        if (j + 1 < b.ny) x[a] -= f[(2 * D + a) * Tn] * rp[(col + b.nx) * D + a];
-        if (i + 1 < b.nx && j + 1 < b.ny) x[a] -= f[(3 * D + a) * Tn] * rp[(col + b.nx + 1) * D + a];
-        if (k + 1 < b.nz) x[a] -= f[(4 * D + a) * Tn] * r1[a];
-        x[a] /= f[uslot(a, a) * Tn];
+        if (a == 0) x[0] -= f[5 * D + 1] * x[1];
+        if (i + 1 < b.nx) x[a] -= f[0 * D + a] * rp[(col + 1) * D + a];
+        if (i > 0 && j + 1 < b.ny) x[a] -= f[1 * D + a] * rp[(col + b.nx - 1) * D + a];
+        if (j + 1 < b.ny) x[a] -= f[2 * D + a] * rp[(col + b.nx) * D + a];
+        if (i + 1 < b.nx && j + 1 < b.ny) x[a] -= f[3 * D + a] * rp[(col + b.nx + 1) * D + a];
+        if (k + 1 < b.nz) x[a] -= f[4 * D + a] * r1[a];
+        x[a] /= f[a == 0 ? 5 * D : 5 * D + 2];
       }
 #pragma unroll
       for (int a = 0; a < D; ++a) rp[col * D + a] = x[a];
-      const long long g = sG[s * Tn + t];
-      if (g >= 0) {
+      if (q.b.go >= 0) {
 #pragma unroll
-        for (int a = 0; a < D; ++a) z[a * N + g] = (V)x[a];
+        for (int a = 0; a < D; ++a) z[a * N + q.b.go] = (V)x[a];
       }
     }
     __syncthreads();
@@ -1008,14 +1057,13 @@ static fv_status ras_apply_t(const fv_system* s, const V* r, V* z, cudaStream_t 
       bool piped = false;
       if constexpr (D == 2) {
         const int so = (int)S.stage_off;
+        const FwdBlk<T>* bf = (const FwdBlk<T>*)S.blk_f;
         if (S.stage == 8)
-          ras_fwd_stage_kernel<T, D, V, 8><<<S.count, S.dense_threads, S.stage_smem, st>>>(
-              S.cell_off, S.dims, S.lpt, (const T*)S.F, loc, (T*)S.ring, S.ring_in_smem, S.max_cols, N, S.gmap_p,
-              S.ijk, r, so);
+          ras_fwd_stage_kernel<T, V, 8><<<S.count, S.dense_threads, S.stage_smem, st>>>(
+              S.cell_off, S.dims, S.lpt, bf, loc, S.max_cols, N, S.gmap_p, r, so);
         else if (S.stage == 4)
-          ras_fwd_stage_kernel<T, D, V, 4><<<S.count, S.dense_threads, S.stage_smem, st>>>(
-              S.cell_off, S.dims, S.lpt, (const T*)S.F, loc, (T*)S.ring, S.ring_in_smem, S.max_cols, N, S.gmap_p,
-              S.ijk, r, so);
+          ras_fwd_stage_kernel<T, V, 4><<<S.count, S.dense_threads, S.stage_smem, st>>>(
+              S.cell_off, S.dims, S.lpt, bf, loc, S.max_cols, N, S.gmap_p, r, so);
         piped = S.stage != 0;
       }
       if constexpr (sizeof(T) == 4 || D < 7) {
@@ -1038,14 +1086,13 @@ static fv_status ras_apply_t(const fv_system* s, const V* r, V* z, cudaStream_t 
       bool piped = false;
       if constexpr (D == 2) {
         const int so = (int)S.stage_off;
+        const BwdBlk<T>* bb = (const BwdBlk<T>*)S.blk_b;
         if (S.stage == 8)
-          ras_bwd_stage_kernel<T, D, V, 8><<<S.count, S.dense_threads, S.stage_smem, st>>>(
-              S.cell_off, S.dims, S.lpt, (const T*)S.F, loc, (T*)S.ring, S.ring_in_smem, S.max_cols, N, S.go, S.ijk,
-              z, so);
+          ras_bwd_stage_kernel<T, V, 8><<<S.count, S.dense_threads, S.stage_smem, st>>>(
+              S.cell_off, S.dims, S.lpt, bb, loc, S.max_cols, N, z, so);
         else if (S.stage == 4)
-          ras_bwd_stage_kernel<T, D, V, 4><<<S.count, S.dense_threads, S.stage_smem, st>>>(
-              S.cell_off, S.dims, S.lpt, (const T*)S.F, loc, (T*)S.ring, S.ring_in_smem, S.max_cols, N, S.go, S.ijk,
-              z, so);
+          ras_bwd_stage_kernel<T, V, 4><<<S.count, S.dense_threads, S.stage_smem, st>>>(
+              S.cell_off, S.dims, S.lpt, bb, loc, S.max_cols, N, z, so);
         piped = S.stage != 0;
       }
       if constexpr (sizeof(T) == 4 || D < 7) {
@@ -1077,10 +1124,10 @@ static fv_status set_smem_attr(int limit) {
     FV_CUDA(cudaFuncSetAttribute(ras_bwd_pipe_kernel<T, D, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
   }
   if constexpr (D == 2) {
-    FV_CUDA(cudaFuncSetAttribute(ras_fwd_stage_kernel<T, D, T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
-    FV_CUDA(cudaFuncSetAttribute(ras_bwd_stage_kernel<T, D, T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
-    FV_CUDA(cudaFuncSetAttribute(ras_fwd_stage_kernel<T, D, T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
-    FV_CUDA(cudaFuncSetAttribute(ras_bwd_stage_kernel<T, D, T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    FV_CUDA(cudaFuncSetAttribute(ras_fwd_stage_kernel<T, T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    FV_CUDA(cudaFuncSetAttribute(ras_bwd_stage_kernel<T, T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    FV_CUDA(cudaFuncSetAttribute(ras_fwd_stage_kernel<T, T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    FV_CUDA(cudaFuncSetAttribute(ras_bwd_stage_kernel<T, T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
   }
   return FV_OK;
 }
