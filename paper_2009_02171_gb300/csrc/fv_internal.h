@@ -113,6 +113,7 @@ struct Subdomains {
   int ring_in_smem = 0;
   int stage = 0;                  // d = 2: depth of the shared-memory staged sweeps (8 or 4), 0 = not used
   size_t stage_off = 0;           // offset of the stage ring in dynamic shared memory
+  int stage_pad = 0;              // zero padding (elements) on each side of the staged sweeps' 4-plane ring
   size_t stage_smem = 0;          // dynamic shared memory of the staged sweeps
   void* blk_f = nullptr;          // [total_cells] staged sweeps: forward operand block per packed position
   void* blk_b = nullptr;          // [total_cells] staged sweeps: backward operand block per packed position

@@ -445,7 +445,11 @@ fv_status prepare_sweeps(fv_system* s, int fp32) {
     const size_t fwd = (fp32 ? sizeof(FwdBlk<float>) : sizeof(FwdBlk<double>)) + d * es + 8;
     const size_t bwd = (fp32 ? sizeof(BwdBlk<float>) : sizeof(BwdBlk<double>)) + d * es;
     const size_t per = (size_t)S.dense_threads * std::max(fwd, bwd);
-    const size_t off = (S.smem + 15) / 16 * 16;
+    int max_nx = 0;
+    for (int sd = 0; sd < S.count; ++sd) max_nx = std::max(max_nx, dims[3 * sd]);
+    S.stage_pad = (max_nx + 1) * d;  // the ring's zero padding on each side (elements)
+    const size_t sring = ((4 * (size_t)S.max_cols * d + 2 * S.stage_pad) * es + 15) / 16 * 16;
+    const size_t off = (sring + tab + 15) / 16 * 16;
     for (int sg : {8, 4})
       if (off + sg * per <= 200 * 1024) {
         S.stage = sg, S.stage_off = off, S.stage_smem = off + sg * per;
@@ -864,7 +868,10 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_bwd_pipe_kernel(const lo
 // cost, with a few 16-byte copies a cell.  A thread reads only what it copied itself: the wait orders
 // it, and the step keeps one barrier (for the 4-plane ring).  Chunk c of thread t's block in slot s
 // sits at 16-byte element (s * nchunks + c) * blockDim + t (no bank conflicts); the forward result
-// is kept per cell, [cell][d], so the backward sweep stages it with one copy.
+// is kept per cell, [cell][d], so the backward sweep stages it with one copy.  The ring is zeroed
+// at launch and padded by `pad` >= (nx + 1) d elements on each side, so every neighbour is read
+// unconditionally: the factor slot of a neighbour outside the box is exactly zero (assembly writes
+// zero there and the factorization never updates it), and the ring holds only finite values.
 template <int B>
 __device__ __forceinline__ void cp_async(void* dst, const void* src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
@@ -889,17 +896,19 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_fwd_stage_kernel(const l
                                                                        const int* __restrict__ dims,
                                                                        const int* __restrict__ lpt,
                                                                        const FwdBlk<T>* __restrict__ blk,
-                                                                       T* __restrict__ loc, int max_cols, long long N,
+                                                                       T* __restrict__ loc, int max_cols, int pad,
+                                                                       long long N,
                                                                        const long long* __restrict__ gmap_p,
                                                                        const V* __restrict__ r, int stage_off) {
   constexpr int D = 2, NC = sizeof(FwdBlk<T>) / 16;
   extern __shared__ __align__(16) unsigned char smem[];
   const int sd = lpt[blockIdx.x];
   const SweepBox b = sweep_box(cell_off, dims, sd);
-  const int ring_bytes = (4 * max_cols * D * (int)sizeof(T) + 15) / 16 * 16;
-  T* ring = (T*)smem;  // the 4-plane ring: the staged sweeps run only where it fits in shared memory
+  const int ring_bytes = ((4 * max_cols * D + 2 * pad) * (int)sizeof(T) + 15) / 16 * 16;
+  T* ring = (T*)smem + pad;  // the padded 4-plane ring: the staged sweeps run only where it fits
   int* lvl = (int*)(smem + ring_bytes);
-  build_tables(b, lvl, nullptr);
+  for (int e = threadIdx.x; e < 4 * b.ncols * D + 2 * pad; e += blockDim.x) ((T*)smem)[e] = T(0);
+  build_tables(b, lvl, nullptr);  // its barriers also order the zeroing
   const int Tn = blockDim.x, t = threadIdx.x;
   uint4* sB = (uint4*)(smem + stage_off);                 // [SG][NC][Tn] operand blocks
   V* sY = (V*)(sB + (size_t)SG * NC * Tn);                // [SG][D][Tn] gathered right-hand side
@@ -949,11 +958,11 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_fwd_stage_kernel(const l
 #pragma unroll
       for (int a = 0; a < D; ++a) {
         y[a] = (T)sY[(s * D + a) * Tn + t];
-        if (k > 0) y[a] -= f[0 * D + a] * r0[a];
-        if (i > 0 && j > 0) y[a] -= f[1 * D + a] * rp[(col - b.nx - 1) * D + a];
-        if (j > 0) y[a] -= f[2 * D + a] * rp[(col - b.nx) * D + a];
-        if (j > 0 && i + 1 < b.nx) y[a] -= f[3 * D + a] * rp[(col - b.nx + 1) * D + a];
-        if (i > 0) y[a] -= f[4 * D + a] * rp[(col - 1) * D + a];
+        y[a] -= f[0 * D + a] * r0[a];
+        y[a] -= f[1 * D + a] * rp[(col - b.nx - 1) * D + a];
+        y[a] -= f[2 * D + a] * rp[(col - b.nx) * D + a];
+        y[a] -= f[3 * D + a] * rp[(col - b.nx + 1) * D + a];
+        y[a] -= f[4 * D + a] * rp[(col - 1) * D + a];
       }
       y[1] -= f[5 * D] * y[0];
       const long long cp = lvl[L] + t;
@@ -977,16 +986,17 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_bwd_stage_kernel(const l
                                                                        const int* __restrict__ lpt,
                                                                        const BwdBlk<T>* __restrict__ blk,
                                                                        const T* __restrict__ loc, int max_cols,
-                                                                       long long N,
+                                                                       int pad, long long N,
                                                                        V* __restrict__ z, int stage_off) {
   constexpr int D = 2, NC = sizeof(BwdBlk<T>) / 16;
   extern __shared__ __align__(16) unsigned char smem[];
   const int sd = lpt[blockIdx.x];
   const SweepBox b = sweep_box(cell_off, dims, sd);
-  const int ring_bytes = (4 * max_cols * D * (int)sizeof(T) + 15) / 16 * 16;
-  T* ring = (T*)smem;  // the 4-plane ring: the staged sweeps run only where it fits in shared memory
+  const int ring_bytes = ((4 * max_cols * D + 2 * pad) * (int)sizeof(T) + 15) / 16 * 16;
+  T* ring = (T*)smem + pad;  // the padded 4-plane ring: the staged sweeps run only where it fits
   int* lvl = (int*)(smem + ring_bytes);
-  build_tables(b, lvl, nullptr);
+  for (int e = threadIdx.x; e < 4 * b.ncols * D + 2 * pad; e += blockDim.x) ((T*)smem)[e] = T(0);
+  build_tables(b, lvl, nullptr);  // its barriers also order the zeroing
   const int Tn = blockDim.x, t = threadIdx.x;
   uint4* sB = (uint4*)(smem + stage_off);  // [SG][NC][Tn] operand blocks
   T* sX = (T*)(sB + (size_t)SG * NC * Tn); // [SG][Tn][D] forward result
@@ -1023,11 +1033,11 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_bwd_stage_kernel(const l
 #pragma unroll
       for (int a = D - 1; a >= 0; --a) {
         if (a == 0) x[0] -= f[5 * D + 1] * x[1];
-        if (i + 1 < b.nx) x[a] -= f[0 * D + a] * rp[(col + 1) * D + a];
-        if (i > 0 && j + 1 < b.ny) x[a] -= f[1 * D + a] * rp[(col + b.nx - 1) * D + a];
-        if (j + 1 < b.ny) x[a] -= f[2 * D + a] * rp[(col + b.nx) * D + a];
-        if (i + 1 < b.nx && j + 1 < b.ny) x[a] -= f[3 * D + a] * rp[(col + b.nx + 1) * D + a];
-        if (k + 1 < b.nz) x[a] -= f[4 * D + a] * r1[a];
+        x[a] -= f[0 * D + a] * rp[(col + 1) * D + a];
+        x[a] -= f[1 * D + a] * rp[(col + b.nx - 1) * D + a];
+        x[a] -= f[2 * D + a] * rp[(col + b.nx) * D + a];
+        x[a] -= f[3 * D + a] * rp[(col + b.nx + 1) * D + a];
+        x[a] -= f[4 * D + a] * r1[a];
         x[a] /= f[a == 0 ? 5 * D : 5 * D + 2];
       }
 #pragma unroll
@@ -1060,10 +1070,10 @@ static fv_status ras_apply_t(const fv_system* s, const V* r, V* z, cudaStream_t 
         const FwdBlk<T>* bf = (const FwdBlk<T>*)S.blk_f;
         if (S.stage == 8)
           ras_fwd_stage_kernel<T, V, 8><<<S.count, S.dense_threads, S.stage_smem, st>>>(
-              S.cell_off, S.dims, S.lpt, bf, loc, S.max_cols, N, S.gmap_p, r, so);
+              S.cell_off, S.dims, S.lpt, bf, loc, S.max_cols, S.stage_pad, N, S.gmap_p, r, so);
         else if (S.stage == 4)
           ras_fwd_stage_kernel<T, V, 4><<<S.count, S.dense_threads, S.stage_smem, st>>>(
-              S.cell_off, S.dims, S.lpt, bf, loc, S.max_cols, N, S.gmap_p, r, so);
+              S.cell_off, S.dims, S.lpt, bf, loc, S.max_cols, S.stage_pad, N, S.gmap_p, r, so);
         piped = S.stage != 0;
       }
       if constexpr (sizeof(T) == 4 || D < 7) {
@@ -1089,10 +1099,10 @@ static fv_status ras_apply_t(const fv_system* s, const V* r, V* z, cudaStream_t 
         const BwdBlk<T>* bb = (const BwdBlk<T>*)S.blk_b;
         if (S.stage == 8)
           ras_bwd_stage_kernel<T, V, 8><<<S.count, S.dense_threads, S.stage_smem, st>>>(
-              S.cell_off, S.dims, S.lpt, bb, loc, S.max_cols, N, z, so);
+              S.cell_off, S.dims, S.lpt, bb, loc, S.max_cols, S.stage_pad, N, z, so);
         else if (S.stage == 4)
           ras_bwd_stage_kernel<T, V, 4><<<S.count, S.dense_threads, S.stage_smem, st>>>(
-              S.cell_off, S.dims, S.lpt, bb, loc, S.max_cols, N, z, so);
+              S.cell_off, S.dims, S.lpt, bb, loc, S.max_cols, S.stage_pad, N, z, so);
         piped = S.stage != 0;
       }
       if constexpr (sizeof(T) == 4 || D < 7) {

@@ -1,4 +1,4 @@
-"""The bench's multi-rank logic on CPU: two gloo ranks (one process per GPU on a GPU machine).
+"""The bench's multi-rank logic on CPU: two gloo ranks (one process per GPU in a real run).
 
 bench.py runs one independent shell per rank (replicas, no collective on the data
 path); the ranks only agree on the time, which is the slowest rank's, and only rank 0
