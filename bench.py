@@ -480,9 +480,7 @@ def main():
             'precision': head,
             'arms': others,
             'learned': ({k: (round(v, 4) if isinstance(v, float) else v) for k, v in info.items()} if info else None),
-            'config': {'workload': WORKLOAD if not args.ns else WORKLOAD.replace(
-                           'shell 6x64^2x64 (1.57M cells)', 'shell 6x%d^2x%d (%d cells)' % (args.ns, args.ns, 6 * args.ns ** 3)).replace(
-                           'coarse 32', 'coarse %d' % (args.ns // 2)),
+            'config': {'workload': workload_name(args.ns),
                        'cells': 6 * c['Ns'] ** 2 * c['Nr'], 'subdomains': 6 * 16,
                        'overlap': c['overlap'], 'ppbe_levels': c['levels'], 'rtol': c['rtol'],
                        'restart': c['restart'], 'l2': 'working set > L2 (no flush needed)',
@@ -531,6 +529,13 @@ def network_flops(c):
     for l in range(L):
         f += 2 * 27 * 2 * C * C * cells[l]
     return f + 2 * 27 * C * 2 * cells[0]
+
+
+def workload_name(ns=0):
+    """The workload description, for the default 6 x 64^2 x 64 shell or a 6 x ns^2 x ns profiling case."""
+    if not ns:
+        return WORKLOAD
+    return WORKLOAD.replace('shell 6x64^2x64 (1.57M cells)', 'shell 6x%d^2x%d (%d cells)' % (ns, ns, 6 * ns ** 3))
 
 
 def algorithmic_bytes(cat, c, N, es):

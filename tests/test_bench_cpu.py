@@ -1,0 +1,39 @@
+"""Host-side logic of bench.py that needs no GPU: workload names, algorithmic bytes, measured-traffic sources."""
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_workload_name_of_a_profiling_size_keeps_the_precisions():
+    """--ns replaces the shell size only (not the '64' of 'FP64')."""
+    w = bench.workload_name(32)
+    assert w.startswith('shell 6x32^2x32 (196608 cells)')
+    assert 'FP64 residual' in w and 'FP64 outer FGMRES' in w
+    assert bench.workload_name(0) == bench.WORKLOAD
+
+
+def test_algorithmic_bytes_of_the_bench_categories():
+    """apply: read x and write y; the sweeps read more than the vector (factors) and the backward writes z."""
+    c = dict(bench.CFG)
+    N = 6 * c['Ns'] ** 2 * c['Nr']
+    assert bench.algorithmic_bytes('apply_ppbe_fp32', c, N, 4) == 2 * 2 * N * 4
+    assert bench.algorithmic_bytes('apply_vtbe', c, N, 8) == 2 * 7 * N * 8
+    assert bench.algorithmic_bytes('apply_ppbe_coarse_fp32', c, N, 4) == 2 * 2 * (N // 8) * 4
+    fwd = bench.algorithmic_bytes('ras_fwd_ppbe_coarse_fp32', c, N, 4)
+    bwd = bench.algorithmic_bytes('ras_bwd_ppbe_coarse_fp32', c, N, 4)
+    cells = bench.box_cells(c['Ns'] // 2, c['Nr'] // 2, c['p'], c['overlap_coarse'])
+    assert cells > N // 8  # overlapping boxes hold more cells than the grid
+    assert fwd == cells * (4 * (2 * 2 + 5 * 2 + 1) + 8)
+    assert bwd == cells * (4 * (2 + 5 * 2 + 3) + 9) + (N // 8) * 2 * 4
+    assert bench.algorithmic_bytes('net_fwd', c, N, 4) is None
+
+
+def test_measured_traffic_entries_name_a_committed_capture_that_holds_the_figure():
+    for cat, (nbytes, src) in bench.TRAFFIC.items():
+        path = os.path.join(ROOT, src)
+        assert src.startswith('profiles/') and os.path.exists(path), src
+        assert str(nbytes) in open(path).read(), (cat, src)
