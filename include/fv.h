@@ -76,7 +76,10 @@ typedef struct {
  * (Ns/2, Nr/2), coarse overlap `overlap_coarse`, coarse system solved by inner
  * FGMRES(coarse_restart) to relative tolerance coarse_rtol (at most
  * coarse_maxit iterations) preconditioned by one-level RAS on the coarse mesh
- * (eqn:coarsepreconditioner).  levels = 2 needs even Ns and Nr. */
+ * (eqn:coarsepreconditioner).  levels = 2 needs even Ns and Nr.  Every box,
+ * overlap included, must be smaller than 1024 cells in each dimension, and
+ * its sweep tables must fit in the device's shared memory (FV_EINVAL
+ * otherwise). */
 typedef struct {
   int p1, p2, p3;
   int overlap;
