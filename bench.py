@@ -3,27 +3,35 @@
 
 Workload (the mid-size mixed-vs-plain shell of the project's configuration
 list): 6 x 64^2 x 64 cells (1,572,864), E = 1e-3, Pm = 5, Ra = 100, Pr = 1,
-dt = 1e-4, seeded synthetic fields (seed 1 + rank).  One step = the paper's
-predictor-corrector time step (Sec. 3.1): nonlinear terms, VTBE solve
-(FGMRES(30), one-level RAS, 96 subdomains = 6 x (2 x 2 x 4), overlap 2),
-PPBE solve (FGMRES(30), hybrid two-level RAS, coarse 32^3 x 6 with overlap 1),
-projection; both systems to a 1e-8 relative FP64 residual.  Three arms, all
-timed on the same steps: fp64 (FP64 throughout, coarse inner GMRES to 0.1),
-mixed (FP32 inner FGMRES in FP64 outer FGMRES, 10 coarse iterations) and the
-headline learned (mixed, with the coarse solve replaced by a BF16 cubed-sphere
-U-Net followed by 6 coarse iterations; its training on seeded pairs from the
-plain coarse solver is setup, reported in `learned`).
+seeded synthetic fields (seed 1 + rank).  The time step dt is chosen from the
+seeded field so that the Alfven CFL number is at most 0.9 (dt = 0.9 / CFL_A
+per unit dt, rounded down to two significant digits; 5.7e-5 on this shell),
+the stability margin the paper keeps on every grid of its Table of grid
+levels (Sec. 4.2).  One step = the paper's predictor-corrector time step
+(Sec. 3.1): nonlinear terms, VTBE solve (FGMRES(30), one-level RAS,
+96 subdomains = 6 x (2 x 2 x 4), overlap 2), PPBE solve (FGMRES(30), hybrid
+two-level RAS, coarse 32^3 x 6 with overlap 1), projection; both systems to a
+1e-8 relative FP64 residual.  Three arms, each timed on the same steps of the
+same trajectory (every pass restarts from the seeded fields with a fresh
+history): fp64 (FP64 throughout, coarse inner GMRES to 0.1), mixed (FP32
+inner FGMRES in FP64 outer FGMRES, 10 coarse iterations) and the headline
+learned (mixed, with the coarse solve replaced by a BF16 cubed-sphere U-Net
+followed by 6 coarse iterations; its training on seeded pairs from the plain
+coarse solver is setup, reported in `learned`).
 
 value       -- ms per time step (max over ranks; one independent shell per GPU)
 e2e         -- the same through the C ABI with the state copied host->device
                before and device->host after every step (pinned host buffers)
 roofline    -- live CUDA-event duration of the dominant kernel category over
                the timed region against its algorithmic bytes
-cpu_baseline-- the CPU oracle (rank 0, N = 1) on a bounded sample
---impl reference runs only the oracle arm.
+stencil     -- the same for the FP32 operator applies (VTBE, PPBE)
+cpu_baseline-- the CPU oracle (rank 0, N = 1): real time steps of the same
+               workload (fewer than --steps; the count is stated)
+--impl reference runs only the oracle arm, on the same workload.
 """
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -33,7 +41,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 CFG = dict(Ns=64, Nr=64, p=(2, 2, 4), overlap=2, overlap_coarse=1, levels=2, E=1e-3, Ra=100.0, Pr=1.0, Pm=5.0,
-           dt=1e-4, rtol=1e-8, restart=30, seed=1, vtbe_inner=4, ppbe_inner=8, coarse_its=10, inner_gs=1)
+           rtol=1e-8, restart=30, seed=1, vtbe_inner=4, ppbe_inner=8, coarse_its=10, inner_gs=1)
+# largest Alfven CFL number of the seeded field the time step may give (paper Sec. 4.2 keeps <= 1.19 and
+# notes instability about 10 % above its choices)
+CFL_TARGET = 0.9
 WORKLOAD = ('shell 6x64^2x64 (1.57M cells), time step: VTBE one-level RAS + PPBE two-level RAS, '
             '96 subdomains overlap 2, FGMRES(30) to 1e-8 relative FP64 residual; mixed precision = FP32 inner '
             'FGMRES (operator, ILU(0) sweeps, coarse level; one Gram-Schmidt pass) inside FP64 outer FGMRES '
@@ -47,8 +58,8 @@ METRIC = 'wall time per time step at 1e-8 residual'
 # workload, from the ncu capture in the file named beside it; a category leaves this table when its kernels
 # change, until they are captured again
 TRAFFIC = {'net_fwd': (51663360, 'profiles/launches_net_forward_c16_coarse32.md')}
-# oracle sample: the same step on 6 x 32^2 x 32 (1/8 of the cells), scaled by the cell ratio
-ORACLE_NS = 32
+# CPU oracle: wall-clock budget for its real time steps (after its setup); at least one step always runs
+ORACLE_BUDGET_S = float(os.environ.get('FV_ORACLE_BUDGET_S', '100'))
 
 
 def parse():
@@ -66,6 +77,18 @@ def parse():
     ap.add_argument('--workload', default='step', choices=['step', 'batch', 'net'],
                     help='step: the time step (headline); batch: 32 right-hand sides on uneven subdomains')
     return ap.parse_args()
+
+
+def floor2(x):
+    """x > 0 rounded down to two significant digits (exact decimal, e.g. 5.7e-05)."""
+    e = math.floor(math.log10(x)) - 1
+    m = math.floor(x / 10.0 ** e + 1e-9)
+    return float('%de%d' % (m, e))
+
+
+def stable_dt(cfl_per_unit_dt):
+    """The step whose Alfven CFL number is at most CFL_TARGET, rounded down to two significant digits."""
+    return floor2(CFL_TARGET / cfl_per_unit_dt)
 
 
 def max_over_ranks(value, device):
@@ -129,40 +152,60 @@ class ClockSampler:
                 'reasons': reasons}
 
 
-def oracle_step_time(steps, warmup):
-    """CPU oracle (FP64, numpy/scipy + plain-C ILU(0), one thread) on the 6 x 32^2 x 32 sample."""
+def oracle_cfl_per_unit_dt(c):
+    """Alfven CFL number of the seeded field per unit dt, from the oracle's diagnostic (CPU)."""
+    from oracle.diagnostics import cfl_alfven
+    from oracle.grid import Grid
+    from paper_2009_02171_gb300.inputs import initial_state
+    s = initial_state(c['Ns'], c['Nr'], c['seed'])
+    return cfl_alfven(Grid(c['Ns'], c['Nr']), s['B'], c['E'], c['Pm'], 1.0)
+
+
+def oracle_step_time(c, max_steps, budget_s=ORACLE_BUDGET_S):
+    """Real time steps of the CPU oracle (FP64, numpy/scipy + plain-C ILU(0), one thread) on workload c:
+    its setup (matrices, subdomain ILU(0) factors) untimed, then steps 1, 2, ... of the trajectory until
+    max_steps or budget_s seconds (at least one).  Returns (ms per step, description)."""
     os.environ.setdefault('OMP_NUM_THREADS', '1')
     os.environ.setdefault('OPENBLAS_NUM_THREADS', '1')
     from oracle.grid import Grid
     from oracle.timestep import Physics, SolverOptions, Stepper
     from paper_2009_02171_gb300.inputs import initial_state
-    n = ORACLE_NS
-    st = Stepper(Grid(n, n), Physics(CFG['E'], CFG['Ra'], CFG['Pr'], CFG['Pm'], CFG['dt']),
-                 SolverOptions(parts=CFG['p'], delta=CFG['overlap'], ppbe_levels=CFG['levels'],
-                               delta_c=CFG['overlap_coarse'], rtol=CFG['rtol'], restart=CFG['restart']))
-    s = dict(initial_state(n, n, CFG['seed']), first=True)
-    for _ in range(warmup):
-        s, _ = st.step(s)
-    t = time.perf_counter()
-    for _ in range(steps):
-        s, _ = st.step(s)
-    per = (time.perf_counter() - t) / steps * 1e3
-    scale = (CFG['Ns'] ** 2 * CFG['Nr']) / (n * n * n)
-    return per * scale, dict(kind='oracle', cores=1, unit='ms/step',
-                             sample='oracle time step on 6x%d^2x%d (%d cells, same solver options), %d steps '
-                                    'after %d warm-up; ms/step scaled by the cell ratio %.0f'
-                                    % (n, n, 6 * n ** 3, steps, warmup, scale))
+    t0 = time.perf_counter()
+    dt = stable_dt(oracle_cfl_per_unit_dt(c))
+    st = Stepper(Grid(c['Ns'], c['Nr']), Physics(c['E'], c['Ra'], c['Pr'], c['Pm'], dt),
+                 SolverOptions(parts=c['p'], delta=c['overlap'], ppbe_levels=c['levels'],
+                               delta_c=c['overlap_coarse'], rtol=c['rtol'], restart=c['restart']))
+    setup = time.perf_counter() - t0
+    s = dict(initial_state(c['Ns'], c['Nr'], c['seed']), first=True)
+    times, its = [], []
+    t_all = time.perf_counter()
+    while len(times) < max(1, max_steps) and (not times or time.perf_counter() - t_all < budget_s):
+        t = time.perf_counter()
+        s, info = st.step(s)
+        times.append(time.perf_counter() - t)
+        its.append((info['vtbe'].iters, info['ppbe'].iters))
+    ms = sum(times) / len(times) * 1e3
+    cells = 6 * c['Ns'] ** 2 * c['Nr']
+    return ms, dict(kind='oracle', cores=1, unit='ms/step', timed_steps=len(times), setup_s=round(setup, 1),
+                    dt=dt, iterations_vtbe_ppbe=its, nproc=os.cpu_count(),
+                    sample='oracle time steps 1..%d of the same workload (6x%d^2x%d, %d cells, dt %.2g, same solver '
+                           'options), no warm-up, one thread; setup (matrices, ILU(0) factors) %.0f s untimed'
+                           % (len(times), c['Ns'], c['Nr'], cells, dt, setup))
 
 
 def reference_arm(args, rank, ws):
     if rank != 0:
         return
-    ms, cb = oracle_step_time(args.steps, args.warmup)
+    c = dict(CFG)
+    if args.ns:
+        c['Ns'] = c['Nr'] = args.ns
+    ms, cb = oracle_step_time(c, args.steps)
     cb['value'] = ms
     print(json.dumps({'impl': 'reference', 'metric': METRIC, 'value': ms, 'unit': 'ms/step', 'n_gpus': args.gpus,
-                      'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': ms, 'higher_is_better': False,
+                      'steps': cb['timed_steps'], 'requested_steps': args.steps, 'warmup': 0,
+                      'requested_warmup': args.warmup, 'ms_per_step': ms, 'higher_is_better': False,
                       'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic',
-                      'config': {'workload': WORKLOAD}, 'cpu_baseline': cb,
+                      'config': {'workload': workload_name(args.ns), 'dt': cb['dt']}, 'cpu_baseline': cb,
                       'e2e': {'value': ms, 'unit': 'ms/step', 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0}}))
 
 
@@ -285,6 +328,41 @@ def net_workload(args, fv, torch, rank, ws):
     fv.fv_net_free(net)
 
 
+def build_arm(fv, torch, c, dt, mode, host):
+    """(handles, setup seconds, learned-correction info) of arm mode in {fp64, mixed, learned} on workload c."""
+    ph = dict(E=c['E'], Ra=c['Ra'], Pr=c['Pr'], Pm=c['Pm'], dt=dt)
+    t = time.perf_counter()
+    mixed = mode != 'fp64'
+    g = fv.fv_build_grid(c['Ns'], c['Nr'])
+    mv = dict(precision=fv.FV_PREC_FP32, inner_maxit=c['vtbe_inner'], inner_gs_passes=c['inner_gs']) if mixed else {}
+    mpp = dict(precision=fv.FV_PREC_FP32, inner_maxit=c['ppbe_inner'], coarse_maxit=c['coarse_its'],
+               inner_gs_passes=c['inner_gs']) if mixed else {}
+    V = fv.fv_assemble_system(g, fv.FV_VTBE, **ph, p=c['p'], overlap=c['overlap'], levels=1, **mv)
+    P = fv.fv_assemble_system(g, fv.FV_PPBE, **ph, p=c['p'], overlap=c['overlap'], levels=c['levels'],
+                              overlap_coarse=c['overlap_coarse'], **mpp)
+    net, info = None, None
+    if mode == 'learned':
+        from paper_2009_02171_gb300.learned import train_learned_correction
+        L = LEARN
+        net, info = train_learned_correction(P, c['Ns'], c['Nr'], C=L['C'], levels=L['levels'], npairs=L['pairs'],
+                                             epochs=L['epochs'], batch=L['batch'], lr=L['lr'],
+                                             coarse_its=L['coarse_its'])
+    init = torch.tensor(host, device='cuda')
+    st = fv.fv_state_create(g, init, **ph)
+    torch.cuda.synchronize()
+    return dict(g=g, V=V, P=P, st=st, net=net, init=init), time.perf_counter() - t, info
+
+
+def free_arm(fv, h):
+    if h['net'] is not None:
+        fv.fv_pc_set_learned(h['P'], None)
+        fv.fv_net_free(h['net'])
+    fv.fv_free_state(h['st'])
+    fv.fv_free_system(h['V'])
+    fv.fv_free_system(h['P'])
+    fv.fv_free_grid(h['g'])
+
+
 def main():
     args = parse()
     if args.impl == 'reference':
@@ -310,46 +388,25 @@ def main():
     c = dict(CFG)
     if args.ns:
         c['Ns'] = c['Nr'] = args.ns
-    ph = dict(E=c['E'], Ra=c['Ra'], Pr=c['Pr'], Pm=c['Pm'], dt=c['dt'])
     s0 = initial_state(c['Ns'], c['Nr'], c['seed'] + rank)
     host = np.concatenate([s0['u'].ravel(), s0['T'], s0['B'].ravel(), s0['P'], s0['Pb']])
     N = host.size // 9
+    # time step from the live Alfven CFL number of the seeded field (computed by the library on the GPU)
+    g0 = fv.fv_build_grid(c['Ns'], c['Nr'])
+    st0 = fv.fv_state_create(g0, torch.tensor(host, device='cuda'), E=c['E'], Ra=c['Ra'], Pr=c['Pr'], Pm=c['Pm'],
+                             dt=1.0)
+    cfl_unit = fv.fv_state_diagnostics(st0)['cfl_alfven']
+    fv.fv_free_state(st0)
+    fv.fv_free_grid(g0)
+    dt = stable_dt(cfl_unit)
     opts = dict(restart=c['restart'], rtol=c['rtol'])
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
-    def build(mode):
-        """(handles, setup seconds, learned-correction info) for arm mode in {fp64, mixed, learned}."""
-        t = time.perf_counter()
-        mixed = mode != 'fp64'
-        g = fv.fv_build_grid(c['Ns'], c['Nr'])
-        mv = dict(precision=fv.FV_PREC_FP32, inner_maxit=c['vtbe_inner'], inner_gs_passes=c['inner_gs']) if mixed else {}
-        mpp = dict(precision=fv.FV_PREC_FP32, inner_maxit=c['ppbe_inner'], coarse_maxit=c['coarse_its'],
-                   inner_gs_passes=c['inner_gs']) if mixed else {}
-        V = fv.fv_assemble_system(g, fv.FV_VTBE, **ph, p=c['p'], overlap=c['overlap'], levels=1, **mv)
-        P = fv.fv_assemble_system(g, fv.FV_PPBE, **ph, p=c['p'], overlap=c['overlap'], levels=c['levels'],
-                                  overlap_coarse=c['overlap_coarse'], **mpp)
-        net, info = None, None
-        if mode == 'learned':
-            from paper_2009_02171_gb300.learned import train_learned_correction
-            L = LEARN
-            net, info = train_learned_correction(P, c['Ns'], c['Nr'], C=L['C'], levels=L['levels'],
-                                                 npairs=L['pairs'], epochs=L['epochs'], batch=L['batch'],
-                                                 lr=L['lr'], coarse_its=L['coarse_its'])
-        st = fv.fv_state_create(g, torch.tensor(host, device='cuda'), **ph)
-        torch.cuda.synchronize()
-        return (g, V, P, st, net), time.perf_counter() - t, info
-
-    def free(h):
-        g, V, P, st, net = h
-        if net is not None:
-            fv.fv_pc_set_learned(P, None)
-            fv.fv_net_free(net)
-        for x, f in ((st, fv.fv_free_state), (V, fv.fv_free_system), (P, fv.fv_free_system), (g, fv.fv_free_grid)):
-            f(x)
-
-    def timed(h, steps, warmup, profile, label=None):
-        g, V, P, st, _ = h
+    def timed(h, steps, warmup, profile=False, label=None):
+        """Restart from the seeded fields (fresh history), `warmup` untimed steps, `steps` timed steps."""
+        V, P, st = h['V'], h['P'], h['st']
+        fv.fv_state_reset(st, h['init'])
         for _ in range(warmup):
             fv.fv_time_step(st, V, P, 1, **opts)
         iters = []
@@ -364,7 +421,7 @@ def main():
             e0.record(stream)
             for _ in range(steps):
                 s = fv.fv_time_step(st, V, P, 1, **opts)
-                iters.append((s[0].iters, s[1].iters, s[0].inner_iters, s[1].inner_iters))
+                iters.append((s[0].iters, s[1].iters, s[0].inner_iters, s[1].inner_iters, s[1].rfinal))
             e1.record(stream)
             if label:
                 torch.cuda.nvtx.range_pop()
@@ -376,23 +433,47 @@ def main():
             ms = max_over_ranks(ms, 'cuda')
         return ms, iters, clk.summary()
 
+    def final_fields(h):
+        out = torch.empty(9 * N, dtype=torch.float64, device='cuda')
+        fv.fv_state_get(h['st'], out)
+        return out.cpu().numpy()
+
+    def errors(x, ref):
+        """max |x - ref| / max |ref| per field against the FP64 arm after the same steps."""
+        sl = {'u': slice(0, 3 * N), 'T': slice(3 * N, 4 * N), 'B': slice(4 * N, 7 * N), 'P': slice(7 * N, 8 * N),
+              'Pb': slice(8 * N, 9 * N)}
+        return {k: float(np.abs(x[v] - ref[v]).max() / max(np.abs(ref[v]).max(), 1e-300)) for k, v in sl.items()}
+
+    def diag_summary(h, iters):
+        d = fv.fv_state_diagnostics(h['st'], h['P'])
+        return {'E_kin': d['E_kin'], 'E_mag': d['E_mag'], 'cfl_alfven': d['cfl_alfven'],
+                'divB_face': d['divB_face'], 'divB_face_over_rhs': d['divB_face'] / d['divB_rhs'],
+                'divB_face_le_ppbe_rfinal': bool(d['divB_face'] <= iters[-1][4] * (1 + 1e-6)),
+                'divB_cell_over_rhs': d['divB_cell'] / d['divB_rhs'], 'steps': d['steps']}
+
     head = args.precision
-    others = {}
-    # the other arms first (same steps), then the headline arm, then its kernel breakdown:
-    # the same number of steps again with CUDA-event timing on (eager launches)
+    others, ref_fields = {}, None
+    # the other arms first (same steps), fp64 first so its final fields are the reference of the others
     if not args.single:
         for mode in [m for m in ('fp64', 'mixed', 'learned') if m != head]:
-            other, t_other, info_o = build(mode)
-            ms_o, it_o, _ = timed(other, args.steps, args.warmup, False)
+            other, t_other, info_o = build_arm(fv, torch, c, dt, mode, host)
+            ms_o, it_o, _ = timed(other, args.steps, args.warmup)
+            x = final_fields(other)
             others[mode] = {'ms_per_step': round(ms_o, 3), 'iterations_vtbe_ppbe': [(i[0], i[1]) for i in it_o],
-                            'setup_s': round(t_other, 2)}
+                            'setup_s': round(t_other, 2), 'diag': diag_summary(other, it_o)}
+            if mode == 'fp64':
+                ref_fields = x
+            elif ref_fields is not None:
+                others[mode]['error_vs_fp64'] = errors(x, ref_fields)
             if info_o:
                 others[mode]['learned'] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in info_o.items()}
-            free(other)
-    h, t_setup, info = build(head)
-    g, V, P, st, net = h
-    ms, iters, clocks = timed(h, args.steps, args.warmup, False, label='timed_steps')
-    ms_prof, _, _ = timed(h, args.steps, 0, True)
+            free_arm(fv, other)
+    h, t_setup, info = build_arm(fv, torch, c, dt, head)
+    ms, iters, clocks = timed(h, args.steps, args.warmup, label='timed_steps')
+    x_head = final_fields(h)
+    diag = diag_summary(h, iters)
+    err = errors(x_head, ref_fields) if ref_fields is not None and head != 'fp64' else None
+    ms_prof, _, _ = timed(h, args.steps, args.warmup, profile=True)
     kern = {}
     for cat in range(fv.K_COUNT):
         if cat % 16 not in fv.K_NAMES:
@@ -403,27 +484,31 @@ def main():
                                            'ms_per_step': round(t / args.steps, 3)}
     fv.fv_profile_enable(False)
 
-    # end to end through the C ABI: state host -> device, step, device -> host
+    # end to end through the C ABI: the same steps from the seeded fields, every timed step with the state
+    # host -> device (pinned), the step, device -> host
     hbuf = torch.empty(9 * N, dtype=torch.float64).pin_memory()
     dbuf = torch.empty(9 * N, dtype=torch.float64, device='cuda')
-    fv.fv_state_get(st, dbuf)
+    fv.fv_state_reset(h['st'], h['init'])
+    for _ in range(args.warmup):
+        fv.fv_time_step(h['st'], h['V'], h['P'], 1, **opts)
+    fv.fv_state_get(h['st'], dbuf)
     hbuf.copy_(dbuf)
     torch.cuda.synchronize()
-    ke = max(1, args.steps // 2)
     if ws > 1:
         dist.barrier()
     e0.record(stream)
-    for _ in range(ke):
+    for _ in range(args.steps):
         dbuf.copy_(hbuf, non_blocking=True)
-        fv.fv_state_set(st, dbuf)
-        fv.fv_time_step(st, V, P, 1, **opts)
-        fv.fv_state_get(st, dbuf)
+        fv.fv_state_set(h['st'], dbuf)
+        fv.fv_time_step(h['st'], h['V'], h['P'], 1, **opts)
+        fv.fv_state_get(h['st'], dbuf)
         hbuf.copy_(dbuf, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    ms_e2e = e0.elapsed_time(e1) / ke
+    ms_e2e = e0.elapsed_time(e1) / args.steps
     if ws > 1:
         ms_e2e = max_over_ranks(ms_e2e, 'cuda')
+    e2e_same = bool(np.array_equal(hbuf.numpy(), x_head))
 
     # roofline of the dominant kernel category (measured live over the timed region)
     peaks = json.load(open(os.path.join(ROOT, 'MEASURED_PEAKS.json'))) if os.path.exists(
@@ -436,7 +521,8 @@ def main():
         tr = TRAFFIC.get(top) if not args.ns else None
         common = {'kernel': top, 'ms_per_launch': round(per_launch_ms, 4), 'traffic': tr[0] if tr else None,
                   'traffic_source': tr[1] if tr else None,
-                  'share_of_step': round(kern[top]['ms_total'] / (ms * args.steps), 3), 'top_kernel': ranked[-1][1]}
+                  'share_of_step': round(kern[top]['ms_total'] / (ms_prof * args.steps), 3),
+                  'top_kernel': ranked[-1][1]}
         if top.startswith('net_fwd'):
             flops = network_flops(c)
             ach = flops / (per_launch_ms * 1e-3) / 1e12
@@ -463,10 +549,12 @@ def main():
             break
     if roof is not roof_hbm and roof_hbm is not None and roof is not None and roof['kernel'] != roof_hbm['kernel']:
         roof['next_hbm_bound'] = roof_hbm
+    stencil = {k: roof_of(k) for k in ('apply_vtbe_fp32', 'apply_ppbe_fp32', 'apply_vtbe', 'apply_ppbe')
+               if k in kern}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        v, cpu = oracle_step_time(2, 1)
+        v, cpu = oracle_step_time(c, args.steps)
         cpu['value'] = round(v, 1)
 
     if rank == 0:
@@ -481,20 +569,22 @@ def main():
             'arms': others,
             'learned': ({k: (round(v, 4) if isinstance(v, float) else v) for k, v in info.items()} if info else None),
             'config': {'workload': workload_name(args.ns),
-                       'cells': 6 * c['Ns'] ** 2 * c['Nr'], 'subdomains': 6 * 16,
+                       'cells': 6 * c['Ns'] ** 2 * c['Nr'], 'subdomains': 6 * c['p'][0] * c['p'][1] * c['p'][2],
                        'overlap': c['overlap'], 'ppbe_levels': c['levels'], 'rtol': c['rtol'],
-                       'restart': c['restart'], 'l2': 'working set > L2 (no flush needed)',
+                       'restart': c['restart'], 'dt': dt, 'cfl_alfven_initial': round(cfl_unit * dt, 4),
+                       'l2': 'working set > L2 (no flush needed)',
                        'parallelism': 'replicas' if ws > 1 else 'single GPU'},
             'iterations': {'vtbe': [i[0] for i in iters], 'ppbe': [i[1] for i in iters],
                            'vtbe_inner': [i[2] for i in iters], 'ppbe_inner': [i[3] for i in iters]},
+            'diag': diag, 'error_vs_fp64': err,
             'setup_s': round(t_setup, 2), 'clocks': clocks,
             'e2e': {'value': round(ms_e2e, 3), 'unit': 'ms/step', 'h2d_bytes_per_step': 9 * N * 8,
-                    'd2h_bytes_per_step': 9 * N * 8},
+                    'd2h_bytes_per_step': 9 * N * 8, 'same_fields_as_timed_pass': e2e_same},
             'gpu_launches': int(sum(v['launches'] for k, v in kern.items() if not k.startswith('phase'))),
-            'kernels_note': 'per-category CUDA-event times of a profiled re-run of the same steps (eager launches, '
+            'kernels_note': 'per-category CUDA-event times of a profiled pass over the same steps (eager launches, '
                             '%.1f ms/step with timing on)' % ms_prof,
-            'kernels': kern, 'roofline': roof, 'cpu_baseline': cpu}))
-    free(h)
+            'kernels': kern, 'roofline': roof, 'stencil': stencil, 'cpu_baseline': cpu}))
+    free_arm(fv, h)
     if ws > 1:
         dist.destroy_process_group()
 

@@ -197,14 +197,43 @@ fv_status fv_free_state(fv_state* st);
 /* copy the current 9N fields of the state into `out` (device FP64) */
 fv_status fv_state_get(const fv_state* st, double* out, void* stream);
 /* overwrite the 9N fields of the state from `in` (device FP64); the
- * Adams-Bashforth history and previous solutions are kept */
+ * Adams-Bashforth history (f^{n-1}) and the previous solutions used as initial
+ * guesses are kept, so the next step continues the trajectory those fields
+ * came from (e.g. fields read with fv_state_get and written back). */
 fv_status fv_state_set(fv_state* st, const double* in, void* stream);
+/* overwrite the 9N fields from `in` and drop the history: the next
+ * fv_time_step is a first step (f^{1/2} = f^0, u^0 = u^0, B^0 = B^0,
+ * Sec. 3.1; initial guesses from the fields), exactly as after
+ * fv_state_create with the same `in`. */
+fv_status fv_state_reset(fv_state* st, const double* in, void* stream);
 
 /* Advance nsteps steps of the predictor-corrector scheme (Steps 1-3 of
  * Sec. 3.1): VTBE solve, PPBE solve, projection.  stats: NULL or 2*nsteps
  * entries (VTBE, PPBE per step). */
 fv_status fv_time_step(fv_state* st, const fv_system* vtbe, const fv_system* ppbe, const fv_gmres_opts* opts,
                        int nsteps, fv_solve_stats* stats, void* stream);
+
+/* Diagnostics of the state after its last step (paper Sec. 4.2 and the
+ * divergence constraint eqn:divtime).  Norms are Euclidean over cells.
+ * - E_kin = Pm^2/2 sum V |u|^2, E_mag = Pm/(2E) sum V |B|^2 (Sec. 4.2);
+ * - cfl_alfven: dt max(|v^1|/h_s + |v^2|/h_s + |v^3|/h_r), v = B/sqrt(E Pm) in
+ *   contravariant components (Sec. 4.2, tab:gridlevels);
+ * - divB_face: ||D_f B^{n+1}|| of the projected face fluxes
+ *   F_f(B~) - dt/2 (G_f P_b).S_f, which equals the P_b block of the last PPBE
+ *   residual and so is bounded by that solve's rfinal; divB_rhs = ||D(B~)||,
+ *   its right-hand side.  divU_face, divU_rhs: the same for u and P;
+ * - divB_cell, divU_cell: ||D B^{n+1}||, ||D u^{n+1}|| of the cell-centred
+ *   fields of eqn:ubtilde (discretization error, O(h^2)).
+ * ppbe: the PPBE system of the last step, or NULL (face values -1, as before
+ * the first step).  Synchronizes `stream`. */
+typedef struct {
+  double E_kin, E_mag;
+  double cfl_alfven;
+  double divB_face, divB_rhs, divU_face, divU_rhs;
+  double divB_cell, divU_cell;
+  long long steps;             /* steps since fv_state_create / fv_state_reset */
+} fv_diag;
+fv_status fv_state_diagnostics(fv_state* st, const fv_system* ppbe, fv_diag* out, void* stream);
 
 /* Kernel timing (optional).  While enabled, the library brackets each launch of
  * the categories below with CUDA events on the launching stream (a few

@@ -266,6 +266,24 @@ class Discretization:
             pads = [vp[c * self.n_pad:(c + 1) * self.n_pad] for c in range(3)]
         return sum(self.face_div_matrix(c) @ pads[c] for c in range(3))
 
+    def projected_divergence(self, v, kind, phi, bc, coef):
+        """D_f of the projected face fluxes F_f(v) - coef (grad phi)_f . S_f (reading R2, eqn:ubtilde on faces).
+
+        The face normal flux of v is (v_f . S_f) with v_f the mean of the two adjacent values (as in
+        `divergence`); the face gradient flux of phi is the one of the compact Laplacian (F_h, F_r).
+        With v = B~, phi = P_b, bc = 'odd' and coef = dt/(2E) this is the discrete divergence of
+        B^{n+1} taken on the faces (eqn:divtime)."""
+        if kind == 'u':
+            Eu = self.extension('odd')
+            pads = [Eu @ v[c] for c in range(3)]
+        else:
+            vp = self.extension_B() @ np.concatenate([v[0], v[1], v[2]])
+            pads = [vp[c * self.n_pad:(c + 1) * self.n_pad] for c in range(3)]
+        php = self.extension(bc) @ phi
+        fh = sum(self.S_h[c] * (self.M_h @ pads[c]) for c in range(3)) - coef * (self.F_h @ php)
+        fr = sum(self.S_r[c] * (self.M_r @ pads[c]) for c in range(3)) - coef * (self.F_r @ php)
+        return self.Div_h @ (self.Avg @ fh) + self.Div_r @ fr
+
     def gradient(self, phi, bc, E_ekman):
         """Cell gradient G(phi) = (1/E) grad phi by the Gauss theorem, (3, N)."""
         ph = self.extension(bc) @ phi

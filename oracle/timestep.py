@@ -49,6 +49,24 @@ class SolverOptions:
     maxit: int = 3000
 
 
+def nonlinear_terms(d: Discretization, E, Pm, u, T, B, Eu=None, EB=None):
+    """(f1, f2, f3) of eqn:nonlinearoperator stacked as 7 x N, in the conservative form of eqn:nonlinearint
+    with Cartesian components: f1_k = -div(u u_k) + div(B B_k)/(E Pm), f2 = -div(u Theta),
+    f3_k = div(B u_k) - div(u B_k).  u, B: (3, N); T: (N,).  Eu, EB: the wall extensions (built if None)."""
+    npd = d.n_pad
+    Eu = d.extension('odd') if Eu is None else Eu
+    EB = d.extension_B() if EB is None else EB
+    up = [Eu @ u[c] for c in range(3)]
+    Tp = Eu @ T
+    Bpa = EB @ np.concatenate(B)
+    Bp = [Bpa[c * npd:(c + 1) * npd] for c in range(3)]
+    c = 1.0 / (E * Pm)
+    f1 = [-d.advective_div(up, up[k]) + c * d.advective_div(Bp, Bp[k]) for k in range(3)]
+    f2 = [-d.advective_div(up, Tp)]
+    f3 = [d.advective_div(Bp, up[k]) - d.advective_div(up, Bp[k]) for k in range(3)]
+    return np.stack(f1 + f2 + f3)
+
+
 class Stepper:
     def __init__(self, grid: Grid, phys: Physics, opt: SolverOptions):
         self.g, self.ph, self.opt = grid, phys, opt
@@ -68,16 +86,24 @@ class Stepper:
 
     def nonlinear(self, u, T, B):
         """(f1, f2, f3) stacked as 7 x N (eqn:nonlinearoperator, eqn:nonlinearint)."""
-        d, npd = self.d, self.d.n_pad
-        up = [self.Eu @ u[c] for c in range(3)]
-        Tp = self.Eu @ T
-        Bpa = self.EB @ np.concatenate(B)
-        Bp = [Bpa[c * npd:(c + 1) * npd] for c in range(3)]
-        c = 1.0 / (self.ph.E * self.ph.Pm)
-        f1 = [-d.advective_div(up, up[k]) + c * d.advective_div(Bp, Bp[k]) for k in range(3)]
-        f2 = [-d.advective_div(up, Tp)]
-        f3 = [d.advective_div(Bp, up[k]) - d.advective_div(up, Bp[k]) for k in range(3)]
-        return np.stack(f1 + f2 + f3)
+        return nonlinear_terms(self.d, self.ph.E, self.ph.Pm, u, T, B, self.Eu, self.EB)
+
+    def divergence_diagnostics(self, state):
+        """Norms of the divergence of u^{n+1}, B^{n+1} after a step (eqn:divtime): 'face' from the projected
+        face fluxes (equal to the PPBE residual blocks), 'cell' from the cell-centred fields (O(h^2));
+        'rhs' = ||D(u~)||, ||D(B~)||."""
+        N, ph = self.g.N, self.ph
+        xt = state['xV']
+        ut, Bt = xt[:3 * N].reshape(3, N), xt[4 * N:].reshape(3, N)
+        c = 0.5 * ph.dt / ph.E
+        bu = self.d.divergence(ut, 'u')
+        bu = bu - (self.d.V @ bu) / self.d.V.sum()
+        du_f = bu - c * (self.d.laplacian('even') @ state['P'])
+        dB_f = self.d.projected_divergence(Bt, 'B', state['Pb'], 'odd', c)
+        n2 = np.linalg.norm
+        return dict(divU_face=n2(du_f), divB_face=n2(dB_f), divU_rhs=n2(bu),
+                    divB_rhs=n2(self.d.divergence(Bt, 'B')),
+                    divU_cell=n2(self.d.divergence(state['u'], 'u')), divB_cell=n2(self.d.divergence(state['B'], 'B')))
 
     def vtbe_rhs(self, state):
         """x^ and the VTBE right-hand side of Step 1."""

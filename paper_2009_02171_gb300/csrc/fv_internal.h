@@ -75,6 +75,7 @@ struct fv_grid {
   fv::GeoF geof;               // the same tables in FP32 (mixed-precision inner solves)
   std::vector<void*> allocs;   // device allocations owned by the grid
   fv_grid* coarse = nullptr;   // (Ns/2, Nr/2) grid, built on demand
+  double* cbasis = nullptr;    // [j][i][6] r grad(xi), r grad(eta) at cell centres, local frame (diagnostics)
 };
 
 namespace fv {
@@ -120,6 +121,23 @@ struct Subdomains {
 };
 
 }  // namespace fv
+
+// time-stepping state of fv_state_create / fv_time_step (timestep.cu, diag.cu)
+struct fv_state {
+  const fv_grid* grid = nullptr;
+  fv_phys phys{};
+  long long N = 0;
+  bool first = true;                    // next step is a first step (no history)
+  long long steps = 0;                  // steps since create / reset
+  double *X = nullptr;                  // [9N] u, Theta, B, P, P_b
+  double *fprev = nullptr, *fcur = nullptr, *fh = nullptr, *xhat = nullptr, *bV = nullptr, *tmp = nullptr;
+  double *xV = nullptr;                 // [7N] last VTBE solution (u~, Theta, B~)
+  double *bP = nullptr, *xP = nullptr;  // [2N] last PPBE right-hand side (D u~, D B~) and solution
+  double *grad = nullptr;
+  double *gh = nullptr;                 // 7-component ghost layer
+  double *part = nullptr, *sums = nullptr;
+  std::vector<void*> allocs;
+};
 
 struct fv_system {
   const fv_grid* grid = nullptr;

@@ -112,7 +112,7 @@ fv_status build_grid(const fv_grid_desc* desc, fv_grid** out) {
 
   std::vector<double> ax11(Ns * (Ns + 1)), ax12(Ns * (Ns + 1)), ay22((Ns + 1) * Ns), ay12((Ns + 1) * Ns);
   std::vector<double> sx(3 * Ns * (Ns + 1)), sy(3 * (Ns + 1) * Ns), sr(3 * Ns * Ns), xhat(3 * Ns * Ns);
-  std::vector<double> crf(Ns * Ns), invsig(Ns * Ns), rf2(Nr + 1), invr2(Nr), rc(Nr);
+  std::vector<double> crf(Ns * Ns), invsig(Ns * Ns), rf2(Nr + 1), invr2(Nr), rc(Nr), cbasis(6 * Ns * Ns);
   for (int j = 0; j < Ns; ++j)
     for (int f = 0; f <= Ns; ++f) {
       Ang a = ang(xf(f), xc(j));
@@ -138,6 +138,9 @@ fv_status build_grid(const fv_grid_desc* desc, fv_grid** out) {
       for (int c = 0; c < 3; ++c) {
         xhat[3 * id + c] = a.xh[c];
         sr[3 * id + c] = a.sigma * hs * hs * a.xh[c];
+        // contravariant basis r grad(xi), r grad(eta) = (sqrt(g) g^{1b} e_b) / sigma on the unit sphere
+        cbasis[6 * id + c] = (a.a11 * a.e1[c] + a.a12 * a.e2[c]) / a.sigma;
+        cbasis[6 * id + 3 + c] = (a.a12 * a.e1[c] + a.a22 * a.e2[c]) / a.sigma;
       }
     }
   for (int k = 0; k <= Nr; ++k) {
@@ -220,7 +223,7 @@ fv_status build_grid(const fv_grid_desc* desc, fv_grid** out) {
             (G.xhat = upload(g, xhat)) && (G.sx = upload(g, sx)) && (G.sy = upload(g, sy)) &&
             (G.sr = upload(g, sr)) && (G.gq = upload(g, h.gq)) && (G.gsrc = upload(g, h.gsrc)) &&
             (G.gw = upload(g, h.gw)) && (G.pq = upload(g, h.pq)) && (G.psq = upload(g, h.psq)) &&
-            (G.psgn = upload(g, h.psgn)) && (G.ptmap = upload(g, h.ptmap));
+            (G.psgn = upload(g, h.psgn)) && (G.ptmap = upload(g, h.ptmap)) && (g->cbasis = upload(g, cbasis));
   if (ok) {
     Geo* dself = nullptr;
     if (cudaMalloc(&dself, sizeof(Geo)) != cudaSuccess) ok = false;

@@ -16,19 +16,6 @@
 
 #include "fv_internal.h"
 
-struct fv_state {
-  const fv_grid* grid = nullptr;
-  fv_phys phys{};
-  long long N = 0;
-  bool first = true;
-  double *X = nullptr;                  // [9N] u, Theta, B, P, P_b
-  double *fprev = nullptr, *fcur = nullptr, *fh = nullptr, *xhat = nullptr, *bV = nullptr, *tmp = nullptr;
-  double *xV = nullptr, *bP = nullptr, *xP = nullptr, *grad = nullptr;
-  double *gh = nullptr;                 // 7-component ghost layer
-  double *part = nullptr, *sums = nullptr;
-  std::vector<void*> allocs;
-};
-
 using namespace fv;
 
 extern "C" {
@@ -75,6 +62,16 @@ fv_status fv_state_get(const fv_state* s, double* out, void* stream) {
 fv_status fv_state_set(fv_state* s, const double* in, void* stream) {
   if (!s || !in) return set_error("fv_state_set: null argument"), FV_EINVAL;
   FV_CUDA(cudaMemcpyAsync(s->X, in, 9 * (size_t)s->N * sizeof(double), cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  return FV_OK;
+}
+
+// fields from `in` and a fresh history: the next step is a first step (f^{1/2} = f^0, u^ = u, B^ = B,
+// initial guesses from the state), exactly as after fv_state_create
+fv_status fv_state_reset(fv_state* s, const double* in, void* stream) {
+  if (!s || !in) return set_error("fv_state_reset: null argument"), FV_EINVAL;
+  FV_CUDA(cudaMemcpyAsync(s->X, in, 9 * (size_t)s->N * sizeof(double), cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  s->first = true;
+  s->steps = 0;
   return FV_OK;
 }
 
@@ -131,6 +128,7 @@ fv_status fv_time_step(fv_state* s, const fv_system* vtbe, const fv_system* ppbe
     FV_CUDA(cudaMemcpyAsync(P, s->xP, 2 * N * sizeof(double), cudaMemcpyDeviceToDevice, st));
     std::swap(s->fprev, s->fcur);
     s->first = false;
+    ++s->steps;
     if (stats) stats[2 * step] = sv, stats[2 * step + 1] = sp;
   }
   FV_CUDA(cudaStreamSynchronize(st));

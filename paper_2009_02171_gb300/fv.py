@@ -52,6 +52,14 @@ class fv_solve_stats(ctypes.Structure):
                 ('fallback', ctypes.c_int)]
 
 
+class fv_diag(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ('E_kin', 'E_mag', 'cfl_alfven', 'divB_face', 'divB_rhs', 'divU_face',
+                                               'divU_rhs', 'divB_cell', 'divU_cell')] + [('steps', ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
 class fv_net_desc(ctypes.Structure):
     _fields_ = [('C', ctypes.c_int), ('levels', ctypes.c_int), ('Ns', ctypes.c_int), ('Nr', ctypes.c_int),
                 ('max_batch', ctypes.c_int)]
@@ -84,6 +92,8 @@ SIGNATURES = {
     'fv_free_state': [_VP],
     'fv_state_get': [_VP, _DP, _VP],
     'fv_state_set': [_VP, _DP, _VP],
+    'fv_state_reset': [_VP, _DP, _VP],
+    'fv_state_diagnostics': [_VP, _VP, _P(fv_diag), _VP],
     'fv_time_step': [_VP, _VP, _VP, _P(fv_gmres_opts), ctypes.c_int, _P(fv_solve_stats), _VP],
     'fv_profile_enable': [ctypes.c_int],
     'fv_profile_read': [ctypes.c_int, _P(ctypes.c_longlong), _P(ctypes.c_double)],
@@ -224,6 +234,18 @@ def fv_state_get(state, out):
 
 def fv_state_set(state, src):
     _check(lib.fv_state_set(state, _ptr(src), _stream()))
+
+
+def fv_state_reset(state, src):
+    """Fields from src and a fresh history: the next step is a first step, as after fv_state_create."""
+    _check(lib.fv_state_reset(state, _ptr(src), _stream()))
+
+
+def fv_state_diagnostics(state, ppbe=None):
+    """Energies, Alfven CFL number and divergence norms of the state (fv_diag as a dict)."""
+    d = fv_diag()
+    _check(lib.fv_state_diagnostics(state, ppbe, ctypes.byref(d), _stream()))
+    return d.as_dict()
 
 
 def fv_time_step(state, vtbe, ppbe, nsteps=1, restart=30, max_it=3000, atol=0.0, rtol=1e-8):

@@ -37,3 +37,12 @@ def test_measured_traffic_entries_name_a_committed_capture_that_holds_the_figure
         path = os.path.join(ROOT, src)
         assert src.startswith('profiles/') and os.path.exists(path), src
         assert str(nbytes) in open(path).read(), (cat, src)
+
+
+def test_stable_dt_keeps_the_alfven_cfl_number_below_the_target():
+    """dt = 0.9 / CFL_A(dt = 1) rounded down to two significant digits (paper Sec. 4.2 stability margin)."""
+    assert bench.stable_dt(15671.774610187082) == 5.7e-05     # the 6 x 64^2 x 64 bench shell, seed 1
+    for c in (3599.6, 7615.4, 23735.2, 31799.0, 41877.8, 1.0, 12345.678):
+        dt = bench.stable_dt(c)
+        assert 0.8 < c * dt <= bench.CFL_TARGET
+        assert float('%.2g' % dt) == dt

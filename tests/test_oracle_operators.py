@@ -113,7 +113,7 @@ def test_face_divergence_is_conservative_and_consistent():
         assert abs(d.V @ dv) < 1e-12 * abs(dv).max() * d.V.sum()
         dv = d.divergence(np.array(fv(*X)), 'u')
         errs.append(np.sqrt((dv * dv * d.V).sum()))
-    assert _rates(errs)[0] > 1.0
+    assert _rates(errs)[0] > 1.1  # |u| ~ b at the walls: O(h) wall layer (test_noslip_wall_layer_lowers_the_order_of_u_fluxes)
 
 
 def test_gradient_and_nonlinear_flux_second_order():
