@@ -74,8 +74,11 @@ def parse():
                          'arms are timed beside it with the same steps')
     ap.add_argument('--single', action='store_true', help='time the headline arm only (profiling runs)')
     ap.add_argument('--ns', type=int, default=0, help='override Ns = Nr (small profiling cases)')
-    ap.add_argument('--workload', default='step', choices=['step', 'batch', 'net'],
-                    help='step: the time step (headline); batch: 32 right-hand sides on uneven subdomains')
+    ap.add_argument('--workload', default='step', choices=['step', 'batch', 'net', 'trajectory'],
+                    help='step: the time step (headline); batch: 32 right-hand sides on uneven subdomains; '
+                         'trajectory: one arm (--precision) for --steps steps from the seeded fields, one JSON '
+                         'line of diagnostics per step')
+    ap.add_argument('--dt', type=float, default=0.0, help='trajectory: time step (default: the CFL-limited dt)')
     return ap.parse_args()
 
 
@@ -328,6 +331,31 @@ def net_workload(args, fv, torch, rank, ws):
     fv.fv_net_free(net)
 
 
+def trajectory_workload(args, fv, torch, rank, ws, c, host, dt):
+    """Per-step metrics of one arm (JSON lines): iterations, final residuals, E_kin, E_mag, Alfven CFL number,
+    face and cell divergence of B (fv_state_diagnostics); stops at the first failed step and reports it."""
+    h, t_setup, _ = build_arm(fv, torch, c, dt, args.precision, host)
+    d = fv.fv_state_diagnostics(h['st'], h['P'])
+    if rank == 0:
+        print(json.dumps({'step': 0, 'dt': dt, 'precision': args.precision, 'workload': workload_name(args.ns),
+                          'setup_s': round(t_setup, 2), 'E_kin': d['E_kin'], 'E_mag': d['E_mag'],
+                          'cfl_alfven': d['cfl_alfven']}), flush=True)
+    for n in range(1, args.steps + 1):
+        try:
+            s = fv.fv_time_step(h['st'], h['V'], h['P'], 1, restart=c['restart'], rtol=c['rtol'])
+        except fv.FvError as e:
+            if rank == 0:
+                print(json.dumps({'step': n, 'error': str(e)}), flush=True)
+            break
+        d = fv.fv_state_diagnostics(h['st'], h['P'])
+        if rank == 0:
+            print(json.dumps({'step': n, 'iters_vtbe': s[0].iters, 'iters_ppbe': s[1].iters,
+                              'rfinal_vtbe': s[0].rfinal, 'rfinal_ppbe': s[1].rfinal, 'E_kin': d['E_kin'],
+                              'E_mag': d['E_mag'], 'cfl_alfven': d['cfl_alfven'], 'divB_face': d['divB_face'],
+                              'divB_rhs': d['divB_rhs'], 'divB_cell': d['divB_cell']}), flush=True)
+    free_arm(fv, h)
+
+
 def build_arm(fv, torch, c, dt, mode, host):
     """(handles, setup seconds, learned-correction info) of arm mode in {fp64, mixed, learned} on workload c."""
     ph = dict(E=c['E'], Ra=c['Ra'], Pr=c['Pr'], Pm=c['Pm'], dt=dt)
@@ -399,6 +427,11 @@ def main():
     fv.fv_free_state(st0)
     fv.fv_free_grid(g0)
     dt = stable_dt(cfl_unit)
+    if args.workload == 'trajectory':
+        trajectory_workload(args, fv, torch, rank, ws, c, host, args.dt or dt)
+        if ws > 1:
+            dist.destroy_process_group()
+        return
     opts = dict(restart=c['restart'], rtol=c['rtol'])
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -468,7 +501,7 @@ def main():
             if info_o:
                 others[mode]['learned'] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in info_o.items()}
             free_arm(fv, other)
-    h, t_setup, info = build_arm(fv, torch, c, dt, head)
+    h, t_setup, info = build_arm(fv, torch, c, dt, head, host)
     ms, iters, clocks = timed(h, args.steps, args.warmup, label='timed_steps')
     x_head = final_fields(h)
     diag = diag_summary(h, iters)
