@@ -74,10 +74,10 @@ def parse():
                          'arms are timed beside it with the same steps')
     ap.add_argument('--single', action='store_true', help='time the headline arm only (profiling runs)')
     ap.add_argument('--ns', type=int, default=0, help='override Ns = Nr (small profiling cases)')
-    ap.add_argument('--workload', default='step', choices=['step', 'batch', 'net', 'trajectory'],
+    ap.add_argument('--workload', default='step', choices=['step', 'batch', 'net', 'trajectory', 'apply'],
                     help='step: the time step (headline); batch: 32 right-hand sides on uneven subdomains; '
                          'trajectory: one arm (--precision) for --steps steps from the seeded fields, one JSON '
-                         'line of diagnostics per step')
+                         'line of diagnostics per step; apply: the operator applies alone (FP64 and FP32)')
     ap.add_argument('--dt', type=float, default=0.0, help='trajectory: time step (default: the CFL-limited dt)')
     return ap.parse_args()
 
@@ -356,6 +356,61 @@ def trajectory_workload(args, fv, torch, rank, ws, c, host, dt):
     free_arm(fv, h)
 
 
+def apply_workload(args, fv, torch, rank, ws, c, dt):
+    """y = A x alone, VTBE and PPBE, FP64 (fv_apply_op) and FP32 (fv_apply_op_fp32), on workload c: CUDA-event
+    time per apply over --steps applies (after --warmup) on inputs larger than L2 (a ring of vectors whose
+    total exceeds 129 MB, so every apply reads x from HBM), kernel split from the library's timers."""
+    from paper_2009_02171_gb300.inputs import random_vector
+    g = fv.fv_build_grid(c['Ns'], c['Nr'])
+    peaks = json.load(open(os.path.join(ROOT, 'MEASURED_PEAKS.json'))) if os.path.exists(
+        os.path.join(ROOT, 'MEASURED_PEAKS.json')) else {}
+    hbm = peaks.get('hbm_gbs', 6800.0)
+    out = {}
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    N = 6 * c['Ns'] ** 2 * c['Nr']
+    for kind, name in ((fv.FV_VTBE, 'vtbe'), (fv.FV_PPBE, 'ppbe')):
+        s = fv.fv_assemble_system(g, kind, E=c['E'], Ra=c['Ra'], Pr=c['Pr'], Pm=c['Pm'], dt=dt,
+                                  precision=fv.FV_PREC_FP32, inner_maxit=1, coarse_maxit=1)
+        n = fv.fv_system_size(s)
+        for dtype, es, call in ((torch.float64, 8, fv.fv_apply_op), (torch.float32, 4, fv.fv_apply_op_fp32)):
+            ring = max(2, int(3 * 129e6 / (2 * n * es)) + 1)
+            X = [torch.tensor(random_vector(n, 7 + q), dtype=dtype, device='cuda') for q in range(ring)]
+            Y = [torch.empty_like(X[0]) for _ in range(ring)]
+            for q in range(args.warmup):
+                call(s, X[q % ring], Y[q % ring])
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for q in range(args.steps):
+                call(s, X[q % ring], Y[q % ring])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            fv.fv_profile_enable(True)
+            for q in range(args.steps):
+                call(s, X[q % ring], Y[q % ring])
+            kern = {}
+            for cat in (fv.K_NAMES_INV['ghost'], fv.K_NAMES_INV['apply_' + name]):
+                cat += fv.K_FP32 if es == 4 else 0
+                nl, t = fv.fv_profile_read(cat)
+                kern[fv.category_name(cat)] = round(t / max(nl, 1) * 1e3, 2)
+            fv.fv_profile_enable(False)
+            d = 7 if kind == fv.FV_VTBE else 2
+            nbytes = 2 * d * N * es
+            out['%s_%s' % (name, 'fp64' if es == 8 else 'fp32')] = {
+                'us_per_apply': round(ms * 1e3, 2), 'bytes': nbytes, 'GBps': round(nbytes / (ms * 1e-3) / 1e9, 1),
+                'frac_of_hbm': round(nbytes / (ms * 1e-3) / 1e9 / hbm, 4), 'kernel_us_edge_tile': kern}
+            del X, Y
+        fv.fv_free_system(s)
+    fv.fv_free_grid(g)
+    if rank == 0:
+        print(json.dumps({'metric': 'operator apply time and algorithmic HBM bandwidth', 'workload':
+                          'y = A x on 6x%d^2x%d (%d cells), dt %.2g' % (c['Ns'], c['Nr'], N, dt),
+                          'steps': args.steps, 'warmup': args.warmup, 'hbm_peak_gbs': hbm,
+                          'peak_source': 'MEASURED_PEAKS.json hbm_gbs (of measured)',
+                          'l2': 'ring of input vectors > 3 x L2', 'applies': out}))
+
+
 def build_arm(fv, torch, c, dt, mode, host):
     """(handles, setup seconds, learned-correction info) of arm mode in {fp64, mixed, learned} on workload c."""
     ph = dict(E=c['E'], Ra=c['Ra'], Pr=c['Pr'], Pm=c['Pm'], dt=dt)
@@ -427,8 +482,11 @@ def main():
     fv.fv_free_state(st0)
     fv.fv_free_grid(g0)
     dt = stable_dt(cfl_unit)
-    if args.workload == 'trajectory':
-        trajectory_workload(args, fv, torch, rank, ws, c, host, args.dt or dt)
+    if args.workload in ('trajectory', 'apply'):
+        if args.workload == 'trajectory':
+            trajectory_workload(args, fv, torch, rank, ws, c, host, args.dt or dt)
+        else:
+            apply_workload(args, fv, torch, rank, ws, c, args.dt or dt)
         if ws > 1:
             dist.destroy_process_group()
         return

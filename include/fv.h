@@ -130,6 +130,12 @@ fv_status fv_system_size(const fv_system* s, long long* n);
  * x, y: device FP64, n values each, must not overlap. */
 fv_status fv_apply_op(const fv_system* s, const double* x, double* y, void* stream);
 
+/* y = A x in FP32: the operator of the mixed-precision inner solves (FP32
+ * coefficient tables and arithmetic, paper eqn:divdiscretization).  s must
+ * have been assembled with precision = FV_PREC_FP32 (FV_EINVAL otherwise).
+ * x, y: device FP32, n values each, must not overlap. */
+fv_status fv_apply_op_fp32(const fv_system* s, const float* x, float* y, void* stream);
+
 /* y = A x like fv_apply_op, for callers that must not allocate device memory
  * while they run -- for instance code whose device memory is owned by a
  * framework's pool allocator (a cudaMalloc behind its back would bypass the

@@ -47,6 +47,8 @@ struct GeoT {
   const int* psq;              // [p][side]  its side
   const int* psgn;             // [p][side]  F_p = psgn F_q for the shared face
   const int* ptmap;            // [p][side][t] tangential index on the neighbour side
+  const R* w9;                 // [j][i][9] horizontal 9-point weights of sum_faces F (panel-edge faces left out),
+                               // index (dj + 1) * 3 + (di + 1)
   const GeoT* self;            // device copy of this struct (out-of-line device code reads it
                                // through this pointer so kernels never take a parameter's address)
 };
@@ -76,6 +78,12 @@ struct fv_grid {
   std::vector<void*> allocs;   // device allocations owned by the grid
   fv_grid* coarse = nullptr;   // (Ns/2, Nr/2) grid, built on demand
   double* cbasis = nullptr;    // [j][i][6] r grad(xi), r grad(eta) at cell centres, local frame (diagnostics)
+  // panel-edge face fluxes as linear combinations of cell values of one level (apply.cu), per face
+  // (p, side, t): term count, then (cell offset within the level, weight) slots
+  int* edge_cnt = nullptr;
+  int* edge_off = nullptr;
+  double* edge_w = nullptr;
+  float* edge_wf = nullptr;
 };
 
 namespace fv {
@@ -198,14 +206,14 @@ struct ProfScope {
   } while (0)
 
 // grid.cpp
+fv_status build_edge_table(fv_grid* g);
 fv_status build_grid(const fv_grid_desc* desc, fv_grid** out);
 void free_grid(fv_grid* g);
 
-// ops.cu
+// apply.cu (tiled operator apply), ops.cu
 fv_status apply_op(const fv_system* s, const double* x, double* y, cudaStream_t st);
 fv_status apply_op32(const fv_system* s, const float* x, float* y, cudaStream_t st);
 fv_status apply_op_noalloc(const fv_system* s, const double* x, double* y, cudaStream_t st);
-fv_status fill_ghosts(const fv_system* s, const double* x, cudaStream_t st);
 fv_status ghost_fill(const Geo& G, const double* x, double* gh, int d, cudaStream_t st);
 fv_status assemble_subdomains(fv_system* s);
 // glue kernels of the time step

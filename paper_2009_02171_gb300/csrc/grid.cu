@@ -152,6 +152,33 @@ fv_status build_grid(const fv_grid_desc* desc, fv_grid** out) {
     invr2[k] = 1.0 / (rc[k] * rc[k] * hs * hs * hr);
   }
 
+  // 9-point horizontal weights of F(j, i+1) - F(j, i) + G(j+1, i) - G(j, i) (face fluxes of the Laplacian
+  // with F(j, f) = ax11 (x[j][f] - x[j][f-1]) + ax12 (x[j+1][f-1] - x[j-1][f-1] + x[j+1][f] - x[j-1][f]) and
+  // G likewise with ay22, ay12 and the roles of i and j exchanged).  A face on a panel edge is left out: its
+  // flux is the mean of the two panels' one-sided fluxes, added separately.
+  std::vector<double> w9(9 * Ns * Ns, 0.0);
+  for (int j = 0; j < Ns; ++j)
+    for (int i = 0; i < Ns; ++i) {
+      double* w = &w9[9 * (j * Ns + i)];
+      auto W = [&](int dj, int di) -> double& { return w[(dj + 1) * 3 + (di + 1)]; };
+      if (i + 1 < Ns) {  // + F(j, i+1)
+        const double a = ax11[j * (Ns + 1) + i + 1], b = ax12[j * (Ns + 1) + i + 1];
+        W(0, 1) += a, W(0, 0) -= a, W(1, 0) += b, W(-1, 0) -= b, W(1, 1) += b, W(-1, 1) -= b;
+      }
+      if (i > 0) {  // - F(j, i)
+        const double a = ax11[j * (Ns + 1) + i], b = ax12[j * (Ns + 1) + i];
+        W(0, 0) -= a, W(0, -1) += a, W(1, -1) -= b, W(-1, -1) += b, W(1, 0) -= b, W(-1, 0) += b;
+      }
+      if (j + 1 < Ns) {  // + G(j+1, i)
+        const double c = ay22[(j + 1) * Ns + i], e = ay12[(j + 1) * Ns + i];
+        W(1, 0) += c, W(0, 0) -= c, W(0, 1) += e, W(0, -1) -= e, W(1, 1) += e, W(1, -1) -= e;
+      }
+      if (j > 0) {  // - G(j, i)
+        const double c = ay22[j * Ns + i], e = ay12[j * Ns + i];
+        W(0, 0) -= c, W(-1, 0) += c, W(-1, 1) -= e, W(-1, -1) += e, W(0, 1) -= e, W(0, -1) += e;
+      }
+    }
+
   // panel-edge ghost interpolation and face pairing, from the geometry
   h.gq.assign(6 * 4 * Ns, 0);
   h.gsrc.assign(6 * 4 * Ns * 3, 0);
@@ -223,7 +250,8 @@ fv_status build_grid(const fv_grid_desc* desc, fv_grid** out) {
             (G.xhat = upload(g, xhat)) && (G.sx = upload(g, sx)) && (G.sy = upload(g, sy)) &&
             (G.sr = upload(g, sr)) && (G.gq = upload(g, h.gq)) && (G.gsrc = upload(g, h.gsrc)) &&
             (G.gw = upload(g, h.gw)) && (G.pq = upload(g, h.pq)) && (G.psq = upload(g, h.psq)) &&
-            (G.psgn = upload(g, h.psgn)) && (G.ptmap = upload(g, h.ptmap)) && (g->cbasis = upload(g, cbasis));
+            (G.psgn = upload(g, h.psgn)) && (G.ptmap = upload(g, h.ptmap)) && (g->cbasis = upload(g, cbasis)) &&
+            (G.w9 = upload(g, w9));
   if (ok) {
     Geo* dself = nullptr;
     if (cudaMalloc(&dself, sizeof(Geo)) != cudaSuccess) ok = false;
@@ -243,7 +271,7 @@ fv_status build_grid(const fv_grid_desc* desc, fv_grid** out) {
        (F.ay12 = upload(g, f32(ay12))) && (F.crf = upload(g, f32(crf))) && (F.rf2 = upload(g, f32(rf2))) &&
        (F.invsig = upload(g, f32(invsig))) && (F.invr2 = upload(g, f32(invr2))) && (F.rc = upload(g, f32(rc))) &&
        (F.xhat = upload(g, f32(xhat))) && (F.sx = upload(g, f32(sx))) && (F.sy = upload(g, f32(sy))) &&
-       (F.sr = upload(g, f32(sr))) && (F.gw = upload(g, f32(h.gw)));
+       (F.sr = upload(g, f32(sr))) && (F.gw = upload(g, f32(h.gw))) && (F.w9 = upload(g, f32(w9)));
   if (ok) {
     GeoF* dself = nullptr;
     if (cudaMalloc(&dself, sizeof(GeoF)) != cudaSuccess) ok = false;
@@ -256,6 +284,10 @@ fv_status build_grid(const fv_grid_desc* desc, fv_grid** out) {
   if (!ok) {
     free_grid(g);
     return set_error("fv_build_grid: device allocation of geometry tables failed"), FV_ENOMEM;
+  }
+  if (fv_status rc = build_edge_table(g)) {
+    free_grid(g);
+    return rc;
   }
   *out = g;
   return FV_OK;

@@ -54,17 +54,9 @@ fv_status ghost_fill(const Geo& G, const double* x, double* gh, int d, cudaStrea
   return FV_OK;
 }
 
-fv_status fill_ghosts(const fv_system* s, const double* x, cudaStream_t st) {
-  const Geo& G = s->grid->geo;
-  const long long total = (long long)s->d * 6 * 4 * G.Nr * (G.Ns + 2);
-  ProfScope ps(FV_K_GHOST + FV_K_COARSE * s->level, st);
-  ghost_kernel<double, Geo><<<grid_blocks(total, 256), 256, 0, st>>>(G, x, s->ghost, s->d);
-  FV_CUDA(cudaGetLastError());
-  return FV_OK;
-}
-
-// ---------------------------------------------------------------- apply
-// One launch covers every row: the first blocks map threads onto the (Ns-2)^2 interior of
+// ---------------------------------------------------------------- apply (term visitor)
+// The row-visitor apply of fv_apply_op_noalloc (fv_apply_op and the FP32 inner solves use the tiled
+// kernels of apply.cu).  One launch covers every row: the first blocks map threads onto the (Ns-2)^2 interior of
 // each panel layer (no warp touches a panel edge, so none diverges into the out-of-line edge
 // path), the remaining blocks onto the 4 (Ns-1) cells of each layer's boundary ring, so the
 // edge rows run beside the interior ones.  grid.y = k, grid.z = comp * 6 + panel; 32-bit index math.
@@ -103,39 +95,6 @@ static void launch_apply(const GT& G, const Coefs<typename GT::real>& cf, int d,
   const int ni = G.Ns - 2;
   const int blocks = (ni * ni + APPLY_THREADS - 1) / APPLY_THREADS + (4 * (G.Ns - 1) + APPLY_THREADS - 1) / APPLY_THREADS;
   apply_kernel<KIND, T, GT><<<dim3(blocks, G.Nr, 6 * d), APPLY_THREADS, 0, st>>>(G, cf, x, gh, y);
-}
-
-fv_status apply_op(const fv_system* s, const double* x, double* y, cudaStream_t st) {
-  const Geo& G = s->grid->geo;
-  fv_status rc = fill_ghosts(s, x, st);
-  if (rc) return rc;
-  const Coefs<double> cf = make_coefs<double>(Phys{s->phys.E, s->phys.Ra, s->phys.Pr, s->phys.Pm, s->phys.dt},
-                                               s->grid->h.ri, s->grid->h.ro);
-  const long long n = s->n;
-  ProfScope ps((s->kind == FV_VTBE ? FV_K_APPLY_VTBE : FV_K_APPLY_PPBE) + FV_K_COARSE * s->level, st);
-  (void)n;
-  if (s->kind == FV_VTBE) launch_apply<FV_VTBE>(G, cf, s->d, x, (const double*)s->ghost, y, st);
-  else launch_apply<FV_PPBE>(G, cf, s->d, x, (const double*)s->ghost, y, st);
-  FV_CUDA(cudaGetLastError());
-  return FV_OK;
-}
-
-// FP32 operator (mixed-precision inner solves): FP32 tables, FP32 arithmetic
-fv_status apply_op32(const fv_system* s, const float* x, float* y, cudaStream_t st) {
-  const GeoF& G = s->grid->geof;
-  const long long total = (long long)s->d * 6 * 4 * G.Nr * (G.Ns + 2);
-  {
-    ProfScope ps(FV_K_GHOST + FV_K_COARSE * s->level + FV_K_FP32, st);
-    ghost_kernel<float, GeoF><<<grid_blocks(total, 256), 256, 0, st>>>(G, x, s->ghost32, s->d);
-  }
-  FV_CUDA(cudaGetLastError());
-  const Coefs<float> cf = make_coefs<float>(Phys{s->phys.E, s->phys.Ra, s->phys.Pr, s->phys.Pm, s->phys.dt},
-                                             s->grid->h.ri, s->grid->h.ro);
-  ProfScope ps((s->kind == FV_VTBE ? FV_K_APPLY_VTBE : FV_K_APPLY_PPBE) + FV_K_COARSE * s->level + FV_K_FP32, st);
-  if (s->kind == FV_VTBE) launch_apply<FV_VTBE>(G, cf, s->d, x, (const float*)s->ghost32, y, st);
-  else launch_apply<FV_PPBE>(G, cf, s->d, x, (const float*)s->ghost32, y, st);
-  FV_CUDA(cudaGetLastError());
-  return FV_OK;
 }
 
 // ---------------------------------------------------------------- apply without allocation

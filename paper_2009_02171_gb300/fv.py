@@ -85,6 +85,7 @@ SIGNATURES = {
     'fv_system_size': [_VP, _P(ctypes.c_longlong)],
     'fv_apply_op': [_VP, _DP, _DP, _VP],
     'fv_apply_op_noalloc': [_VP, _DP, _DP, _VP],
+    'fv_apply_op_fp32': [_VP, _DP, _DP, _VP],
     'fv_precond_apply': [_VP, _DP, _DP, _VP],
     'fv_gmres_solve': [_VP, _DP, _DP, _P(fv_gmres_opts), _P(fv_solve_stats), _VP],
     'fv_gmres_solve_batch': [_VP, ctypes.c_int, _DP, _DP, _P(fv_gmres_opts), _P(fv_solve_stats), _VP],
@@ -181,6 +182,19 @@ def fv_apply_op(system, x, y):
     return y
 
 
+def _ptr32(t, n):
+    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous() and t.numel() == n):
+        raise ValueError('expected a contiguous CUDA float32 tensor of %d values' % n)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def fv_apply_op_fp32(system, x, y):
+    """y = A x in FP32 (float32 CUDA tensors) for a system assembled with FV_PREC_FP32."""
+    n = fv_system_size(system)
+    _check(lib.fv_apply_op_fp32(system, _ptr32(x, n), _ptr32(y, n), _stream()))
+    return y
+
+
 def fv_apply_op_noalloc(system, x, y):
     """y = A x with the ghost layer in the library's static device array (no allocation)."""
     n = fv_system_size(system)
@@ -270,6 +284,7 @@ def fv_free_state(h):
 K_NAMES = {0: 'ghost', 1: 'apply_vtbe', 2: 'apply_ppbe', 3: 'ras_fwd_vtbe', 4: 'ras_bwd_vtbe', 5: 'cgs', 6: 'vec',
            7: 'glue', 8: 'transfer', 9: 'phase_pc_c', 10: 'phase_pc_f', 11: 'phase_pc_i', 12: 'ras_fwd_ppbe',
            13: 'ras_bwd_ppbe', 14: 'net_fwd', 15: 'net_train'}
+K_NAMES_INV = {v: k for k, v in K_NAMES.items()}
 K_COARSE, K_FP32, K_COUNT = 16, 32, 64
 
 

@@ -39,7 +39,7 @@ def _rel(a, b):
 
 
 @pytest.mark.parametrize('kind', [0, 1])
-@pytest.mark.parametrize('Ns,Nr', [(8, 6), (13, 5)])
+@pytest.mark.parametrize('Ns,Nr', [(8, 6), (13, 5), (40, 9), (33, 17)])
 def test_apply_matches_oracle(fv, kind, Ns, Nr):
     """y = A x (matrix-free CUDA) vs the oracle's assembled A @ x: 1e-12 relative."""
     A, d, _ = _oracle_matrix(kind, Ns, Nr)
@@ -48,6 +48,30 @@ def test_apply_matches_oracle(fv, kind, Ns, Nr):
     x = random_vector(A.shape[0], 1 + kind)
     y = fv.fv_apply_op(s, _dev(x), torch.empty(A.shape[0], dtype=torch.float64, device='cuda')).cpu().numpy()
     assert _rel(y, A @ x) < 1e-12
+    fv.fv_free_system(s)
+    fv.fv_free_grid(g)
+
+
+@pytest.mark.parametrize('kind', [0, 1])
+@pytest.mark.parametrize('Ns,Nr', [(8, 6), (40, 9), (33, 17)])
+def test_fp32_apply_matches_oracle(fv, kind, Ns, Nr):
+    """FP32 operator of the mixed-precision inner solves (FP32 tables and arithmetic) vs the oracle's FP64
+    A @ x: 2e-5 of max |A x| (FP32 rounding of an 11-point stencil; an index error is O(1)).  The sizes
+    span several 32-wide tiles, ragged tiles (33, 40) and several level chunks."""
+    A, d, _ = _oracle_matrix(kind, Ns, Nr)
+    g = fv.fv_build_grid(Ns, Nr)
+    s = fv.fv_assemble_system(g, kind, **PH, precision=fv.FV_PREC_FP32, inner_maxit=2, coarse_maxit=2)
+    x = random_vector(A.shape[0], 3 + kind)
+    xt = torch.tensor(x, dtype=torch.float32, device='cuda')
+    y = fv.fv_apply_op_fp32(s, xt, torch.empty_like(xt)).double().cpu().numpy()
+    want = A @ xt.double().cpu().numpy()
+    assert _rel(y, want) < 2e-5
+    with pytest.raises(fv.FvError):
+        s64 = fv.fv_assemble_system(g, kind, **PH)
+        try:
+            fv.fv_apply_op_fp32(s64, xt, torch.empty_like(xt))
+        finally:
+            fv.fv_free_system(s64)
     fv.fv_free_system(s)
     fv.fv_free_grid(g)
 
