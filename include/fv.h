@@ -76,7 +76,11 @@ typedef struct {
  * (Ns/2, Nr/2), coarse overlap `overlap_coarse`, coarse system solved by inner
  * FGMRES(coarse_restart) to relative tolerance coarse_rtol (at most
  * coarse_maxit iterations) preconditioned by one-level RAS on the coarse mesh
- * (eqn:coarsepreconditioner).  levels = 2 needs even Ns and Nr.  Every box,
+ * (eqn:coarsepreconditioner).  levels = L > 2 (up to 6): the multilevel hybrid
+ * RAS of Sec. 3.3 -- the coarse system's preconditioner is itself the
+ * (L-1)-level construction on the next 1:2 mesh, with the same coarse_rtol,
+ * coarse_restart, coarse_maxit and overlap_coarse on every coarse level.
+ * Every mesh that is coarsened needs even Ns >= 8 and even Nr >= 4.  Every box,
  * overlap included, must be smaller than 1024 cells in each dimension, and
  * its sweep tables must fit in the device's shared memory (FV_EINVAL
  * otherwise). */

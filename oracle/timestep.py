@@ -24,7 +24,7 @@ import numpy as np
 from .discrete import Discretization, ppbe_matrix, vtbe_matrix
 from .grid import Grid
 from .krylov import fgmres
-from .schwarz import OneLevelRAS, TwoLevelRAS
+from .schwarz import OneLevelRAS, hybrid_ras
 
 
 @dataclass
@@ -74,11 +74,9 @@ class Stepper:
         self.AV = vtbe_matrix(self.d, phys.E, phys.Ra, phys.Pr, phys.Pm, phys.dt)
         self.AP = ppbe_matrix(self.d, phys.E, phys.dt)
         self.MV = OneLevelRAS(grid, self.AV, 7, opt.parts, opt.delta)
-        if opt.ppbe_levels == 2:
-            gc = Grid(grid.Ns // 2, grid.Nr // 2, grid.ri, grid.ro)
-            Ac = ppbe_matrix(Discretization(gc), phys.E, phys.dt)
-            self.MP = TwoLevelRAS(grid, self.AP, gc, Ac, 2, opt.parts, opt.delta, opt.delta_c, opt.rtol_c,
-                                  neumann_first=True)
+        if opt.ppbe_levels >= 2:
+            self.MP = hybrid_ras(grid, self.AP, lambda g: ppbe_matrix(Discretization(g), phys.E, phys.dt), 2,
+                                 opt.parts, opt.delta, opt.delta_c, opt.ppbe_levels, opt.rtol_c, neumann_first=True)
         else:
             self.MP = OneLevelRAS(grid, self.AP, 2, opt.parts, opt.delta)
         self.Eu = self.d.extension('odd')

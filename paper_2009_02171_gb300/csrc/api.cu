@@ -30,6 +30,7 @@ static void free_system(fv_system* s) {
 static fv_status make_system(const fv_grid* g, int kind, const fv_phys* ph, const fv_pc_desc* pc, fv_system** out) {
   if (pc->inner_gs_passes < 0 || pc->inner_gs_passes > 2)
     return set_error("fv_assemble_system: inner_gs_passes must be 0, 1 or 2"), FV_EINVAL;
+  if (pc->levels < 1 || pc->levels > 6) return set_error("fv_assemble_system: levels must be 1..6"), FV_EINVAL;
   fv_system* s = new fv_system();
   s->grid = g, s->kind = kind, s->d = kind == FV_VTBE ? 7 : 2;
   s->n = s->d * g->h.N;
@@ -74,8 +75,10 @@ static fv_status make_system(const fv_grid* g, int kind, const fv_phys* ph, cons
         return rc;
       }
     }
+    // multilevel hybrid RAS (Sec. 3.3): the coarse system's own preconditioner is the same construction
+    // with one level fewer, down to one-level RAS on the coarsest mesh
     fv_pc_desc cpc = *pc;
-    cpc.levels = 1;
+    cpc.levels = pc->levels - 1;
     cpc.overlap = pc->overlap_coarse;
     cpc.p1 = std::min(pc->p1, g->h.Ns / 2), cpc.p2 = std::min(pc->p2, g->h.Ns / 2), cpc.p3 = std::min(pc->p3, g->h.Nr / 2);
     std::vector<int> cboxes;

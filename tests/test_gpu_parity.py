@@ -113,6 +113,38 @@ def test_two_level_ras_matches_oracle(fv):
     fv.fv_free_grid(g)
 
 
+def test_three_level_ras_matches_oracle(fv):
+    """Multilevel hybrid RAS (Sec. 3.3): the coarse GMRES of the two-level preconditioner is itself
+    preconditioned by the two-level construction on the next 1:2 mesh (16 x 8 -> 8 x 4 -> 4 x 2)."""
+    from oracle.schwarz import hybrid_ras
+    Ns, Nr, parts = 16, 8, (2, 2, 1)
+    A, d, _ = _oracle_matrix(1, Ns, Nr)
+    mat = lambda gg: ppbe_matrix(Discretization(gg), PH['E'], PH['dt'])
+    M = hybrid_ras(Grid(Ns, Nr), A, mat, 2, parts, 1, 1, 3, neumann_first=True)
+    g = fv.fv_build_grid(Ns, Nr)
+    s = fv.fv_assemble_system(g, 1, **PH, p=parts, overlap=1, levels=3, overlap_coarse=1)
+    r = random_vector(A.shape[0], 9)
+    z = fv.fv_precond_apply(s, _dev(r), torch.empty(A.shape[0], dtype=torch.float64, device='cuda')).cpu().numpy()
+    assert _rel(z, M.apply(r)) < 1e-9
+    # a 3-level FGMRES solve (Neumann P block of the right-hand side made consistent): solution to 1e-7 at a
+    # 1e-8 residual after removing P's mean, iterations within one
+    N, V = 6 * Ns * Ns * Nr, Grid(Ns, Nr).volumes().ravel()
+    b = random_vector(A.shape[0], 12)
+    b[:N] -= (V @ b[:N]) / V.sum()
+    ref = fgmres(lambda v: A @ v, M.apply, b, np.zeros_like(b), restart=30, rtol=1e-8, maxit=500)
+    x = torch.zeros(A.shape[0], dtype=torch.float64, device='cuda')
+    st = fv.fv_gmres_solve(s, _dev(b), x, rtol=1e-8, max_it=500)
+    assert st.converged and abs(st.iters - ref.iters) <= 1
+    xs, rx = x.cpu().numpy(), ref.x.copy()
+    for v in (xs, rx):
+        v[:N] -= (V @ v[:N]) / V.sum()
+    assert _rel(xs, rx) < 1e-7
+    with pytest.raises(fv.FvError):   # 16 x 8 has no fourth 1:2 mesh with Nr >= 4 to coarsen
+        fv.fv_assemble_system(g, 1, **PH, p=parts, overlap=1, levels=4, overlap_coarse=1)
+    fv.fv_free_system(s)
+    fv.fv_free_grid(g)
+
+
 @pytest.mark.parametrize('kind,levels', [(0, 1), (1, 1), (1, 2)])
 def test_gmres_solution_matches_oracle(fv, kind, levels):
     """Solutions at a 1e-8 relative residual agree to 1e-7 (same algorithm, same ordering)."""
@@ -249,3 +281,21 @@ def test_mixed_precision_time_step_matches_oracle(fv):
     assert _rel(out[4 * N:7 * N], ref2['B'].ravel()) < 1e-7
     for h, f in ((st, fv.fv_free_state), (V, fv.fv_free_system), (P, fv.fv_free_system), (g, fv.fv_free_grid)):
         f(h)
+
+
+def test_mixed_precision_three_level_solve_reaches_fp64_residual(fv):
+    """FP32 inner FGMRES whose two-level preconditioner's coarse solve is itself two-level (three meshes,
+    16 -> 8 -> 4): the true FP64 residual against the oracle matrix reaches 1e-8."""
+    Ns = Nr = 16
+    A, d, disc = _oracle_matrix(1, Ns, Nr)
+    b = random_vector(A.shape[0], 21)
+    b[:disc.g.N] -= (disc.V @ b[:disc.g.N]) / disc.V.sum()
+    g = fv.fv_build_grid(Ns, Nr)
+    s = fv.fv_assemble_system(g, 1, **PH, p=(2, 2, 2), overlap=1, levels=3, precision=fv.FV_PREC_FP32,
+                              inner_maxit=6, coarse_maxit=6)
+    x = torch.zeros(A.shape[0], dtype=torch.float64, device='cuda')
+    st = fv.fv_gmres_solve(s, _dev(b), x, rtol=1e-8)
+    assert st.converged
+    assert np.linalg.norm(b - A @ x.cpu().numpy()) <= 1.0001e-8 * np.linalg.norm(b)
+    fv.fv_free_system(s)
+    fv.fv_free_grid(g)

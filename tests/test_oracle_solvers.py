@@ -189,3 +189,30 @@ def test_two_level_neumann_coarse_projection_prevents_stagnation():
         assert info['ppbe'].converged
         its.append(info['ppbe'].iters)
     assert max(its) <= 2 * min(its) + 2
+
+
+def test_multilevel_with_exact_coarse_solves_equals_two_level():
+    """Sec. 3.3 multilevel hybrid RAS: when each coarse GMRES is solved exactly (tiny coarse tolerance), the
+    coarse preconditioner (one-level, or two-level on the next mesh) no longer matters, so the 3-level
+    operator equals the 2-level one; with the default 0.1 coarse tolerance both stay valid preconditioners."""
+    from oracle.schwarz import hybrid_ras
+    E, dt = 1e-3, 1e-4
+    g = Grid(16, 8)
+    A = ppbe_matrix(Discretization(g), E, dt)
+    mat = lambda gg: ppbe_matrix(Discretization(gg), E, dt)
+    r = random_vector(A.shape[0], 11)
+    r[:g.N] -= (g.volumes().ravel() @ r[:g.N]) / g.volumes().sum()
+    z2 = hybrid_ras(g, A, mat, 2, (2, 2, 1), 1, 1, 2, rtol_c=1e-13, maxit_c=400, neumann_first=True).apply(r)
+    z3 = hybrid_ras(g, A, mat, 2, (2, 2, 1), 1, 1, 3, rtol_c=1e-13, maxit_c=400, neumann_first=True).apply(r)
+    # the coarse Neumann pressure matrix is singular: exact coarse solves agree up to a constant in P
+    V = g.volumes().ravel()
+    for z in (z2, z3):
+        z[:g.N] -= (V @ z[:g.N]) / V.sum()
+    assert np.abs(z3 - z2).max() < 1e-8 * np.abs(z2).max()
+    its = {}
+    for lv in (1, 2, 3):
+        M = hybrid_ras(g, A, mat, 2, (2, 2, 1), 1, 1, lv, neumann_first=True)
+        res = fgmres(lambda v: A @ v, M.apply, r, np.zeros_like(r), restart=30, rtol=1e-8, maxit=400)
+        assert res.converged and np.linalg.norm(r - A @ res.x) <= 1.0001e-8 * np.linalg.norm(r)
+        its[lv] = res.iters
+    assert its[2] < its[1] and its[3] <= its[2] + 2
