@@ -40,19 +40,24 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-CFG = dict(Ns=64, Nr=64, p=(2, 2, 4), overlap=2, overlap_coarse=1, levels=2, E=1e-3, Ra=100.0, Pr=1.0, Pm=5.0,
-           rtol=1e-8, restart=30, seed=1, vtbe_inner=4, ppbe_inner=8, coarse_its=10, inner_gs=1)
+# the shells of the project's configuration list (seeded synthetic fields, E = 1e-3, Pm = 5, Ra = 100, Pr = 1):
+# boxes of 32 x 32 x 16 cells + overlap 2 in every case but the tiny one
+COMMON = dict(overlap_coarse=1, E=1e-3, Ra=100.0, Pr=1.0, Pm=5.0, rtol=1e-8, vtbe_inner=4, ppbe_inner=8,
+              coarse_its=10, inner_gs=1)
+CONFIGS = {
+    'shell16': dict(COMMON, Ns=16, Nr=16, p=(1, 1, 1), overlap=1, levels=1, restart=30, seed=0),
+    'shell64': dict(COMMON, Ns=64, Nr=64, p=(2, 2, 4), overlap=2, levels=2, restart=30, seed=1),
+    'shell128': dict(COMMON, Ns=128, Nr=96, p=(4, 4, 6), overlap=2, levels=2, restart=30, seed=3),
+    'shell192': dict(COMMON, Ns=192, Nr=128, p=(6, 6, 8), overlap=2, levels=3, restart=20, seed=4, coarse_its=4),
+}
+CFG = CONFIGS['shell64']
 # largest Alfven CFL number of the seeded field the time step may give (paper Sec. 4.2 keeps <= 1.19 and
 # notes instability about 10 % above its choices)
 CFL_TARGET = 0.9
-WORKLOAD = ('shell 6x64^2x64 (1.57M cells), time step: VTBE one-level RAS + PPBE two-level RAS, '
-            '96 subdomains overlap 2, FGMRES(30) to 1e-8 relative FP64 residual; mixed precision = FP32 inner '
-            'FGMRES (operator, ILU(0) sweeps, coarse level; one Gram-Schmidt pass) inside FP64 outer FGMRES '
-            '(two passes); learned = mixed with the '
-            'PPBE coarse solve replaced by a BF16 cubed-sphere U-Net followed by 6 coarse FGMRES iterations')
 # learned coarse correction of the headline arm: network and training (seeded synthetic pairs from the plain
-# coarse solver; data generation and training are counted in setup_s)
+# coarse solver; data generation and training are counted in setup_s); deeper networks on larger coarse grids
 LEARN = dict(C=16, levels=3, pairs=256, epochs=40, batch=8, lr=3e-4, coarse_its=6)
+LEARN_BY_CONFIG = {'shell128': dict(LEARN, levels=4, coarse_its=8), 'shell192': dict(LEARN, levels=4, coarse_its=8)}
 METRIC = 'wall time per time step at 1e-8 residual'
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a kernel category at the default
 # workload, from the ncu capture in the file named beside it; a category leaves this table when its kernels
@@ -74,10 +79,17 @@ def parse():
                          'arms are timed beside it with the same steps')
     ap.add_argument('--single', action='store_true', help='time the headline arm only (profiling runs)')
     ap.add_argument('--ns', type=int, default=0, help='override Ns = Nr (small profiling cases)')
-    ap.add_argument('--workload', default='step', choices=['step', 'batch', 'net', 'trajectory', 'apply'],
+    ap.add_argument('--config', default='shell64', choices=sorted(CONFIGS),
+                    help='shell of the time-step workload (shell64: the mid-size mixed-vs-plain shell; shell128, '
+                         'shell192: the learned-correction and full-scale shells)')
+    ap.add_argument('--levels', type=int, default=0, help='override the PPBE preconditioner levels')
+    ap.add_argument('--coarse-its', type=int, default=0, help='override the fixed coarse iterations (mixed precision)')
+    ap.add_argument('--ppbe-inner', type=int, default=0, help='override the PPBE inner iterations (mixed precision)')
+    ap.add_argument('--workload', default='step', choices=['step', 'batch', 'net', 'trajectory', 'apply', 'strong'],
                     help='step: the time step (headline); batch: 32 right-hand sides on uneven subdomains; '
                          'trajectory: one arm (--precision) for --steps steps from the seeded fields, one JSON '
-                         'line of diagnostics per step; apply: the operator applies alone (FP64 and FP32)')
+                         'line of diagnostics per step; apply: the operator applies alone (FP64 and FP32); strong: '
+                         'the strong-scaling workload of the paper replayed on one GPU')
     ap.add_argument('--dt', type=float, default=0.0, help='trajectory: time step (default: the CFL-limited dt)')
     return ap.parse_args()
 
@@ -199,20 +211,18 @@ def oracle_step_time(c, max_steps, budget_s=ORACLE_BUDGET_S):
 def reference_arm(args, rank, ws):
     if rank != 0:
         return
-    c = dict(CFG)
-    if args.ns:
-        c['Ns'] = c['Nr'] = args.ns
+    c = config_of(args)
     ms, cb = oracle_step_time(c, args.steps)
     cb['value'] = ms
     print(json.dumps({'impl': 'reference', 'metric': METRIC, 'value': ms, 'unit': 'ms/step', 'n_gpus': args.gpus,
                       'steps': cb['timed_steps'], 'requested_steps': args.steps, 'warmup': 0,
                       'requested_warmup': args.warmup, 'ms_per_step': ms, 'higher_is_better': False,
                       'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic',
-                      'config': {'workload': workload_name(args.ns), 'dt': cb['dt']}, 'cpu_baseline': cb,
+                      'config': {'workload': workload_name(c), 'dt': cb['dt']}, 'cpu_baseline': cb,
                       'e2e': {'value': ms, 'unit': 'ms/step', 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0}}))
 
 
-BATCH = dict(Ns=48, Nr=48, nrhs=32, nboxes=512, overlap=2, rtol=1e-8, restart=30)
+BATCH = dict(Ns=48, Nr=48, nrhs=32, nboxes=512, overlap=2, rtol=1e-8, restart=30, dt=1e-4)
 
 
 def batch_workload(args, fv, torch, rank, ws):
@@ -223,7 +233,7 @@ def batch_workload(args, fv, torch, rank, ws):
     c = BATCH
     boxes = uneven_boxes(c['Ns'], c['Nr'], target=c['nboxes'], seed=0)
     g = fv.fv_build_grid(c['Ns'], c['Nr'])
-    s = fv.fv_assemble_system(g, fv.FV_PPBE, E=CFG['E'], Ra=CFG['Ra'], Pr=CFG['Pr'], Pm=CFG['Pm'], dt=CFG['dt'],
+    s = fv.fv_assemble_system(g, fv.FV_PPBE, E=CFG['E'], Ra=CFG['Ra'], Pr=CFG['Pr'], Pm=CFG['Pm'], dt=c['dt'],
                               overlap=c['overlap'], boxes=boxes, precision=fv.FV_PREC_FP32)
     n = fv.fv_system_size(s)
     # right-hand sides b = A x for seeded random x: in the range of A, so consistent for the
@@ -278,10 +288,8 @@ def net_workload(args, fv, torch, rank, ws):
     """The learned correction's network alone on the bench's coarse grid (6 x 32^3, C = 16, 3 levels):
     forward of one sample (as inside the preconditioner) and one training step of a batch of 8."""
     from paper_2009_02171_gb300.inputs import multiscale_fields
-    c = dict(CFG)
-    if args.ns:
-        c['Ns'] = c['Nr'] = args.ns
-    ns, nr, L = c['Ns'] // 2, c['Nr'] // 2, LEARN
+    c = config_of(args)
+    ns, nr, L = c['Ns'] // 2, c['Nr'] // 2, c['learn']
     net = fv.fv_net_create(L['C'], ns, nr, levels=L['levels'], max_batch=L['batch'])
     fv.fv_net_init(net, 1)
     R = torch.tensor(multiscale_fields(ns, nr, L['batch'], seed=1), device='cuda')
@@ -337,7 +345,7 @@ def trajectory_workload(args, fv, torch, rank, ws, c, host, dt):
     h, t_setup, _ = build_arm(fv, torch, c, dt, args.precision, host)
     d = fv.fv_state_diagnostics(h['st'], h['P'])
     if rank == 0:
-        print(json.dumps({'step': 0, 'dt': dt, 'precision': args.precision, 'workload': workload_name(args.ns),
+        print(json.dumps({'step': 0, 'dt': dt, 'precision': args.precision, 'workload': workload_name(c),
                           'setup_s': round(t_setup, 2), 'E_kin': d['E_kin'], 'E_mag': d['E_mag'],
                           'cfl_alfven': d['cfl_alfven']}), flush=True)
     for n in range(1, args.steps + 1):
@@ -411,6 +419,72 @@ def apply_workload(args, fv, torch, rank, ws, c, dt):
                           'l2': 'ring of input vectors > 3 x L2', 'applies': out}))
 
 
+# the paper's strong-scaling workload (Sec. 4.3, tab:strong): benchmark P8 (E = 1e-3, Pr = 1, Ra = 100,
+# Pm = 8) from its initial condition (eqn:initial) on 6 x 144^2 x 168 at dt = 1e-5, overlap 1, ILU(0),
+# GMRES(30), VTBE one-level RAS, PPBE one- and two-level (coarse inner GMRES to 0.1); tolerances
+# eps_a / eps_r 1e-10 / 1e-8 (VTBE) and 1e-8 / 1e-6 (PPBE); one subdomain per processor core of the
+# paper's runs: np = 6 p1 p2 p3.  Printed averages over the first ten steps (tab:strong) for context:
+# np -> (VTBE its, VTBE s, PPBE one-level its, s, two-level its, inner its, s).
+STRONG = dict(Ns=144, Nr=168, E=1e-3, Ra=100.0, Pr=1.0, Pm=8.0, dt=1e-5, overlap=1, restart=30,
+              vtbe=dict(atol=1e-10, rtol=1e-8), ppbe=dict(atol=1e-8, rtol=1e-6),
+              decomps={1296: (6, 6, 6), 2592: (6, 6, 12), 5184: (12, 6, 12), 10368: (12, 12, 12)})
+STRONG_PAPER = {1296: (3.0, 6.65, 144.9, 29.69, 22.0, 13.4, 15.80), 2592: (3.0, 3.41, 154.0, 16.90, 22.2, 16.0, 10.18),
+                5184: (3.0, 1.77, 158.0, 9.60, 22.1, 14.0, 5.72), 10368: (3.0, 0.92, 151.1, 5.24, 22.4, 16.1, 4.20)}
+
+
+def strong_workload(args, fv, torch, rank, ws):
+    """tab:strong replayed on one GB300, FP64 throughout: for each of the paper's subdomain counts, --steps time
+    steps (first steps of the trajectory) with one-level and with two-level PPBE; averages of the outer
+    iterations, coarse inner iterations and GPU solve times per step of each system."""
+    import numpy as np
+    from paper_2009_02171_gb300.inputs import benchmark_state
+    c = STRONG
+    ph = dict(E=c['E'], Ra=c['Ra'], Pr=c['Pr'], Pm=c['Pm'], dt=c['dt'])
+    s0 = benchmark_state(c['Ns'], c['Nr'])
+    host = np.concatenate([s0['u'].ravel(), s0['T'], s0['B'].ravel(), s0['P'], s0['Pb']])
+    g = fv.fv_build_grid(c['Ns'], c['Nr'])
+    init = torch.tensor(host, device='cuda')
+    st = fv.fv_state_create(g, init, **ph)
+    cfl = fv.fv_state_diagnostics(st)['cfl_alfven']
+    rows = {}
+    for npc, parts in c['decomps'].items():
+        t0 = time.perf_counter()
+        V = fv.fv_assemble_system(g, fv.FV_VTBE, **ph, p=parts, overlap=c['overlap'], levels=1)
+        row = {'subdomains': 6 * parts[0] * parts[1] * parts[2], 'boxes': [c['Ns'] // parts[0], c['Ns'] // parts[1],
+                                                                           c['Nr'] // parts[2]]}
+        for lv in (1, 2):
+            P = fv.fv_assemble_system(g, fv.FV_PPBE, **ph, p=parts, overlap=c['overlap'], levels=lv, overlap_coarse=1,
+                                      coarse_rtol=0.1)
+            fv.fv_state_reset(st, init)
+            vi, vt, pi, pin, pt = [], [], [], [], []
+            for _ in range(args.steps):
+                sv, sp = fv.fv_time_step_opts(st, V, P, 1, vtbe_opts=dict(c['vtbe'], restart=c['restart']),
+                                              ppbe_opts=dict(c['ppbe'], restart=c['restart']))
+                vi.append(sv.iters), vt.append(sv.time_ms), pi.append(sp.iters), pin.append(sp.inner_iters)
+                pt.append(sp.time_ms)
+            mean = lambda a: round(sum(a) / len(a), 2)
+            if lv == 1:
+                row.update(vtbe_its=mean(vi), vtbe_ms=mean(vt), ppbe1_its=mean(pi), ppbe1_ms=mean(pt))
+            else:
+                row.update(ppbe2_its=mean(pi), ppbe2_inner_per_outer=round(sum(pin) / max(sum(pi), 1), 1),
+                           ppbe2_ms=mean(pt))
+            fv.fv_free_system(P)
+        fv.fv_free_system(V)
+        row['setup_s'] = round(time.perf_counter() - t0, 1)
+        pp = STRONG_PAPER[npc]
+        row['paper_taihulight'] = dict(vtbe_its=pp[0], vtbe_s=pp[1], ppbe1_its=pp[2], ppbe1_s=pp[3], ppbe2_its=pp[4],
+                                       ppbe2_inner=pp[5], ppbe2_s=pp[6])
+        rows[npc] = row
+        if rank == 0:
+            print(json.dumps({'np': npc, **row}), flush=True)
+    fv.fv_free_state(st)
+    fv.fv_free_grid(g)
+    if rank == 0:
+        print(json.dumps({'metric': 'strong-scaling workload replayed on one GPU (tab:strong)', 'workload':
+                          'P8 on 6x144^2x168 (20.9M cells), dt 1e-5, FP64, GMRES(30), overlap 1, ILU(0)',
+                          'cfl_alfven': round(cfl, 3), 'steps': args.steps, 'rows': rows}))
+
+
 def build_arm(fv, torch, c, dt, mode, host):
     """(handles, setup seconds, learned-correction info) of arm mode in {fp64, mixed, learned} on workload c."""
     ph = dict(E=c['E'], Ra=c['Ra'], Pr=c['Pr'], Pm=c['Pm'], dt=dt)
@@ -426,7 +500,7 @@ def build_arm(fv, torch, c, dt, mode, host):
     net, info = None, None
     if mode == 'learned':
         from paper_2009_02171_gb300.learned import train_learned_correction
-        L = LEARN
+        L = c.get('learn', LEARN)
         net, info = train_learned_correction(P, c['Ns'], c['Nr'], C=L['C'], levels=L['levels'], npairs=L['pairs'],
                                              epochs=L['epochs'], batch=L['batch'], lr=L['lr'],
                                              coarse_its=L['coarse_its'])
@@ -462,15 +536,13 @@ def main():
     torch.cuda.set_device(local)
     from paper_2009_02171_gb300 import fv
     from paper_2009_02171_gb300.inputs import initial_state
-    if args.workload in ('batch', 'net'):
-        (batch_workload if args.workload == 'batch' else net_workload)(args, fv, torch, rank, ws)
+    if args.workload in ('batch', 'net', 'strong'):
+        {'batch': batch_workload, 'net': net_workload, 'strong': strong_workload}[args.workload](args, fv, torch, rank, ws)
         if ws > 1:
             dist.destroy_process_group()
         return
 
-    c = dict(CFG)
-    if args.ns:
-        c['Ns'] = c['Nr'] = args.ns
+    c = config_of(args)
     s0 = initial_state(c['Ns'], c['Nr'], c['seed'] + rank)
     host = np.concatenate([s0['u'].ravel(), s0['T'], s0['B'].ravel(), s0['P'], s0['Pb']])
     N = host.size // 9
@@ -659,7 +731,7 @@ def main():
             'precision': head,
             'arms': others,
             'learned': ({k: (round(v, 4) if isinstance(v, float) else v) for k, v in info.items()} if info else None),
-            'config': {'workload': workload_name(args.ns),
+            'config': {'workload': workload_name(c),
                        'cells': 6 * c['Ns'] ** 2 * c['Nr'], 'subdomains': 6 * c['p'][0] * c['p'][1] * c['p'][2],
                        'overlap': c['overlap'], 'ppbe_levels': c['levels'], 'rtol': c['rtol'],
                        'restart': c['restart'], 'dt': dt, 'cfl_alfven_initial': round(cfl_unit * dt, 4),
@@ -701,7 +773,8 @@ def box_cells(Ns, Nr, p, delta):
 def network_flops(c):
     """Algorithmic FLOPs of one forward pass of the learned correction (one sample): 2 * 27 * ci * co per cell
     of each convolution's level, logical channel counts."""
-    C, L = LEARN['C'], LEARN['levels']
+    learn = c.get('learn', LEARN)
+    C, L = learn['C'], learn['levels']
     ns, nr = c['Ns'] // 2, c['Nr'] // 2
     cells = [6 * (ns >> l) ** 2 * (nr >> l) for l in range(L + 1)]
     f = 0
@@ -712,11 +785,30 @@ def network_flops(c):
     return f + 2 * 27 * C * 2 * cells[0]
 
 
-def workload_name(ns=0):
-    """The workload description, for the default 6 x 64^2 x 64 shell or a 6 x ns^2 x ns profiling case."""
-    if not ns:
-        return WORKLOAD
-    return WORKLOAD.replace('shell 6x64^2x64 (1.57M cells)', 'shell 6x%d^2x%d (%d cells)' % (ns, ns, 6 * ns ** 3))
+def workload_name(c):
+    """Description of the time-step workload c (a CONFIGS entry, possibly resized)."""
+    cells = 6 * c['Ns'] ** 2 * c['Nr']
+    nsub = 6 * c['p'][0] * c['p'][1] * c['p'][2]
+    lv = {1: 'one-level', 2: 'two-level', 3: 'three-level'}.get(c['levels'], '%d-level' % c['levels'])
+    return ('shell 6x%d^2x%d (%.2fM cells), time step: VTBE one-level RAS + PPBE %s RAS, %d subdomains overlap %d, '
+            'FGMRES(%d) to 1e-8 relative FP64 residual; mixed precision = FP32 inner FGMRES (operator, ILU(0) sweeps, '
+            'coarse levels; one Gram-Schmidt pass) inside FP64 outer FGMRES (two passes); learned = mixed with the '
+            'PPBE coarse solve replaced by a BF16 cubed-sphere U-Net followed by a few coarse FGMRES iterations'
+            % (c['Ns'], c['Nr'], cells / 1e6, lv, nsub, c['overlap'], c['restart']))
+
+
+def config_of(args):
+    """The workload of the command line: --config, optionally resized to 6 x ns^2 x ns by --ns."""
+    c = dict(CONFIGS[args.config], name=args.config, learn=LEARN_BY_CONFIG.get(args.config, LEARN))
+    if args.ns:
+        c['Ns'] = c['Nr'] = args.ns
+    if args.levels:
+        c['levels'] = args.levels
+    if args.coarse_its:
+        c['coarse_its'] = args.coarse_its
+    if args.ppbe_inner:
+        c['ppbe_inner'] = args.ppbe_inner
+    return c
 
 
 def algorithmic_bytes(cat, c, N, es):

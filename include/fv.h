@@ -151,8 +151,10 @@ fv_status fv_apply_op_fp32(const fv_system* s, const float* x, float* y, void* s
  * holds until the process exits.  Systems whose ghost layer is larger (e.g.
  * VTBE beyond Ns = Nr = 64, PPBE beyond Ns = Nr = 128) are rejected with
  * FV_EINVAL.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the array: calls whose kernels
+ * (cudaGetSymbolAddress) with that device current, once per device and
+ * process (concurrent first calls from several host threads are safe); make
+ * that first call before any stream capture.  The address is not looked up
+ * again: after cudaDeviceReset, do not call this on that device again.  All calls share the array: calls whose kernels
  * overlap on the GPU (e.g. on two streams at once) race on it; serialise them.
  * The array keeps the last call's contents, and each call overwrites every
  * slot it reads.  The paper has no counterpart: this is a deployment
@@ -222,6 +224,11 @@ fv_status fv_state_reset(fv_state* st, const double* in, void* stream);
  * entries (VTBE, PPBE per step). */
 fv_status fv_time_step(fv_state* st, const fv_system* vtbe, const fv_system* ppbe, const fv_gmres_opts* opts,
                        int nsteps, fv_solve_stats* stats, void* stream);
+/* fv_time_step with separate stopping rules for the two systems: vopts for
+ * VTBE, popts for PPBE (the paper's presets of Sec. 4 are eps_a/eps_r =
+ * 1e-10/1e-8 for VTBE and 1e-8/1e-6 for PPBE). */
+fv_status fv_time_step_opts(fv_state* st, const fv_system* vtbe, const fv_system* ppbe, const fv_gmres_opts* vopts,
+                            const fv_gmres_opts* popts, int nsteps, fv_solve_stats* stats, void* stream);
 
 /* Diagnostics of the state after its last step (paper Sec. 4.2 and the
  * divergence constraint eqn:divtime).  Norms are Euclidean over cells.

@@ -1,6 +1,7 @@
 // Operator kernels: panel-edge ghost layer, matrix-free VTBE / PPBE apply,
 // and extraction of the structured subdomain matrices for ILU(0).
 #include <cstdio>
+#include <mutex>
 #include <string>
 
 #include "stencil.cuh"
@@ -102,17 +103,22 @@ static void launch_apply(const GT& G, const Coefs<typename GT::real>& cf, int d,
 static __device__ __align__(256) double g_static_ghost[FV_STATIC_GHOST_DOUBLES];
 
 static const int kMaxDevices = 64;
-static double* g_static_ghost_addr[kMaxDevices] = {};  // device address per device, looked up once
+// device address of the array per device, looked up once per device (std::call_once makes concurrent first
+// calls from several host threads safe); a device reset invalidates it (documented in fv.h)
+static double* g_static_ghost_addr[kMaxDevices] = {};
+static cudaError_t g_static_ghost_err[kMaxDevices] = {};
+static std::once_flag g_static_ghost_once[kMaxDevices];
 
 static fv_status static_ghost_address(double** out) {
   int dev = 0;
   FV_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return set_error("fv_apply_op_noalloc: device ordinal out of range"), FV_EINVAL;
-  if (!g_static_ghost_addr[dev]) {
+  std::call_once(g_static_ghost_once[dev], [dev] {
     void* p = nullptr;
-    FV_CUDA(cudaGetSymbolAddress(&p, g_static_ghost));
+    g_static_ghost_err[dev] = cudaGetSymbolAddress(&p, g_static_ghost);
     g_static_ghost_addr[dev] = static_cast<double*>(p);
-  }
+  });
+  FV_CUDA(g_static_ghost_err[dev]);
   *out = g_static_ghost_addr[dev];
   return FV_OK;
 }

@@ -77,7 +77,12 @@ fv_status fv_state_reset(fv_state* s, const double* in, void* stream) {
 
 fv_status fv_time_step(fv_state* s, const fv_system* vtbe, const fv_system* ppbe, const fv_gmres_opts* opts,
                        int nsteps, fv_solve_stats* stats, void* stream) {
-  if (!s || !vtbe || !ppbe || !opts || nsteps < 0 || vtbe->kind != FV_VTBE || ppbe->kind != FV_PPBE ||
+  return fv_time_step_opts(s, vtbe, ppbe, opts, opts, nsteps, stats, stream);
+}
+
+fv_status fv_time_step_opts(fv_state* s, const fv_system* vtbe, const fv_system* ppbe, const fv_gmres_opts* opts,
+                            const fv_gmres_opts* popts, int nsteps, fv_solve_stats* stats, void* stream) {
+  if (!s || !vtbe || !ppbe || !opts || !popts || nsteps < 0 || vtbe->kind != FV_VTBE || ppbe->kind != FV_PPBE ||
       vtbe->grid != s->grid || ppbe->grid != s->grid)
     return set_error("fv_time_step: bad argument (systems must be VTBE and PPBE of the state's grid)"), FV_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
@@ -115,7 +120,7 @@ fv_status fv_time_step(fv_state* s, const fv_system* vtbe, const fv_system* ppbe
         (rc = weighted_mean_remove(g, s->bP, st, s->part, s->sums)))
       return rc;
     FV_CUDA(cudaMemcpyAsync(s->xP, P, 2 * N * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    rc = gmres(ppbe, s->bP, s->xP, opts, &sp, st, false);
+    rc = gmres(ppbe, s->bP, s->xP, popts, &sp, st, false);
     if (rc) return rc;
     if ((rc = weighted_mean_remove(g, s->xP, st, s->part, s->sums))) return rc;
     // projection: u = u~ - dt/2 G P, B = B~ - dt/2 G P_b

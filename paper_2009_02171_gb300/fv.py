@@ -96,6 +96,7 @@ SIGNATURES = {
     'fv_state_reset': [_VP, _DP, _VP],
     'fv_state_diagnostics': [_VP, _VP, _P(fv_diag), _VP],
     'fv_time_step': [_VP, _VP, _VP, _P(fv_gmres_opts), ctypes.c_int, _P(fv_solve_stats), _VP],
+    'fv_time_step_opts': [_VP, _VP, _VP, _P(fv_gmres_opts), _P(fv_gmres_opts), ctypes.c_int, _P(fv_solve_stats), _VP],
     'fv_profile_enable': [ctypes.c_int],
     'fv_profile_read': [ctypes.c_int, _P(ctypes.c_longlong), _P(ctypes.c_double)],
     'fv_last_error': [],
@@ -266,6 +267,17 @@ def fv_time_step(state, vtbe, ppbe, nsteps=1, restart=30, max_it=3000, atol=0.0,
     stats = (fv_solve_stats * (2 * nsteps))()
     _check(lib.fv_time_step(state, vtbe, ppbe, ctypes.byref(fv_gmres_opts(restart, max_it, atol, rtol)), nsteps,
                             stats, _stream()))
+    return list(stats)
+
+
+def fv_time_step_opts(state, vtbe, ppbe, nsteps=1, vtbe_opts=None, ppbe_opts=None):
+    """Time steps with separate FGMRES options per system: dicts of restart, max_it, atol, rtol."""
+    def mk(o):
+        o = dict(dict(restart=30, max_it=3000, atol=0.0, rtol=1e-8), **(o or {}))
+        return fv_gmres_opts(o['restart'], o['max_it'], o['atol'], o['rtol'])
+    stats = (fv_solve_stats * (2 * nsteps))()
+    _check(lib.fv_time_step_opts(state, vtbe, ppbe, ctypes.byref(mk(vtbe_opts)), ctypes.byref(mk(ppbe_opts)), nsteps,
+                                 stats, _stream()))
     return list(stats)
 
 

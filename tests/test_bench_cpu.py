@@ -8,12 +8,13 @@ sys.path.insert(0, ROOT)
 import bench  # noqa: E402
 
 
-def test_workload_name_of_a_profiling_size_keeps_the_precisions():
-    """--ns replaces the shell size only (not the '64' of 'FP64')."""
-    w = bench.workload_name(32)
-    assert w.startswith('shell 6x32^2x32 (196608 cells)')
-    assert 'FP64 residual' in w and 'FP64 outer FGMRES' in w
-    assert bench.workload_name(0) == bench.WORKLOAD
+def test_workload_names_state_the_shell_levels_and_precisions():
+    for name, c in bench.CONFIGS.items():
+        w = bench.workload_name(c)
+        assert w.startswith('shell 6x%d^2x%d' % (c['Ns'], c['Nr']))
+        assert 'FP64 residual' in w and 'FP64 outer FGMRES' in w and 'FGMRES(%d)' % c['restart'] in w
+    assert '%d subdomains' % (6 * 6 * 6 * 8) in bench.workload_name(bench.CONFIGS['shell192'])
+    assert 'three-level' in bench.workload_name(bench.CONFIGS['shell192'])
 
 
 def test_algorithmic_bytes_of_the_bench_categories():

@@ -215,6 +215,31 @@ def test_learned_preconditioner_converges_and_reports_gain(fv, ppbe):
     assert hybrid.fallback == 0
 
 
+def test_learned_correction_gains_over_the_same_coarse_budget(fv, ppbe):
+    """What the trained network gains over the method without it, at the same coarse work per application:
+    the plain two-level preconditioner with exactly 2 coarse FGMRES iterations against the network's
+    correction followed by the same 2 iterations (seeded right-hand sides, FGMRES(30) to 1e-8)."""
+    fv, s, net, n, _ = ppbe
+    g = fv.fv_build_grid(16, 16)
+    s2 = fv.fv_assemble_system(g, 1, **PH, p=(2, 2, 2), overlap=1, levels=2, overlap_coarse=1, coarse_maxit=2,
+                               coarse_rtol=1e-30)
+    plain, learned = [], []
+    for seed in (31, 33, 35):
+        st, res = _solve(fv, s2, n, seed)
+        assert st.converged and res < 1.0001e-8
+        plain.append(st.iters)
+        fv.fv_pc_set_learned(s2, net, coarse_its=2)
+        st, res = _solve(fv, s2, n, seed)
+        fv.fv_pc_set_learned(s2, None)
+        assert st.converged and res < 1.0001e-8 and st.fallback == 0
+        learned.append(st.iters)
+    print('\nsame coarse budget (2 coarse iterations per application): outer iterations plain %s, learned %s'
+          % (plain, learned))
+    assert sum(learned) < sum(plain) and all(a <= b for a, b in zip(learned, plain))
+    fv.fv_free_system(s2)
+    fv.fv_free_grid(g)
+
+
 @pytest.mark.parametrize('bad', ['zero', 'nan'])
 def test_plain_fallback_finishes_a_failed_learned_solve(fv, ppbe, bad):
     fv, s, _, n, _ = ppbe

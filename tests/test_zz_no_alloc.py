@@ -42,6 +42,24 @@ def test_noalloc_apply_matches_apply_on_consecutive_calls(fv, kind, Ns, Nr):
     fv.fv_free_grid(g)
 
 
+def test_noalloc_larger_then_smaller_system(fv):
+    """A call on a system with a larger ghost layer, then one on a smaller system: the second call
+    overwrites every slot it reads, so the stale tail of the array does not leak into its result."""
+    res = []
+    for kind, Ns, Nr in ((0, 16, 14), (1, 8, 6)):
+        g = fv.fv_build_grid(Ns, Nr)
+        s = fv.fv_assemble_system(g, kind, **PH)
+        n = fv.fv_system_size(s)
+        x = torch.tensor(random_vector(n, 200 + kind), device='cuda')
+        ref = fv.fv_apply_op(s, x, torch.empty_like(x))
+        got = fv.fv_apply_op_noalloc(s, x, torch.empty_like(x))
+        torch.cuda.synchronize()
+        res.append((got - ref).abs().max().item() / ref.abs().max().item())
+        fv.fv_free_system(s)
+        fv.fv_free_grid(g)
+    assert max(res) < 1e-12, res
+
+
 def test_noalloc_rejects_systems_beyond_the_static_limit(fv):
     g = fv.fv_build_grid(8, 640)           # VTBE ghost layer 7 x 24 x 640 x 10 = 1,075,200 doubles > 2^20
     s = fv.fv_assemble_system(g, 0, **PH, p=(1, 1, 8), overlap=1)
