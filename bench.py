@@ -88,11 +88,17 @@ def parse():
     ap.add_argument('--levels', type=int, default=0, help='override the PPBE preconditioner levels')
     ap.add_argument('--coarse-its', type=int, default=0, help='override the fixed coarse iterations (mixed precision)')
     ap.add_argument('--ppbe-inner', type=int, default=0, help='override the PPBE inner iterations (mixed precision)')
-    ap.add_argument('--workload', default='step', choices=['step', 'batch', 'net', 'trajectory', 'apply', 'strong'],
+    ap.add_argument('--vtbe-inner', type=int, default=0, help='override the VTBE inner iterations (mixed precision)')
+    ap.add_argument('--workload', default='step', choices=['step', 'batch', 'net', 'trajectory', 'apply', 'strong',
+                                                           'p8', 'convergence'],
                     help='step: the time step (headline); batch: 32 right-hand sides on uneven subdomains; '
                          'trajectory: one arm (--precision) for --steps steps from the seeded fields, one JSON '
                          'line of diagnostics per step; apply: the operator applies alone (FP64 and FP32); strong: '
-                         'the strong-scaling workload of the paper replayed on one GPU')
+                         'the strong-scaling workload of the paper replayed on one GPU; p8: benchmark P8 on grid '
+                         'G48 (--steps steps, energies every --every steps); convergence: the spatial and temporal '
+                         'convergence study of Sec. 4.1')
+    ap.add_argument('--every', type=int, default=1000, help='p8: steps between diagnostics lines')
+    ap.add_argument('--budget-min', type=float, default=0.0, help='p8: stop after this many minutes (0: none)')
     ap.add_argument('--dt', type=float, default=0.0, help='trajectory: time step (default: the CFL-limited dt)')
     return ap.parse_args()
 
@@ -488,6 +494,167 @@ def strong_workload(args, fv, torch, rank, ws):
                           'cfl_alfven': round(cfl, 3), 'steps': args.steps, 'rows': rows}))
 
 
+# benchmark P8 (Sec. 4.2, tab:gridlevels, tab:comparison): E = 1e-3, Pr = 1, Ra = 100, Pm = 8 from the
+# initial condition eqn:initial on grid G48 (6 x 48^2 x 72), dt = 8e-5 (CFL_A 1.12), run to t = 8 (one magnetic
+# diffusion time, 100,000 steps); the paper's G48 energies at the quasi-steady state and the pseudospectral
+# reference (tab:comparison)
+P8 = dict(Ns=48, Nr=72, E=1e-3, Ra=100.0, Pr=1.0, Pm=8.0, dt=8e-5, p=(3, 3, 3), overlap=2, overlap_coarse=1,
+          levels=2, vtbe_inner=4, ppbe_inner=8, coarse_its=10, inner_gs=1,
+          vtbe=dict(atol=1e-10, rtol=1e-8), ppbe=dict(atol=1e-8, rtol=1e-6))
+P8_PAPER = dict(G48=dict(E_mag=313663.1, E_kin=21928.4), PS=dict(E_mag=312754.7, E_kin=21634.9))
+
+
+def p8_workload(args, fv, torch, rank, ws):
+    """Benchmark P8 on G48 with the mixed-precision solver (both systems to the paper's stopping rules):
+    E_kin and E_mag (Sec. 4.2 definitions) every --every steps, to compare with tab:comparison."""
+    import numpy as np
+    from paper_2009_02171_gb300.inputs import benchmark_state
+    c = dict(P8)
+    for k, a in (('coarse_its', args.coarse_its), ('ppbe_inner', args.ppbe_inner), ('vtbe_inner', args.vtbe_inner)):
+        if a:
+            c[k] = a
+    ph = dict(E=c['E'], Ra=c['Ra'], Pr=c['Pr'], Pm=c['Pm'], dt=c['dt'])
+    s0 = benchmark_state(c['Ns'], c['Nr'])
+    host = np.concatenate([s0['u'].ravel(), s0['T'], s0['B'].ravel(), s0['P'], s0['Pb']])
+    t0 = time.perf_counter()
+    g = fv.fv_build_grid(c['Ns'], c['Nr'])
+    mv = dict(precision=fv.FV_PREC_FP32, inner_maxit=c['vtbe_inner'], inner_gs_passes=c['inner_gs'])
+    mp = dict(precision=fv.FV_PREC_FP32, inner_maxit=c['ppbe_inner'], coarse_maxit=c['coarse_its'],
+              inner_gs_passes=c['inner_gs'])
+    V = fv.fv_assemble_system(g, fv.FV_VTBE, **ph, p=c['p'], overlap=c['overlap'], levels=1, **mv)
+    P = fv.fv_assemble_system(g, fv.FV_PPBE, **ph, p=c['p'], overlap=c['overlap'], levels=c['levels'],
+                              overlap_coarse=c['overlap_coarse'], **mp)
+    st = fv.fv_state_create(g, torch.tensor(host, device='cuda'), **ph)
+    d = fv.fv_state_diagnostics(st, P)
+    if rank == 0:
+        print(json.dumps({'step': 0, 't': 0.0, 'E_kin': d['E_kin'], 'E_mag': d['E_mag'], 'cfl_alfven': d['cfl_alfven'],
+                          'setup_s': round(time.perf_counter() - t0, 1)}), flush=True)
+    vo, po = dict(c['vtbe'], restart=30), dict(c['ppbe'], restart=30)
+    t_run, n, its = time.perf_counter(), 0, [0, 0]
+    while n < args.steps:
+        k = min(args.every, args.steps - n)
+        ss = fv.fv_time_step_opts(st, V, P, k, vtbe_opts=vo, ppbe_opts=po)
+        n += k
+        its[0] += sum(x.iters for x in ss[0::2])
+        its[1] += sum(x.iters for x in ss[1::2])
+        d = fv.fv_state_diagnostics(st, P)
+        el = time.perf_counter() - t_run
+        if rank == 0:
+            print(json.dumps({'step': n, 't': round(n * c['dt'], 5), 'E_kin': d['E_kin'], 'E_mag': d['E_mag'],
+                              'cfl_alfven': d['cfl_alfven'], 'divB_face_over_rhs': d['divB_face'] / d['divB_rhs'],
+                              'its_vtbe_ppbe_mean': [round(its[0] / n, 2), round(its[1] / n, 2)],
+                              'ms_per_step': round(el / n * 1e3, 2)}), flush=True)
+        if not (np.isfinite(d['E_kin']) and np.isfinite(d['E_mag'])):
+            break
+        if args.budget_min and el > args.budget_min * 60:
+            break
+    if rank == 0:
+        print(json.dumps({'metric': 'benchmark P8 on G48 (tab:comparison)', 'steps': n, 't': n * c['dt'],
+                          'inner_iterations_vtbe_ppbe_coarse': [c['vtbe_inner'], c['ppbe_inner'], c['coarse_its']],
+                          't_magnetic': n * c['dt'] / c['Pm'], 'E_kin': d['E_kin'], 'E_mag': d['E_mag'],
+                          'paper': P8_PAPER, 'rel_vs_paper_G48': {k: d[k] / P8_PAPER['G48'][k] - 1 for k in
+                                                                  ('E_mag', 'E_kin')},
+                          'ms_per_step': round((time.perf_counter() - t_run) / max(n, 1) * 1e3, 2)}), flush=True)
+    for h, f in ((st, fv.fv_free_state), (V, fv.fv_free_system), (P, fv.fv_free_system), (g, fv.fv_free_grid)):
+        f(h)
+
+
+# convergence study (Sec. 4.1): Pr = 1, Ra = 100, E = 0.1, Pm = 1000, initial condition eqn:initial.  Space:
+# dt = 1e-5 to t = 1e-3 on 6 x N^3 against N = 128 (reference restricted by 2 x 2 x 2 means).  Time: 6 x 32^3 to
+# t = 1 against the smallest step (the paper's printed reference step is read as garbled).  FP64 solves to a
+# 1e-10 relative residual; boxes of 16^3 cells, two-level PPBE.
+CONV = dict(E=0.1, Ra=100.0, Pr=1.0, Pm=1000.0, rtol=1e-10, space_grids=(16, 32, 64), space_ref=128,
+            space_dt=1e-5, space_t=1e-3, time_grid=32, time_dts=(8e-3, 4e-3, 2e-3, 1e-3), time_ref_dt=2.5e-4,
+            time_t=1.0)
+
+
+def convergence_workload(args, fv, torch, rank, ws):
+    """L2 errors (Sec. 4.1 definition, sqrt(sum_c sum_cells (v - v_ref)^2 V)) of u, Theta and B against a
+    finer reference, in space and in time, and the observed orders."""
+    import numpy as np
+    from paper_2009_02171_gb300.inputs import benchmark_state
+    c = CONV
+    ph0 = dict(E=c['E'], Ra=c['Ra'], Pr=c['Pr'], Pm=c['Pm'])
+
+    def run(n, dt, t_end):
+        g = fv.fv_build_grid(n, n)
+        ph = dict(ph0, dt=dt)
+        parts = (max(1, n // 16),) * 3
+        V = fv.fv_assemble_system(g, fv.FV_VTBE, **ph, p=parts, overlap=1, levels=1)
+        P = fv.fv_assemble_system(g, fv.FV_PPBE, **ph, p=parts, overlap=1, levels=2 if n >= 16 else 1,
+                                  overlap_coarse=1)
+        s0 = benchmark_state(n, n)
+        host = np.concatenate([s0['u'].ravel(), s0['T'], s0['B'].ravel(), s0['P'], s0['Pb']])
+        st = fv.fv_state_create(g, torch.tensor(host, device='cuda'), **ph)
+        steps = int(round(t_end / dt))
+        t0 = time.perf_counter()
+        left = steps
+        while left:
+            k = min(left, 100)
+            fv.fv_time_step(st, V, P, k, rtol=c['rtol'])
+            left -= k
+        out = torch.empty(host.size, dtype=torch.float64, device='cuda')
+        x = fv.fv_state_get(st, out).cpu().numpy()
+        el = time.perf_counter() - t0
+        for h, f in ((st, fv.fv_free_state), (V, fv.fv_free_system), (P, fv.fv_free_system), (g, fv.fv_free_grid)):
+            f(h)
+        return x, steps, el
+
+    def volumes(n, ri=7.0 / 13.0, ro=20.0 / 13.0):
+        """Cell volumes sqrt(g)(centre) h_s^2 h_r (Sec. 3.2), [panel][k][j][i]."""
+        hs, hr = np.pi / (2 * n), (ro - ri) / n
+        xi = -np.pi / 4 + (np.arange(n) + 0.5) * hs
+        X, Y = np.tan(xi)[None, :], np.tan(xi)[:, None]
+        d = 1 + X * X + Y * Y
+        sig = (1 + X * X) * (1 + Y * Y) / d ** 1.5
+        r = ri + (np.arange(n) + 0.5) * hr
+        v = (r ** 2)[:, None, None] * sig[None] * hs * hs * hr
+        return np.broadcast_to(v, (6, n, n, n)).ravel()
+
+    def restrict(x, n, levels):
+        """Mean of the 2 x 2 x 2 children, `levels` times, per field ([comp][panel][k][j][i])."""
+        a = x.reshape(-1, 6, n, n, n)
+        for _ in range(levels):
+            m = a.shape[2] // 2
+            a = a.reshape(a.shape[0], 6, m, 2, m, 2, m, 2).mean(axis=(3, 5, 7))
+        return a.reshape(a.shape[0], -1)
+
+    def l2(x, ref, n):
+        v = volumes(n)
+        xa, ra = x.reshape(9, -1), ref.reshape(9, -1)
+        out = {}
+        for name, sl in (('u', slice(0, 3)), ('T', slice(3, 4)), ('B', slice(4, 7))):
+            out[name] = float(np.sqrt((((xa[sl] - ra[sl]) ** 2) * v).sum()))
+        return out
+
+    res = {'space': {}, 'time': {}}
+    ref, _, el = run(c['space_ref'], c['space_dt'], c['space_t'])
+    res['space']['reference'] = dict(n=c['space_ref'], seconds=round(el, 1))
+    lev = {n: int(round(np.log2(c['space_ref'] / n))) for n in c['space_grids']}
+    errs = {}
+    for n in c['space_grids']:
+        x, steps, el = run(n, c['space_dt'], c['space_t'])
+        errs[n] = l2(x, restrict(ref, c['space_ref'], lev[n]).ravel(), n)
+        res['space'][n] = dict(errs[n], steps=steps, seconds=round(el, 1))
+    ns = list(c['space_grids'])
+    res['space']['orders'] = {f: [round(np.log2(errs[a][f] / errs[b][f]), 2) for a, b in zip(ns, ns[1:])]
+                              for f in ('u', 'T', 'B')}
+    n = c['time_grid']
+    ref, steps, el = run(n, c['time_ref_dt'], c['time_t'])
+    res['time']['reference'] = dict(dt=c['time_ref_dt'], steps=steps, seconds=round(el, 1))
+    errs = {}
+    for dt in c['time_dts']:
+        x, steps, el = run(n, dt, c['time_t'])
+        errs[dt] = l2(x, ref, n)
+        res['time'][dt] = dict(errs[dt], steps=steps, seconds=round(el, 1))
+    ds = list(c['time_dts'])
+    res['time']['orders'] = {f: [round(np.log2(errs[a][f] / errs[b][f]), 2) for a, b in zip(ds, ds[1:])]
+                             for f in ('u', 'T', 'B')}
+    if rank == 0:
+        print(json.dumps({'metric': 'convergence study (Sec. 4.1): L2 errors and orders', 'physics': ph0,
+                          'results': {k: {str(kk): vv for kk, vv in v.items()} for k, v in res.items()}}))
+
+
 def build_arm(fv, torch, c, dt, mode, host):
     """(handles, setup seconds, learned-correction info) of arm mode in {fp64, mixed, learned} on workload c."""
     ph = dict(E=c['E'], Ra=c['Ra'], Pr=c['Pr'], Pm=c['Pm'], dt=dt)
@@ -539,8 +706,9 @@ def main():
     torch.cuda.set_device(local)
     from paper_2009_02171_gb300 import fv
     from paper_2009_02171_gb300.inputs import initial_state
-    if args.workload in ('batch', 'net', 'strong'):
-        {'batch': batch_workload, 'net': net_workload, 'strong': strong_workload}[args.workload](args, fv, torch, rank, ws)
+    if args.workload in ('batch', 'net', 'strong', 'p8', 'convergence'):
+        {'batch': batch_workload, 'net': net_workload, 'strong': strong_workload, 'p8': p8_workload,
+         'convergence': convergence_workload}[args.workload](args, fv, torch, rank, ws)
         if ws > 1:
             dist.destroy_process_group()
         return
