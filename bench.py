@@ -77,7 +77,7 @@ def parse():
     ap.add_argument('--warmup', type=int, default=3)
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
     ap.add_argument('--no-cpu-baseline', action='store_true')
-    ap.add_argument('--precision', default=None, choices=['learned', 'mixed', 'fp64'],
+    ap.add_argument('--precision', default=None, choices=['learned', 'mixed', 'bf16', 'fp64'],
                     help='headline arm (learned = mixed precision with the learned coarse correction; default: the '
                          'last arm of the shell, learned where it has one); the other arms are timed beside it')
     ap.add_argument('--single', action='store_true', help='time the headline arm only (profiling runs)')
@@ -656,13 +656,15 @@ def convergence_workload(args, fv, torch, rank, ws):
 
 
 def build_arm(fv, torch, c, dt, mode, host):
-    """(handles, setup seconds, learned-correction info) of arm mode in {fp64, mixed, learned} on workload c."""
+    """(handles, setup seconds, learned-correction info) of arm mode in {fp64, mixed, bf16, learned} on workload c
+    (bf16: mixed precision with the ILU(0) factors stored in BF16)."""
     ph = dict(E=c['E'], Ra=c['Ra'], Pr=c['Pr'], Pm=c['Pm'], dt=dt)
     t = time.perf_counter()
     mixed = mode != 'fp64'
+    prec = fv.FV_PREC_BF16 if mode == 'bf16' else fv.FV_PREC_FP32
     g = fv.fv_build_grid(c['Ns'], c['Nr'])
-    mv = dict(precision=fv.FV_PREC_FP32, inner_maxit=c['vtbe_inner'], inner_gs_passes=c['inner_gs']) if mixed else {}
-    mpp = dict(precision=fv.FV_PREC_FP32, inner_maxit=c['ppbe_inner'], coarse_maxit=c['coarse_its'],
+    mv = dict(precision=prec, inner_maxit=c['vtbe_inner'], inner_gs_passes=c['inner_gs']) if mixed else {}
+    mpp = dict(precision=prec, inner_maxit=c['ppbe_inner'], coarse_maxit=c['coarse_its'],
                inner_gs_passes=c['inner_gs']) if mixed else {}
     V = fv.fv_assemble_system(g, fv.FV_VTBE, **ph, p=c['p'], overlap=c['overlap'], levels=1, **mv)
     P = fv.fv_assemble_system(g, fv.FV_PPBE, **ph, p=c['p'], overlap=c['overlap'], levels=c['levels'],
@@ -897,7 +899,7 @@ def main():
             'metric': METRIC, 'value': round(ms, 3), 'unit': 'ms/step', 'n_gpus': ws, 'steps': args.steps,
             'warmup': args.warmup, 'ms_per_step': round(ms, 3), 'higher_is_better': False, 'scaling': 'weak',
             'vs_baseline': None,
-            'dtype': {'fp64': 'f64', 'mixed': 'f32 inner / f64 outer',
+            'dtype': {'fp64': 'f64', 'mixed': 'f32 inner / f64 outer', 'bf16': 'f32 inner (bf16 factors) / f64 outer',
                       'learned': 'f32 inner / f64 outer, bf16 network'}[head],
             'data': 'synthetic',
             'precision': head,

@@ -120,6 +120,11 @@ typedef struct {
 } fv_pc_desc;
 #define FV_PREC_FP64 0
 #define FV_PREC_FP32 1
+/* FV_PREC_BF16: FV_PREC_FP32 with the ILU(0) factors of every level stored in
+ * BF16 (rounded from the FP64 factorization; the sweeps convert them and
+ * compute in FP32), halving the factor bytes the sweeps read.  The outer
+ * residual stays FP64.  fv_gmres_solve_batch rejects such systems. */
+#define FV_PREC_BF16 2
 
 /* Builds the system `kind` (FV_VTBE: A = I - dt/2 [L1 R1; R2 L2; L3];
  * FV_PPBE: A = dt/2 D G for (P Neumann, P_b Dirichlet)), its subdomain

@@ -31,11 +31,13 @@ static fv_status make_system(const fv_grid* g, int kind, const fv_phys* ph, cons
   if (pc->inner_gs_passes < 0 || pc->inner_gs_passes > 2)
     return set_error("fv_assemble_system: inner_gs_passes must be 0, 1 or 2"), FV_EINVAL;
   if (pc->levels < 1 || pc->levels > 6) return set_error("fv_assemble_system: levels must be 1..6"), FV_EINVAL;
+  if (pc->precision < FV_PREC_FP64 || pc->precision > FV_PREC_BF16)
+    return set_error("fv_assemble_system: precision must be FV_PREC_FP64, FV_PREC_FP32 or FV_PREC_BF16"), FV_EINVAL;
   fv_system* s = new fv_system();
   s->grid = g, s->kind = kind, s->d = kind == FV_VTBE ? 7 : 2;
   s->n = s->d * g->h.N;
   s->phys = *ph, s->pc = *pc;
-  s->prec32 = pc->precision == FV_PREC_FP32;
+  s->prec32 = pc->precision != FV_PREC_FP64;
   fv_status rc = FV_OK;
   const size_t ng = (size_t)s->d * 6 * 4 * g->h.Nr * (g->h.Ns + 2);
   if (cudaMalloc(&s->ghost, ng * sizeof(double)) != cudaSuccess) {
@@ -58,7 +60,7 @@ static fv_status make_system(const fv_grid* g, int kind, const fv_phys* ph, cons
     s->allocs.insert(s->allocs.end(), {s->ghost32, s->r32, s->x32});
   }
   if ((rc = build_subdomains(s, g)) || (rc = assemble_subdomains(s)) || (rc = ilu_factor(s)) ||
-      (rc = prepare_sweeps(s, s->prec32)) || (rc = sweeps_smem_attr(s))) {
+      (rc = prepare_sweeps(s, pc->precision == FV_PREC_BF16 ? 2 : s->prec32)) || (rc = sweeps_smem_attr(s))) {
     free_system(s);
     return rc;
   }

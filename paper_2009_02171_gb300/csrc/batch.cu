@@ -28,6 +28,14 @@ constexpr int BK = 32;        // max basis vectors
 constexpr int BBLOCKS = 152;  // reduction blocks per right-hand side
 constexpr int BTHREADS = 256;
 
+// device-side Arnoldi bookkeeping of one right-hand side (Hessenberg column-major H[j * BK + i])
+struct BatchArn {
+  double H[BK * BK];
+  double cs[BK], sn[BK], g[BK + 1], y[BK];
+  double beta, r0, target;
+  int its, kk, done;
+};
+
 struct BatchWork {
   int nrhs = 0, m = 0, G = 0;
   long long n = 0;
@@ -40,6 +48,12 @@ struct BatchWork {
   int ctas = 0;            // persistent CTAs
   size_t smem = 0;
   int ring_in_smem = 0;
+  BatchArn* arn = nullptr;       // [nrhs] device Arnoldi state
+  BatchArn* arn_host = nullptr;  // pinned copy for the convergence check after a cycle
+  cudaGraphExec_t cycle = nullptr;  // one restart cycle, captured for (B, X, m)
+  const double* gB = nullptr;
+  double* gX = nullptr;
+  int gm = 0, warm = 0;
 };
 
 void free_batch(BatchWork* b) {
@@ -47,6 +61,8 @@ void free_batch(BatchWork* b) {
   cudaFree(b->gh), cudaFree(b->V), cudaFree(b->Z), cudaFree(b->w), cudaFree(b->r), cudaFree(b->part), cudaFree(b->h);
   cudaFree(b->coef), cudaFree(b->ticket), cudaFree(b->loc), cudaFree(b->ring), cudaFree(b->task);
   cudaFreeHost(b->hhost), cudaFreeHost(b->coef_host);
+  cudaFree(b->arn), cudaFreeHost(b->arn_host);
+  if (b->cycle) cudaGraphExecDestroy(b->cycle);
   delete b;
 }
 
@@ -471,12 +487,12 @@ static void cgs_batch_dispatch(int nv, dim3 grid, long long n, const double* V, 
   table[nv]<<<grid, BTHREADS, 0, st>>>(n, V, vs, h, w, part, out, ticket, mode);
 }
 
-// out_r = a_r x_r + b y_r  (a per right-hand side from coef[rhs])
+// out_r = a_r x_r + b y_r  (a per right-hand side from coef[rhs]; coef null: a = -1)
 __global__ void scale_batch_kernel(long long n, const double* __restrict__ coef, const double* __restrict__ x,
                                    long long xs, double b, const double* __restrict__ y, double* __restrict__ out,
                                    long long os) {
   const int rhs = blockIdx.y;
-  const double a = coef[rhs];
+  const double a = coef ? coef[rhs] : -1.0;
   x += rhs * xs, out += rhs * os;
   if (y) y += rhs * n;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
@@ -512,6 +528,7 @@ static fv_status ensure_batch(const fv_system* s, int nrhs, int m) {
       cudaMalloc(&bw->h, R * 3 * BK * 8) || cudaMalloc(&bw->coef, R * BK * 8) || cudaMalloc(&bw->ticket, R * 4) ||
       cudaMalloc(&bw->loc, (size_t)s->subs.total_cells * s->d * R * es) || cudaMalloc(&bw->task, 2 * sizeof(int)) ||
       cudaMallocHost(&bw->hhost, R * 3 * BK * 8) || cudaMallocHost(&bw->coef_host, R * BK * 8) ||
+      cudaMalloc(&bw->arn, R * sizeof(BatchArn)) || cudaMallocHost(&bw->arn_host, R * sizeof(BatchArn)) ||
       cudaMemset(bw->ticket, 0, R * 4)) {
     free_batch(bw);
     sm->batch = nullptr;
@@ -548,6 +565,131 @@ static fv_status ensure_batch(const fv_system* s, int nrhs, int m) {
   return setup_ras(s, bw, tab);
 }
 
+// after r = B - A X and its squared norm (h[2 BK] per right-hand side): beta, the target on the first call,
+// the convergence flag, 1 / beta into coef, g = beta e_1 (one thread per right-hand side)
+__global__ void batch_start_kernel(int nrhs, BatchArn* __restrict__ arn, const double* __restrict__ h,
+                                   double* __restrict__ coef, int first, double atol, double rtol, int max_it) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nrhs) return;
+  BatchArn& a = arn[t];
+  const double beta = sqrt(h[t * 3 * BK + 2 * BK]);
+  if (first) a.r0 = beta, a.target = fmax(atol, rtol * beta), a.its = 0;
+  a.beta = beta;
+  a.done = !(isfinite(beta) && beta > a.target && a.its < max_it);
+  a.kk = 0;
+  for (int i = 0; i <= BK; ++i) a.g[i] = 0.0;
+  for (int i = 0; i < BK; ++i) a.y[i] = 0.0;
+  a.g[0] = a.done ? 0.0 : beta;
+  coef[t] = a.done ? 0.0 : 1.0 / beta;
+}
+
+// column j of every active right-hand side's Hessenberg from the two Gram-Schmidt passes (h = h1 + h2,
+// h_{j+1,j} = sqrt(||w||^2)), previous rotations, a new rotation, the right-hand side update; the next basis
+// vector's scale 1 / h_{j+1,j} into coef, 0 once converged (its later columns are zero and unused)
+__global__ void batch_givens_kernel(int nrhs, int j, BatchArn* __restrict__ arn, const double* __restrict__ h,
+                                    double* __restrict__ coef, int max_it) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nrhs) return;
+  BatchArn& a = arn[t];
+  if (a.done) {
+    coef[t] = 0.0;
+    return;
+  }
+  const double* hh = h + t * 3 * BK;
+  double col[BK + 1];
+  for (int i = 0; i <= j; ++i) col[i] = hh[i] + hh[BK + i];
+  const double hn = sqrt(hh[2 * BK]);
+  col[j + 1] = hn;
+  for (int i = 0; i < j; ++i) {
+    const double x = a.cs[i] * col[i] + a.sn[i] * col[i + 1];
+    col[i + 1] = -a.sn[i] * col[i] + a.cs[i] * col[i + 1];
+    col[i] = x;
+  }
+  const double den = hypot(col[j], col[j + 1]);
+  a.cs[j] = den > 0 ? col[j] / den : 1.0, a.sn[j] = den > 0 ? col[j + 1] / den : 0.0;
+  col[j] = den;
+  a.g[j + 1] = -a.sn[j] * a.g[j];
+  a.g[j] = a.cs[j] * a.g[j];
+  for (int i = 0; i <= j; ++i) a.H[j * BK + i] = col[i];
+  ++a.its;
+  a.kk = j + 1;
+  if (fabs(a.g[j + 1]) <= a.target || a.its >= max_it || !(hn > 0.0) || !isfinite(hn)) {
+    a.done = 1;
+    coef[t] = 0.0;
+  } else {
+    coef[t] = 1.0 / hn;
+  }
+}
+
+// y of the least-squares problem (back substitution over each right-hand side's kk columns) into coef
+__global__ void batch_lsq_kernel(int nrhs, BatchArn* __restrict__ arn, double* __restrict__ coef) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nrhs) return;
+  BatchArn& a = arn[t];
+  double* y = coef + t * BK;
+  for (int i = 0; i < BK; ++i) y[i] = 0.0;
+  for (int i = a.kk - 1; i >= 0; --i) {
+    double s = a.g[i];
+    for (int q = i + 1; q < a.kk; ++q) s -= a.H[q * BK + i] * y[q];
+    y[i] = a.H[i * BK + i] != 0.0 ? s / a.H[i * BK + i] : 0.0;
+  }
+}
+
+// r = B - A X, its norm, and the start of a cycle (no host synchronisation)
+static fv_status batch_residual(const fv_system* s, BatchWork* bw, int nrhs, const double* B, const double* X,
+                                const fv_gmres_opts* o, int first, cudaStream_t st) {
+  const long long n = s->n;
+  const dim3 gv(bblocks(n), nrhs), gc(BBLOCKS, nrhs);
+  fv_status rc;
+  if ((rc = apply_batch(s, bw, nrhs, X, n, bw->r, n, st))) return rc;
+  scale_batch_kernel<<<gv, 256, 0, st>>>(n, nullptr, bw->r, n, 1.0, B, bw->r, n);
+  cgs_batch_dispatch(0, gc, n, bw->r, n, bw->h, bw->r, bw->part, bw->h, bw->ticket, 2, st,
+                     std::make_integer_sequence<int, BK>{});
+  batch_start_kernel<<<(nrhs + 31) / 32, 32, 0, st>>>(nrhs, bw->arn, bw->h, bw->coef, first, o->atol, o->rtol,
+                                                       o->max_it);
+  FV_CUDA(cudaGetLastError());
+  return FV_OK;
+}
+
+// one restart cycle of m Arnoldi steps for every right-hand side, the update X += Z y, and the next cycle's
+// residual: a fixed launch sequence (converged right-hand sides carry zero columns), captured as one graph
+static fv_status batch_cycle(const fv_system* s, BatchWork* bw, int nrhs, const double* B, double* X,
+                             const fv_gmres_opts* o, cudaStream_t st) {
+  const int m = o->restart;
+  const long long n = s->n;
+  const long long vs = (long long)(m + 1) * n, zs = (long long)m * n;
+  const dim3 gv(bblocks(n), nrhs), gc(BBLOCKS, nrhs);
+  fv_status rc;
+  scale_batch_kernel<<<gv, 256, 0, st>>>(n, bw->coef, bw->r, n, 0.0, nullptr, bw->V, vs);
+  for (int j = 0; j < m; ++j) {
+    double* vj = bw->V + (size_t)j * n;
+    double* zj = bw->Z + (size_t)j * n;
+    // Z_j = M^{-1} V_j and w = A Z_j for every right-hand side (strided in the bases)
+    if ((rc = ras_batch(s, bw, nrhs, vj, vs, zj, zs, st))) return rc;
+    if ((rc = apply_batch(s, bw, nrhs, zj, zs, bw->w, n, st))) return rc;
+    const int nv = j + 1;
+    {
+      ProfScope ps(FV_K_CGS, st);
+      cgs_batch_dispatch(nv, gc, n, bw->V, vs, nullptr, bw->w, bw->part, bw->h, bw->ticket, 0, st,
+                         std::make_integer_sequence<int, BK>{});
+      cgs_batch_dispatch(nv, gc, n, bw->V, vs, bw->h, bw->w, bw->part, bw->h, bw->ticket, 1, st,
+                         std::make_integer_sequence<int, BK>{});
+      cgs_batch_dispatch(nv, gc, n, bw->V, vs, bw->h + BK, bw->w, bw->part, bw->h, bw->ticket, 2, st,
+                         std::make_integer_sequence<int, BK>{});
+      batch_givens_kernel<<<(nrhs + 31) / 32, 32, 0, st>>>(nrhs, j, bw->arn, bw->h, bw->coef, o->max_it);
+    }
+    FV_CUDA(cudaGetLastError());
+    if (j + 1 < m) scale_batch_kernel<<<gv, 256, 0, st>>>(n, bw->coef, bw->w, n, 0.0, nullptr, bw->V + (size_t)(j + 1) * n, vs);
+  }
+  {
+    ProfScope ps(FV_K_VEC, st);
+    batch_lsq_kernel<<<(nrhs + 31) / 32, 32, 0, st>>>(nrhs, bw->arn, bw->coef);
+    update_batch_kernel<<<gv, 256, 0, st>>>(n, m, bw->Z, zs, bw->coef, X);
+  }
+  FV_CUDA(cudaGetLastError());
+  return batch_residual(s, bw, nrhs, B, X, o, 0, st);
+}
+
 fv_status gmres_batch(const fv_system* s, int nrhs, const double* B, double* X, const fv_gmres_opts* o,
                       fv_solve_stats* stats, cudaStream_t st) {
   auto t0 = std::chrono::steady_clock::now();
@@ -555,143 +697,68 @@ fv_status gmres_batch(const fv_system* s, int nrhs, const double* B, double* X, 
   if (nrhs < 1 || m < 1 || m > BK - 1 || o->max_it < 0)
     return set_error("fv_gmres_solve_batch: nrhs >= 1 and restart in [1, 31] required"), FV_EINVAL;
   if (s->pc.levels != 1) return set_error("fv_gmres_solve_batch: one-level RAS systems only"), FV_EINVAL;
+  if (s->subs.bf16) return set_error("fv_gmres_solve_batch: BF16 factors are not supported"), FV_EINVAL;
   fv_status rc = ensure_batch(s, nrhs, m);
   if (rc) return rc;
   BatchWork* bw = s->batch;
-  const long long n = s->n;
-  const long long vs = (long long)(m + 1) * n, zs = (long long)m * n;
-  const dim3 gv(bblocks(n), nrhs), gc(BBLOCKS, nrhs);
-  std::vector<double> beta(nrhs), r0(nrhs), target(nrhs), H((size_t)nrhs * (m + 1) * m), cs((size_t)nrhs * m),
-      sn((size_t)nrhs * m), g((size_t)nrhs * (m + 1)), yv((size_t)nrhs * BK);
-  std::vector<int> its(nrhs, 0), kk(nrhs), done(nrhs);
-  auto residual = [&]() -> fv_status {  // r = B - A X, beta = ||r||
-    fv_status q;
-    if ((q = apply_batch(s, bw, nrhs, X, n, bw->r, n, st))) return q;
-    for (int t = 0; t < nrhs; ++t) bw->coef_host[t] = -1.0;
-    FV_CUDA(cudaMemcpyAsync(bw->coef, bw->coef_host, nrhs * 8, cudaMemcpyHostToDevice, st));
-    scale_batch_kernel<<<gv, 256, 0, st>>>(n, bw->coef, bw->r, n, 1.0, B, bw->r, n);
-    cgs_batch_dispatch(0, gc, n, bw->r, n, bw->h, bw->r, bw->part, bw->h, bw->ticket, 2, st,
-                       std::make_integer_sequence<int, BK>{});
-    FV_CUDA(cudaGetLastError());
-    FV_CUDA(cudaMemcpyAsync(bw->hhost, bw->h, nrhs * 3 * BK * 8, cudaMemcpyDeviceToHost, st));
+  if ((rc = batch_residual(s, bw, nrhs, B, X, o, 1, st))) return rc;
+  auto fetch_state = [&]() -> fv_status {
+    FV_CUDA(cudaMemcpyAsync(bw->arn_host, bw->arn, nrhs * sizeof(BatchArn), cudaMemcpyDeviceToHost, st));
     FV_CUDA(cudaStreamSynchronize(st));
-    for (int t = 0; t < nrhs; ++t) beta[t] = std::sqrt(bw->hhost[t * 3 * BK + 2 * BK]);
     return FV_OK;
   };
-  if ((rc = residual())) return rc;
-  for (int t = 0; t < nrhs; ++t) r0[t] = beta[t], target[t] = std::max(o->atol, o->rtol * r0[t]);
-  int total = 0;
-  auto active = [&](int t) { return std::isfinite(beta[t]) && beta[t] > target[t] && its[t] < o->max_it; };
-  while (true) {
-    bool any = false;
-    for (int t = 0; t < nrhs; ++t) any = any || active(t);
-    if (!any) break;
-    for (int t = 0; t < nrhs; ++t) {
-      done[t] = !active(t);
-      kk[t] = 0;
-      bw->coef_host[t] = done[t] ? 0.0 : 1.0 / beta[t];
-      for (int i = 0; i <= m; ++i) g[(size_t)t * (m + 1) + i] = 0.0;
-      g[(size_t)t * (m + 1)] = done[t] ? 0.0 : beta[t];
-    }
-    FV_CUDA(cudaMemcpyAsync(bw->coef, bw->coef_host, nrhs * 8, cudaMemcpyHostToDevice, st));
-    scale_batch_kernel<<<gv, 256, 0, st>>>(n, bw->coef, bw->r, n, 0.0, nullptr, bw->V, vs);
-    int j = 0;
-    for (; j < m; ++j) {
-      double* vj = bw->V + (size_t)j * n;
-      double* zj = bw->Z + (size_t)j * n;
-      // Z_j = M^{-1} V_j and w = A Z_j for every right-hand side (strided in the bases)
-      if ((rc = ras_batch(s, bw, nrhs, vj, vs, zj, zs, st))) return rc;
-      if ((rc = apply_batch(s, bw, nrhs, zj, zs, bw->w, n, st))) return rc;
-      const int nv = j + 1;
-      {
-        ProfScope ps(FV_K_CGS, st);
-        cgs_batch_dispatch(nv, gc, n, bw->V, vs, nullptr, bw->w, bw->part, bw->h, bw->ticket, 0, st,
-                           std::make_integer_sequence<int, BK>{});
-        cgs_batch_dispatch(nv, gc, n, bw->V, vs, bw->h, bw->w, bw->part, bw->h, bw->ticket, 1, st,
-                           std::make_integer_sequence<int, BK>{});
-        cgs_batch_dispatch(nv, gc, n, bw->V, vs, bw->h + BK, bw->w, bw->part, bw->h, bw->ticket, 2, st,
-                           std::make_integer_sequence<int, BK>{});
+  if ((rc = fetch_state())) return rc;
+  auto any_active = [&]() {
+    for (int t = 0; t < nrhs; ++t)
+      if (!bw->arn_host[t].done) return true;
+    return false;
+  };
+  // the cycle runs eagerly on its first use (and while kernel timing is on); afterwards it is captured once
+  // for these (B, X, restart) and replayed
+  if (bw->cycle && (bw->gB != B || bw->gX != X || bw->gm != m)) {
+    cudaGraphExecDestroy(bw->cycle);
+    bw->cycle = nullptr;
+  }
+  while (any_active()) {
+    if (prof_enabled() || !bw->warm) {
+      if ((rc = batch_cycle(s, bw, nrhs, B, X, o, st))) return rc;
+      bw->warm = 1;
+    } else {
+      if (!bw->cycle) {
+        cudaStream_t cs;
+        FV_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t graph;
+        FV_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        rc = batch_cycle(s, bw, nrhs, B, X, o, cs);
+        cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+        cudaStreamDestroy(cs);
+        if (rc) return rc;
+        FV_CUDA(ce);
+        ce = cudaGraphInstantiate(&bw->cycle, graph, 0);
+        cudaGraphDestroy(graph);
+        FV_CUDA(ce);
+        bw->gB = B, bw->gX = X, bw->gm = m;
       }
-      FV_CUDA(cudaGetLastError());
-      FV_CUDA(cudaMemcpyAsync(bw->hhost, bw->h, nrhs * 3 * BK * 8, cudaMemcpyDeviceToHost, st));
-      FV_CUDA(cudaStreamSynchronize(st));
-      bool all_done = true;
-      ++total;
-      for (int t = 0; t < nrhs; ++t) {
-        const double* hh = bw->hhost + t * 3 * BK;
-        if (done[t]) {
-          bw->coef_host[t] = 0.0;
-          continue;
-        }
-        double* Ht = &H[(size_t)t * (m + 1) * m];
-        double *ct = &cs[(size_t)t * m], *st_ = &sn[(size_t)t * m], *gt = &g[(size_t)t * (m + 1)];
-        std::vector<double> col(j + 2);
-        for (int i = 0; i <= j; ++i) col[i] = hh[i] + hh[BK + i];
-        const double hn = std::sqrt(hh[2 * BK]);
-        col[j + 1] = hn;
-        for (int i = 0; i < j; ++i) {
-          const double a = ct[i] * col[i] + st_[i] * col[i + 1];
-          col[i + 1] = -st_[i] * col[i] + ct[i] * col[i + 1];
-          col[i] = a;
-        }
-        const double den = std::hypot(col[j], col[j + 1]);
-        ct[j] = den > 0 ? col[j] / den : 1.0, st_[j] = den > 0 ? col[j + 1] / den : 0.0;
-        col[j] = den, col[j + 1] = 0.0;
-        gt[j + 1] = -st_[j] * gt[j];
-        gt[j] = ct[j] * gt[j];
-        for (int i = 0; i <= j; ++i) Ht[i * m + j] = col[i];
-        ++its[t];
-        kk[t] = j + 1;
-        if (std::fabs(gt[j + 1]) <= target[t] || its[t] >= o->max_it || !(hn > 0.0) || !std::isfinite(hn)) {
-          done[t] = 1;
-          bw->coef_host[t] = 0.0;
-        } else {
-          bw->coef_host[t] = 1.0 / hn;
-          all_done = false;
-        }
-      }
-      if (all_done || j + 1 == m) {
-        ++j;
-        break;
-      }
-      FV_CUDA(cudaMemcpyAsync(bw->coef, bw->coef_host, nrhs * 8, cudaMemcpyHostToDevice, st));
-      scale_batch_kernel<<<gv, 256, 0, st>>>(n, bw->coef, bw->w, n, 0.0, nullptr, bw->V + (size_t)(j + 1) * n, vs);
+      FV_CUDA(cudaGraphLaunch(bw->cycle, st));
     }
-    // x_r += Z_r y_r
-    for (int t = 0; t < nrhs; ++t) {
-      const double* Ht = &H[(size_t)t * (m + 1) * m];
-      const double* gt = &g[(size_t)t * (m + 1)];
-      double* y = &yv[(size_t)t * BK];
-      for (int i = 0; i < BK; ++i) y[i] = 0.0;
-      for (int i = kk[t] - 1; i >= 0; --i) {
-        double a = gt[i];
-        for (int q = i + 1; q < kk[t]; ++q) a -= Ht[i * m + q] * y[q];
-        y[i] = Ht[i * m + i] != 0.0 ? a / Ht[i * m + i] : 0.0;
-      }
-    }
-    FV_CUDA(cudaMemcpyAsync(bw->coef, yv.data(), nrhs * BK * 8, cudaMemcpyHostToDevice, st));
-    {
-      ProfScope ps(FV_K_VEC, st);
-      update_batch_kernel<<<gv, 256, 0, st>>>(n, std::min(j, m), bw->Z, zs, bw->coef, X);
-    }
-    FV_CUDA(cudaGetLastError());
-    if ((rc = residual())) return rc;
+    if ((rc = fetch_state())) return rc;
   }
   bool all_conv = true, nan = false;
   for (int t = 0; t < nrhs; ++t) {
-    const bool conv = std::isfinite(beta[t]) && beta[t] <= target[t];
-    nan = nan || !std::isfinite(beta[t]);
+    const BatchArn& a = bw->arn_host[t];
+    const bool conv = std::isfinite(a.beta) && a.beta <= a.target;
+    nan = nan || !std::isfinite(a.beta);
     all_conv = all_conv && conv;
     if (stats) {
-      stats[t].iters = its[t];
+      stats[t].iters = a.its;
       stats[t].inner_iters = 0;
       stats[t].converged = conv;
-      stats[t].r0 = r0[t];
-      stats[t].rfinal = beta[t];
+      stats[t].r0 = a.r0;
+      stats[t].rfinal = a.beta;
       stats[t].time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      stats[t].fallback = 0;
     }
   }
-  (void)total;
   if (nan) return set_error("fv_gmres_solve_batch: NaN or Inf residual"), FV_ENAN;
   if (!all_conv) return set_error("fv_gmres_solve_batch: max_it reached before the tolerance"), FV_ENOCONV;
   return FV_OK;

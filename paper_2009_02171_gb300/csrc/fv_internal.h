@@ -114,7 +114,8 @@ struct Subdomains {
   void* F = nullptr;              // [cell_off * Q + q * ncell + pos], Q = 10 d + d^2, element type per `fp32`
   void* loc = nullptr;            // [cell_off * d + a * ncell + pos] sweep vector
   void* ring = nullptr;           // global 4-plane ring per CTA when it does not fit in shared memory
-  int fp32 = 0;                   // 1: factors and sweeps in FP32
+  int fp32 = 0;                   // 1: sweeps in FP32 (factors FP32, or BF16 when bf16)
+  int bf16 = 0;                   // 1: factors stored in BF16 (FV_PREC_BF16)
   int max_cols = 0;               // max nx * ny
   int dense_threads = 0;          // CTA size of the level-mapped generic sweeps
   int dense_single = 0;           // 1: no step is wider than the CTA (the pipelined sweeps apply)
@@ -226,7 +227,7 @@ fv_status cell_gradient(const fv_grid* g, const double* x, int wall, double scal
 // precond.cu
 fv_status build_subdomains(fv_system* s, const fv_grid* g);
 fv_status ilu_factor(fv_system* s);
-fv_status prepare_sweeps(fv_system* s, int fp32);
+fv_status prepare_sweeps(fv_system* s, int prec);
 fv_status sweeps_smem_attr(const fv_system* s);
 fv_status precond_apply(const fv_system* s, const double* r, double* z, cudaStream_t st);
 fv_status precond_apply32(const fv_system* s, const float* r, float* z, cudaStream_t st);

@@ -25,9 +25,20 @@
 #include <numeric>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "fv_internal.h"
 
 namespace fv {
+
+// factor storage (FP64, FP32, or BF16 for the FP32 sweeps of FV_PREC_BF16) to the sweep arithmetic type
+__device__ __forceinline__ float fcvt(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float fcvt(float v) { return v; }
+__device__ __forceinline__ double fcvt(double v) { return v; }
+template <class FT>
+__device__ __forceinline__ FT to_factor(double v) { return (FT)v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_factor<__nv_bfloat16>(double v) { return __double2bfloat16(v); }
 
 __device__ __constant__ static const signed char kSlot[11][3] = {
     {0, 0, -1}, {-1, -1, 0}, {0, -1, 0}, {1, -1, 0}, {-1, 0, 0}, {0, 0, 0},
@@ -317,11 +328,11 @@ __global__ void repack_kernel(int d, int count, const long long* __restrict__ ce
       if (s == 5) continue;
       for (int a = 0; a < d; ++a) {
         const int q = s < 5 ? s * d + a : 5 * d + d * d + (s - 6) * d + a;
-        Fs[q * nc] = (T)off[(C * 11 + s) * d + a];
+        Fs[q * nc] = to_factor<T>(off[(C * 11 + s) * d + a]);
       }
     }
     for (int a = 0; a < d; ++a)
-      for (int b = 0; b < d; ++b) Fs[(5 * d + a * d + b) * nc] = (T)diag[(C * d + a) * d + b];
+      for (int b = 0; b < d; ++b) Fs[(5 * d + a * d + b) * nc] = to_factor<T>(diag[(C * d + a) * d + b]);
   }
 }
 
@@ -343,6 +354,7 @@ struct alignas(16) BwdBlk {
 };
 static_assert(sizeof(FwdBlk<float>) == 48 && sizeof(BwdBlk<float>) == 64, "block layout");
 static_assert(sizeof(FwdBlk<double>) == 96 && sizeof(BwdBlk<double>) == 128, "block layout");
+static_assert(sizeof(FwdBlk<__nv_bfloat16>) == 32 && sizeof(BwdBlk<__nv_bfloat16>) == 48, "block layout");
 
 template <class T>
 __global__ void stage_pack_kernel(int count, const long long* __restrict__ cell_off, const T* __restrict__ F,
@@ -374,16 +386,23 @@ constexpr int DENSE_THREADS = 384;  // CTA size bound of the generic sweeps (170
 
 static size_t table_bytes(int levels, int ny) { return (size_t)(levels + 1 + levels * ny) * sizeof(int); }
 
-fv_status prepare_sweeps(fv_system* s, int fp32) {
+// prec: 0 FP64 factors and sweeps, 1 FP32, 2 FP32 sweeps reading BF16 factors
+fv_status prepare_sweeps(fv_system* s, int prec) {
   Subdomains& S = s->subs;
   const int d = S.d, Q = 10 * d + d * d;
-  const size_t es = fp32 ? sizeof(float) : sizeof(double);
+  const int fp32 = prec != 0;
+  const size_t es = fp32 ? sizeof(float) : sizeof(double);  // the sweep vectors and rings
   S.fp32 = fp32;
-  S.F = fp32 ? (void*)dalloc<float>(s, (size_t)S.total_cells * Q) : (void*)dalloc<double>(s, (size_t)S.total_cells * Q);
+  S.bf16 = prec == 2;
+  S.F = S.bf16 ? (void*)dalloc<__nv_bfloat16>(s, (size_t)S.total_cells * Q)
+        : fp32 ? (void*)dalloc<float>(s, (size_t)S.total_cells * Q)
+               : (void*)dalloc<double>(s, (size_t)S.total_cells * Q);
   S.loc = fp32 ? (void*)dalloc<float>(s, (size_t)S.total_cells * d) : (void*)dalloc<double>(s, (size_t)S.total_cells * d);
   if (!S.F || !S.loc) return set_error("fv_assemble_system: allocation of sweep data failed"), FV_ENOMEM;
   const int blocks = (int)std::min<long long>((S.total_cells + 255) / 256, 152LL * 32);
-  if (fp32)
+  if (S.bf16)
+    repack_kernel<__nv_bfloat16><<<blocks, 256>>>(d, S.count, S.cell_off, S.perm, S.off, S.diag, (__nv_bfloat16*)S.F);
+  else if (fp32)
     repack_kernel<float><<<blocks, 256>>>(d, S.count, S.cell_off, S.perm, S.off, S.diag, (float*)S.F);
   else
     repack_kernel<double><<<blocks, 256>>>(d, S.count, S.cell_off, S.perm, S.off, S.diag, (double*)S.F);
@@ -442,8 +461,10 @@ fv_status prepare_sweeps(fv_system* s, int fp32) {
   // d right-hand side values and an 8-byte cell map entry, or the backward's block and d values)
   S.stage = 0;
   if (d == 2 && S.dense_single && S.ring_in_smem) {
-    const size_t fwd = (fp32 ? sizeof(FwdBlk<float>) : sizeof(FwdBlk<double>)) + d * es + 8;
-    const size_t bwd = (fp32 ? sizeof(BwdBlk<float>) : sizeof(BwdBlk<double>)) + d * es;
+    const size_t fwd = (S.bf16 ? sizeof(FwdBlk<__nv_bfloat16>) : fp32 ? sizeof(FwdBlk<float>) : sizeof(FwdBlk<double>)) +
+                       d * es + 8;
+    const size_t bwd = (S.bf16 ? sizeof(BwdBlk<__nv_bfloat16>) : fp32 ? sizeof(BwdBlk<float>) : sizeof(BwdBlk<double>)) +
+                       d * es;
     const size_t per = (size_t)S.dense_threads * std::max(fwd, bwd);
     int max_nx = 0;
     for (int sd = 0; sd < S.count; ++sd) max_nx = std::max(max_nx, dims[3 * sd]);
@@ -456,7 +477,13 @@ fv_status prepare_sweeps(fv_system* s, int fp32) {
         break;
       }
     if (S.stage) {
-      if (fp32) {
+      if (S.bf16) {
+        using B = __nv_bfloat16;
+        S.blk_f = dalloc<FwdBlk<B>>(s, S.total_cells), S.blk_b = dalloc<BwdBlk<B>>(s, S.total_cells);
+        if (S.blk_f && S.blk_b)
+          stage_pack_kernel<B><<<blocks, 256>>>(S.count, S.cell_off, (const B*)S.F, S.ijk, S.gmap_p, S.owned_p,
+                                                (FwdBlk<B>*)S.blk_f, (BwdBlk<B>*)S.blk_b);
+      } else if (fp32) {
         S.blk_f = dalloc<FwdBlk<float>>(s, S.total_cells), S.blk_b = dalloc<BwdBlk<float>>(s, S.total_cells);
         if (S.blk_f && S.blk_b)
           stage_pack_kernel<float><<<blocks, 256>>>(S.count, S.cell_off, (const float*)S.F, S.ijk, S.gmap_p,
@@ -544,10 +571,10 @@ __device__ __forceinline__ void level_cell(const SweepBox& b, const int* rowoff,
   k = L - i - 2 * j;
 }
 
-template <class T, int D, class V>
+template <class T, int D, class V, class FT = T>
 __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_fwd_kernel(const long long* __restrict__ cell_off,
                                                                  const int* __restrict__ dims, const int* __restrict__ lpt,
-                                                                 const T* __restrict__ F, T* __restrict__ loc, T* ring_g,
+                                                                 const FT* __restrict__ F, T* __restrict__ loc, T* ring_g,
                                                                  int ring_in_smem, int max_cols, long long N,
                                                                  const long long* __restrict__ gmap_p,
                                                                  const V* __restrict__ r) {
@@ -560,7 +587,7 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_fwd_kernel(const long lo
   int* rowoff = lvl + b.levels + 1;
   build_tables(b, lvl, rowoff);
   constexpr int Q = 10 * D + D * D;
-  const T* Fb = F + b.base * Q;
+  const FT* Fb = F + b.base * Q;
   T* Lb = loc + b.base * D;
   const long long* gm = gmap_p + b.base;
   const long long nc = b.nc;
@@ -586,11 +613,11 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_fwd_kernel(const long lo
         // unconditionally so they are in flight together; only the neighbour reads are guarded
         T fl[5 * D], fd[D * D];
 #pragma unroll
-        for (int q = 0; q < 5 * D; ++q) fl[q] = Fb[q * nc + pos];
+        for (int q = 0; q < 5 * D; ++q) fl[q] = fcvt(Fb[q * nc + pos]);
 #pragma unroll
         for (int a = 1; a < D; ++a)
 #pragma unroll
-          for (int c = 0; c < a; ++c) fd[a * D + c] = Fb[(5 * D + a * D + c) * nc + pos];
+          for (int c = 0; c < a; ++c) fd[a * D + c] = fcvt(Fb[(5 * D + a * D + c) * nc + pos]);
 #pragma unroll
         for (int a = 0; a < D; ++a) {
           if (k > 0) y[a] -= fl[0 * D + a] * r0[a];
@@ -604,13 +631,13 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_fwd_kernel(const long lo
       } else {  // FP64 7x7 blocks: too many registers to batch; FP64 arithmetic bounds this path
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-          if (k > 0) y[a] -= Fb[(0 * D + a) * nc + pos] * r0[a];
-          if (i > 0 && j > 0) y[a] -= Fb[(1 * D + a) * nc + pos] * rp[(col - b.nx - 1) * D + a];
-          if (j > 0) y[a] -= Fb[(2 * D + a) * nc + pos] * rp[(col - b.nx) * D + a];
-          if (j > 0 && i + 1 < b.nx) y[a] -= Fb[(3 * D + a) * nc + pos] * rp[(col - b.nx + 1) * D + a];
-          if (i > 0) y[a] -= Fb[(4 * D + a) * nc + pos] * rp[(col - 1) * D + a];
+          if (k > 0) y[a] -= fcvt(Fb[(0 * D + a) * nc + pos]) * r0[a];
+          if (i > 0 && j > 0) y[a] -= fcvt(Fb[(1 * D + a) * nc + pos]) * rp[(col - b.nx - 1) * D + a];
+          if (j > 0) y[a] -= fcvt(Fb[(2 * D + a) * nc + pos]) * rp[(col - b.nx) * D + a];
+          if (j > 0 && i + 1 < b.nx) y[a] -= fcvt(Fb[(3 * D + a) * nc + pos]) * rp[(col - b.nx + 1) * D + a];
+          if (i > 0) y[a] -= fcvt(Fb[(4 * D + a) * nc + pos]) * rp[(col - 1) * D + a];
 #pragma unroll
-          for (int c = 0; c < a; ++c) y[a] -= Fb[(5 * D + a * D + c) * nc + pos] * y[c];
+          for (int c = 0; c < a; ++c) y[a] -= fcvt(Fb[(5 * D + a * D + c) * nc + pos]) * y[c];
         }
       }
 #pragma unroll
@@ -624,10 +651,10 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_fwd_kernel(const long lo
   }
 }
 
-template <class T, int D, class V>
+template <class T, int D, class V, class FT = T>
 __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_bwd_kernel(const long long* __restrict__ cell_off,
                                                                  const int* __restrict__ dims, const int* __restrict__ lpt,
-                                                                 const T* __restrict__ F, const T* __restrict__ loc,
+                                                                 const FT* __restrict__ F, const T* __restrict__ loc,
                                                                  T* ring_g, int ring_in_smem, int max_cols, long long N,
                                                                  const long long* __restrict__ gmap_p,
                                                                  const unsigned char* __restrict__ owned_p,
@@ -641,7 +668,7 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_bwd_kernel(const long lo
   int* rowoff = lvl + b.levels + 1;
   build_tables(b, lvl, rowoff);
   constexpr int Q = 10 * D + D * D;
-  const T* Fb = F + b.base * Q;
+  const FT* Fb = F + b.base * Q;
   const T* Lb = loc + b.base * D;
   const long long* gm = gmap_p + b.base;
   const unsigned char* ow = owned_p + b.base;
@@ -662,11 +689,11 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_bwd_kernel(const long lo
       if constexpr (sizeof(T) == 4 || D < 7) {
         T fu[5 * D], fd[D * D];
 #pragma unroll
-        for (int q = 0; q < 5 * D; ++q) fu[q] = Fb[(U + q) * nc + pos];
+        for (int q = 0; q < 5 * D; ++q) fu[q] = fcvt(Fb[(U + q) * nc + pos]);
 #pragma unroll
         for (int a = 0; a < D; ++a)
 #pragma unroll
-          for (int c = a; c < D; ++c) fd[a * D + c] = Fb[(5 * D + a * D + c) * nc + pos];
+          for (int c = a; c < D; ++c) fd[a * D + c] = fcvt(Fb[(5 * D + a * D + c) * nc + pos]);
 #pragma unroll
         for (int a = D - 1; a >= 0; --a) {
 #pragma unroll
@@ -682,14 +709,14 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_bwd_kernel(const long lo
 #pragma unroll
         for (int a = D - 1; a >= 0; --a) {
 #pragma unroll
-          for (int c = a + 1; c < D; ++c) x[a] -= Fb[(5 * D + a * D + c) * nc + pos] * x[c];
-          if (i + 1 < b.nx) x[a] -= Fb[(U + 0 * D + a) * nc + pos] * rp[(col + 1) * D + a];
-          if (i > 0 && j + 1 < b.ny) x[a] -= Fb[(U + 1 * D + a) * nc + pos] * rp[(col + b.nx - 1) * D + a];
-          if (j + 1 < b.ny) x[a] -= Fb[(U + 2 * D + a) * nc + pos] * rp[(col + b.nx) * D + a];
+          for (int c = a + 1; c < D; ++c) x[a] -= fcvt(Fb[(5 * D + a * D + c) * nc + pos]) * x[c];
+          if (i + 1 < b.nx) x[a] -= fcvt(Fb[(U + 0 * D + a) * nc + pos]) * rp[(col + 1) * D + a];
+          if (i > 0 && j + 1 < b.ny) x[a] -= fcvt(Fb[(U + 1 * D + a) * nc + pos]) * rp[(col + b.nx - 1) * D + a];
+          if (j + 1 < b.ny) x[a] -= fcvt(Fb[(U + 2 * D + a) * nc + pos]) * rp[(col + b.nx) * D + a];
           if (i + 1 < b.nx && j + 1 < b.ny)
-            x[a] -= Fb[(U + 3 * D + a) * nc + pos] * rp[(col + b.nx + 1) * D + a];
-          if (k + 1 < b.nz) x[a] -= Fb[(U + 4 * D + a) * nc + pos] * r1[a];
-          x[a] /= Fb[(5 * D + a * D + a) * nc + pos];
+            x[a] -= fcvt(Fb[(U + 3 * D + a) * nc + pos]) * rp[(col + b.nx + 1) * D + a];
+          if (k + 1 < b.nz) x[a] -= fcvt(Fb[(U + 4 * D + a) * nc + pos]) * r1[a];
+          x[a] /= fcvt(Fb[(5 * D + a * D + a) * nc + pos]);
         }
       }
 #pragma unroll
@@ -709,11 +736,11 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_bwd_kernel(const long lo
 // CTA): the next step's factors and right-hand side are loaded into registers before the barrier
 // (they do not depend on this step's results) and the cell map two steps ahead, so a step's
 // critical path is the barrier, shared-memory ring reads and arithmetic.
-template <class T, int D, class V>
+template <class T, int D, class V, class FT = T>
 __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_fwd_pipe_kernel(const long long* __restrict__ cell_off,
                                                                       const int* __restrict__ dims,
                                                                       const int* __restrict__ lpt,
-                                                                      const T* __restrict__ F, T* __restrict__ loc,
+                                                                      const FT* __restrict__ F, T* __restrict__ loc,
                                                                       T* ring_g, int ring_in_smem, int max_cols,
                                                                       long long N, const long long* __restrict__ gmap_p,
                                                                       const int* __restrict__ ijk,
@@ -726,7 +753,7 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_fwd_pipe_kernel(const lo
   int* lvl = (int*)(smem + ring_bytes);
   build_tables(b, lvl, nullptr);
   constexpr int Q = 10 * D + D * D;
-  const T* Fb = F + b.base * Q;
+  const FT* Fb = F + b.base * Q;
   T* Lb = loc + b.base * D;
   const long long* gm = gmap_p + b.base;
   const long long nc = b.nc;
@@ -747,11 +774,11 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_fwd_pipe_kernel(const lo
 #pragma unroll
     for (int a = 0; a < D; ++a) y0[a] = g >= 0 ? (T)r[a * N + g] : T(0);
 #pragma unroll
-    for (int q = 0; q < 5 * D; ++q) fl[q] = Fb[q * nc + cp];
+    for (int q = 0; q < 5 * D; ++q) fl[q] = fcvt(Fb[q * nc + cp]);
 #pragma unroll
     for (int a = 1; a < D; ++a)
 #pragma unroll
-      for (int c = 0; c < a; ++c) fd[a * D + c] = Fb[(5 * D + a * D + c) * nc + cp];
+      for (int c = 0; c < a; ++c) fd[a * D + c] = fcvt(Fb[(5 * D + a * D + c) * nc + cp]);
   };
   fetch(0);
   gn = t < cnt_of(1) ? gm[lvl[1] + t] : -1;
@@ -784,11 +811,11 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_fwd_pipe_kernel(const lo
   }
 }
 
-template <class T, int D, class V>
+template <class T, int D, class V, class FT = T>
 __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_bwd_pipe_kernel(const long long* __restrict__ cell_off,
                                                                       const int* __restrict__ dims,
                                                                       const int* __restrict__ lpt,
-                                                                      const T* __restrict__ F, const T* __restrict__ loc,
+                                                                      const FT* __restrict__ F, const T* __restrict__ loc,
                                                                       T* ring_g, int ring_in_smem, int max_cols,
                                                                       long long N, const long long* __restrict__ gmap_p,
                                                                       const unsigned char* __restrict__ owned_p,
@@ -803,7 +830,7 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_bwd_pipe_kernel(const lo
   build_tables(b, lvl, nullptr);
   constexpr int Q = 10 * D + D * D, U = 5 * D + D * D;
   const int* cells = ijk + b.base;
-  const T* Fb = F + b.base * Q;
+  const FT* Fb = F + b.base * Q;
   const T* Lb = loc + b.base * D;
   const long long* gm = gmap_p + b.base;
   const unsigned char* ow = owned_p + b.base;
@@ -821,11 +848,11 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_bwd_pipe_kernel(const lo
 #pragma unroll
     for (int a = 0; a < D; ++a) x0[a] = Lb[a * nc + cp];
 #pragma unroll
-    for (int q = 0; q < 5 * D; ++q) fu[q] = Fb[(U + q) * nc + cp];
+    for (int q = 0; q < 5 * D; ++q) fu[q] = fcvt(Fb[(U + q) * nc + cp]);
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
-      for (int c = a; c < D; ++c) fd[a * D + c] = Fb[(5 * D + a * D + c) * nc + cp];
+      for (int c = a; c < D; ++c) fd[a * D + c] = fcvt(Fb[(5 * D + a * D + c) * nc + cp]);
     const long long g = gm[cp];
     go = ow[cp] ? g : -1;
   };
@@ -891,16 +918,16 @@ union StagedBlk {
   uint4 u[sizeof(Blk) / 16];
 };
 
-template <class T, class V, int SG>
+template <class T, class V, int SG, class FT = T>
 __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_fwd_stage_kernel(const long long* __restrict__ cell_off,
                                                                        const int* __restrict__ dims,
                                                                        const int* __restrict__ lpt,
-                                                                       const FwdBlk<T>* __restrict__ blk,
+                                                                       const FwdBlk<FT>* __restrict__ blk,
                                                                        T* __restrict__ loc, int max_cols, int pad,
                                                                        long long N,
                                                                        const long long* __restrict__ gmap_p,
                                                                        const V* __restrict__ r, int stage_off) {
-  constexpr int D = 2, NC = sizeof(FwdBlk<T>) / 16;
+  constexpr int D = 2, NC = sizeof(FwdBlk<FT>) / 16;
   extern __shared__ __align__(16) unsigned char smem[];
   const int sd = lpt[blockIdx.x];
   const SweepBox b = sweep_box(cell_off, dims, sd);
@@ -913,7 +940,7 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_fwd_stage_kernel(const l
   uint4* sB = (uint4*)(smem + stage_off);                 // [SG][NC][Tn] operand blocks
   V* sY = (V*)(sB + (size_t)SG * NC * Tn);                // [SG][D][Tn] gathered right-hand side
   long long* sG = (long long*)(sY + (size_t)SG * D * Tn); // [SG][Tn] cell map entry SG - 1 steps later
-  const FwdBlk<T>* Bb = blk + b.base;
+  const FwdBlk<FT>* Bb = blk + b.base;
   T* Lb = loc + b.base * D;
   const long long* gm = gmap_p + b.base;
   auto cnt_of = [&](int L) { return L < b.levels ? lvl[L + 1] - lvl[L] : 0; };
@@ -947,10 +974,10 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_fwd_stage_kernel(const l
     const int s = L % SG;
     issue(L + SG - 1, t < cnt_of(L + SG - 1) ? sG[s * Tn + t] : -1);  // into the slot step L - 1 used
     if (t < cnt_of(L)) {
-      StagedBlk<FwdBlk<T>> q;
+      StagedBlk<FwdBlk<FT>> q;
 #pragma unroll
       for (int c = 0; c < NC; ++c) q.u[c] = sB[(s * NC + c) * Tn + t];
-      const T* f = q.b.f;
+      const FT* f = q.b.f;
       const int i = q.b.ijk & 1023, j = (q.b.ijk >> 10) & 1023, k = q.b.ijk >> 20, col = j * b.nx + i;
       T* rp = ring + ((k & 3) * b.ncols) * D;
       const T* r0 = ring + (((k - 1) & 3) * b.ncols + col) * D;
@@ -958,13 +985,13 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_fwd_stage_kernel(const l
 #pragma unroll
       for (int a = 0; a < D; ++a) {
         y[a] = (T)sY[(s * D + a) * Tn + t];
-        y[a] -= f[0 * D + a] * r0[a];
-        y[a] -= f[1 * D + a] * rp[(col - b.nx - 1) * D + a];
-        y[a] -= f[2 * D + a] * rp[(col - b.nx) * D + a];
-        y[a] -= f[3 * D + a] * rp[(col - b.nx + 1) * D + a];
-        y[a] -= f[4 * D + a] * rp[(col - 1) * D + a];
+        y[a] -= fcvt(f[0 * D + a]) * r0[a];
+        y[a] -= fcvt(f[1 * D + a]) * rp[(col - b.nx - 1) * D + a];
+        y[a] -= fcvt(f[2 * D + a]) * rp[(col - b.nx) * D + a];
+        y[a] -= fcvt(f[3 * D + a]) * rp[(col - b.nx + 1) * D + a];
+        y[a] -= fcvt(f[4 * D + a]) * rp[(col - 1) * D + a];
       }
-      y[1] -= f[5 * D] * y[0];
+      y[1] -= fcvt(f[5 * D]) * y[0];
       const long long cp = lvl[L] + t;
 #pragma unroll
       for (int a = 0; a < D; ++a) {
@@ -980,15 +1007,15 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_fwd_stage_kernel(const l
 // Backward sweep of the staged pair: steps in reverse; each thread's block and its cell's forward
 // result are copied SG - 1 steps ahead.  Nothing a copy needs depends on a staged value, so a step's
 // copies are issued before it waits.
-template <class T, class V, int SG>
+template <class T, class V, int SG, class FT = T>
 __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_bwd_stage_kernel(const long long* __restrict__ cell_off,
                                                                        const int* __restrict__ dims,
                                                                        const int* __restrict__ lpt,
-                                                                       const BwdBlk<T>* __restrict__ blk,
+                                                                       const BwdBlk<FT>* __restrict__ blk,
                                                                        const T* __restrict__ loc, int max_cols,
                                                                        int pad, long long N,
                                                                        V* __restrict__ z, int stage_off) {
-  constexpr int D = 2, NC = sizeof(BwdBlk<T>) / 16;
+  constexpr int D = 2, NC = sizeof(BwdBlk<FT>) / 16;
   extern __shared__ __align__(16) unsigned char smem[];
   const int sd = lpt[blockIdx.x];
   const SweepBox b = sweep_box(cell_off, dims, sd);
@@ -1000,7 +1027,7 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_bwd_stage_kernel(const l
   const int Tn = blockDim.x, t = threadIdx.x;
   uint4* sB = (uint4*)(smem + stage_off);  // [SG][NC][Tn] operand blocks
   T* sX = (T*)(sB + (size_t)SG * NC * Tn); // [SG][Tn][D] forward result
-  const BwdBlk<T>* Bb = blk + b.base;
+  const BwdBlk<FT>* Bb = blk + b.base;
   const T* Lb = loc + b.base * D;
   auto issue = [&](int n) {  // n-th step of the backward order (level levels - 1 - n) into slot n % SG
     const int L = b.levels - 1 - n, s = n % SG;
@@ -1019,10 +1046,10 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_bwd_stage_kernel(const l
     cp_wait<SG - 1>();  // step n's group has landed
     const int L = b.levels - 1 - n, s = n % SG;
     if (t < lvl[L + 1] - lvl[L]) {
-      StagedBlk<BwdBlk<T>> q;
+      StagedBlk<BwdBlk<FT>> q;
 #pragma unroll
       for (int c = 0; c < NC; ++c) q.u[c] = sB[(s * NC + c) * Tn + t];
-      const T* f = q.b.f;
+      const FT* f = q.b.f;
       const int i = q.b.ijk & 1023, j = (q.b.ijk >> 10) & 1023, k = q.b.ijk >> 20, col = j * b.nx + i;
       T* rp = ring + ((k & 3) * b.ncols) * D;
       const T* r1 = ring + (((k + 1) & 3) * b.ncols + col) * D;
@@ -1032,13 +1059,13 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_bwd_stage_kernel(const l
       // U's diagonal block at f[5 d + 0, 1, 2] = (0,0), (0,1), (1,1)
 #pragma unroll
       for (int a = D - 1; a >= 0; --a) {
-        if (a == 0) x[0] -= f[5 * D + 1] * x[1];
-        x[a] -= f[0 * D + a] * rp[(col + 1) * D + a];
-        x[a] -= f[1 * D + a] * rp[(col + b.nx - 1) * D + a];
-        x[a] -= f[2 * D + a] * rp[(col + b.nx) * D + a];
-        x[a] -= f[3 * D + a] * rp[(col + b.nx + 1) * D + a];
-        x[a] -= f[4 * D + a] * r1[a];
-        x[a] /= f[a == 0 ? 5 * D : 5 * D + 2];
+        if (a == 0) x[0] -= fcvt(f[5 * D + 1]) * x[1];
+        x[a] -= fcvt(f[0 * D + a]) * rp[(col + 1) * D + a];
+        x[a] -= fcvt(f[1 * D + a]) * rp[(col + b.nx - 1) * D + a];
+        x[a] -= fcvt(f[2 * D + a]) * rp[(col + b.nx) * D + a];
+        x[a] -= fcvt(f[3 * D + a]) * rp[(col + b.nx + 1) * D + a];
+        x[a] -= fcvt(f[4 * D + a]) * r1[a];
+        x[a] /= fcvt(f[a == 0 ? 5 * D : 5 * D + 2]);
       }
 #pragma unroll
       for (int a = 0; a < D; ++a) rp[col * D + a] = x[a];
@@ -1052,7 +1079,7 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_bwd_stage_kernel(const l
   cp_wait<0>();
 }
 
-template <class T, int D, class V>
+template <class T, int D, class V, class FT = T>
 static fv_status ras_apply_t(const fv_system* s, const V* r, V* z, cudaStream_t st) {
   const Subdomains& S = s->subs;
   const long long N = s->grid->geo.N;
@@ -1067,26 +1094,26 @@ static fv_status ras_apply_t(const fv_system* s, const V* r, V* z, cudaStream_t 
       bool piped = false;
       if constexpr (D == 2) {
         const int so = (int)S.stage_off;
-        const FwdBlk<T>* bf = (const FwdBlk<T>*)S.blk_f;
+        const FwdBlk<FT>* bf = (const FwdBlk<FT>*)S.blk_f;
         if (S.stage == 8)
-          ras_fwd_stage_kernel<T, V, 8><<<S.count, S.dense_threads, S.stage_smem, st>>>(
+          ras_fwd_stage_kernel<T, V, 8, FT><<<S.count, S.dense_threads, S.stage_smem, st>>>(
               S.cell_off, S.dims, S.lpt, bf, loc, S.max_cols, S.stage_pad, N, S.gmap_p, r, so);
         else if (S.stage == 4)
-          ras_fwd_stage_kernel<T, V, 4><<<S.count, S.dense_threads, S.stage_smem, st>>>(
+          ras_fwd_stage_kernel<T, V, 4, FT><<<S.count, S.dense_threads, S.stage_smem, st>>>(
               S.cell_off, S.dims, S.lpt, bf, loc, S.max_cols, S.stage_pad, N, S.gmap_p, r, so);
         piped = S.stage != 0;
       }
       if constexpr (sizeof(T) == 4 || D < 7) {
         if (S.dense_single && !piped) {
-          ras_fwd_pipe_kernel<T, D, V><<<S.count, S.dense_threads, S.smem, st>>>(
-              S.cell_off, S.dims, S.lpt, (const T*)S.F, loc, (T*)S.ring, S.ring_in_smem, S.max_cols, N, S.gmap_p,
+          ras_fwd_pipe_kernel<T, D, V, FT><<<S.count, S.dense_threads, S.smem, st>>>(
+              S.cell_off, S.dims, S.lpt, (const FT*)S.F, loc, (T*)S.ring, S.ring_in_smem, S.max_cols, N, S.gmap_p,
               S.ijk, r);
           piped = true;
         }
       }
       if (!piped)
-        ras_fwd_kernel<T, D, V><<<S.count, S.dense_threads, S.smem, st>>>(
-            S.cell_off, S.dims, S.lpt, (const T*)S.F, loc, (T*)S.ring, S.ring_in_smem, S.max_cols, N, S.gmap_p, r);
+        ras_fwd_kernel<T, D, V, FT><<<S.count, S.dense_threads, S.smem, st>>>(
+            S.cell_off, S.dims, S.lpt, (const FT*)S.F, loc, (T*)S.ring, S.ring_in_smem, S.max_cols, N, S.gmap_p, r);
     }
   }
   FV_CUDA(cudaGetLastError());
@@ -1096,26 +1123,26 @@ static fv_status ras_apply_t(const fv_system* s, const V* r, V* z, cudaStream_t 
       bool piped = false;
       if constexpr (D == 2) {
         const int so = (int)S.stage_off;
-        const BwdBlk<T>* bb = (const BwdBlk<T>*)S.blk_b;
+        const BwdBlk<FT>* bb = (const BwdBlk<FT>*)S.blk_b;
         if (S.stage == 8)
-          ras_bwd_stage_kernel<T, V, 8><<<S.count, S.dense_threads, S.stage_smem, st>>>(
+          ras_bwd_stage_kernel<T, V, 8, FT><<<S.count, S.dense_threads, S.stage_smem, st>>>(
               S.cell_off, S.dims, S.lpt, bb, loc, S.max_cols, S.stage_pad, N, z, so);
         else if (S.stage == 4)
-          ras_bwd_stage_kernel<T, V, 4><<<S.count, S.dense_threads, S.stage_smem, st>>>(
+          ras_bwd_stage_kernel<T, V, 4, FT><<<S.count, S.dense_threads, S.stage_smem, st>>>(
               S.cell_off, S.dims, S.lpt, bb, loc, S.max_cols, S.stage_pad, N, z, so);
         piped = S.stage != 0;
       }
       if constexpr (sizeof(T) == 4 || D < 7) {
         if (S.dense_single && !piped) {
-          ras_bwd_pipe_kernel<T, D, V><<<S.count, S.dense_threads, S.smem, st>>>(
-              S.cell_off, S.dims, S.lpt, (const T*)S.F, loc, (T*)S.ring, S.ring_in_smem, S.max_cols, N, S.gmap_p,
+          ras_bwd_pipe_kernel<T, D, V, FT><<<S.count, S.dense_threads, S.smem, st>>>(
+              S.cell_off, S.dims, S.lpt, (const FT*)S.F, loc, (T*)S.ring, S.ring_in_smem, S.max_cols, N, S.gmap_p,
               S.owned_p, S.ijk, z);
           piped = true;
         }
       }
       if (!piped)
-        ras_bwd_kernel<T, D, V><<<S.count, S.dense_threads, S.smem, st>>>(
-            S.cell_off, S.dims, S.lpt, (const T*)S.F, loc, (T*)S.ring, S.ring_in_smem, S.max_cols, N, S.gmap_p,
+        ras_bwd_kernel<T, D, V, FT><<<S.count, S.dense_threads, S.smem, st>>>(
+            S.cell_off, S.dims, S.lpt, (const FT*)S.F, loc, (T*)S.ring, S.ring_in_smem, S.max_cols, N, S.gmap_p,
             S.owned_p, z);
     }
   }
@@ -1125,19 +1152,19 @@ static fv_status ras_apply_t(const fv_system* s, const V* r, V* z, cudaStream_t 
 
 // The limit is a property of the kernel function, shared by every system that launches it:
 // raise it to the device's opt-in maximum (never lower it for a smaller system).
-template <class T, int D>
+template <class T, int D, class FT = T>
 static fv_status set_smem_attr(int limit) {
-  FV_CUDA(cudaFuncSetAttribute(ras_fwd_kernel<T, D, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
-  FV_CUDA(cudaFuncSetAttribute(ras_bwd_kernel<T, D, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+  FV_CUDA(cudaFuncSetAttribute(ras_fwd_kernel<T, D, T, FT>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+  FV_CUDA(cudaFuncSetAttribute(ras_bwd_kernel<T, D, T, FT>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
   if constexpr (sizeof(T) == 4 || D < 7) {
-    FV_CUDA(cudaFuncSetAttribute(ras_fwd_pipe_kernel<T, D, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
-    FV_CUDA(cudaFuncSetAttribute(ras_bwd_pipe_kernel<T, D, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    FV_CUDA(cudaFuncSetAttribute(ras_fwd_pipe_kernel<T, D, T, FT>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    FV_CUDA(cudaFuncSetAttribute(ras_bwd_pipe_kernel<T, D, T, FT>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
   }
   if constexpr (D == 2) {
-    FV_CUDA(cudaFuncSetAttribute(ras_fwd_stage_kernel<T, T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
-    FV_CUDA(cudaFuncSetAttribute(ras_bwd_stage_kernel<T, T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
-    FV_CUDA(cudaFuncSetAttribute(ras_fwd_stage_kernel<T, T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
-    FV_CUDA(cudaFuncSetAttribute(ras_bwd_stage_kernel<T, T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    FV_CUDA(cudaFuncSetAttribute(ras_fwd_stage_kernel<T, T, 8, FT>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    FV_CUDA(cudaFuncSetAttribute(ras_bwd_stage_kernel<T, T, 8, FT>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    FV_CUDA(cudaFuncSetAttribute(ras_fwd_stage_kernel<T, T, 4, FT>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    FV_CUDA(cudaFuncSetAttribute(ras_bwd_stage_kernel<T, T, 4, FT>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
   }
   return FV_OK;
 }
@@ -1149,6 +1176,7 @@ fv_status sweeps_smem_attr(const fv_system* s) {
   FV_CUDA(cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   if (S.smem > (size_t)limit || S.stage_smem > (size_t)limit)
     return set_error("fv_assemble_system: sweep tables exceed shared memory"), FV_EINVAL;
+  if (S.bf16) return S.d == 2 ? set_smem_attr<float, 2, __nv_bfloat16>(limit) : set_smem_attr<float, 7, __nv_bfloat16>(limit);
   if (S.d == 2) return S.fp32 ? set_smem_attr<float, 2>(limit) : set_smem_attr<double, 2>(limit);
   return S.fp32 ? set_smem_attr<float, 7>(limit) : set_smem_attr<double, 7>(limit);
 }
@@ -1163,6 +1191,9 @@ fv_status ras_apply(const fv_system* s, const double* r, double* z, cudaStream_t
 static fv_status ras_apply32(const fv_system* s, const float* r, float* z, cudaStream_t st) {
   const Subdomains& S = s->subs;
   if (!S.fp32) return set_error("ras_apply32: FP64 factors need FP64 vectors"), FV_EINVAL;
+  if (S.bf16)
+    return S.d == 2 ? ras_apply_t<float, 2, float, __nv_bfloat16>(s, r, z, st)
+                    : ras_apply_t<float, 7, float, __nv_bfloat16>(s, r, z, st);
   if (S.d == 2) return ras_apply_t<float, 2, float>(s, r, z, st);
   return ras_apply_t<float, 7, float>(s, r, z, st);
 }

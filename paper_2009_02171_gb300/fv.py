@@ -15,7 +15,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, 'libfv.so')
 
 FV_VTBE, FV_PPBE = 0, 1
-FV_PREC_FP64, FV_PREC_FP32 = 0, 1
+FV_PREC_FP64, FV_PREC_FP32, FV_PREC_BF16 = 0, 1, 2
 ERRORS = {-1: 'FV_EINVAL', -2: 'FV_ENOMEM', -3: 'FV_ECUDA', -4: 'FV_ENOCONV', -5: 'FV_EBREAKDOWN', -6: 'FV_ENAN'}
 
 

@@ -299,3 +299,32 @@ def test_mixed_precision_three_level_solve_reaches_fp64_residual(fv):
     assert np.linalg.norm(b - A @ x.cpu().numpy()) <= 1.0001e-8 * np.linalg.norm(b)
     fv.fv_free_system(s)
     fv.fv_free_grid(g)
+
+
+@pytest.mark.parametrize('kind,levels', [(0, 1), (1, 2)])
+def test_bf16_factor_solve_reaches_fp64_residual(fv, kind, levels):
+    """FV_PREC_BF16: the FP32 inner solves read their ILU(0) factors stored in BF16 (every level, staged and
+    register-pipelined sweeps).  The outer FP64 FGMRES still reaches a true FP64 residual of 1e-8 against the
+    oracle's matrix, in at most two more outer iterations than with FP32 factors."""
+    Ns = Nr = 12
+    A, d, disc = _oracle_matrix(kind, Ns, Nr)
+    b = random_vector(A.shape[0], 23)
+    if kind == 1:
+        b[:disc.g.N] -= (disc.V @ b[:disc.g.N]) / disc.V.sum()
+    g = fv.fv_build_grid(Ns, Nr)
+    its = {}
+    for prec in (fv.FV_PREC_FP32, fv.FV_PREC_BF16):
+        s = fv.fv_assemble_system(g, kind, **PH, p=(2, 2, 2), overlap=1, levels=levels, precision=prec,
+                                  inner_maxit=6, coarse_maxit=6)
+        x = torch.zeros(A.shape[0], dtype=torch.float64, device='cuda')
+        st = fv.fv_gmres_solve(s, _dev(b), x, rtol=1e-8)
+        assert st.converged
+        assert np.linalg.norm(b - A @ x.cpu().numpy()) <= 1.0001e-8 * np.linalg.norm(b)
+        its[prec] = st.iters
+        if prec == fv.FV_PREC_BF16 and kind == 1:
+            with pytest.raises(fv.FvError):
+                fv.fv_gmres_solve_batch(s, _dev(b[None]), torch.zeros(1, A.shape[0], dtype=torch.float64,
+                                                                       device='cuda'))
+        fv.fv_free_system(s)
+    assert its[fv.FV_PREC_BF16] <= its[fv.FV_PREC_FP32] + 2
+    fv.fv_free_grid(g)
