@@ -28,7 +28,8 @@
 namespace fv {
 
 constexpr int KMAX = 32;     // max basis vectors in one fused pass
-constexpr int RBLOCKS = 304; // reduction blocks (2 per SM)
+constexpr int RBLOCKS = 304; // reduction blocks of the weighted sums (2 per SM)
+constexpr int CGS_BMAX = 608; // reduction blocks of a basis pass at most (4 per SM)
 constexpr int RTHREADS = 256;
 
 // Arnoldi bookkeeping of a device-driven solve (no host synchronisation)
@@ -44,7 +45,7 @@ struct KrylovT {
   int m = 0;
   long long n = 0;
   T *V = nullptr, *Z = nullptr, *w = nullptr, *r = nullptr;
-  double* part = nullptr;   // [KMAX][RBLOCKS]
+  double* part = nullptr;   // [KMAX][CGS_BMAX]
   double* h = nullptr;      // [3][KMAX]: h1, h2, nrm2
   double* hhost = nullptr;  // pinned [3][KMAX]
   ArnoldiDev* ad = nullptr; // device-driven solves
@@ -88,7 +89,7 @@ static fv_status ensure_krylov(const fv_system* s, int m) {
   const size_t n = (size_t)s->n;
   if (cudaMalloc(&k.V, (m + 1) * n * sizeof(T)) != cudaSuccess || cudaMalloc(&k.Z, m * n * sizeof(T)) != cudaSuccess ||
       cudaMalloc(&k.w, n * sizeof(T)) != cudaSuccess || cudaMalloc(&k.r, n * sizeof(T)) != cudaSuccess ||
-      cudaMalloc(&k.part, KMAX * RBLOCKS * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&k.part, KMAX * CGS_BMAX * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&k.h, 3 * KMAX * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&k.ad, sizeof(ArnoldiDev)) != cudaSuccess || cudaMalloc(&k.ticket, sizeof(unsigned)) != cudaSuccess ||
       cudaMemset(k.ticket, 0, sizeof(unsigned)) != cudaSuccess ||
@@ -112,6 +113,26 @@ __device__ __forceinline__ void block_store(double (&acc)[KMAX], int nv, double*
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int v = 0; v < KMAX; ++v) {
+    if (v < nv) {
+      double t = warp_sum(acc[v]);
+      if (lane == 0) sm[wid][v] = t;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < nv) {
+    double t = 0.0;
+    for (int q = 0; q < RTHREADS / 32; ++q) t += sm[q][threadIdx.x];
+    part[threadIdx.x * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+// block-reduce acc[0..nv) (nv <= NA) into part[v * gridDim.x + blockIdx.x]
+template <int NA>
+__device__ __forceinline__ void block_store_n(double (&acc)[NA], int nv, double* part) {
+  __shared__ double sm[RTHREADS / 32][NA];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int v = 0; v < NA; ++v) {
     if (v < nv) {
       double t = warp_sum(acc[v]);
       if (lane == 0) sm[wid][v] = t;
@@ -150,56 +171,170 @@ __device__ void givens_update(int j, const double* __restrict__ h, double nrm2, 
   ad->scale = hn > 0.0 ? 1.0 / hn : 0.0;
 }
 
+// sum of the nb partials p[0..nb) by one warp in a fixed order; the loads of a lane are issued
+// together (L2, written by other blocks of this launch) before they are added
+__device__ __forceinline__ double last_block_sum(const double* p, int nb, int lane) {
+  double t = 0.0;
+  for (int b0 = 0; b0 < nb; b0 += 32 * 8) {
+    double q[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int b = b0 + u * 32 + lane;
+      q[u] = b < nb ? __ldcg(p + b) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) t += q[u];
+  }
+  return warp_sum(t);
+}
+
+// 16-byte vector of T: four floats or two doubles
+template <class T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  static constexpr int L = 4;
+  __device__ static void load(const float* p, float (&v)[4]) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+  }
+  __device__ static void ldg(const float* p, float (&v)[4]) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+  }
+  __device__ static void store(float* p, const float (&v)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+template <>
+struct Vec16<double> {
+  static constexpr int L = 2;
+  __device__ static void load(const double* p, double (&v)[2]) {
+    const double2 q = *reinterpret_cast<const double2*>(p);
+    v[0] = q.x, v[1] = q.y;
+  }
+  __device__ static void ldg(const double* p, double (&v)[2]) {
+    const double2 q = __ldg(reinterpret_cast<const double2*>(p));
+    v[0] = q.x, v[1] = q.y;
+  }
+  __device__ static void store(double* p, const double (&v)[2]) {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  }
+};
+
 // mode 0: part = V^T w
 // mode 1: w -= V h; part = V^T w
 // mode 2: w -= V h; part[0] = w^T w
 // NV (the number of basis vectors) is a template parameter so the loops over
-// the basis unroll exactly.  Products are summed in T for up to 32 elements
-// of a thread, then in FP64.  With `out`, the last block to finish sums the
-// per-block partials in a fixed order into out[0..nv) (and, for mode 2 with
-// `ad`, applies the Givens update of column gj), so no separate reduction
-// launch is needed.
+// the basis unroll exactly; h is staged in shared memory.  With `vec` (n a
+// multiple of the 16-byte width and 16-byte aligned bases) a thread moves 16
+// bytes of every vector per iteration, which keeps enough loads in flight to
+// stream the basis at HBM rate; otherwise one element at a time.  FP32
+// products are summed in FP32 for up to 32 elements of a thread, then in FP64;
+// FP64 products go straight into the FP64 accumulators.  With `out`, the last
+// block to finish sums the per-block partials in a fixed order into
+// out[0..nv) (and, for mode 2 with `ad`, applies the Givens update of column
+// gj), so no separate reduction launch is needed.
 template <int NV, class T>
-__global__ void __launch_bounds__(RTHREADS) cgs_kernel(long long n, const T* __restrict__ V,
-                                                       const double* __restrict__ h, T* __restrict__ w,
-                                                       double* __restrict__ part, int mode, double* out,
-                                                       unsigned* ticket, ArnoldiDev* ad, int gj,
-                                                       const double* __restrict__ hg) {
-  double acc[KMAX];
-  T hv[NV > 0 ? NV : 1];
-  T cur[NV > 0 ? NV : 1];
+__global__ void __launch_bounds__(RTHREADS, (NV > 12 ? 1 : 2)) cgs_kernel(long long n, int vec, const T* __restrict__ V,
+                                                          const double* __restrict__ h, T* __restrict__ w,
+                                                          double* __restrict__ part, int mode, double* out,
+                                                          unsigned* ticket, ArnoldiDev* ad, int gj,
+                                                          const double* __restrict__ hg) {
+  constexpr int NA = NV > 0 ? NV : 1;
+  constexpr int L = Vec16<T>::L;
+  constexpr bool F32 = sizeof(T) == 4;
+  __shared__ T hs[NA];
+  if (mode > 0)
+    for (int v = threadIdx.x; v < NV; v += blockDim.x) hs[v] = (T)h[v];
+  __syncthreads();
+  double acc[NA];
+  T cur[NA];
+#pragma unroll
+  for (int v = 0; v < NA; ++v) acc[v] = 0.0, cur[v] = T(0);
+  double accn = 0.0;
   T curn = T(0);
-#pragma unroll
-  for (int v = 0; v < KMAX; ++v) acc[v] = 0.0;
-#pragma unroll
-  for (int v = 0; v < NV; ++v) hv[v] = mode > 0 ? (T)h[v] : T(0), cur[v] = T(0);
   int cnt = 0;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    T we = w[e];
-    if (mode > 0) {
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x, stride = (long long)gridDim.x * blockDim.x;
+  const long long ng = vec ? n / L : 0;
+  for (long long g = tid; g < ng; g += stride) {
+    const long long e = g * L;
+    T we[L];
+    Vec16<T>::load(w + e, we);
+    if (mode > 0 && NV > 0) {
 #pragma unroll
-      for (int v = 0; v < NV; ++v) we -= hv[v] * V[v * n + e];
+      for (int v = 0; v < NV; ++v) {
+        T vv[L];
+        Vec16<T>::ldg(V + v * n + e, vv);
+        const T hv = hs[v];
+#pragma unroll
+        for (int l = 0; l < L; ++l) we[l] -= hv * vv[l];
+      }
+      Vec16<T>::store(w + e, we);
+    }
+    if (mode < 2) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        T vv[L];
+        Vec16<T>::ldg(V + v * n + e, vv);
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+          if constexpr (F32) cur[v] += vv[l] * we[l];
+          else acc[v] += vv[l] * we[l];
+        }
+      }
+    } else {
+#pragma unroll
+      for (int l = 0; l < L; ++l) {
+        if constexpr (F32) curn += we[l] * we[l];
+        else accn += we[l] * we[l];
+      }
+    }
+    if constexpr (F32) {  // FP32 partial sums go into the FP64 accumulators every 32 elements
+      cnt += L;
+      if (cnt >= 32) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[v] += (double)cur[v], cur[v] = T(0);
+        accn += (double)curn, curn = T(0);
+        cnt = 0;
+      }
+    }
+  }
+  for (long long e = ng * L + tid; e < n; e += stride) {
+    T we = w[e];
+    if (mode > 0 && NV > 0) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) we -= hs[v] * V[v * n + e];
       w[e] = we;
     }
     if (mode < 2) {
 #pragma unroll
-      for (int v = 0; v < NV; ++v) cur[v] += V[v * n + e] * we;
+      for (int v = 0; v < NV; ++v) {
+        if constexpr (F32) cur[v] += V[v * n + e] * we;
+        else acc[v] += V[v * n + e] * we;
+      }
     } else {
-      curn += we * we;
+      if constexpr (F32) curn += we * we;
+      else accn += we * we;
     }
-    if (++cnt == 32) {
+    if constexpr (F32) {  // FP32 partial sums go into the FP64 accumulators every 32 elements
+      cnt += 1;
+      if (cnt >= 32) {
 #pragma unroll
-      for (int v = 0; v < NV; ++v) acc[v] += (double)cur[v], cur[v] = T(0);
-      acc[0] += mode == 2 ? (double)curn : 0.0;
-      curn = T(0);
-      cnt = 0;
+        for (int v = 0; v < NV; ++v) acc[v] += (double)cur[v], cur[v] = T(0);
+        accn += (double)curn, curn = T(0);
+        cnt = 0;
+      }
     }
   }
+  if constexpr (F32) {
 #pragma unroll
-  for (int v = 0; v < NV; ++v) acc[v] += (double)cur[v];
-  if (mode == 2) acc[0] += (double)curn;
+    for (int v = 0; v < NV; ++v) acc[v] += (double)cur[v];
+    accn += (double)curn;
+  }
+  if (mode == 2) acc[0] = accn;
   const int nvv = mode < 2 ? NV : 1;
-  block_store(acc, nvv, part);
+  block_store_n<NA>(acc, nvv, part);
   if (!out) return;
   __shared__ bool last;
   __threadfence();
@@ -209,17 +344,26 @@ __global__ void __launch_bounds__(RTHREADS) cgs_kernel(long long n, const T* __r
   if (!last) return;
   __threadfence();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int v = wid; v < nvv; v += nw) {
-    double t = 0.0;
-    for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(part + v * gridDim.x + b);
-    t = warp_sum(t);
-    if (lane == 0) out[v] = t;
-  }
+  for (int v = wid; v < nvv; v += nw) out[v] = last_block_sum(part + v * gridDim.x, (int)gridDim.x, lane);
   __syncthreads();
   if (threadIdx.x == 0) {
     if (mode == 2 && ad) givens_update(gj, hg, out[0], ad);
     *ticket = 0u;
   }
+}
+
+// reduction blocks of a basis pass over n elements: about four 16-byte groups (or elements) a
+// thread, at most CGS_BMAX blocks (short vectors: fewer partials for the final sum); consumers of
+// the partials take the same count
+template <class T>
+static int cgs_blocks(long long n, bool vec) {
+  const long long g = vec ? n / Vec16<T>::L : n;
+  return (int)std::min<long long>(std::max<long long>((g + 4 * RTHREADS - 1) / (4 * RTHREADS), 1), CGS_BMAX);
+}
+
+template <class T>
+static bool cgs_vec(long long n, const T* V, const T* w) {
+  return n % Vec16<T>::L == 0 && (reinterpret_cast<uintptr_t>(V) & 15) == 0 && (reinterpret_cast<uintptr_t>(w) & 15) == 0;
 }
 
 struct CgsFuse {
@@ -233,7 +377,9 @@ struct CgsFuse {
 template <int NV, class T>
 static void cgs_launch_t(long long n, const T* V, const double* h, T* w, double* part, int mode, CgsFuse f,
                          cudaStream_t st) {
-  cgs_kernel<NV, T><<<RBLOCKS, RTHREADS, 0, st>>>(n, V, h, w, part, mode, f.out, f.ticket, f.ad, f.gj, f.hg);
+  const bool vec = cgs_vec<T>(n, V, w);
+  cgs_kernel<NV, T><<<cgs_blocks<T>(n, vec), RTHREADS, 0, st>>>(n, vec ? 1 : 0, V, h, w, part, mode, f.out, f.ticket,
+                                                                 f.ad, f.gj, f.hg);
 }
 
 template <class T, int... I>
@@ -339,7 +485,7 @@ static fv_status axpby_t(long long n, double a, const T* x, double b, const T* y
 template <class T>
 static fv_status norm2(KrylovT<T>& k, long long n, const T* x, cudaStream_t st, double* out) {
   cgs_launch<T>(0, n, x, nullptr, const_cast<T*>(x), k.part, 2, st);
-  reduce_kernel<<<1, RTHREADS, 0, st>>>(k.part, RBLOCKS, 1, k.h + 2 * KMAX);
+  reduce_kernel<<<1, RTHREADS, 0, st>>>(k.part, cgs_blocks<T>(n, cgs_vec<T>(n, x, x)), 1, k.h + 2 * KMAX);
   FV_CUDA(cudaGetLastError());
   FV_CUDA(cudaMemcpyAsync(k.hhost, k.h + 2 * KMAX, sizeof(double), cudaMemcpyDeviceToHost, st));
   FV_CUDA(cudaStreamSynchronize(st));
@@ -447,7 +593,7 @@ static fv_status gmres_fixed_t(const fv_system* s, const T* b, T* x, int m, cuda
     ProfScope ps(FV_K_CGS + lvl, st);
     if (once) FV_CUDA(cudaMemsetAsync(k.h + KMAX, 0, KMAX * sizeof(double), st));
     cgs_launch<T>(0, n, b, nullptr, const_cast<T*>(b), k.part, 2, st);
-    start_kernel<<<1, 32, 0, st>>>(k.part, RBLOCKS, k.ad);
+    start_kernel<<<1, 32, 0, st>>>(k.part, cgs_blocks<T>(n, cgs_vec<T>(n, b, b)), k.ad);
     dscale_kernel<T><<<vblocks(n), 256, 0, st>>>(n, b, &k.ad->scale, k.V);
   }
   for (int j = 0; j < m; ++j) {

@@ -552,11 +552,25 @@ __global__ void sumsq_kernel(const T* __restrict__ r, long long n1, double* sspa
   if (threadIdx.x == 0) sspart[blockIdx.y * gridDim.x + blockIdx.x] = part[0];
 }
 
+// one warp a sample: lane l adds the partials l, l + 32, ... (loads issued together), then the
+// warp's fixed butterfly; the order is the same on every call
 __global__ void sssum_kernel(const double* __restrict__ sspart, int blocks, int nb, double* ss) {
-  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  for (int i = threadIdx.x >> 5; i < nb; i += blockDim.x >> 5) {
     double s = 0.0;
-    for (int b = 0; b < blocks; ++b) s += sspart[i * blocks + b];
-    ss[i] = s;
+    for (int b0 = 0; b0 < blocks; b0 += 32 * 4) {
+      double q[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int b = b0 + u * 32 + lane;
+        q[u] = b < blocks ? sspart[i * blocks + b] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) s += q[u];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) ss[i] = s;
   }
 }
 
@@ -802,7 +816,7 @@ fv_status forward_t(fv_net* n, int nb, const T* r, cudaStream_t st) {
   const int C = n->C, P = 6 * nb, Lv = n->levels;
   const int sblk = std::min(gridsz(2 * n->V1, RED_THREADS) / 8 + 1, SS_BLOCKS);
   sumsq_kernel<T><<<dim3(sblk, nb), RED_THREADS, 0, st>>>(r, 2 * n->V1, n->sspart);
-  sssum_kernel<<<1, 128, 0, st>>>(n->sspart, sblk, nb, n->ss);
+  sssum_kernel<<<1, 256, 0, st>>>(n->sspart, sblk, nb, n->ss);
   pack_kernel<T><<<gridsz(n->V1 * nb, 256), 256, 0, st>>>(r, n->ss, n->V1, nb, n->lv[0], n->x0);
   halo(n, n->x0, 16, P, n->lv[0], st);
   fv_status rc;
