@@ -88,6 +88,9 @@ def parse():
     ap.add_argument('--levels', type=int, default=0, help='override the PPBE preconditioner levels')
     ap.add_argument('--coarse-its', type=int, default=0, help='override the fixed coarse iterations (mixed precision)')
     ap.add_argument('--ppbe-inner', type=int, default=0, help='override the PPBE inner iterations (mixed precision)')
+    ap.add_argument('--coarse-p', default='', help='coarse-level box split a,b,c per panel (default: the fine split)')
+    ap.add_argument('--learned-its', type=int, default=0, help='override the coarse iterations after the network (learned arm)')
+    ap.add_argument('--learn-guess', action='store_true', help='learned arm: also correct each initial guess with the network')
     ap.add_argument('--vtbe-inner', type=int, default=0, help='override the VTBE inner iterations (mixed precision)')
     ap.add_argument('--workload', default='step', choices=['step', 'batch', 'net', 'trajectory', 'apply', 'strong',
                                                            'p8', 'convergence'],
@@ -678,14 +681,15 @@ def build_arm(fv, torch, c, dt, mode, host):
                inner_gs_passes=c['inner_gs']) if mixed else {}
     V = fv.fv_assemble_system(g, fv.FV_VTBE, **ph, p=c['p'], overlap=c['overlap'], levels=1, **mv)
     P = fv.fv_assemble_system(g, fv.FV_PPBE, **ph, p=c['p'], overlap=c['overlap'], levels=c['levels'],
-                              overlap_coarse=c['overlap_coarse'], **mpp)
+                              overlap_coarse=c['overlap_coarse'], coarse_p=c.get('coarse_p', (0, 0, 0)), **mpp)
     net, info = None, None
     if mode == 'learned':
         from paper_2009_02171_gb300.learned import train_learned_correction
         L = c.get('learn', LEARN)
         net, info = train_learned_correction(P, c['Ns'], c['Nr'], C=L['C'], levels=L['levels'], npairs=L['pairs'],
                                              epochs=L['epochs'], batch=L['batch'], lr=L['lr'],
-                                             coarse_its=L['coarse_its'])
+                                             coarse_its=L['coarse_its'],
+                                             flags=fv.FV_LEARN_GUESS if L.get('guess') else 0)
     init = torch.tensor(host, device='cuda')
     st = fv.fv_state_create(g, init, **ph)
     torch.cuda.synchronize()
@@ -978,7 +982,8 @@ def workload_name(c):
             'FGMRES(%d) to 1e-8 relative FP64 residual; mixed precision = FP32 inner FGMRES (operator, ILU(0) sweeps, '
             'coarse levels; one Gram-Schmidt pass) inside FP64 outer FGMRES (two passes); learned = mixed with the '
             'PPBE coarse solve replaced by a BF16 cubed-sphere U-Net followed by a few coarse FGMRES iterations'
-            % (c['Ns'], c['Nr'], cells / 1e6, lv, nsub, c['overlap'], c['restart']))
+            % (c['Ns'], c['Nr'], cells / 1e6, lv, nsub, c['overlap'], c['restart'])
+            + ('; coarse boxes %d x %d x %d a panel' % tuple(c['coarse_p']) if c.get('coarse_p') else ''))
 
 
 def config_of(args):
@@ -992,6 +997,14 @@ def config_of(args):
         c['coarse_its'] = args.coarse_its
     if args.ppbe_inner:
         c['ppbe_inner'] = args.ppbe_inner
+    if args.vtbe_inner:
+        c['vtbe_inner'] = args.vtbe_inner
+    if args.coarse_p:
+        c['coarse_p'] = tuple(int(v) for v in args.coarse_p.split(','))
+    if args.learned_its:
+        c['learn'] = dict(c['learn'], coarse_its=args.learned_its)
+    if args.learn_guess:
+        c['learn'] = dict(c['learn'], guess=True)
     return c
 
 
@@ -1014,7 +1027,9 @@ def algorithmic_bytes(cat, c, N, es):
     if base.startswith('ras_'):
         d = 7 if base.endswith('vtbe') else 2
         if coarse:
-            cells = box_cells(c['Ns'] // 2, c['Nr'] // 2, c['p'], c['overlap_coarse'])
+            cp = tuple(min(a or b, m) for a, b, m in zip(c.get('coarse_p', (0, 0, 0)), c['p'],
+                                                          (c['Ns'] // 2, c['Ns'] // 2, c['Nr'] // 2)))
+            cells = box_cells(c['Ns'] // 2, c['Nr'] // 2, cp, c['overlap_coarse'])
         else:
             cells = box_cells(c['Ns'], c['Nr'], c['p'], c['overlap'])
         fwd = cells * (es * (2 * d + 5 * d + d * (d - 1) // 2) + 8)

@@ -117,6 +117,11 @@ typedef struct {
    * precision only): 2 (classical Gram-Schmidt twice, the default; 0 means 2)
    * or 1 (once).  The FP64 outer FGMRES always uses two passes. */
   int inner_gs_passes;
+  /* Box split of the coarse levels (not in the paper): cp1 x cp2 x cp3 boxes
+   * a panel on every coarse mesh, each capped by that mesh's size; 0 (the
+   * default) takes p1, p2, p3, so a coarse box covers the coarse cells of one
+   * fine box.  Ignored with nboxes > 0 (the coarse level halves the boxes). */
+  int cp1, cp2, cp3;
 } fv_pc_desc;
 #define FV_PREC_FP64 0
 #define FV_PREC_FP32 1

@@ -31,6 +31,8 @@ static fv_status make_system(const fv_grid* g, int kind, const fv_phys* ph, cons
   if (pc->inner_gs_passes < 0 || pc->inner_gs_passes > 2)
     return set_error("fv_assemble_system: inner_gs_passes must be 0, 1 or 2"), FV_EINVAL;
   if (pc->levels < 1 || pc->levels > 6) return set_error("fv_assemble_system: levels must be 1..6"), FV_EINVAL;
+  if (pc->cp1 < 0 || pc->cp2 < 0 || pc->cp3 < 0)
+    return set_error("fv_assemble_system: coarse box splits must be >= 0"), FV_EINVAL;
   if (pc->precision < FV_PREC_FP64 || pc->precision > FV_PREC_BF16)
     return set_error("fv_assemble_system: precision must be FV_PREC_FP64, FV_PREC_FP32 or FV_PREC_BF16"), FV_EINVAL;
   fv_system* s = new fv_system();
@@ -82,7 +84,9 @@ static fv_status make_system(const fv_grid* g, int kind, const fv_phys* ph, cons
     fv_pc_desc cpc = *pc;
     cpc.levels = pc->levels - 1;
     cpc.overlap = pc->overlap_coarse;
-    cpc.p1 = std::min(pc->p1, g->h.Ns / 2), cpc.p2 = std::min(pc->p2, g->h.Ns / 2), cpc.p3 = std::min(pc->p3, g->h.Nr / 2);
+    cpc.p1 = std::min(pc->cp1 > 0 ? pc->cp1 : pc->p1, g->h.Ns / 2);
+    cpc.p2 = std::min(pc->cp2 > 0 ? pc->cp2 : pc->p2, g->h.Ns / 2);
+    cpc.p3 = std::min(pc->cp3 > 0 ? pc->cp3 : pc->p3, g->h.Nr / 2);
     std::vector<int> cboxes;
     if (pc->nboxes > 0) {  // the coarse level uses the halved boxes (bounds must be even)
       for (int q = 0; q < 7 * pc->nboxes; ++q) {

@@ -26,6 +26,7 @@ namespace fv {
 constexpr int TILE_I = 32;    // tile width in i: one warp per row set
 constexpr int TILE_WARPS = 4;
 constexpr int EDGE_TERMS = 40;  // bound on the terms of one panel-edge face flux (checked when tabulated)
+constexpr int RING = 8;         // planes of the tile ring: levels k - 1 .. k + 3 in use, a power of two
 
 template <class T>
 struct TileShape {
@@ -150,11 +151,25 @@ __global__ void __launch_bounds__(256) edge_flux_kernel(int Ns, int Nr, EdgeTab<
   R acc[D];
 #pragma unroll
   for (int c = 0; c < D; ++c) acc[c] = R(0);
-  for (int m = 0; m < n; ++m) {
-    const int o = et.off[m * nf + f];
-    const R w = et.w[m * nf + f];
+  // four terms at a time: their table slots, then all their cell values, are in flight together
+  for (int m0 = 0; m0 < n; m0 += 4) {
+    int o[4];
+    R w[4];
 #pragma unroll
-    for (int c = 0; c < D; ++c) acc[c] += w * (R)xk[c * N + o];
+    for (int u = 0; u < 4; ++u) {
+      const bool on = m0 + u < n;
+      o[u] = on ? et.off[(m0 + u) * nf + f] : 0;
+      w[u] = on ? et.w[(m0 + u) * nf + f] : R(0);
+    }
+    T xv[4][D];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int c = 0; c < D; ++c) xv[u][c] = m0 + u < n ? xk[c * N + o[u]] : T(0);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int c = 0; c < D; ++c) acc[c] += w[u] * (R)xv[u][c];
   }
 #pragma unroll
   for (int c = 0; c < D; ++c) E[(c * Nr + k) * nf + f] = (T)acc[c];
@@ -175,7 +190,7 @@ __device__ __forceinline__ T halo_value(const GT& G, const T* __restrict__ x, in
 // one component c of one tile and level chunk (blockIdx.x = tile * D + c, so the D components of a tile run
 // side by side and the couplings below read each other's values from L2; y = level chunk, z = panel)
 template <int KIND, class T, class GT>
-__global__ void __launch_bounds__(TILE_I* TILE_WARPS, sizeof(T) == 8 ? 3 : (KIND == FV_VTBE ? 4 : 5)) tile_apply_kernel(
+__global__ void __launch_bounds__(TILE_I* TILE_WARPS, sizeof(T) == 8 ? (KIND == FV_VTBE ? 2 : 3) : (KIND == FV_VTBE ? 4 : 5)) tile_apply_kernel(
     GT G, Coefs<typename GT::real> cf, const T* __restrict__ x, T* __restrict__ y, int kchunk,
     const T* __restrict__ E) {
   using R = typename GT::real;
@@ -183,7 +198,7 @@ __global__ void __launch_bounds__(TILE_I* TILE_WARPS, sizeof(T) == 8 ? 3 : (KIND
   constexpr int D = KIND == FV_VTBE ? 7 : 2;
   constexpr int RJ = S::RJ, TJ = S::TJ, PW = S::PW, PLANE = S::PLANE;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* const sh = reinterpret_cast<T*>(smem_raw);  // ring of four planes, slot = level & 3 (level -1: slot 3)
+  T* const sh = reinterpret_cast<T*>(smem_raw);  // ring of RING planes, slot = level & (RING - 1)
   const int Ns = G.Ns, Nr = G.Nr, Ns2 = Ns * Ns;
   const int NP = Nr * Ns2;  // cells of one panel
   const int N = 6 * NP;
@@ -256,25 +271,28 @@ __global__ void __launch_bounds__(TILE_I* TILE_WARPS, sizeof(T) == 8 ? 3 : (KIND
   const int vpos0 = ty * RJ * PW + tx;           // top-left of its 3 x (RJ + 2) neighbourhood
   const unsigned sbase = (unsigned)__cvta_generic_to_shared(sh);
 
-  // levels kb - 1 .. kb + 1 (walls as ghost planes at the mirror radius: odd -x, even +x,
-  // B: -B + fac (B.rhat) rhat); then the halo of kb + 2 into registers
-  R hnext = R(0);
-  for (int k = kb - 1; k <= kb + 1; ++k) {
-    T* pl = sh + (k & 3) * PLANE;
-    if (k < 0 || k >= Nr) {
-      const int kw = k < 0 ? 0 : Nr - 1;
-      const R fac = k < 0 ? G.wall_in : G.wall_out;
+  // the outer wall's ghost plane (level Nr) at the mirror radius: odd -x, even +x, B: -B + fac (B.rhat) rhat;
+  // the inner wall's (level -1) likewise from level 0
+  auto wall_plane = [&](int k, T* pl) {
+    const int kw = k < 0 ? 0 : Nr - 1;
+    const R fac = k < 0 ? G.wall_in : G.wall_out;
 #pragma unroll
-      for (int r = 0; r < RJ; ++r) {
-        if (i >= Ns || jb + r >= Ns) continue;
-        const int e = own0 + kw * Ns2 + r * Ns;
-        const R v0 = (R)xc[e];
-        R g = wall == 1 ? v0 : -v0;
-        if (wall == 2)
-          g += fac * rhc[r] *
-               (rh[r][0] * (R)x[4 * N + e] + rh[r][1] * (R)x[5 * N + e] + rh[r][2] * (R)x[6 * N + e]);
-        pl[pos0 + r * PW] = (T)g;
-      }
+    for (int r = 0; r < RJ; ++r) {
+      if (i >= Ns || jb + r >= Ns) continue;
+      const int e = own0 + kw * Ns2 + r * Ns;
+      const R v0 = (R)xc[e];
+      R g = wall == 1 ? v0 : -v0;
+      if (wall == 2)
+        g += fac * rhc[r] * (rh[r][0] * (R)x[4 * N + e] + rh[r][1] * (R)x[5 * N + e] + rh[r][2] * (R)x[6 * N + e]);
+      pl[pos0 + r * PW] = (T)g;
+    }
+  };
+  // planes kb - 1 .. kb + 2 (up to the chunk's last plane ke), then the halo of kb + 3 into registers
+  R hnext = R(0);
+  for (int k = kb - 1; k <= kb + 2 && k <= ke; ++k) {
+    T* pl = sh + (k & (RING - 1)) * PLANE;
+    if (k < 0 || k >= Nr) {
+      wall_plane(k, pl);
     } else {
       if (tid < S::HALO) {
         const T* xk = xc + k * Ns2;
@@ -289,72 +307,79 @@ __global__ void __launch_bounds__(TILE_I* TILE_WARPS, sizeof(T) == 8 ? 3 : (KIND
       }
     }
   }
-  if (kb + 2 < Nr && tid < S::HALO) {
-    const T* xk = xc + (kb + 2) * Ns2;
+  if (kb + 3 < Nr && kb + 3 <= ke && tid < S::HALO) {
+    const T* xk = xc + (kb + 3) * Ns2;
     hnext = hw[0] * (R)xk[ho[0]] + hw[1] * (R)xk[ho[1]] + hw[2] * (R)xk[ho[2]];
   }
+  // the other components a VTBE row of (u, Theta) couples with at one cell (Coriolis, buoyancy, r . u),
+  // loaded one level ahead: c = 3 reads u_x, u_y, u_z; c < 3 reads Theta and (c = 0, 1) u_y or u_x
+  constexpr bool CPL = KIND == FV_VTBE;
+  const bool cpl_on = CPL && c <= 3;
+  const int cc0 = c == 3 ? 0 : 3, cc1 = c == 3 ? 1 : (c == 0 ? 1 : 0), cc2 = 2;
+  const int ncc = c == 3 ? 3 : (c == 2 ? 1 : 2);
+  R cv[RJ][3];
+  auto load_cpl = [&](int k) {
+#pragma unroll
+    for (int r = 0; r < RJ; ++r) {
+      cv[r][0] = cv[r][1] = cv[r][2] = R(0);
+      if (!cpl_on || k >= Nr || i >= Ns || jb + r >= Ns) continue;
+      const int e = own0 + k * Ns2 + r * Ns;
+      cv[r][0] = (R)x[cc0 * N + e];
+      if (ncc > 1) cv[r][1] = (R)x[cc1 * N + e];
+      if (ncc > 2) cv[r][2] = (R)x[cc2 * N + e];
+    }
+  };
+  if (CPL) load_cpl(kb);
   __syncthreads();
 
   const R cdiag = KIND == FV_PPBE ? cf.pp : (c < 3 ? cf.h : (c == 3 ? cf.hpr : cf.hpm));
   for (int k = kb; k < ke; ++k) {
-    const int s0 = (k & 3) * PLANE, sm = ((k + 3) & 3) * PLANE, sp = ((k + 1) & 3) * PLANE;
-    // level k + 2 into the slot of level k - 2 (no thread reads it after the last barrier); the own cells by
-    // asynchronous copies that land while level k is computed
-    if (k + 2 <= ke && k + 2 < Nr) {
-      const int s2 = ((k + 2) & 3) * PLANE;
-      if (tid < S::HALO) sh[s2 + hpos] = (T)hnext;
+    const int s0 = (k & (RING - 1)) * PLANE, sm = ((k - 1) & (RING - 1)) * PLANE, sp = ((k + 1) & (RING - 1)) * PLANE;
+    // level k + 3 into the slot of level k - 5 (no thread reads it after the last barrier); the own cells by
+    // asynchronous copies that land while levels k and k + 1 are computed (one commit group a level)
+    if (k + 3 <= ke && k + 3 < Nr) {
+      const int s3 = ((k + 3) & (RING - 1)) * PLANE;
+      if (tid < S::HALO) sh[s3 + hpos] = (T)hnext;
       if (full) {
-        const T* src = xc + own0 + (k + 2) * Ns2;
+        const T* src = xc + own0 + (k + 3) * Ns2;
 #pragma unroll
         for (int r = 0; r < RJ; ++r)
-          asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sbase + (unsigned)((s2 + pos0 + r * PW) * sizeof(T))),
+          asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sbase + (unsigned)((s3 + pos0 + r * PW) * sizeof(T))),
                        "l"(src + r * Ns), "n"(sizeof(T)));
       } else {
 #pragma unroll
         for (int r = 0; r < RJ; ++r)
-          sh[s2 + pos0 + r * PW] = (i < Ns && jb + r < Ns) ? xc[own0 + (k + 2) * Ns2 + r * Ns]
-                                                           : halo_value(G, x, c, p, k + 2, jb + r, i);
+          sh[s3 + pos0 + r * PW] = (i < Ns && jb + r < Ns) ? xc[own0 + (k + 3) * Ns2 + r * Ns]
+                                                           : halo_value(G, x, c, p, k + 3, jb + r, i);
       }
-      asm volatile("cp.async.commit_group;\n" ::);
-      if (k + 3 < Nr && tid < S::HALO) {
-        const T* xk = xc + (k + 3) * Ns2;
+      if (k + 4 < Nr && k + 4 <= ke && tid < S::HALO) {
+        const T* xk = xc + (k + 4) * Ns2;
         hnext = hw[0] * (R)xk[ho[0]] + hw[1] * (R)xk[ho[1]] + hw[2] * (R)xk[ho[2]];
       }
-    } else if (k + 2 == Nr && k + 2 <= ke) {  // the outer wall's ghost plane
-      const int s2 = ((k + 2) & 3) * PLANE;
-#pragma unroll
-      for (int r = 0; r < RJ; ++r) {
-        if (i >= Ns || jb + r >= Ns) continue;
-        const int e = own0 + (Nr - 1) * Ns2 + r * Ns;
-        const R v0 = (R)xc[e];
-        R g = wall == 1 ? v0 : -v0;
-        if (wall == 2)
-          g += G.wall_out * rhc[r] *
-               (rh[r][0] * (R)x[4 * N + e] + rh[r][1] * (R)x[5 * N + e] + rh[r][2] * (R)x[6 * N + e]);
-        sh[s2 + pos0 + r * PW] = (T)g;
-      }
+    } else if (k + 3 == Nr && k + 3 <= ke) {  // the outer wall's ghost plane
+      wall_plane(Nr, sh + ((k + 3) & (RING - 1)) * PLANE);
     }
+    asm volatile("cp.async.commit_group;\n" ::);
     const R q = G.invr2[k], rb = G.rf2[k], rt = G.rf2[k + 1], rk = G.rc[k];
     const int ek = own0 + k * Ns2;
-    // couplings of a VTBE row with other components of the same cell (buoyancy, Coriolis, r . u)
+    // couplings of a VTBE row with other components of the same cell, from the values loaded a level ago
     R cpl[RJ];
 #pragma unroll
     for (int r = 0; r < RJ; ++r) cpl[r] = R(0);
-    if (KIND == FV_VTBE && c <= 3) {
+    if (CPL && c <= 3) {
       const R b1 = cf.r1 * rk, b2 = cf.r2 / (rk * rk);
 #pragma unroll
       for (int r = 0; r < RJ; ++r) {
-        if (i >= Ns || jb + r >= Ns) continue;
-        const int e = ek + r * Ns;
         if (c == 3) {
-          cpl[r] = b2 * (rh[r][0] * (R)x[e] + rh[r][1] * (R)x[N + e] + rh[r][2] * (R)x[2 * N + e]);
+          cpl[r] = b2 * (rh[r][0] * cv[r][0] + rh[r][1] * cv[r][1] + rh[r][2] * cv[r][2]);
         } else {
-          cpl[r] = b1 * rhc[r] * (R)x[3 * N + e];
-          if (c == 0) cpl[r] += cf.cor * (R)x[N + e];
-          if (c == 1) cpl[r] -= cf.cor * (R)x[e];
+          cpl[r] = b1 * rhc[r] * cv[r][0];
+          if (c == 0) cpl[r] += cf.cor * cv[r][1];
+          if (c == 1) cpl[r] -= cf.cor * cv[r][1];
         }
       }
     }
+    if (CPL && k + 1 < ke) load_cpl(k + 1);
     R v[RJ + 2][3];
 #pragma unroll
     for (int rr = 0; rr < RJ + 2; ++rr)
@@ -382,9 +407,11 @@ __global__ void __launch_bounds__(TILE_I* TILE_WARPS, sizeof(T) == 8 ? 3 : (KIND
       const R out = KIND == FV_PPBE ? cdiag * lap : x0 + cdiag * lap + cpl[r];
       if (i < Ns && jb + r < Ns) yc[ek + r * Ns] = (T)out;
     }
-    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    // level k + 1 reads plane k + 2, whose copies were issued a level ago: all but the newest group landed
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
     __syncthreads();
   }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
 template <int KIND, class T, class GT>
@@ -392,7 +419,7 @@ static fv_status launch_tiled(const GT& G, const Coefs<typename GT::real>& cf, c
                               const T* x, T* E, T* y, cudaStream_t st, int cat) {
   using S = TileShape<T>;
   const int D = KIND == FV_VTBE ? 7 : 2;
-  const size_t smem = (size_t)4 * S::PLANE * sizeof(T);
+  const size_t smem = (size_t)RING * S::PLANE * sizeof(T);
   static std::once_flag once[64];
   static cudaError_t attr_err[64];
   int dev = 0;

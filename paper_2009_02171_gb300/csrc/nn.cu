@@ -6,8 +6,8 @@
 // cell of a pyramid level, each panel padded by a one-cell ring in (eta, xi):
 // [panel][k][j + 1][i + 1][channel], (Ns_l + 2)^2 voxels a plane, panel = sample
 // * 6 + cubed-sphere panel.  The ring holds the neighbouring panel's cells across
-// each edge (written by the producing convolution's epilogue, or by halo_fill for the
-// input and the pooled tensors); ring corners stay zero.  A convolution is an implicit
+// each edge (written by whichever kernel produces the tensor: the convolution epilogue,
+// the input packing, the pooling); ring corners stay zero.  A convolution is an implicit
 // GEMM (M = voxels, N = output channels, K = 27 taps x input channels) on the
 // tensor cores (mma.sync m16n8k16, BF16 x BF16 -> FP32): one CTA computes a
 // 4 x 4 x 8 brick of output voxels from a (6 x 6 x 10)-voxel halo of its input
@@ -16,8 +16,9 @@
 // transposed weights over the whole padded plane (the gradient of the ring
 // included), followed by halo_adjoint (ring gradients added to the neighbour
 // cells they were copied from); the weight gradient is a GEMM over voxels
-// (M = input channels, N = output channels) split over (tap, voxel range) CTAs
-// with FP32 atomics into the master gradient.
+// (M = input channels, N = output channels) split over (tap, voxel range) CTAs,
+// whose partial tiles are added in a fixed order (no atomics: training is bitwise
+// reproducible).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -63,6 +64,23 @@ __device__ __forceinline__ void side_cell(int side, int t, int n, bool ring, int
   else if (side == 1) y = t + 1, x = hi;
   else if (side == 2) y = lo, x = t + 1;
   else y = hi, x = t + 1;
+}
+
+// The ring voxels that copy interior cell (pp, z, jj, ii) of a level with n x n cells a plane: one beyond
+// each panel edge the cell touches, in the neighbouring panel's ring (the copy a ring voxel takes from the neighbouring panel);
+// f(voxel index) stores the value there
+template <class F>
+__device__ __forceinline__ void ring_targets(const Halo& H, int n, int Z, int pp, int z, int jj, int ii, F&& f) {
+  const int pl = pp % 6, base = pp - pl, Yp = n + 2, Xp = n + 2;
+#pragma unroll
+  for (int sd = 0; sd < 4; ++sd) {
+    const bool on = sd == 0 ? ii == 0 : sd == 1 ? ii == n - 1 : sd == 2 ? jj == 0 : jj == n - 1;
+    if (!on) continue;
+    const int e = pl * 4 + sd, t = sd < 2 ? jj : ii;
+    int yr, xr;
+    side_cell(H.s[e], H.flip[e] ? n - 1 - t : t, n, true, yr, xr);
+    f((((long long)(base + H.q[e]) * Z + z) * Yp + yr) * Xp + xr);
+  }
 }
 
 struct ConvArgs {
@@ -221,47 +239,15 @@ __global__ void __launch_bounds__(CONV_THREADS) conv_kernel(ConvArgs a) {
         }
         const __nv_bfloat162 o = __floats2bfloat162_rn(u0, u1);
         *reinterpret_cast<__nv_bfloat162*>(a.out + v * a.cout + col) = o;
-        if (a.ring) {  // the cell is the source of the ring voxel across each panel edge it touches
-          const int n = a.L.Y, jj = y - 1, ii = x - 1, pl = p % 6, base = p - pl;
-#pragma unroll
-          for (int sd = 0; sd < 4; ++sd) {
-            const bool on = sd == 0 ? ii == 0 : sd == 1 ? ii == n - 1 : sd == 2 ? jj == 0 : jj == n - 1;
-            if (!on) continue;
-            const int e = pl * 4 + sd, t = sd < 2 ? jj : ii;
-            int yr, xr;
-            side_cell(a.H.s[e], a.H.flip[e] ? n - 1 - t : t, n, true, yr, xr);
-            const long long rv = (((long long)(base + a.H.q[e]) * a.L.Z + z) * Yp + yr) * Xp + xr;
+        if (a.ring)  // the cell is the source of the ring voxel across each panel edge it touches
+          ring_targets(a.H, a.L.Y, a.L.Z, p, z, y - 1, x - 1, [&](long long rv) {
             *reinterpret_cast<__nv_bfloat162*>(a.out + rv * a.cout + col) = o;
-          }
-        }
+          });
       }
     }
 }
 
-__global__ void halo_fill_kernel(bf16* __restrict__ a, int C, int P, Lvl L, Halo H) {
-  const int n = L.Y, qn = C / 8;
-  const long long total = (long long)P * 4 * n * L.Z * qn;
-  const int Yp = L.Y + 2, Xp = L.X + 2;
-  for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total; it += (long long)gridDim.x * blockDim.x) {
-    const int q = (int)(it % qn);
-    long long t = it / qn;
-    const int z = (int)(t % L.Z);
-    t /= L.Z;
-    const int tt = (int)(t % n);
-    t /= n;
-    const int side = (int)(t % 4);
-    const int pp = (int)(t / 4), p = pp % 6, base = pp - p;
-    const int e = p * 4 + side;
-    int yd, xd, ys, xs;
-    side_cell(side, tt, n, true, yd, xd);
-    side_cell(H.s[e], H.flip[e] ? n - 1 - tt : tt, n, false, ys, xs);
-    const long long src = (((long long)(base + H.q[e]) * L.Z + z) * Yp + ys) * Xp + xs;
-    const long long dst = (((long long)pp * L.Z + z) * Yp + yd) * Xp + xd;
-    *reinterpret_cast<uint4*>(a + dst * C + q * 8) = *reinterpret_cast<const uint4*>(a + src * C + q * 8);
-  }
-}
-
-// Adjoint of halo_fill on a gradient over the whole padded plane: every edge cell gets
+// Adjoint of the ring fill on a gradient over the whole padded plane: every edge cell gets
 // the ring gradients copied from it added (1 side, 2 at a panel corner, 4 when n = 1).
 // Ring values are left in place (consumers read interior cells only).
 __global__ void halo_adjoint_kernel(bf16* __restrict__ g, int C, int P, Lvl L, Halo H) {
@@ -320,8 +306,9 @@ __device__ __forceinline__ long long padded(long long cell, const Lvl& L) {
   return (t * (L.Y + 2) + y + 1) * (L.X + 2) + x + 1;
 }
 
-// 2x2x2 mean pooling of the interior of a (level l) into the interior of out (level l + 1 = Lc)
-__global__ void pool_kernel(const bf16* __restrict__ a, bf16* __restrict__ out, int C, int P, Lvl Lc) {
+// 2x2x2 mean pooling of the interior of a (level l) into the interior of out (level l + 1 = Lc), and of
+// the pooled panel-edge cells into the neighbouring panels' rings
+__global__ void pool_kernel(const bf16* __restrict__ a, bf16* __restrict__ out, int C, int P, Lvl Lc, Halo H) {
   const Lvl L{Lc.Z * 2, Lc.Y * 2, Lc.X * 2};
   const int qn = C / 8;
   const long long total = Lc.cells(P) * qn;
@@ -347,6 +334,7 @@ __global__ void pool_kernel(const bf16* __restrict__ a, bf16* __restrict__ out, 
     __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&o);
     for (int k = 0; k < 4; ++k) h[k] = __floats2bfloat162_rn(0.125f * s[2 * k], 0.125f * s[2 * k + 1]);
     *reinterpret_cast<uint4*>(out + padded(cell, Lc) * C + q * 8) = o;
+    ring_targets(H, Lc.Y, Lc.Z, (int)p, z, y, x, [&](long long rv) { *reinterpret_cast<uint4*>(out + rv * C + q * 8) = o; });
   }
 }
 
@@ -578,7 +566,7 @@ __global__ void sssum_kernel(const double* __restrict__ sspart, int blocks, int 
 // s the RMS of the sample (ss = its sum of squares over 2 V1 values): O(1) activations
 template <class T>
 __global__ void pack_kernel(const T* __restrict__ r, const double* __restrict__ ss, long long V1, int nb, Lvl L,
-                            bf16* __restrict__ x) {
+                            bf16* __restrict__ x, Halo H) {
   const long long n = V1 * nb;
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
     const long long b = v / V1, vl = v - b * V1;
@@ -590,6 +578,14 @@ __global__ void pack_kernel(const T* __restrict__ r, const double* __restrict__ 
     uint4* dst = reinterpret_cast<uint4*>(x + padded(v, L) * 16);
     dst[0] = o[0];
     dst[1] = o[1];
+    // panel-edge cells also fill the neighbouring panels' rings
+    const int xi = (int)(v % L.X), yj = (int)((v / L.X) % L.Y);
+    const long long pz = v / ((long long)L.X * L.Y);
+    ring_targets(H, L.Y, L.Z, (int)(pz / L.Z), (int)(pz % L.Z), yj, xi, [&](long long rv) {
+      uint4* d = reinterpret_cast<uint4*>(x + rv * 16);
+      d[0] = o[0];
+      d[1] = o[1];
+    });
   }
 }
 
@@ -792,10 +788,6 @@ fv_status wgrad(fv_net* n, const bf16* s0, int c0, const bf16* s1, int c1, const
   return FV_OK;
 }
 
-void halo(fv_net* n, bf16* a, int C, int P, const Lvl& L, cudaStream_t st) {
-  halo_fill_kernel<<<gridsz((long long)P * 4 * L.Y * L.Z * (C / 8), 256), 256, 0, st>>>(a, C, P, L, n->halo);
-}
-
 void halo_adj(fv_net* n, bf16* g, int C, int P, const Lvl& L, cudaStream_t st) {
   const long long ne = L.Y > 1 ? 4 * L.Y - 4 : 1;
   halo_adjoint_kernel<<<gridsz((long long)P * L.Z * ne * C, 256), 256, 0, st>>>(g, C, P, L, n->halo);
@@ -817,16 +809,14 @@ fv_status forward_t(fv_net* n, int nb, const T* r, cudaStream_t st) {
   const int sblk = std::min(gridsz(2 * n->V1, RED_THREADS) / 8 + 1, SS_BLOCKS);
   sumsq_kernel<T><<<dim3(sblk, nb), RED_THREADS, 0, st>>>(r, 2 * n->V1, n->sspart);
   sssum_kernel<<<1, 256, 0, st>>>(n->sspart, sblk, nb, n->ss);
-  pack_kernel<T><<<gridsz(n->V1 * nb, 256), 256, 0, st>>>(r, n->ss, n->V1, nb, n->lv[0], n->x0);
-  halo(n, n->x0, 16, P, n->lv[0], st);
+  pack_kernel<T><<<gridsz(n->V1 * nb, 256), 256, 0, st>>>(r, n->ss, n->V1, nb, n->lv[0], n->x0, n->halo);
   fv_status rc;
   for (int l = 0; l <= Lv; ++l) {
     const Lvl& L = n->lv[l];
     const bf16* in = n->x0;
     int cin = 16;
     if (l > 0) {
-      pool_kernel<<<gridsz(L.cells(P) * (C / 8), 256), 256, 0, st>>>(n->E[l - 1], n->In[l], C, P, L);
-      halo(n, n->In[l], C, P, L, st);
+      pool_kernel<<<gridsz(L.cells(P) * (C / 8), 256), 256, 0, st>>>(n->E[l - 1], n->In[l], C, P, L, n->halo);
       in = n->In[l], cin = C;
     }
     ConvArgs a = fwd_args(in, cin, nullptr, 0, n->L[eA(l)], P, L, EPI_RELU);

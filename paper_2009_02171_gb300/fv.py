@@ -38,7 +38,8 @@ class fv_pc_desc(ctypes.Structure):
                 ('levels', ctypes.c_int), ('overlap_coarse', ctypes.c_int), ('coarse_rtol', ctypes.c_double),
                 ('coarse_restart', ctypes.c_int), ('coarse_maxit', ctypes.c_int), ('precision', ctypes.c_int),
                 ('inner_rtol', ctypes.c_double), ('inner_restart', ctypes.c_int), ('inner_maxit', ctypes.c_int),
-                ('nboxes', ctypes.c_int), ('boxes', ctypes.POINTER(ctypes.c_int)), ('inner_gs_passes', ctypes.c_int)]
+                ('nboxes', ctypes.c_int), ('boxes', ctypes.POINTER(ctypes.c_int)), ('inner_gs_passes', ctypes.c_int),
+                ('cp1', ctypes.c_int), ('cp2', ctypes.c_int), ('cp3', ctypes.c_int)]
 
 
 class fv_gmres_opts(ctypes.Structure):
@@ -158,14 +159,14 @@ def fv_build_grid(Ns, Nr, ri=7.0 / 13.0, ro=20.0 / 13.0):
 
 def fv_assemble_system(grid, kind, E, Ra, Pr, Pm, dt, p=(1, 1, 1), overlap=1, levels=1, overlap_coarse=1,
                        coarse_rtol=0.1, coarse_restart=30, coarse_maxit=30, precision=FV_PREC_FP64, inner_rtol=1e-3,
-                       inner_restart=30, inner_maxit=30, boxes=None, inner_gs_passes=2):
+                       inner_restart=30, inner_maxit=30, boxes=None, inner_gs_passes=2, coarse_p=(0, 0, 0)):
     h = ctypes.c_void_p()
     nb, bp = 0, None
     if boxes is not None:
         flat = (ctypes.c_int * (7 * len(boxes)))(*[int(v) for bx in boxes for v in bx])
         nb, bp = len(boxes), ctypes.cast(flat, ctypes.POINTER(ctypes.c_int))
     pc = fv_pc_desc(p[0], p[1], p[2], overlap, levels, overlap_coarse, coarse_rtol, coarse_restart, coarse_maxit,
-                    precision, inner_rtol, inner_restart, inner_maxit, nb, bp, inner_gs_passes)
+                    precision, inner_rtol, inner_restart, inner_maxit, nb, bp, inner_gs_passes, *coarse_p)
     _check(lib.fv_assemble_system(grid, kind, ctypes.byref(fv_phys(E, Ra, Pr, Pm, dt)), ctypes.byref(pc),
                                   ctypes.byref(h)))
     return h

@@ -51,7 +51,7 @@ def coarse_training_pairs(system, Ns, Nr, npairs, seed=5, target_rtol=1e-6, chun
 
 
 def train_learned_correction(system, Ns, Nr, C=16, levels=3, npairs=256, epochs=40, batch=8, lr=3e-4,
-                             data_seed=5, init_seed=9, train_seed=3, coarse_its=6, attach=True):
+                             data_seed=5, init_seed=9, train_seed=3, coarse_its=6, attach=True, flags=0):
     """Train a network for the coarse grid of `system` (fine grid Ns x Ns x Nr) and attach it.
 
     Returns (net, info).  The caller frees the network (after detaching it) with fv_net_free."""
@@ -66,5 +66,5 @@ def train_learned_correction(system, Ns, Nr, C=16, levels=3, npairs=256, epochs=
                  'loss_last_epoch': float(losses[-1]), 'coarse_its': coarse_its})
     del R, E
     if attach:
-        fv.fv_pc_set_learned(system, net, coarse_its=coarse_its)
+        fv.fv_pc_set_learned(system, net, coarse_its=coarse_its, flags=flags)
     return net, info
