@@ -182,7 +182,7 @@ class TwoLevelRAS:
     """Hybrid two-level RAS, y = w + M_one^{-1}(x - A_f w), w = I_c^f A_c^{-1} I_f^c x."""
 
     def __init__(self, grid, A, grid_c, A_c, d, parts, delta, delta_c, rtol_c=0.1, restart_c=30, maxit_c=30,
-                 neumann_first=False, coarse_pc=None):
+                 neumann_first=False, coarse_pc=None, parts_c=None):
         self.g, self.A, self.Ac, self.d = grid, A, A_c, d
         # the Neumann pressure (first PPBE component) has a singular coarse matrix whose left null
         # vector is the coarse cell volumes; its restricted right-hand side is projected onto the range
@@ -190,7 +190,8 @@ class TwoLevelRAS:
         self.fine = OneLevelRAS(grid, A, d, parts, delta)
         # the coarse GMRES's preconditioner: one-level RAS (eqn:coarsepreconditioner), or for more levels the
         # hybrid construction again on the next coarser mesh (Sec. 3.3)
-        self.coarse = coarse_pc if coarse_pc is not None else OneLevelRAS(grid_c, A_c, d, parts, delta_c)
+        # (parts_c: the coarse box split when it is chosen apart from the fine one)
+        self.coarse = coarse_pc if coarse_pc is not None else OneLevelRAS(grid_c, A_c, d, parts_c or parts, delta_c)
         self.rtol_c, self.restart_c, self.maxit_c = rtol_c, restart_c, maxit_c
         self.inner_iters = 0
 
@@ -212,17 +213,18 @@ def coarse_parts(parts, grid_c):
 
 
 def hybrid_ras(grid, A, matrix_of, d, parts, delta, delta_c, levels, rtol_c=0.1, restart_c=30, maxit_c=30,
-               neumann_first=False):
+               neumann_first=False, parts_c=None):
     """levels-level hybrid RAS (Sec. 3.3): levels = 1 is one-level RAS (eqn:onelevel); otherwise
     eqn:twolevel with the coarse system (the same discretization on the 1:2 mesh, matrix_of(coarse grid))
     solved by GMRES preconditioned by the (levels - 1)-level construction on that mesh.  Every coarse level
-    uses overlap delta_c and the same inner tolerance, restart and iteration cap."""
+    uses overlap delta_c and the same inner tolerance, restart and iteration cap; parts_c (optional) is the box
+    split of every coarse level, capped by each coarse mesh (default: the fine split)."""
     if levels <= 1:
         return OneLevelRAS(grid, A, d, parts, delta)
     gc = Grid(grid.Ns // 2, grid.Nr // 2, grid.ri, grid.ro)
     Ac = matrix_of(gc)
-    pc = coarse_parts(parts, gc)
+    pc = coarse_parts(parts_c or parts, gc)
     inner = hybrid_ras(gc, Ac, matrix_of, d, pc, delta_c, delta_c, levels - 1, rtol_c, restart_c, maxit_c,
-                       neumann_first) if levels > 2 else None
+                       neumann_first, parts_c) if levels > 2 else None
     return TwoLevelRAS(grid, A, gc, Ac, d, parts, delta, delta_c, rtol_c, restart_c, maxit_c, neumann_first,
-                       coarse_pc=inner)
+                       coarse_pc=inner, parts_c=pc if parts_c else None)

@@ -39,6 +39,7 @@ class Physics:
 @dataclass
 class SolverOptions:
     parts: tuple = (1, 1, 1)
+    parts_c: tuple = None   # coarse box split (None: the fine split)
     delta: int = 1
     ppbe_levels: int = 1
     delta_c: int = 1
@@ -76,7 +77,8 @@ class Stepper:
         self.MV = OneLevelRAS(grid, self.AV, 7, opt.parts, opt.delta)
         if opt.ppbe_levels >= 2:
             self.MP = hybrid_ras(grid, self.AP, lambda g: ppbe_matrix(Discretization(g), phys.E, phys.dt), 2,
-                                 opt.parts, opt.delta, opt.delta_c, opt.ppbe_levels, opt.rtol_c, neumann_first=True)
+                                 opt.parts, opt.delta, opt.delta_c, opt.ppbe_levels, opt.rtol_c, neumann_first=True,
+                                 parts_c=opt.parts_c)
         else:
             self.MP = OneLevelRAS(grid, self.AP, 2, opt.parts, opt.delta)
         self.Eu = self.d.extension('odd')

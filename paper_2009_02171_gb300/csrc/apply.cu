@@ -190,7 +190,7 @@ __device__ __forceinline__ T halo_value(const GT& G, const T* __restrict__ x, in
 // one component c of one tile and level chunk (blockIdx.x = tile * D + c, so the D components of a tile run
 // side by side and the couplings below read each other's values from L2; y = level chunk, z = panel)
 template <int KIND, class T, class GT>
-__global__ void __launch_bounds__(TILE_I* TILE_WARPS, sizeof(T) == 8 ? (KIND == FV_VTBE ? 2 : 3) : (KIND == FV_VTBE ? 4 : 5)) tile_apply_kernel(
+__global__ void __launch_bounds__(TILE_I* TILE_WARPS, sizeof(T) == 8 ? 3 : (KIND == FV_VTBE ? 4 : 5)) tile_apply_kernel(
     GT G, Coefs<typename GT::real> cf, const T* __restrict__ x, T* __restrict__ y, int kchunk,
     const T* __restrict__ E) {
   using R = typename GT::real;
@@ -314,6 +314,7 @@ __global__ void __launch_bounds__(TILE_I* TILE_WARPS, sizeof(T) == 8 ? (KIND == 
   // the other components a VTBE row of (u, Theta) couples with at one cell (Coriolis, buoyancy, r . u),
   // loaded one level ahead: c = 3 reads u_x, u_y, u_z; c < 3 reads Theta and (c = 0, 1) u_y or u_x
   constexpr bool CPL = KIND == FV_VTBE;
+  constexpr bool CPL_AHEAD = CPL && sizeof(T) == 4;  // FP64 (bound by its pipe) loads them at their own level
   const bool cpl_on = CPL && c <= 3;
   const int cc0 = c == 3 ? 0 : 3, cc1 = c == 3 ? 1 : (c == 0 ? 1 : 0), cc2 = 2;
   const int ncc = c == 3 ? 3 : (c == 2 ? 1 : 2);
@@ -329,7 +330,7 @@ __global__ void __launch_bounds__(TILE_I* TILE_WARPS, sizeof(T) == 8 ? (KIND == 
       if (ncc > 2) cv[r][2] = (R)x[cc2 * N + e];
     }
   };
-  if (CPL) load_cpl(kb);
+  if (CPL_AHEAD) load_cpl(kb);
   __syncthreads();
 
   const R cdiag = KIND == FV_PPBE ? cf.pp : (c < 3 ? cf.h : (c == 3 ? cf.hpr : cf.hpm));
@@ -363,6 +364,7 @@ __global__ void __launch_bounds__(TILE_I* TILE_WARPS, sizeof(T) == 8 ? (KIND == 
     const R q = G.invr2[k], rb = G.rf2[k], rt = G.rf2[k + 1], rk = G.rc[k];
     const int ek = own0 + k * Ns2;
     // couplings of a VTBE row with other components of the same cell, from the values loaded a level ago
+    if (CPL && !CPL_AHEAD) load_cpl(k);
     R cpl[RJ];
 #pragma unroll
     for (int r = 0; r < RJ; ++r) cpl[r] = R(0);
@@ -379,7 +381,7 @@ __global__ void __launch_bounds__(TILE_I* TILE_WARPS, sizeof(T) == 8 ? (KIND == 
         }
       }
     }
-    if (CPL && k + 1 < ke) load_cpl(k + 1);
+    if (CPL_AHEAD && k + 1 < ke) load_cpl(k + 1);
     R v[RJ + 2][3];
 #pragma unroll
     for (int rr = 0; rr < RJ + 2; ++rr)

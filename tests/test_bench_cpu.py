@@ -26,7 +26,8 @@ def test_algorithmic_bytes_of_the_bench_categories():
     assert bench.algorithmic_bytes('apply_ppbe_coarse_fp32', c, N, 4) == 2 * 2 * (N // 8) * 4
     fwd = bench.algorithmic_bytes('ras_fwd_ppbe_coarse_fp32', c, N, 4)
     bwd = bench.algorithmic_bytes('ras_bwd_ppbe_coarse_fp32', c, N, 4)
-    cells = bench.box_cells(c['Ns'] // 2, c['Nr'] // 2, c['p'], c['overlap_coarse'])
+    cp = c.get('coarse_p') or c['p']
+    cells = bench.box_cells(c['Ns'] // 2, c['Nr'] // 2, cp, c['overlap_coarse'])
     assert cells > N // 8  # overlapping boxes hold more cells than the grid
     assert fwd == cells * (4 * (2 * 2 + 5 * 2 + 1) + 8)
     assert bwd == cells * (4 * (2 + 5 * 2 + 3) + 9) + (N // 8) * 2 * 4

@@ -113,6 +113,23 @@ def test_two_level_ras_matches_oracle(fv):
     fv.fv_free_grid(g)
 
 
+def test_two_level_ras_with_its_own_coarse_box_split_matches_oracle(fv):
+    """The coarse one-level RAS (eqn:coarsepreconditioner) over boxes split apart from the fine ones
+    (fv_pc_desc cp1..cp3 against the oracle's parts_c): 12 x 8 fine boxes (2, 2, 1), coarse (3, 3, 2)."""
+    Ns, Nr, parts, cparts = 12, 8, (2, 2, 1), (3, 3, 2)
+    A, d, _ = _oracle_matrix(1, Ns, Nr)
+    Ac, _, _ = _oracle_matrix(1, Ns // 2, Nr // 2)
+    M = TwoLevelRAS(Grid(Ns, Nr), A, Grid(Ns // 2, Nr // 2), Ac, 2, parts, 1, 1, 0.1, 30, 30, neumann_first=True,
+                    parts_c=cparts)
+    g = fv.fv_build_grid(Ns, Nr)
+    s = fv.fv_assemble_system(g, 1, **PH, p=parts, overlap=1, levels=2, overlap_coarse=1, coarse_p=cparts)
+    r = random_vector(A.shape[0], 9)
+    z = fv.fv_precond_apply(s, _dev(r), torch.empty(A.shape[0], dtype=torch.float64, device='cuda')).cpu().numpy()
+    assert _rel(z, M.apply(r)) < 1e-9
+    fv.fv_free_system(s)
+    fv.fv_free_grid(g)
+
+
 def test_three_level_ras_matches_oracle(fv):
     """Multilevel hybrid RAS (Sec. 3.3): the coarse GMRES of the two-level preconditioner is itself
     preconditioned by the two-level construction on the next 1:2 mesh (16 x 8 -> 8 x 4 -> 4 x 2)."""

@@ -216,3 +216,30 @@ def test_multilevel_with_exact_coarse_solves_equals_two_level():
         assert res.converged and np.linalg.norm(r - A @ res.x) <= 1.0001e-8 * np.linalg.norm(r)
         its[lv] = res.iters
     assert its[2] < its[1] and its[3] <= its[2] + 2
+
+
+def test_coarse_box_split_changes_only_the_coarse_preconditioner():
+    """Sec. 3.3: the coarse GMRES of eqn:coarsesolve is preconditioned by one-level RAS on the coarse mesh; its
+    box split (parts_c) is a free parameter.  With exact coarse solves the two-level operator does not depend on
+    it (up to the Neumann constant); parts_c equal to the fine split is the default operator bit for bit; at the
+    default coarse tolerance both splits give valid preconditioners."""
+    from oracle.schwarz import hybrid_ras
+    E, dt = 1e-3, 1e-4
+    g = Grid(16, 8)
+    A = ppbe_matrix(Discretization(g), E, dt)
+    mat = lambda gg: ppbe_matrix(Discretization(gg), E, dt)
+    r = random_vector(A.shape[0], 13)
+    V = g.volumes().ravel()
+    r[:g.N] -= (V @ r[:g.N]) / V.sum()
+    base = hybrid_ras(g, A, mat, 2, (2, 2, 1), 1, 1, 2, neumann_first=True).apply(r)
+    same = hybrid_ras(g, A, mat, 2, (2, 2, 1), 1, 1, 2, neumann_first=True, parts_c=(2, 2, 1)).apply(r)
+    assert np.array_equal(base, same)
+    ze = [hybrid_ras(g, A, mat, 2, (2, 2, 1), 1, 1, 2, rtol_c=1e-13, maxit_c=400, neumann_first=True,
+                     parts_c=pc).apply(r) for pc in (None, (4, 4, 2))]
+    for z in ze:
+        z[:g.N] -= (V @ z[:g.N]) / V.sum()
+    assert np.abs(ze[1] - ze[0]).max() < 1e-8 * np.abs(ze[0]).max()
+    M = hybrid_ras(g, A, mat, 2, (2, 2, 1), 1, 1, 2, neumann_first=True, parts_c=(4, 4, 2))
+    assert len(M.coarse.subs) == 6 * 4 * 4 * 2
+    res = fgmres(lambda v: A @ v, M.apply, r, np.zeros_like(r), restart=30, rtol=1e-8, maxit=400)
+    assert res.converged and np.linalg.norm(r - A @ res.x) <= 1.0001e-8 * np.linalg.norm(r)
