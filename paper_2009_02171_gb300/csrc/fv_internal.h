@@ -40,6 +40,9 @@ struct GeoT {
   const R* sx;                 // [j][if][3] (a11 e1 + a12 e2) h_s h_r, local frame (times r_k)
   const R* sy;                 // [jf][i][3] (a12 e1 + a22 e2) h_s h_r
   const R* sr;                 // [j][i][3]  sigma h_s^2 xhat     (times r_f^2)
+  const R* sxp;                // [p][j][if][3] sx in Cartesian components of panel p (FP64 tables only)
+  const R* syp;                // [p][jf][i][3]
+  const R* srp;                // [p][j][i][3]
   const int* gq;               // [p][side][t]      panel holding the ghost's source line
   const int* gsrc;             // [p][side][t][3]   source cells (j*Ns + i) on that panel
   const R* gw;                 // [p][side][t][3]   quadratic Lagrange weights

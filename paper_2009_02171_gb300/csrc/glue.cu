@@ -60,15 +60,16 @@ __device__ __forceinline__ double face_val(const Geo& G, const Field& F, int c, 
   return fma(0.5, xc[0], 0.5 * xc[-d]);
 }
 
+// face area vector S_f (Cartesian) of face (type, k, j, i) of panel p: the panel's tabulated vector times
+// the radius factor of the level (r_k for horizontal faces, r_f^2 for radial ones)
 __device__ __forceinline__ void face_area(const Geo& G, int p, int type, int k, int j, int i, double S[3]) {
   const double* l;
   double sc;
-  if (type == 0) l = G.sx + 3 * (j * (G.Ns + 1) + i), sc = G.rc[k];
-  else if (type == 1) l = G.sy + 3 * (j * G.Ns + i), sc = G.rc[k];
-  else l = G.sr + 3 * (j * G.Ns + i), sc = G.rf2[k];
-  double v[3] = {l[0], l[1], l[2]};
-  rotate(p, v, S);
-  S[0] *= sc, S[1] *= sc, S[2] *= sc;
+  const int Ns = G.Ns;
+  if (type == 0) l = G.sxp + 3 * (((long long)p * Ns + j) * (Ns + 1) + i), sc = G.rc[k];
+  else if (type == 1) l = G.syp + 3 * (((long long)p * (Ns + 1) + j) * Ns + i), sc = G.rc[k];
+  else l = G.srp + 3 * (((long long)p * Ns + j) * Ns + i), sc = G.rf2[k];
+  S[0] = l[0] * sc, S[1] = l[1] * sc, S[2] = l[2] * sc;
 }
 
 template <int MODE>

@@ -239,6 +239,27 @@ fv_status build_grid(const fv_grid_desc* desc, fv_grid** out) {
       h.pq[p * 4 + side] = q_prev, h.psq[p * 4 + side] = sq_prev, h.psgn[p * 4 + side] = -sp * sqq;
     }
 
+  // the face area vectors of every panel in Cartesian components (the panel rotations have entries in
+  // {-1, 0, 1}, so these are the local components permuted and signed, exactly), for the FP64 face kernels
+  static const int kRot[6][9] = {
+      {1, 0, 0, 0, 1, 0, 0, 0, 1},  {0, -1, 0, 1, 0, 0, 0, 0, 1}, {-1, 0, 0, 0, -1, 0, 0, 0, 1},
+      {0, 1, 0, -1, 0, 0, 0, 0, 1}, {0, 0, -1, 0, 1, 0, 1, 0, 0}, {0, 0, 1, 0, 1, 0, -1, 0, 0},
+  };
+  auto per_panel = [&](const std::vector<double>& l) {
+    const size_t n = l.size() / 3;
+    std::vector<double> out(6 * l.size());
+    for (int p = 0; p < 6; ++p)
+      for (size_t e = 0; e < n; ++e)
+        for (int a = 0; a < 3; ++a) {
+          double v = 0.0;
+          for (int b = 0; b < 3; ++b)
+            if (kRot[p][3 * a + b]) v = kRot[p][3 * a + b] > 0 ? l[3 * e + b] : -l[3 * e + b];
+          out[(p * n + e) * 3 + a] = v;
+        }
+    return out;
+  };
+  const std::vector<double> sxp = per_panel(sx), syp = per_panel(sy), srp = per_panel(sr);
+
   Geo& G = g->geo;
   G.Ns = Ns, G.Nr = Nr, G.N = h.N, G.hs = hs, G.hr = hr, G.ri = h.ri, G.ro = h.ro;
   double rci = h.ri + 0.5 * hr, rgi = h.ri - 0.5 * hr, rco = h.ro - 0.5 * hr, rgo = h.ro + 0.5 * hr;
@@ -248,7 +269,8 @@ fv_status build_grid(const fv_grid_desc* desc, fv_grid** out) {
             (G.ay12 = upload(g, ay12)) && (G.crf = upload(g, crf)) && (G.rf2 = upload(g, rf2)) &&
             (G.invsig = upload(g, invsig)) && (G.invr2 = upload(g, invr2)) && (G.rc = upload(g, rc)) &&
             (G.xhat = upload(g, xhat)) && (G.sx = upload(g, sx)) && (G.sy = upload(g, sy)) &&
-            (G.sr = upload(g, sr)) && (G.gq = upload(g, h.gq)) && (G.gsrc = upload(g, h.gsrc)) &&
+            (G.sr = upload(g, sr)) && (G.sxp = upload(g, sxp)) && (G.syp = upload(g, syp)) &&
+            (G.srp = upload(g, srp)) && (G.gq = upload(g, h.gq)) && (G.gsrc = upload(g, h.gsrc)) &&
             (G.gw = upload(g, h.gw)) && (G.pq = upload(g, h.pq)) && (G.psq = upload(g, h.psq)) &&
             (G.psgn = upload(g, h.psgn)) && (G.ptmap = upload(g, h.ptmap)) && (g->cbasis = upload(g, cbasis)) &&
             (G.w9 = upload(g, w9));

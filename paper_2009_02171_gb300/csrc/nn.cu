@@ -140,11 +140,13 @@ __device__ __forceinline__ void cp16(void* dst, const void* src, const void* any
 }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-template <int NT>
+// NT: output channels / 8 (n tiles), CIN: input channels (a.cin); both fixed at compile time, so the
+// staging index arithmetic reduces to shifts and the tap and channel loops unroll
+template <int NT, int CIN>
 __global__ void __launch_bounds__(CONV_THREADS) conv_kernel(ConvArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   bf16* hs = reinterpret_cast<bf16*>(smem_raw);
-  const int cs = a.cin + 8;
+  constexpr int cs = CIN + 8;
   const int nbx = (a.On + BX - 1) / BX, nby = (a.On + BY - 1) / BY, nbz = (a.L.Z + BZ - 1) / BZ;
   int blk = blockIdx.x;
   const int bx = blk % nbx;
@@ -155,7 +157,7 @@ __global__ void __launch_bounds__(CONV_THREADS) conv_kernel(ConvArgs a) {
   const int p = blk / nbz;
   const int x0 = a.o0 + bx * BX, y0 = a.o0 + by * BY, z0 = bz * BZ;  // padded coordinates of the brick origin
 
-  const int qn = a.cin >> 3;
+  constexpr int qn = CIN >> 3;
   for (int it = threadIdx.x; it < HV * qn; it += CONV_THREADS) {
     const int hv = it / qn, q = it - hv * qn;
     const int hx = hv % HX, hy = (hv / HX) % HY, hz = hv / (HX * HY);
@@ -165,9 +167,9 @@ __global__ void __launch_bounds__(CONV_THREADS) conv_kernel(ConvArgs a) {
   // all 27 taps' weights, rows (tap, n) of cin values, staged once: the tap loop then reads the B
   // fragments from shared memory instead of waiting on global loads
   bf16* ws = hs + HV * cs;
-  for (int it = threadIdx.x; it < 27 * a.coutN * qn; it += CONV_THREADS) {
+  for (int it = threadIdx.x; it < 27 * NT * 8 * qn; it += CONV_THREADS) {
     const int row = it / qn, q = it - row * qn;
-    cp16(ws + row * cs + q * 8, a.w + (size_t)row * a.cin + q * 8, a.w);
+    cp16(ws + row * cs + q * 8, a.w + (size_t)row * CIN + q * 8, a.w);
   }
   cp_wait_all();
   __syncthreads();
@@ -190,17 +192,19 @@ __global__ void __launch_bounds__(CONV_THREADS) conv_kernel(ConvArgs a) {
   // B rows: lanes 0-7 / 8-15 give n-tile 2j's rows at k halves 0 / 1, lanes 16-31 n-tile 2j + 1's
   const uint32_t wbase = sbase + (uint32_t)(HV * cs * 2);
   const int brow = ((lane >> 4) * 8 + (lane & 7)), bk = ((lane >> 3) & 1) * 8;
+#pragma unroll
   for (int tap = 0; tap < 27; ++tap) {
     const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
     const int toff = (dz * HY + dy) * HX + dx;
-    for (int kc = 0; kc < a.cin; kc += 16) {
+#pragma unroll
+    for (int kc = 0; kc < CIN; kc += 16) {
       uint32_t af[2][4];
 #pragma unroll
       for (int mt = 0; mt < 2; ++mt) ldsm4(sbase + (uint32_t)(((hv0[mt] + toff) * cs + kc + kh * 8) * 2), af[mt]);
 #pragma unroll
       for (int np = 0; np < (NT + 1) / 2; ++np) {
         uint32_t bf[4];
-        const int row = tap * a.coutN + np * 16 + (NT == 1 ? (lane & 7) : brow);
+        const int row = tap * NT * 8 + np * 16 + (NT == 1 ? (lane & 7) : brow);
         ldsm4(wbase + (uint32_t)((row * cs + kc + bk) * 2), bf);
 #pragma unroll
         for (int mt = 0; mt < 2; ++mt) {
@@ -723,15 +727,26 @@ int eB(int l) { return 2 * l + 1; }
 int dL(const fv_net* n, int l) { return 2 * (n->levels + 1) + (n->levels - 1 - l); }
 int outL(const fv_net* n) { return 2 * (n->levels + 1) + n->levels; }
 
-template <int NT>
+template <int NT, int CIN>
 fv_status conv_launch_nt(const ConvArgs& a, int blocks, size_t smem, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    FV_CUDA(cudaFuncSetAttribute(conv_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    FV_CUDA(cudaFuncSetAttribute(conv_kernel<NT, CIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr = true;
   }
-  conv_kernel<NT><<<blocks, CONV_THREADS, smem, st>>>(a);
+  conv_kernel<NT, CIN><<<blocks, CONV_THREADS, smem, st>>>(a);
   return FV_OK;
+}
+
+template <int NT>
+fv_status conv_launch_cin(const ConvArgs& a, int blocks, size_t smem, cudaStream_t st) {
+  switch (a.cin) {
+    case 16: return conv_launch_nt<NT, 16>(a, blocks, smem, st);
+    case 32: return conv_launch_nt<NT, 32>(a, blocks, smem, st);
+    case 48: return conv_launch_nt<NT, 48>(a, blocks, smem, st);
+    case 64: return conv_launch_nt<NT, 64>(a, blocks, smem, st);
+    default: return set_error("fv_net: unsupported input channel count"), FV_EINVAL;
+  }
 }
 
 fv_status conv(const ConvArgs& a, cudaStream_t st) {
@@ -740,10 +755,10 @@ fv_status conv(const ConvArgs& a, cudaStream_t st) {
   if (a.cin % 16 || a.c0 % 8 || a.cin > MAX_CIN || a.coutN % 8 || smem > 200 * 1024)
     return set_error("fv_net: bad convolution shape"), FV_EINVAL;
   switch (a.coutN / 8) {
-    case 1: return conv_launch_nt<1>(a, blocks, smem, st);
-    case 2: return conv_launch_nt<2>(a, blocks, smem, st);
-    case 4: return conv_launch_nt<4>(a, blocks, smem, st);
-    case 8: return conv_launch_nt<8>(a, blocks, smem, st);
+    case 1: return conv_launch_cin<1>(a, blocks, smem, st);
+    case 2: return conv_launch_cin<2>(a, blocks, smem, st);
+    case 4: return conv_launch_cin<4>(a, blocks, smem, st);
+    case 8: return conv_launch_cin<8>(a, blocks, smem, st);
     default: return set_error("fv_net: unsupported output channel count"), FV_EINVAL;
   }
 }
