@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(512) ras_bwd_batch_kernel(BatchRas R, const T*
             if (j + 1 < ny) x[a] -= fu[2 * D + a] * rp[((col + nx) * D + a) * GC + gg];
             if (i + 1 < nx && j + 1 < ny) x[a] -= fu[3 * D + a] * rp[((col + nx + 1) * D + a) * GC + gg];
             if (k + 1 < nz) x[a] -= fu[4 * D + a] * rq[a * GC + gg];
-            x[a] /= fd[a * D + a];
+            x[a] *= fd[a * D + a];  // 1 / U_aa
           }
 #pragma unroll
           for (int a = 0; a < D; ++a) rp[(col * D + a) * GC + gg] = x[a];

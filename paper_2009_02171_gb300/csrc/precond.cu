@@ -312,7 +312,8 @@ __device__ __forceinline__ int find_subdomain(const long long* cell_off, int cou
 }
 
 // factors: natural layout off[C][11][d], diag[C][d][d]  ->  packed SoA in wavefront order:
-// q = s d + a (lower slots 0..4), 5 d + a d + b (diagonal block), 5 d + d^2 + (s-6) d + a (upper slots)
+// q = s d + a (lower slots 0..4), 5 d + a d + b (diagonal block: L strictly below, U above, 1 / U_aa on the
+// diagonal), 5 d + d^2 + (s-6) d + a (upper slots)
 template <class T>
 __global__ void repack_kernel(int d, int count, const long long* __restrict__ cell_off, const int* __restrict__ perm,
                               const double* __restrict__ off, const double* __restrict__ diag, T* __restrict__ F) {
@@ -331,15 +332,20 @@ __global__ void repack_kernel(int d, int count, const long long* __restrict__ ce
         Fs[q * nc] = to_factor<T>(off[(C * 11 + s) * d + a]);
       }
     }
+    // U's diagonal entries are stored as their reciprocals (computed in FP64), so the backward sweeps
+    // multiply instead of dividing on their critical path
     for (int a = 0; a < d; ++a)
-      for (int b = 0; b < d; ++b) Fs[(5 * d + a * d + b) * nc] = to_factor<T>(diag[(C * d + a) * d + b]);
+      for (int b = 0; b < d; ++b) {
+        const double v = diag[(C * d + a) * d + b];
+        Fs[(5 * d + a * d + b) * nc] = to_factor<T>(a == b ? 1.0 / v : v);
+      }
   }
 }
 
 // Per-cell operand blocks of the staged d = 2 sweeps (packed position order, 16-byte multiples so a
 // thread stages its cell's block with 16-byte copies).  Forward: the 5 d lower off-diagonal slots
 // (slot s, component a at s d + a), then L's strictly lower diagonal-block entry (1, 0), then the packed
-// (i, j, k).  Backward: the 5 d upper slots, then U's diagonal block (0,0), (0,1), (1,1), the packed
+// (i, j, k).  Backward: the 5 d upper slots, then U's diagonal block 1 / (0,0), (0,1), 1 / (1,1), the packed
 // (i, j, k) and the scatter target (grid cell of an owned cell, else -1).
 template <class T>
 struct alignas(16) FwdBlk {
@@ -703,7 +709,7 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_bwd_kernel(const long lo
           if (j + 1 < b.ny) x[a] -= fu[2 * D + a] * rp[(col + b.nx) * D + a];
           if (i + 1 < b.nx && j + 1 < b.ny) x[a] -= fu[3 * D + a] * rp[(col + b.nx + 1) * D + a];
           if (k + 1 < b.nz) x[a] -= fu[4 * D + a] * r1[a];
-          x[a] /= fd[a * D + a];
+          x[a] *= fd[a * D + a];  // 1 / U_aa
         }
       } else {
 #pragma unroll
@@ -716,7 +722,7 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_bwd_kernel(const long lo
           if (i + 1 < b.nx && j + 1 < b.ny)
             x[a] -= fcvt(Fb[(U + 3 * D + a) * nc + pos]) * rp[(col + b.nx + 1) * D + a];
           if (k + 1 < b.nz) x[a] -= fcvt(Fb[(U + 4 * D + a) * nc + pos]) * r1[a];
-          x[a] /= fcvt(Fb[(5 * D + a * D + a) * nc + pos]);
+          x[a] *= fcvt(Fb[(5 * D + a * D + a) * nc + pos]);  // 1 / U_aa
         }
       }
 #pragma unroll
@@ -874,7 +880,7 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_bwd_pipe_kernel(const lo
         if (j + 1 < b.ny) x[a] -= fu[2 * D + a] * rp[(col + b.nx) * D + a];
         if (i + 1 < b.nx && j + 1 < b.ny) x[a] -= fu[3 * D + a] * rp[(col + b.nx + 1) * D + a];
         if (k + 1 < b.nz) x[a] -= fu[4 * D + a] * r1[a];
-        x[a] /= fd[a * D + a];
+        x[a] *= fd[a * D + a];  // 1 / U_aa
       }
 #pragma unroll
       for (int a = 0; a < D; ++a) rp[col * D + a] = x[a];
@@ -1056,7 +1062,7 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_bwd_stage_kernel(const l
       T x[D];
 #pragma unroll
       for (int a = 0; a < D; ++a) x[a] = sX[((size_t)s * Tn + t) * D + a];
-      // U's diagonal block at f[5 d + 0, 1, 2] = (0,0), (0,1), (1,1)
+      // U's diagonal block at f[5 d + 0, 1, 2] = 1 / (0,0), (0,1), 1 / (1,1)
 #pragma unroll
       for (int a = D - 1; a >= 0; --a) {
         if (a == 0) x[0] -= fcvt(f[5 * D + 1]) * x[1];
@@ -1065,7 +1071,7 @@ __global__ void __launch_bounds__(DENSE_THREADS, 1) ras_bwd_stage_kernel(const l
         x[a] -= fcvt(f[2 * D + a]) * rp[(col + b.nx) * D + a];
         x[a] -= fcvt(f[3 * D + a]) * rp[(col + b.nx + 1) * D + a];
         x[a] -= fcvt(f[4 * D + a]) * r1[a];
-        x[a] /= fcvt(f[a == 0 ? 5 * D : 5 * D + 2]);
+        x[a] *= fcvt(f[a == 0 ? 5 * D : 5 * D + 2]);  // 1 / U_aa
       }
 #pragma unroll
       for (int a = 0; a < D; ++a) rp[col * D + a] = x[a];
