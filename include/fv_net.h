@@ -106,6 +106,13 @@ fv_status fv_coarse_system(const fv_system* s, const fv_system** coarse);
  * component's volume-weighted mean removed).  x: n values, xc: coarse n. */
 fv_status fv_restrict_coarse(const fv_system* s, const double* x, double* xc, void* stream);
 
+/* x = I_c^f xc, the piecewise-constant prolongation of the two-level
+ * preconditioner of s (eqn:coarsesolve: every fine cell takes the value of
+ * the coarse cell that contains it).  xc: coarse n values, x: n values
+ * (device, component-major; not aliased).  FV_EINVAL for a one-level
+ * system or null pointers. */
+fv_status fv_prolong_coarse(const fv_system* s, const double* xc, double* x, void* stream);
+
 /* Attach (net != NULL) or detach (net == NULL) a learned coarse correction to
  * a two-level PPBE system whose coarse grid matches the network.  The coarse
  * solve of every preconditioner application becomes e_c = N(r_c) followed by

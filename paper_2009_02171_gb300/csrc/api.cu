@@ -201,6 +201,12 @@ fv_status fv_restrict_coarse(const fv_system* s, const double* x, double* xc, vo
   return restrict_coarse(s, x, xc, (cudaStream_t)stream);
 }
 
+fv_status fv_prolong_coarse(const fv_system* s, const double* xc, double* x, void* stream) {
+  if (!s || !xc || !x || xc == x) return set_error("fv_prolong_coarse: bad argument"), FV_EINVAL;
+  if (!s->coarse) return set_error("fv_prolong_coarse: the system has one level"), FV_EINVAL;
+  return prolong_inject(s->grid, s->d, xc, x, (cudaStream_t)stream);
+}
+
 fv_status fv_pc_set_learned(fv_system* s, fv_net* net, int coarse_its, int flags) {
   if (!s) return set_error("fv_pc_set_learned: null system"), FV_EINVAL;
   if (!net) {

@@ -236,7 +236,7 @@ struct Vec16<double> {
 // out[0..nv) (and, for mode 2 with `ad`, applies the Givens update of column
 // gj), so no separate reduction launch is needed.
 template <int NV, class T>
-__global__ void __launch_bounds__(RTHREADS, (NV > 12 ? 1 : 2)) cgs_kernel(long long n, int vec, const T* __restrict__ V,
+__global__ void __launch_bounds__(RTHREADS, (NV > (sizeof(T) == 8 ? 18 : 14) ? 1 : 2)) cgs_kernel(long long n, int vec, const T* __restrict__ V,
                                                           const double* __restrict__ h, T* __restrict__ w,
                                                           double* __restrict__ part, int mode, double* out,
                                                           unsigned* ticket, ArnoldiDev* ad, int gj,
@@ -799,14 +799,16 @@ fv_status gmres32(const fv_system* s, const float* b, float* x, const fv_gmres_o
 }
 
 // volume-weighted mean removal of the first component (Neumann pressure gauge)
-template <class T>
+// I: the index type, 32-bit whenever N allows (32-bit divisions in the index decomposition)
+template <class T, class I>
 __global__ void wsum_kernel(long long N, int Ns, int Nr, const double* __restrict__ invsig,
                             const double* __restrict__ invr2, const T* __restrict__ x, double* __restrict__ part) {
   double acc[KMAX];
   acc[0] = 0.0, acc[1] = 0.0;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
-    const int ij = (int)(e % ((long long)Ns * Ns));
-    const int k = (int)((e / ((long long)Ns * Ns)) % Nr);
+  const I ns2 = (I)Ns * Ns;
+  for (I e = blockIdx.x * (I)blockDim.x + threadIdx.x; e < (I)N; e += (I)gridDim.x * blockDim.x) {
+    const int ij = (int)(e % ns2);
+    const int k = (int)((e / ns2) % Nr);
     const double V = 1.0 / (invsig[ij] * invr2[k]);
     acc[0] += V * (double)x[e];
     acc[1] += V;
@@ -825,7 +827,10 @@ template <class T>
 static fv_status wmr(const fv_grid* g, T* x, cudaStream_t st, double* part, double* sums) {
   const Geo& G = g->geo;
   ProfScope ps(FV_K_VEC, st);
-  wsum_kernel<T><<<RBLOCKS, RTHREADS, 0, st>>>(G.N, G.Ns, G.Nr, G.invsig, G.invr2, x, part);
+  if (G.N < (1LL << 31) - (1LL << 24))
+    wsum_kernel<T, int><<<RBLOCKS, RTHREADS, 0, st>>>(G.N, G.Ns, G.Nr, G.invsig, G.invr2, x, part);
+  else
+    wsum_kernel<T, long long><<<RBLOCKS, RTHREADS, 0, st>>>(G.N, G.Ns, G.Nr, G.invsig, G.invr2, x, part);
   reduce_kernel<<<1, RTHREADS, 0, st>>>(part, RBLOCKS, 2, sums);
   shift_kernel<T><<<vblocks(G.N), 256, 0, st>>>(G.N, sums, x);
   FV_CUDA(cudaGetLastError());

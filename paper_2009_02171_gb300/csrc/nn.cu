@@ -303,6 +303,10 @@ __global__ void mask_kernel(bf16* __restrict__ g, const bf16* __restrict__ a, in
 
 // interior cell index -> padded voxel index
 __device__ __forceinline__ long long padded(long long cell, const Lvl& L) {
+  if (cell < 0x7fffffffLL) {  // 32-bit divisions whenever the index fits
+    const int c = (int)cell, x = c % L.X, t = c / L.X, y = t % L.Y;
+    return ((long long)(t / L.Y) * (L.Y + 2) + y + 1) * (L.X + 2) + x + 1;
+  }
   const int x = (int)(cell % L.X);
   long long t = cell / L.X;
   const int y = (int)(t % L.Y);
@@ -316,13 +320,22 @@ __global__ void pool_kernel(const bf16* __restrict__ a, bf16* __restrict__ out, 
   const Lvl L{Lc.Z * 2, Lc.Y * 2, Lc.X * 2};
   const int qn = C / 8;
   const long long total = Lc.cells(P) * qn;
+  const bool small = total < 0x7fffffffLL;  // 32-bit divisions whenever the index fits
   for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < total; it += (long long)gridDim.x * blockDim.x) {
-    const int q = (int)(it % qn);
-    const long long cell = it / qn;
-    const int x = (int)(cell % Lc.X), y = (int)((cell / Lc.X) % Lc.Y);
-    const long long pz = cell / ((long long)Lc.X * Lc.Y);  // p * Zc + z
-    const int z = (int)(pz % Lc.Z);
-    const long long p = pz / Lc.Z;
+    int q, x, y, z;
+    long long cell, p;
+    if (small) {
+      const int i32 = (int)it, c32 = i32 / qn, pz = c32 / (Lc.X * Lc.Y);
+      q = i32 - c32 * qn, x = c32 % Lc.X, y = (c32 / Lc.X) % Lc.Y, z = pz % Lc.Z;
+      cell = c32, p = pz / Lc.Z;
+    } else {
+      q = (int)(it % qn);
+      cell = it / qn;
+      x = (int)(cell % Lc.X), y = (int)((cell / Lc.X) % Lc.Y);
+      const long long pz = cell / ((long long)Lc.X * Lc.Y);  // p * Zc + z
+      z = (int)(pz % Lc.Z);
+      p = pz / Lc.Z;
+    }
     float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int c = 0; c < 8; ++c) {
       const long long v = (((p * L.Z + 2 * z + (c >> 2)) * (L.Y + 2) + 2 * y + ((c >> 1) & 1) + 1) * (L.X + 2) + 2 * x +
@@ -546,7 +559,10 @@ __global__ void sumsq_kernel(const T* __restrict__ r, long long n1, double* sspa
 
 // one warp a sample: lane l adds the partials l, l + 32, ... (loads issued together), then the
 // warp's fixed butterfly; the order is the same on every call
-__global__ void sssum_kernel(const double* __restrict__ sspart, int blocks, int nb, double* ss) {
+// with the sum, the sample's two scales: pinv[i] = 1 / s (as the FP32 value the packing multiplies by) and
+// psc[i] = s, s = sqrt(sum / (2 V1)) the RMS, so no element recomputes them
+__global__ void sssum_kernel(const double* __restrict__ sspart, int blocks, int nb, double* ss, long long V1,
+                             double* pinv, double* psc) {
   const int lane = threadIdx.x & 31;
   for (int i = threadIdx.x >> 5; i < nb; i += blockDim.x >> 5) {
     double s = 0.0;
@@ -562,20 +578,23 @@ __global__ void sssum_kernel(const double* __restrict__ sspart, int blocks, int 
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) ss[i] = s;
+    if (lane == 0) {
+      ss[i] = s;
+      pinv[i] = s > 0.0 ? (double)(float)sqrt(2.0 * (double)V1 / s) : 0.0;
+      psc[i] = sqrt(s / (2.0 * (double)V1));
+    }
   }
 }
 
 // x interior [cell][0..15] = (r_P, r_Pb) / s, zero channels 2..15 (cells sample-major), with
 // s the RMS of the sample (ss = its sum of squares over 2 V1 values): O(1) activations
 template <class T>
-__global__ void pack_kernel(const T* __restrict__ r, const double* __restrict__ ss, long long V1, int nb, Lvl L,
+__global__ void pack_kernel(const T* __restrict__ r, const double* __restrict__ pinv, long long V1, int nb, Lvl L,
                             bf16* __restrict__ x, Halo H) {
   const long long n = V1 * nb;
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
-    const long long b = v / V1, vl = v - b * V1;
-    const double s2 = ss[b];
-    const float inv = s2 > 0.0 ? (float)sqrt(2.0 * (double)V1 / s2) : 0.f;
+    const long long b = nb == 1 ? 0 : v / V1, vl = v - b * V1;
+    const float inv = (float)pinv[b];
     uint4 o[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
     __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(o);
     h[0] = __floats2bfloat162_rn((float)r[b * 2 * V1 + vl] * inv, (float)r[b * 2 * V1 + V1 + vl] * inv);
@@ -595,12 +614,12 @@ __global__ void pack_kernel(const T* __restrict__ r, const double* __restrict__ 
 
 // e[b][c][vl] = s_b * y[cell][c] (s_b the RMS of sample b)
 template <class T>
-__global__ void unpack_kernel(const float* __restrict__ y, const double* __restrict__ ss, long long V1, int nb,
+__global__ void unpack_kernel(const float* __restrict__ y, const double* __restrict__ psc, long long V1, int nb,
                               T* __restrict__ e) {
   const long long n = V1 * nb;
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < n; v += (long long)gridDim.x * blockDim.x) {
-    const long long b = v / V1, vl = v - b * V1;
-    const double s = sqrt(ss[b] / (2.0 * (double)V1));
+    const long long b = nb == 1 ? 0 : v / V1, vl = v - b * V1;
+    const double s = psc[b];
     e[b * 2 * V1 + vl] = (T)(s * (double)y[2 * v]);
     e[b * 2 * V1 + V1 + vl] = (T)(s * (double)y[2 * v + 1]);
   }
@@ -694,7 +713,7 @@ struct fv_net {
   fv::Halo halo{};
   float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;  // FP32 masters, gradient, Adam moments
   long long t = 0;        // Adam step counter
-  double* ss = nullptr;   // [nbmax] per-sample sum of squares
+  double* ss = nullptr;   // [3][nbmax] per-sample sum of squares, then 1 / RMS and RMS
   double* sspart = nullptr;  // [nbmax][SS_BLOCKS] its block partials
   float *wpart = nullptr, *bpart = nullptr;  // weight- and bias-gradient partials (training)
   double* loss = nullptr; // [1]
@@ -823,8 +842,8 @@ fv_status forward_t(fv_net* n, int nb, const T* r, cudaStream_t st) {
   const int C = n->C, P = 6 * nb, Lv = n->levels;
   const int sblk = std::min(gridsz(2 * n->V1, RED_THREADS) / 8 + 1, SS_BLOCKS);
   sumsq_kernel<T><<<dim3(sblk, nb), RED_THREADS, 0, st>>>(r, 2 * n->V1, n->sspart);
-  sssum_kernel<<<1, 256, 0, st>>>(n->sspart, sblk, nb, n->ss);
-  pack_kernel<T><<<gridsz(n->V1 * nb, 256), 256, 0, st>>>(r, n->ss, n->V1, nb, n->lv[0], n->x0, n->halo);
+  sssum_kernel<<<1, 256, 0, st>>>(n->sspart, sblk, nb, n->ss, n->V1, n->ss + n->nbmax, n->ss + 2 * n->nbmax);
+  pack_kernel<T><<<gridsz(n->V1 * nb, 256), 256, 0, st>>>(r, n->ss + n->nbmax, n->V1, nb, n->lv[0], n->x0, n->halo);
   fv_status rc;
   for (int l = 0; l <= Lv; ++l) {
     const Lvl& L = n->lv[l];
@@ -957,7 +976,7 @@ fv_status net_forward64(fv_net* n, const double* r, double* e, cudaStream_t st) 
   ProfScope ps(FV_K_NET_FWD, st);
   fv_status rc = forward_t<double>(n, 1, r, st);
   if (rc) return rc;
-  unpack_kernel<double><<<gridsz(n->V1, 256), 256, 0, st>>>(n->y, n->ss, n->V1, 1, e);
+  unpack_kernel<double><<<gridsz(n->V1, 256), 256, 0, st>>>(n->y, n->ss + 2 * n->nbmax, n->V1, 1, e);
   FV_CUDA(cudaGetLastError());
   return FV_OK;
 }
@@ -966,7 +985,7 @@ fv_status net_forward32(fv_net* n, const float* r, float* e, cudaStream_t st) {
   ProfScope ps(FV_K_NET_FWD, st);
   fv_status rc = forward_t<float>(n, 1, r, st);
   if (rc) return rc;
-  unpack_kernel<float><<<gridsz(n->V1, 256), 256, 0, st>>>(n->y, n->ss, n->V1, 1, e);
+  unpack_kernel<float><<<gridsz(n->V1, 256), 256, 0, st>>>(n->y, n->ss + 2 * n->nbmax, n->V1, 1, e);
   FV_CUDA(cudaGetLastError());
   return FV_OK;
 }
@@ -1019,7 +1038,7 @@ fv_status fv_net_create(const fv_net_desc* d, fv_net** out) {
   n->nparam = off;
   const int P = 6 * n->nbmax;
   if ((rc = nalloc(n, &n->w, off)) || (rc = nalloc(n, &n->g, off)) || (rc = nalloc(n, &n->m, off)) ||
-      (rc = nalloc(n, &n->v, off)) || (rc = nalloc(n, &n->ss, n->nbmax)) || (rc = nalloc(n, &n->loss, 1)) ||
+      (rc = nalloc(n, &n->v, off)) || (rc = nalloc(n, &n->ss, 3 * n->nbmax)) || (rc = nalloc(n, &n->loss, 1)) ||
       (rc = nalloc(n, &n->sspart, (size_t)n->nbmax * SS_BLOCKS)) ||
       (rc = nalloc(n, &n->x0, n->lv[0].vox(P) * 16)) || (rc = nalloc(n, &n->y, n->V1 * n->nbmax * 2))) {
     fv_net_free(n);
@@ -1106,7 +1125,7 @@ fv_status fv_net_forward(fv_net* n, int nb, const double* r, double* e, void* st
   cudaStream_t st = (cudaStream_t)stream;
   ProfScope ps(FV_K_NET_FWD, st);
   if ((rc = forward_t<double>(n, nb, r, st))) return rc;
-  unpack_kernel<double><<<gridsz(n->V1 * nb, 256), 256, 0, st>>>(n->y, n->ss, n->V1, nb, e);
+  unpack_kernel<double><<<gridsz(n->V1 * nb, 256), 256, 0, st>>>(n->y, n->ss + 2 * n->nbmax, n->V1, nb, e);
   FV_CUDA(cudaGetLastError());
   return FV_OK;
 }

@@ -1205,22 +1205,23 @@ static fv_status ras_apply32(const fv_system* s, const float* r, float* z, cudaS
 }
 
 // ------------------------------------------------------------------ two levels
-template <class T>
+// The index type I is 32-bit whenever d N fits (every shell here): the index decomposition then uses
+// 32-bit divisions by the grid sizes instead of 64-bit ones.
+template <class T, class I>
 __global__ void restrict_kernel(int d, int Ns, int Nr, const T* __restrict__ x, T* __restrict__ xc) {
-  const int nc = Ns / 2, mc = Nr / 2;
-  const long long Nc = 6LL * nc * nc * mc, N = 6LL * Ns * Ns * Nr;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < d * Nc;
-       e += (long long)gridDim.x * blockDim.x) {
-    long long r = e;
-    const int i = (int)(r % nc);
+  const I nc = Ns / 2, mc = Nr / 2;
+  const I Nc = (I)6 * nc * nc * mc, N = (I)6 * Ns * Ns * Nr;
+  for (I e = blockIdx.x * (I)blockDim.x + threadIdx.x; e < (I)d * Nc; e += (I)gridDim.x * blockDim.x) {
+    I r = e;
+    const I i = r % nc;
     r /= nc;
-    const int j = (int)(r % nc);
+    const I j = r % nc;
     r /= nc;
-    const int k = (int)(r % mc);
+    const I k = r % mc;
     r /= mc;
-    const int p = (int)(r % 6);
-    const int a = (int)(r / 6);
-    const T* xa = x + a * N;
+    const I p = r % 6;
+    const I a = r / 6;
+    const T* xa = x + (long long)a * N;
     T sum = T(0);
     for (int dk = 0; dk < 2; ++dk)
       for (int dj = 0; dj < 2; ++dj)
@@ -1230,24 +1231,27 @@ __global__ void restrict_kernel(int d, int Ns, int Nr, const T* __restrict__ x, 
   }
 }
 
-template <class T>
+template <class T, class I>
 __global__ void prolong_kernel(int d, int Ns, int Nr, const T* __restrict__ xc, T* __restrict__ x) {
-  const int nc = Ns / 2, mc = Nr / 2;
-  const long long N = 6LL * Ns * Ns * Nr, Nc = 6LL * nc * nc * mc;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < d * N;
-       e += (long long)gridDim.x * blockDim.x) {
-    long long r = e;
-    const int i = (int)(r % Ns);
+  const I nc = Ns / 2, mc = Nr / 2;
+  const I N = (I)6 * Ns * Ns * Nr, Nc = (I)6 * nc * nc * mc;
+  for (I e = blockIdx.x * (I)blockDim.x + threadIdx.x; e < (I)d * N; e += (I)gridDim.x * blockDim.x) {
+    I r = e;
+    const I i = r % Ns;
     r /= Ns;
-    const int j = (int)(r % Ns);
+    const I j = r % Ns;
     r /= Ns;
-    const int k = (int)(r % Nr);
+    const I k = r % Nr;
     r /= Nr;
-    const int p = (int)(r % 6);
-    const int a = (int)(r / 6);
-    x[e] = xc[a * Nc + ((long long)(p * mc + k / 2) * nc + j / 2) * nc + i / 2];
+    const I p = r % 6;
+    const I a = r / 6;
+    x[e] = xc[(long long)a * Nc + ((long long)(p * mc + k / 2) * nc + j / 2) * nc + i / 2];
   }
 }
+
+// 32-bit indexing of the transfer kernels: the element count plus one grid stride (at most 152 x 32 x 256)
+// stays below 2^31
+constexpr long long kIndex32 = (1LL << 31) - (1LL << 24);
 
 static int nblocks(long long n) {
   long long b = (n + 255) / 256;
@@ -1257,7 +1261,10 @@ static int nblocks(long long n) {
 template <class T>
 static fv_status restrict_t(const fv_grid* g, int d, const T* x, T* xc, cudaStream_t st) {
   ProfScope ps(FV_K_TRANSFER, st);
-  restrict_kernel<T><<<nblocks(d * g->h.N / 8), 256, 0, st>>>(d, g->h.Ns, g->h.Nr, x, xc);
+  if ((long long)d * g->h.N < kIndex32)
+    restrict_kernel<T, int><<<nblocks(d * g->h.N / 8), 256, 0, st>>>(d, g->h.Ns, g->h.Nr, x, xc);
+  else
+    restrict_kernel<T, long long><<<nblocks(d * g->h.N / 8), 256, 0, st>>>(d, g->h.Ns, g->h.Nr, x, xc);
   FV_CUDA(cudaGetLastError());
   return FV_OK;
 }
@@ -1265,7 +1272,10 @@ static fv_status restrict_t(const fv_grid* g, int d, const T* x, T* xc, cudaStre
 template <class T>
 static fv_status prolong_t(const fv_grid* g, int d, const T* xc, T* x, cudaStream_t st) {
   ProfScope ps(FV_K_TRANSFER, st);
-  prolong_kernel<T><<<nblocks(d * g->h.N), 256, 0, st>>>(d, g->h.Ns, g->h.Nr, xc, x);
+  if ((long long)d * g->h.N < kIndex32)
+    prolong_kernel<T, int><<<nblocks(d * g->h.N), 256, 0, st>>>(d, g->h.Ns, g->h.Nr, xc, x);
+  else
+    prolong_kernel<T, long long><<<nblocks(d * g->h.N), 256, 0, st>>>(d, g->h.Ns, g->h.Nr, xc, x);
   FV_CUDA(cudaGetLastError());
   return FV_OK;
 }

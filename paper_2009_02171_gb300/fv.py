@@ -114,6 +114,7 @@ SIGNATURES = {
     'fv_net_train': [_VP, ctypes.c_int, _DP, _DP, _P(fv_train_opts), _VP, _VP],
     'fv_coarse_system': [_VP, _P(_VP)],
     'fv_restrict_coarse': [_VP, _DP, _DP, _VP],
+    'fv_prolong_coarse': [_VP, _DP, _DP, _VP],
     'fv_pc_set_learned': [_VP, _VP, ctypes.c_int, ctypes.c_int],
 }
 FV_LEARN_GUESS = 1
@@ -400,6 +401,12 @@ def fv_coarse_system(system):
 def fv_restrict_coarse(system, x, xc):
     _check(lib.fv_restrict_coarse(system, _ptr(x), _ptr(xc), _stream()))
     return xc
+
+
+def fv_prolong_coarse(system, xc, x):
+    """x = the piecewise-constant prolongation of coarse vector xc (the two-level preconditioner's I_c^f)."""
+    _check(lib.fv_prolong_coarse(system, _ptr(xc), _ptr(x), _stream()))
+    return x
 
 
 def fv_pc_set_learned(system, net, coarse_its=0, flags=0):

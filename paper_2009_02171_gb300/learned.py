@@ -32,13 +32,14 @@ def coarse_training_pairs(system, Ns, Nr, npairs, seed=5, target_rtol=1e-6, chun
     F = multiscale_fields(ns, nr, npairs, seed=seed)
     R = torch.empty(npairs, nc, dtype=torch.float64, device='cuda')
     tmp = torch.empty(nc, dtype=torch.float64, device='cuda')
+    fine = torch.empty(n, dtype=torch.float64, device='cuda')
     for i in range(npairs):
         f = torch.tensor(F[i], device='cuda')
         if i % 2:
             fv.fv_apply_op(c, f, tmp)
             f = tmp
-        f = f.view(2, 6, nr, ns, ns)
-        fine = f.repeat_interleave(2, 2).repeat_interleave(2, 3).repeat_interleave(2, 4).contiguous().view(-1)
+        # the coarse right-hand side the preconditioner would form from the prolonged field
+        fv.fv_prolong_coarse(system, f, fine)
         fv.fv_restrict_coarse(system, fine, R[i])
     E = torch.zeros_like(R)
     its = []

@@ -345,3 +345,26 @@ def test_bf16_factor_solve_reaches_fp64_residual(fv, kind, levels):
         fv.fv_free_system(s)
     assert its[fv.FV_PREC_BF16] <= its[fv.FV_PREC_FP32] + 2
     fv.fv_free_grid(g)
+
+
+def test_coarse_transfers_match_oracle(fv):
+    """I_f^c (mean of the 8 children, P's volume-weighted mean removed for PPBE) and I_c^f (piecewise
+    constant) of the two-level preconditioner (eqn:coarsesolve), through fv_restrict_coarse and
+    fv_prolong_coarse, against the oracle's restrict and prolong: exact up to rounding of the mean."""
+    from oracle.schwarz import prolong, restrict
+    Ns, Nr = 12, 8
+    g = fv.fv_build_grid(Ns, Nr)
+    s = fv.fv_assemble_system(g, 1, **PH, p=(2, 2, 1), overlap=1, levels=2, overlap_coarse=1)
+    n = fv.fv_system_size(s)
+    x = random_vector(n, 21)
+    xc = random_vector(n // 8, 22)
+    gc = Grid(Ns // 2, Nr // 2)
+    rc = fv.fv_restrict_coarse(s, _dev(x), torch.empty(n // 8, dtype=torch.float64, device='cuda')).cpu().numpy()
+    ref = restrict(Grid(Ns, Nr), x, 2)
+    Vc, Nc = gc.volumes().ravel(), gc.N
+    ref[:Nc] -= (Vc @ ref[:Nc]) / Vc.sum()
+    assert np.abs(rc - ref).max() < 1e-13 * np.abs(ref).max()
+    xf = fv.fv_prolong_coarse(s, _dev(xc), torch.empty(n, dtype=torch.float64, device='cuda')).cpu().numpy()
+    assert np.array_equal(xf, prolong(Grid(Ns, Nr), xc, 2))
+    fv.fv_free_system(s)
+    fv.fv_free_grid(g)
