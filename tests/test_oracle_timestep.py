@@ -3,6 +3,7 @@ import numpy as np
 from scipy.sparse.linalg import expm_multiply
 
 from oracle.diagnostics import energies
+from oracle.discrete import Discretization
 from oracle.grid import Grid
 from oracle.timestep import Physics, SolverOptions, Stepper
 from paper_2009_02171_gb300.inputs import benchmark_state, initial_state
@@ -93,3 +94,19 @@ def test_projected_flow_step_is_second_order_in_time_at_large_dt():
     err = [np.sqrt(((run(dt)[0]['u'] - ref['u']) ** 2 * V).sum()) for dt in (0.02, 0.01)]
     order = np.log2(err[0] / err[1])
     assert order > 1.8, (err, order)
+
+
+def test_magnetic_energy_of_the_benchmark_field_against_its_closed_form():
+    """Sec. 4.2: E_mag = Pm/(2E) int B^2 dV.  For B0 of eqn:initial, int B0^2 dV over the shell
+    (r_i = 7/13, r_o = 20/13) is 5 (4453247915 pi^2 - 202725978) / (540602608 pi) (sympy, exact), so with
+    P8's E = 1e-3, Pm = 8, E_mag = 515194.009...; the paper puts the suggested field's energy inside
+    [407101, 623428].  The oracle's cell-centre quadrature converges to it at second order."""
+    exact = 4000.0 * 5 * (4453247915 * np.pi ** 2 - 202725978) / (540602608 * np.pi)
+    assert abs(exact - 515194.009252519) < 1e-6 and 407101 < exact < 623428
+    errs = []
+    for n in (8, 16):
+        g = Grid(n, n)
+        s = benchmark_state(n, n)
+        _, em = energies(Discretization(g).V, s['u'], s['B'], 1e-3, 8.0)
+        errs.append(abs(em - exact) / exact)
+    assert errs[1] < 2e-3 and np.log2(errs[0] / errs[1]) > 1.7, errs
