@@ -107,6 +107,10 @@ def test_magnetic_energy_of_the_benchmark_field_against_its_closed_form():
     for n in (8, 16):
         g = Grid(n, n)
         s = benchmark_state(n, n)
-        _, em = energies(Discretization(g).V, s['u'], s['B'], 1e-3, 8.0)
+        V = Discretization(g).V
+        _, em = energies(V, s['u'], s['B'], 1e-3, 8.0)
         errs.append(abs(em - exact) / exact)
+        # E_kin = Pm^2/2 int u^2 dV, fed the same field as u: Pm^2 / 2 against Pm / (2E)
+        ek, _ = energies(V, s['B'], np.zeros_like(s['B']), 1e-3, 8.0)
+        assert abs(ek / em - 8.0 * 1e-3) < 1e-14
     assert errs[1] < 2e-3 and np.log2(errs[0] / errs[1]) > 1.7, errs
